@@ -1,0 +1,253 @@
+/*
+ * tn.h -- C ABI of the GB300 sliced tensor-network contraction library.
+ *
+ * The library computes amplitudes <x|U|0^n> of a random quantum circuit U for
+ * a correlated set of bitstrings x (some qubits open, the rest fixed) by
+ * contracting the circuit's tensor network (paper Sec. 2, "RQC simulation
+ * methods": a circuit becomes a network of rank-2 and rank-4 gate tensors
+ * whose contraction yields chosen amplitudes).  The network is cut into
+ * independent sub-networks by fixing the values of chosen edges -- slicing,
+ * "breaking edges" (Sec. 3, Innovations; Sec. 3.1) -- and each slice is
+ * contracted as a sequence of pairwise steps, each one index permutation
+ * followed by a matrix multiplication (Sec. 3.1, device level; Sec. 3.3,
+ * Eq. 2-3: a pairwise einsum is a pure GEMM when its reduced modes are the
+ * modes the two operands share).  Slice results are summed in FP64.  Low-
+ * precision steps use the complex-as-real layout of Sec. 3.3 (Eq. 4-5): the
+ * large operand keeps its interleaved real/imag mode as an extra reduced mode
+ * and the small operand is padded to [[Re, -Im], [Im, Re]], so one real GEMM
+ * with K -> 2K and N -> 2N does the complex product.  Post-selection keeps the
+ * k most probable bitstrings of a correlated subspace (Sec. 1 and Sec. 2,
+ * post-processing).
+ *
+ * Conventions
+ *   - qubit q of a bitstring x is bit q of x;
+ *   - a 2x2 gate is row-major (out, in); a 4x4 gate is row-major over
+ *     |q0 q1>, q0 the high bit of the local index;
+ *   - amplitude index j of an output: bit t of j is qubit open_qubits[t];
+ *   - slice id s: bit j of s is the value of sliced edge j (LSB first).
+ *   - amplitude buffers are complex128, interleaved (re, im) doubles.
+ *
+ * Errors: every int-returning call returns TN_OK (0) or a TN_E* code; no C++
+ * exception crosses this boundary.  tn_strerror() names a code;
+ * tn_last_error() gives a message for the calling thread's last failure.
+ *
+ * Streams: `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = the legacy default stream).  Device pointers must come from the
+ * CUDA runtime of the calling process and belong to the current device.
+ */
+#ifndef TN_H_
+#define TN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TN_OK 0
+#define TN_EINVAL 1        /* bad argument (indices, sizes, ranges)            */
+#define TN_ENOMEM 2        /* host or device allocation failed                 */
+#define TN_ECUDA 3         /* a CUDA runtime/driver call failed                */
+#define TN_ETIMEOUT 4      /* a bounded device wait gave up (kernel returned)  */
+#define TN_EUNSUPPORTED 5  /* valid request this build cannot serve            */
+
+/* ---- element types of the contraction ---- */
+#define TN_C64 0    /* complex64: FP32 re/im, FP32 SIMT arithmetic           */
+#define TN_F16 1    /* complex-half: FP16 re/im, tensor-core FP32 accumulate */
+#define TN_BF16 2   /* BF16 re/im, tensor-core FP32 accumulate               */
+
+/* ---- tile policies (which GEMM tile each step uses) ---- */
+#define TN_TILE_FIXED 0       /* built-in heuristic                              */
+#define TN_TILE_EXHAUSTIVE 1  /* time every legal tile on first contract         */
+#define TN_TILE_LEARNED 2     /* rank tiles with the trained cost model          */
+
+typedef struct {
+    int32_t q0, q1;       /* q1 < 0: single-qubit gate on q0                     */
+    double re[16], im[16];/* 2x2 in [0],[1],[4],[5] (row-major, 4-wide rows)    */
+                          /* or 4x4 row-major over |q0 q1>                       */
+} tn_gate;
+
+typedef struct {
+    int32_t n_qubits;     /* 1..64                                               */
+    int32_t n_gates;
+    const tn_gate *gates; /* host, length n_gates, in circuit order              */
+} tn_circuit;
+
+typedef struct {
+    int32_t n_open;              /* 0..30                                        */
+    const int32_t *open_qubits;  /* host, ascending, length n_open               */
+    const uint8_t *fixed_bits;   /* host, length n_qubits; open entries ignored  */
+} tn_query;
+
+typedef struct {
+    int32_t dtype;            /* TN_C64 | TN_F16 | TN_BF16                       */
+    int32_t max_log2_elems;   /* slice until every per-slice intermediate has
+                                 at most 2^this elements (<= 0: no cap)          */
+    int32_t n_slice_edges;    /* >= 0: slice exactly this many edges;
+                                 -1: as many as the cap needs                    */
+    uint64_t path_seed;       /* seed of the randomized greedy path search       */
+    int32_t path_trials;      /* greedy restarts (>= 1); trial 0 is noiseless    */
+    int32_t slice_batch_log2; /* run 2^this consecutive slices in one pass, the
+                                 batch carried as an extra tensor mode (>= 0)    */
+    int32_t tile_policy;      /* TN_TILE_*                                       */
+    /* Optional device allocator for the plan's workspace (e.g. PyTorch's
+       caching allocator).  NULL: cudaMalloc/cudaFree. */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} tn_plan_opts;
+
+typedef struct tn_plan_s tn_plan_t;  /* opaque */
+
+typedef struct {
+    int32_t n_qubits, n_open;
+    int32_t n_leaves;             /* tensors after absorbing 1q gates/boundaries */
+    int32_t n_edges;              /* internal (contracted) edges before slicing   */
+    int32_t n_slice_edges;
+    int64_t n_slices;             /* 2^n_slice_edges                             */
+    int32_t n_steps;              /* pairwise contractions per slice             */
+    int32_t n_steps_invariant;    /* of those, independent of the slice          */
+    int32_t max_log2_elems;       /* largest intermediate of one slice (log2)    */
+    int32_t slice_batch_log2;
+    double flops_per_slice;       /* sum over steps of 8*M*N*K (real flops)      */
+    double flops_invariant;       /* part of it done once per contract call      */
+    double bytes_per_slice;       /* algorithmic bytes: per step, operands +
+                                     result once, plus permuted copies          */
+    int64_t workspace_bytes;      /* device workspace of the plan                */
+    int32_t n_permutes;           /* explicit permutations per slice             */
+    int32_t dtype;
+} tn_plan_stats;
+
+typedef struct {
+    double ms;                    /* device time of the call (CUDA events)       */
+    double flops;                 /* real flops executed                         */
+    int64_t slices;               /* slices summed                               */
+    int32_t kernels;              /* kernel launches issued                      */
+    int32_t min_exp, max_exp;     /* range of per-slice scale exponents (lp)     */
+} tn_contract_report;
+
+/* One step of a plan (for inspection and tests). */
+typedef struct {
+    int32_t a, b, c;              /* tensor ids: inputs, output                  */
+    int32_t log2_m, log2_n, log2_k, log2_batch;
+    int32_t permute_a;            /* 1 if A is permuted before the GEMM          */
+    int32_t slice_invariant;
+    int32_t kernel;               /* which GEMM kernel variant runs this step    */
+    int32_t tile;                 /* tile configuration index                    */
+} tn_step_info;
+
+/*
+ * tn_plan: build the tensor network of `circuit` for `query`, search a greedy
+ * pairwise contraction path, choose sliced edges and lay out every step.
+ * The circuit becomes one tensor per two-qubit gate; single-qubit gates, the
+ * initial |0> states and the fixed output bits are absorbed into them
+ * (exact).  Host work only; device memory is allocated on the first
+ * tn_contract.  *out receives a plan the caller frees with tn_plan_destroy.
+ * Errors: TN_EINVAL (bad qubit index, repeated/unsorted open qubits, n_open
+ * > 30, bad dtype, a cap the slicing cannot reach), TN_ENOMEM.
+ */
+int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts *opts,
+            tn_plan_t **out);
+
+/* Fill default options (TN_F16, no cap, no slicing, seed 1, 1 trial). */
+void tn_plan_opts_default(tn_plan_opts *opts);
+
+int tn_plan_info(const tn_plan_t *plan, tn_plan_stats *out);
+
+/* Sliced edges as (qubit, after_gate) pairs: edge j is the wire of `qubit`
+ * right after gate index `after_gate` of the circuit.  Writes
+ * min(capacity, n_slice_edges) pairs; returns TN_OK. */
+int tn_plan_sliced_edges(const tn_plan_t *plan, int32_t *qubit, int32_t *after_gate,
+                         int32_t capacity);
+
+/* Step i of the per-slice schedule (0 <= i < n_steps). */
+int tn_plan_step(const tn_plan_t *plan, int32_t i, tn_step_info *out);
+
+/*
+ * tn_contract: contract slices [slice_begin, slice_begin + slice_count) and
+ * add (accumulate != 0) or write (accumulate == 0) their FP64 sum into d_amps
+ * (device, 2^n_open complex128, caller-owned).  Slices are summed in
+ * ascending order, each slice's amplitudes added one slice at a time, so
+ * splitting a range into ordered sub-ranges with accumulate=1 gives
+ * bit-identical sums (plans with slice_batch_log2 = 0).  Enqueued on
+ * `stream`; returns after enqueueing unless `rep` is non-NULL (then it
+ * synchronizes and fills the report).  A plan serves one stream at a time.
+ * Errors: TN_EINVAL (range outside [0, n_slices)), TN_ENOMEM, TN_ECUDA,
+ * TN_ETIMEOUT.
+ */
+int tn_contract(tn_plan_t *plan, int64_t slice_begin, int64_t slice_count, double *d_amps,
+                int accumulate, void *stream, tn_contract_report *rep);
+
+/* As tn_contract, end to end from host memory: the leaf tensors are copied
+ * host->device from the plan's pinned host copy, the slices contracted, and
+ * the 2^n_open amplitudes copied to h_amps (host).  Synchronizes. */
+int tn_contract_host(tn_plan_t *plan, int64_t slice_begin, int64_t slice_count,
+                     double *h_amps, void *stream, tn_contract_report *rep);
+
+/*
+ * tn_contract_batch: contract every slice of n independent plans (uneven
+ * circuits) and write each one's amplitudes to d_amps[i] (device), in one
+ * captured CUDA graph.  Plans must share dtype.
+ */
+int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps, void *stream);
+
+/*
+ * tn_sample: post-selection on one correlated subspace (Sec. 1/2,
+ * post-processing): from d_amps (device, 2^n_open complex128) return the k
+ * indices of largest |amp|^2 and their probabilities, ties to the lower index,
+ * in descending order.  out_idx / out_prob: host, length k, caller-owned.
+ * Synchronizes `stream`.  Errors: TN_EINVAL (k < 1 or k > 2^n_open, n_open
+ * > 30), TN_ENOMEM, TN_ECUDA.
+ */
+int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
+              double *out_prob, void *stream);
+
+/*
+ * tn_metrics: FP64 reductions on the device over n complex128 amplitudes:
+ * out[0] = sum |r|^2, out[1] = rel-L2 ||r - b|| / ||b||, out[2] = fidelity
+ * |<b,r>|^2 / (||b||^2 ||r||^2) (Sec. 4.2, Eq. 9, conjugate-linear inner
+ * product), out[3] = linear XEB 2^n_qubits * mean |r|^2 - 1 of the n entries.
+ * d_ref may be NULL (then out[1], out[2] are NaN).  out: host, 4 doubles.
+ */
+int tn_metrics(const double *d_amps, const double *d_ref, int64_t n, int32_t n_qubits,
+               double *out, void *stream);
+
+void tn_plan_destroy(tn_plan_t *plan);
+
+/* ---- single-kernel entry points (used by tests; same kernels as above) ---- */
+
+/*
+ * tn_permute: out = in with its rank-r dim-2 modes reordered (Sec. 3.1,
+ * "index permutation"): out index bit (r-1-i) = in index bit (r-1-perm[i]),
+ * i.e. output mode i (outermost first) is input mode perm[i].  Bit-exact
+ * data movement.  elem_bytes: 4 (complex-half) or 8 (complex64).  in, out:
+ * device, 2^r elements, non-overlapping.  r <= 34.
+ */
+int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
+               int32_t elem_bytes, void *stream);
+
+/*
+ * tn_gemm: one contraction step as a GEMM, C[b][M][N] = sum_k A[b][M][K] *
+ * B[b][K][N] on interleaved complex data (row-major; batch stride 0 for a
+ * broadcast operand: pass batch_a / batch_b = 0 for no batch mode).
+ *   dtype TN_C64: A, B, C complex64, FP32 accumulation; scale ignored.
+ *   dtype TN_F16/TN_BF16: A, C complex-half; B complex64 (small operand, padded
+ *   on the device to the real 2K x 2N form of Eq. 4-5); FP32 accumulation; C
+ *   is multiplied by 2^scale_exp before rounding.
+ * kernel: -1 = automatic; otherwise a variant index (tests).
+ * out_max: optional device float, receives max |component| of the stored C.
+ */
+int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,
+            int64_t K, int64_t batch, int32_t batch_a, int32_t batch_b, int32_t scale_exp,
+            int32_t kernel, float *out_max, void *stream);
+
+const char *tn_strerror(int code);
+const char *tn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H_ */

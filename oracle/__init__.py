@@ -215,8 +215,10 @@ def linear_xeb(sample_probs: np.ndarray, n_qubits: int) -> float:
 
 
 def topk(amps: np.ndarray, k: int):
-    """Indices and probabilities |amp|^2 of the k largest; ties go to the
-    lower index.  Plain: a stable sort on (-p, index)."""
-    p = np.abs(np.asarray(amps, dtype=np.complex128)) ** 2
+    """Indices and probabilities |amp|^2 = re*re + im*im (each product and the
+    sum rounded once, FP64) of the k largest; ties go to the lower index.
+    Plain: a stable sort on (-p, index)."""
+    a = np.asarray(amps, dtype=np.complex128)
+    p = a.real * a.real + a.imag * a.imag
     idx = np.lexsort((np.arange(p.shape[0]), -p))[:k]
     return idx.astype(np.int64), p[idx]

@@ -1,0 +1,360 @@
+"""GB300 sliced tensor-network contraction of random quantum circuits.
+
+Thin binding over the C ABI in include/tn.h (library: _build/libtn.so).  This
+module only marshals arguments: every step of the contraction runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  There is
+no CPU fallback: if the library cannot be built or loaded, every call raises.
+
+    from paper_2407_00769_gb300 import Plan, F16
+    plan = Plan(circuit, query, dtype=F16, n_slice_edges=8)
+    amps = plan.contract()               # torch complex128 on the GPU
+    idx, prob = sample(amps, k=1)        # post-selection (top-k)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build_mod
+
+C64, F16, BF16 = 0, 1, 2
+TILE_FIXED, TILE_EXHAUSTIVE, TILE_LEARNED = 0, 1, 2
+DTYPE_NAMES = {C64: "c64", F16: "f16", BF16: "bf16"}
+KERNEL_NAMES = {0: "c64_rows", 1: "c64_tiled", 2: "lp_rows", 3: "lp_tc"}
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
+
+EXPORTED = [
+    "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
+    "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
+    "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
+]
+
+
+class TnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class Gate(ctypes.Structure):
+    _fields_ = [("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("re", ctypes.c_double * 16), ("im", ctypes.c_double * 16)]
+
+
+class CircuitC(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32),
+                ("gates", ctypes.POINTER(Gate))]
+
+
+class QueryC(ctypes.Structure):
+    _fields_ = [("n_open", ctypes.c_int32), ("open_qubits", ctypes.POINTER(ctypes.c_int32)),
+                ("fixed_bits", ctypes.POINTER(ctypes.c_uint8))]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("max_log2_elems", ctypes.c_int32),
+                ("n_slice_edges", ctypes.c_int32), ("path_seed", ctypes.c_uint64),
+                ("path_trials", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
+                ("tile_policy", ctypes.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_open", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("n_slice_edges", ctypes.c_int32), ("n_slices", ctypes.c_int64),
+                ("n_steps", ctypes.c_int32), ("n_steps_invariant", ctypes.c_int32),
+                ("max_log2_elems", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
+                ("flops_per_slice", ctypes.c_double), ("flops_invariant", ctypes.c_double),
+                ("bytes_per_slice", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
+                ("n_permutes", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class ContractReport(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("slices", ctypes.c_int64),
+                ("kernels", ctypes.c_int32), ("min_exp", ctypes.c_int32),
+                ("max_exp", ctypes.c_int32)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("log2_m", ctypes.c_int32), ("log2_n", ctypes.c_int32),
+                ("log2_k", ctypes.c_int32), ("log2_batch", ctypes.c_int32),
+                ("permute_a", ctypes.c_int32), ("slice_invariant", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+def build(force: bool = False) -> str:
+    return _build_mod.build(force=force)
+
+
+def lib():
+    """Load libtn.so (building it first if needed).  Raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build_mod.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.tn_plan.argtypes = [ctypes.POINTER(CircuitC), ctypes.POINTER(QueryC),
+                              ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.tn_plan_opts_default.argtypes = [ctypes.POINTER(PlanOpts)]
+        L.tn_plan_opts_default.restype = None
+        L.tn_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
+        L.tn_plan_sliced_edges.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
+        L.tn_plan_step.argtypes = [vp, i32, ctypes.POINTER(StepInfo)]
+        L.tn_contract.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, ctypes.POINTER(ContractReport)]
+        L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp, ctypes.POINTER(ContractReport)]
+        L.tn_contract_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
+        L.tn_sample.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.tn_metrics.argtypes = [vp, vp, i64, i32, vp, vp]
+        L.tn_plan_destroy.argtypes = [vp]
+        L.tn_plan_destroy.restype = None
+        L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
+        L.tn_gemm.argtypes = [i32, vp, vp, vp, i64, i64, i64, i64, i32, i32, i32, i32, vp, vp]
+        L.tn_strerror.argtypes = [ctypes.c_int]
+        L.tn_strerror.restype = ctypes.c_char_p
+        L.tn_last_error.argtypes = []
+        L.tn_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("tn_plan_opts_default", "tn_plan_destroy", "tn_strerror", "tn_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != TN_OK:
+        L = lib()
+        raise TnError(rc, f"{L.tn_strerror(rc).decode()}: {L.tn_last_error().decode()}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def circuit_struct(circuit):
+    """Marshal an rqcgen.Circuit into the C structs (kept alive by the caller)."""
+    n_g = int(circuit.n_gates)
+    gates = (Gate * max(1, n_g))()
+    mats = np.asarray(circuit.mats, dtype=np.complex128).reshape(n_g, 16)
+    for g in range(n_g):
+        gates[g].q0 = int(circuit.q0[g])
+        gates[g].q1 = int(circuit.q1[g])
+        ctypes.memmove(gates[g].re, np.ascontiguousarray(mats[g].real).ctypes.data, 128)
+        ctypes.memmove(gates[g].im, np.ascontiguousarray(mats[g].imag).ctypes.data, 128)
+    c = CircuitC(int(circuit.n_qubits), n_g, gates)
+    return c, gates
+
+
+def query_struct(query, n_qubits):
+    oq = np.ascontiguousarray(query.open_qubits, dtype=np.int32)
+    fb = np.ascontiguousarray(query.fixed_bits, dtype=np.uint8)
+    if fb.shape[0] != n_qubits:
+        raise ValueError("fixed_bits must have one entry per qubit")
+    q = QueryC(int(oq.shape[0]), oq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+               fb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return q, (oq, fb)
+
+
+class _TorchAllocator:
+    """Routes the plan's workspace through PyTorch's caching allocator."""
+
+    def __init__(self):
+        torch = _torch()
+        self._live = {}
+
+        def alloc(nbytes, ctx):
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            p = t.data_ptr()
+            self._live[p] = t
+            return p
+
+        def free(ptr, ctx):
+            self._live.pop(int(ptr or 0), None)
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+class Plan:
+    """A contraction plan (tn_plan): network, path, slicing and schedule."""
+
+    def __init__(self, circuit, query, dtype: int = F16, max_log2_elems: int = 0,
+                 n_slice_edges: int = 0, seed: int = 1, trials: int = 1,
+                 slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
+                 torch_allocator: bool = True):
+        L = lib()
+        self._c, self._gates = circuit_struct(circuit)
+        self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
+        opts = PlanOpts()
+        L.tn_plan_opts_default(ctypes.byref(opts))
+        opts.dtype = int(dtype)
+        opts.max_log2_elems = int(max_log2_elems)
+        opts.n_slice_edges = int(n_slice_edges)
+        opts.path_seed = int(seed)
+        opts.path_trials = int(trials)
+        opts.slice_batch_log2 = int(slice_batch_log2)
+        opts.tile_policy = int(tile_policy)
+        self._alloc = None
+        if torch_allocator:
+            self._alloc = _TorchAllocator()
+            opts.dev_alloc = self._alloc.alloc
+            opts.dev_free = self._alloc.free
+        self._opts = opts
+        h = ctypes.c_void_p()
+        _check(L.tn_plan(ctypes.byref(self._c), ctypes.byref(self._q), ctypes.byref(opts),
+                         ctypes.byref(h)))
+        self._h = h
+        self.n_open = int(query.n_open) if hasattr(query, "n_open") else len(query.open_qubits)
+        self.n_qubits = int(circuit.n_qubits)
+        self.dtype = int(dtype)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().tn_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        s = PlanStats()
+        _check(lib().tn_plan_info(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in PlanStats._fields_}
+
+    def sliced_edges(self):
+        n = self.info()["n_slice_edges"]
+        q = (ctypes.c_int32 * max(1, n))()
+        g = (ctypes.c_int32 * max(1, n))()
+        _check(lib().tn_plan_sliced_edges(self._h, q, g, n))
+        return [(int(q[j]), int(g[j])) for j in range(n)]
+
+    def steps(self):
+        out = []
+        for i in range(self.info()["n_steps"]):
+            st = StepInfo()
+            _check(lib().tn_plan_step(self._h, i, ctypes.byref(st)))
+            out.append({f: getattr(st, f) for f, _ in StepInfo._fields_})
+        return out
+
+    def contract(self, slice_begin: int = 0, slice_count: Optional[int] = None, out=None,
+                 accumulate: bool = False, stream=None, report: bool = False):
+        """Sum of slices [slice_begin, slice_begin+slice_count) into a complex128
+        CUDA tensor of 2^n_open amplitudes (``out`` if given)."""
+        torch = _torch()
+        n_slices = self.info()["n_slices"]
+        if slice_count is None:
+            slice_count = n_slices - slice_begin
+        if out is None:
+            out = torch.zeros(1 << self.n_open, dtype=torch.complex128, device="cuda")
+        if out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() \
+                or out.numel() != (1 << self.n_open):
+            raise ValueError("out must be a contiguous CUDA complex128 tensor of 2^n_open")
+        rep = ContractReport() if report else None
+        _check(lib().tn_contract(self._h, int(slice_begin), int(slice_count), out.data_ptr(),
+                                 1 if accumulate else 0, _stream_ptr(stream),
+                                 ctypes.byref(rep) if rep is not None else None))
+        if report:
+            return out, {f: getattr(rep, f) for f, _ in ContractReport._fields_}
+        return out
+
+    def contract_host(self, slice_begin: int = 0, slice_count: Optional[int] = None, stream=None,
+                      report: bool = False):
+        """End to end from host memory: leaves uploaded, amplitudes downloaded."""
+        n_slices = self.info()["n_slices"]
+        if slice_count is None:
+            slice_count = n_slices - slice_begin
+        h = np.zeros(1 << self.n_open, dtype=np.complex128)
+        rep = ContractReport() if report else None
+        _check(lib().tn_contract_host(self._h, int(slice_begin), int(slice_count),
+                                      h.ctypes.data, _stream_ptr(stream),
+                                      ctypes.byref(rep) if rep is not None else None))
+        if report:
+            return h, {f: getattr(rep, f) for f, _ in ContractReport._fields_}
+        return h
+
+
+def contract_batch(plans, outs, stream=None):
+    n = len(plans)
+    hs = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    ds = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib().tn_contract_batch(hs, n, ds, _stream_ptr(stream)))
+    return outs
+
+
+def sample(amps, k: int = 1, stream=None):
+    """Top-k post-selection: (indices, probabilities) as numpy arrays."""
+    n = amps.numel()
+    n_open = n.bit_length() - 1
+    if (1 << n_open) != n:
+        raise ValueError("amplitude count must be a power of two")
+    idx = np.zeros(k, dtype=np.int64)
+    prob = np.zeros(k, dtype=np.float64)
+    _check(lib().tn_sample(amps.data_ptr(), n_open, int(k), idx.ctypes.data, prob.ctypes.data,
+                           _stream_ptr(stream)))
+    return idx, prob
+
+
+def metrics(amps, ref=None, n_qubits: int = 0, stream=None) -> dict:
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().tn_metrics(amps.data_ptr(), ref.data_ptr() if ref is not None else None,
+                            int(amps.numel()), int(n_qubits), out.ctypes.data,
+                            _stream_ptr(stream)))
+    return {"norm2": out[0], "rel_l2": out[1], "fidelity": out[2], "xeb": out[3]}
+
+
+def permute(x, perm, out=None, elem_bytes=None, stream=None):
+    """Bit-permute a tensor of 2^r elements (4- or 8-byte elements; complex64
+    tensors are 8-byte, anything else is read as 4-byte elements)."""
+    torch = _torch()
+    r = len(perm)
+    if out is None:
+        out = torch.empty_like(x)
+    if elem_bytes is None:
+        elem_bytes = 8 if x.dtype in (torch.complex64, torch.int64, torch.float64) else 4
+    p = (ctypes.c_int32 * max(1, r))(*[int(v) for v in perm])
+    _check(lib().tn_permute(x.data_ptr(), out.data_ptr(), r, p, int(elem_bytes),
+                            _stream_ptr(stream)))
+    return out
+
+
+def gemm(dtype, A, B, C, M, N, K, batch=1, batch_a=False, batch_b=False, scale_exp=0,
+         kernel=-1, out_max=None, stream=None):
+    _check(lib().tn_gemm(int(dtype), A.data_ptr(), B.data_ptr(), C.data_ptr(), int(M), int(N),
+                         int(K), int(batch), 1 if batch_a else 0, 1 if batch_b else 0,
+                         int(scale_exp), int(kernel),
+                         out_max.data_ptr() if out_max is not None else None,
+                         _stream_ptr(stream)))
+    return C

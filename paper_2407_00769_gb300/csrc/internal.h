@@ -1,0 +1,128 @@
+// Internal structures of the contraction library: the tensor network, the
+// contraction path, and the device schedule (ops) that tn_contract replays.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tn.h"
+
+namespace tn {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxRank = 40;   // modes of any device tensor (incl. batch modes)
+
+// ---------------------------------------------------------------- network --
+// An edge is one wire segment between two two-qubit gates: the wire of
+// `qubit` right after gate `after_gate`.  Open edges end at the output.
+struct Edge {
+    int qubit = -1, after_gate = -1;
+    int u = -1, v = -1;   // endpoint leaves (v < 0 for an open edge)
+    int open_t = -1;      // output bit position t for an open edge
+};
+
+// A leaf: one two-qubit gate tensor with its neighbouring single-qubit gates,
+// initial states and fixed output bits absorbed.  legs: edge ids, outermost
+// first; data: row-major over legs.
+struct Leaf {
+    std::vector<int> legs;
+    std::vector<cd> data;
+    int gate = -1;        // circuit gate index it came from (-1: isolated qubit)
+};
+
+struct Network {
+    int n_qubits = 0, n_open = 0;
+    std::vector<Edge> edges;
+    std::vector<Leaf> leaves;
+};
+
+int build_network(const tn_circuit *c, const tn_query *q, Network &out, std::string &err);
+
+// ------------------------------------------------------------------- path --
+struct Path {
+    std::vector<std::pair<int, int>> steps;  // tensor ids; step s makes id L+s
+    double flops = 0;                         // per slice, 8*M*N*K summed
+    int max_log2 = 0;                         // largest intermediate (log2)
+};
+
+// --------------------------------------------------------------- schedule --
+enum OpKind : int32_t {
+    OP_LEAF = 1,    // prepare leaves of one phase (slice bits fixed, dtype convert)
+    OP_PERM = 2,    // bit-permute one tensor
+    OP_BPREP = 3,   // B [batch][K][N] complex-half -> B' real [batch][N'][K'] + colsum
+    OP_GEMM = 4,    // one contraction step
+    OP_SUM = 5,     // final tensor -> FP64 amplitudes
+};
+
+enum GemmKernel : int32_t {
+    GK_C64_ROWS = 0,   // complex64, thread per row, B in shared memory
+    GK_C64_TILED = 1,  // complex64, 2-D shared-memory tiles
+    GK_LP_ROWS = 2,    // complex-half, FP32 math, thread per row
+    GK_LP_TC = 3,      // complex-half as real, tcgen05 + TMA, FP32 in TMEM
+};
+
+struct LeafJob {          // one leaf to prepare (device-side struct)
+    int64_t src;          // element offset into the leaf store (complex128)
+    int64_t dst;          // byte offset into the workspace
+    int32_t rank_in;      // legs of the full leaf
+    int32_t rank_out;     // legs kept
+    int32_t n_fixed;      // legs fixed by looped slice bits
+    int32_t fixed_pos[4]; // bit position (from LSB) of each fixed leg in the input
+    int32_t fixed_bit[4]; // slice-id bit that fixes it
+    int32_t keep_pos[4];  // bit position (from LSB) in the input of output bit i
+    int32_t meta;         // tensor meta slot (complex-half)
+    int32_t pad_;
+};
+
+struct PermOp {
+    int64_t src, dst;     // byte offsets
+    int32_t rank;
+    int32_t perm[kMaxRank];  // output mode i (outermost first) = input mode perm[i]
+};
+
+struct GemmOp {
+    int64_t a, b, c;      // byte offsets; b is [batch][K][N] (c64 / lp rows) or B'
+    int32_t lm, ln, lk, lb;        // log2 of M, N, K, batch
+    int32_t a_batched, b_batched;  // operand carries the batch modes (else broadcast)
+    int32_t meta_a, meta_b, meta_c, step;
+    int32_t kernel, tile;
+};
+
+struct BprepOp {
+    int64_t src, dst;     // [batch][K][N] complex-half -> [batch][N'][K'] real
+    int32_t lk, ln, lb, step;
+    int32_t np;           // padded N' (real columns, >= 16)
+};
+
+struct SumOp {
+    int64_t src;          // final tensor (byte offset)
+    int32_t rank;         // legs of the final tensor
+    int32_t open_pos[32]; // bit position (from LSB) of open output t in the tensor
+    int32_t n_batch;      // batched slice bits in the final tensor
+    int32_t batch_pos[16];// bit position (from LSB) of batched slice bit j
+    int32_t meta;
+};
+
+struct Op {
+    int32_t kind = 0;
+    int32_t phase = 0;    // 0: once per call (slice invariant), 1: every pass
+    int32_t leaf_first = 0, leaf_count = 0;  // OP_LEAF: range in plan leaf jobs
+    PermOp perm{};
+    GemmOp gemm{};
+    BprepOp bprep{};
+    SumOp sum{};
+};
+
+// Per-step record for inspection.
+struct StepRec {
+    int a, b, c;
+    int lm, ln, lk, lb;
+    int permute_a;
+    int invariant;
+    int kernel, tile;
+};
+
+}  // namespace tn

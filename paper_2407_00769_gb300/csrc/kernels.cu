@@ -1,0 +1,645 @@
+// SIMT kernels: leaf preparation (slice decoding), bit-permute transpose,
+// complex GEMMs on CUDA cores, B padding for the tensor-core path, the FP64
+// cross-slice sum, FP64 reductions and top-k post-selection.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace tn {
+
+// ------------------------------------------------------------ lp helpers --
+template <int DT> struct LpT;
+template <> struct LpT<TN_F16> {
+    using T2 = __half2;
+    static __device__ __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ T2 from_f2(float2 v) { return __floats2half2_rn(v.x, v.y); }
+    static __device__ __forceinline__ T2 from_d2(double re, double im) {
+        return __halves2half2(__double2half(re), __double2half(im));
+    }
+};
+template <> struct LpT<TN_BF16> {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ T2 from_f2(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
+    static __device__ __forceinline__ T2 from_d2(double re, double im) {
+        return __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+    }
+};
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float *addr, float v) {
+    atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v));
+}
+
+// exponent e for a product of two scaled tensors: with |A| <= sqrt2 maxA,
+// |B| <= sqrt2 maxB and K terms, |C| <= 2 K maxA maxB; choose e so that
+// 2 K maxA maxB 2^e <= 2^14 (FP16 max is 65504 ~ 2^16).
+__device__ __forceinline__ int scale_exponent(float maxa, float maxb, int lk) {
+    const float t = 2.0f * maxa * maxb;
+    if (!(t > 0.0f) || !isfinite(t)) return 0;
+    int x;
+    const float f = frexpf(t, &x);            // t = f 2^x, f in [0.5, 1)
+    const int c = (f == 0.5f) ? x - 1 : x;    // ceil(log2 t)
+    int e = 14 - lk - c;
+    return max(-120, min(120, e));
+}
+
+__device__ __forceinline__ float exp2i(int e) {   // exact 2^e, |e| <= 126
+    return __int_as_float((127 + e) << 23);
+}
+
+// ------------------------------------------------------------- leaf prep --
+// One block per leaf.  Output element o (over the kept legs) reads input
+// element in(o) = kept bits placed at keep_pos, fixed legs at the value of
+// their slice-id bit (slice decoding: bit j of the slice id is sliced edge
+// j's value).  Converts complex128 -> the contraction dtype (RN).
+template <int DT>
+__global__ void leaf_prep_kernel(const LeafJob *jobs, const double2 *store, char *ws,
+                                 int64_t slice_base, float *tmax, int32_t *texp) {
+    const LeafJob j = jobs[blockIdx.x];
+    const int n_out = 1 << j.rank_out;
+    float m = 0.0f;
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        int64_t in = 0;
+        for (int i = 0; i < j.rank_out; ++i)
+            if ((o >> i) & 1) in |= (int64_t)1 << j.keep_pos[i];
+        for (int f = 0; f < j.n_fixed; ++f)
+            in |= ((slice_base >> j.fixed_bit[f]) & 1) << j.fixed_pos[f];
+        const double2 v = store[j.src + in];
+        if constexpr (DT == TN_C64) {
+            reinterpret_cast<float2 *>(ws + j.dst)[o] = make_float2((float)v.x, (float)v.y);
+        } else {
+            using L = LpT<DT>;
+            const typename L::T2 h = L::from_d2(v.x, v.y);
+            reinterpret_cast<typename L::T2 *>(ws + j.dst)[o] = h;
+            const float2 f = L::to_f2(h);
+            m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+        }
+    }
+    if constexpr (DT != TN_C64) {
+        m = warp_max(m);
+        __shared__ float sm[32];
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float mm = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mm = fmaxf(mm, sm[w]);
+            tmax[j.meta] = mm;
+            texp[j.meta] = 0;
+        }
+    }
+}
+
+cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_store, char *ws,
+                             int dtype, int64_t slice_base, float *tmax, int32_t *texp,
+                             cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (dtype == TN_C64)
+        leaf_prep_kernel<TN_C64><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
+    else if (dtype == TN_F16)
+        leaf_prep_kernel<TN_F16><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
+    else
+        leaf_prep_kernel<TN_BF16><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- permute --
+// Tile = a set of input index bits (the low `lin` input bits plus the input
+// positions of the low `lout` output bits, topped up to `tile_bits`).  A
+// block reads its tile in input order (coalesced), stages it in shared
+// memory, and writes it in output order (coalesced).  The other bits come
+// from the block id.  Pure data movement: bit-exact.
+PermParams make_perm_params(int r, const int32_t *perm) {
+    PermParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.rank = r;
+    // out_of_in[b] = output bit position of input bit position b (LSB = 0)
+    int out_of_in[kMaxRank], in_of_out[kMaxRank];
+    for (int i = 0; i < r; ++i) {
+        const int in_bit = r - 1 - perm[i], out_bit = r - 1 - i;
+        out_of_in[in_bit] = out_bit;
+        in_of_out[out_bit] = in_bit;
+    }
+    const int tb = std::min(10, r);
+    p.lin = std::min(5, r);
+    p.lout = std::min(5, r);
+    bool in_tile[kMaxRank] = {false};
+    for (int b = 0; b < p.lin; ++b) in_tile[b] = true;
+    for (int j = 0; j < p.lout; ++j) in_tile[in_of_out[j]] = true;
+    int count = 0;
+    for (int b = 0; b < r; ++b) count += in_tile[b];
+    for (int b = 0; b < r && count < tb; ++b)
+        if (!in_tile[b]) { in_tile[b] = true; ++count; }
+    p.tile_bits = count;
+    // read order: e bit i < lin -> input bit i; e bit lin+k -> hi_pos[k]
+    int hi_pos[kMaxRank], n_hi = 0;
+    int e_bit_of_in[kMaxRank];
+    for (int b = 0; b < r; ++b) e_bit_of_in[b] = -1;
+    for (int b = 0; b < p.lin; ++b) e_bit_of_in[b] = b;
+    for (int b = p.lin; b < r; ++b)
+        if (in_tile[b]) { e_bit_of_in[b] = p.lin + n_hi; hi_pos[n_hi++] = b; }
+    for (int h = 0; h < (1 << n_hi); ++h) {
+        int64_t off = 0;
+        for (int k = 0; k < n_hi; ++k)
+            if ((h >> k) & 1) off |= (int64_t)1 << hi_pos[k];
+        p.rd_hi_off[h] = off;
+    }
+    // write order: f bit j < lout -> output bit j; f bit lout+k -> the k-th
+    // remaining tile bit (ascending output position)
+    int whi_out[kMaxRank], n_whi = 0;
+    for (int ob = p.lout; ob < r; ++ob)
+        if (in_tile[in_of_out[ob]]) whi_out[n_whi++] = ob;
+    for (int f = 0; f < (1 << p.lout); ++f) {
+        int e = 0;
+        for (int j = 0; j < p.lout; ++j)
+            if ((f >> j) & 1) e |= 1 << e_bit_of_in[in_of_out[j]];
+        p.wr_lo_e[f] = e;
+    }
+    for (int h = 0; h < (1 << n_whi); ++h) {
+        int e = 0;
+        int64_t off = 0;
+        for (int k = 0; k < n_whi; ++k)
+            if ((h >> k) & 1) {
+                e |= 1 << e_bit_of_in[in_of_out[whi_out[k]]];
+                off |= (int64_t)1 << whi_out[k];
+            }
+        p.wr_hi_e[h] = e;
+        p.wr_hi_off[h] = off;
+    }
+    // outer bits
+    int k = 0;
+    for (int b = 0; b < r; ++b)
+        if (!in_tile[b]) {
+            p.outer_in[k] = (int8_t)b;
+            p.outer_out[k] = (int8_t)out_of_in[b];
+            ++k;
+        }
+    p.n_outer = k;
+    return p;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) permute_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                      const __grid_constant__ PermParams p) {
+    __shared__ T tile[1024 + 32];
+    int64_t bin = 0, bout = 0;
+    const int64_t tid = blockIdx.x;
+    for (int k = 0; k < p.n_outer; ++k)
+        if ((tid >> k) & 1) {
+            bin |= (int64_t)1 << p.outer_in[k];
+            bout |= (int64_t)1 << p.outer_out[k];
+        }
+    const int n = 1 << p.tile_bits;
+    const int lo_mask_in = (1 << p.lin) - 1;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int64_t off = bin + (e & lo_mask_in) + p.rd_hi_off[e >> p.lin];
+        tile[e + (e >> 5)] = in[off];
+    }
+    __syncthreads();
+    const int lo_mask_out = (1 << p.lout) - 1;
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+        const int fl = f & lo_mask_out, fh = f >> p.lout;
+        const int e = p.wr_lo_e[fl] | p.wr_hi_e[fh];
+        out[bout + fl + p.wr_hi_off[fh]] = tile[e + (e >> 5)];
+    }
+}
+
+cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int elem_bytes,
+                           cudaStream_t s) {
+    const int64_t blocks = (int64_t)1 << pp.n_outer;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int threads = std::min(256, 1 << pp.tile_bits);
+    if (elem_bytes == 4)
+        permute_kernel<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(
+            (const uint32_t *)in, (uint32_t *)out, pp);
+    else if (elem_bytes == 8)
+        permute_kernel<uint2><<<(unsigned)blocks, threads, 0, s>>>((const uint2 *)in, (uint2 *)out, pp);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- rows GEMMs --
+// C[b][m][n] = sum_k A[b][m][k] B[b][k][n].  A block owns ROWS consecutive
+// rows (one per thread) and NC consecutive columns (grid.y); the A tile is
+// staged through shared memory with coalesced 16-byte loads (its rows are
+// contiguous), B's column chunk sits in shared memory as FP32 complex.
+// K is walked in chunks of KC.
+constexpr int kRows = 128;
+constexpr int kKC = 32;
+
+template <typename T, int NC, int DT>
+__global__ void __launch_bounds__(kRows) gemm_rows_kernel(
+    const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C, int lm, int ln, int lk,
+    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr) {
+    constexpr int KC = kKC;
+    __shared__ __align__(16) T As[kRows * KC];
+    __shared__ float2 Bs[KC][NC];
+    const int64_t M = (int64_t)1 << lm;
+    const int N = 1 << ln, K = 1 << lk;
+    const int64_t b = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * kRows;
+    const int n0 = blockIdx.y * NC;
+    const int nc = min(NC, N);
+    const T *Ab = A + b * sa;
+    const T *Bb = B + b * sb;
+    T *Cb = C + b * sc;
+    const int rows = (int)min((int64_t)kRows, M - m0);
+    float2 acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const int kc = min(KC, K - k0);
+        __syncthreads();
+        // A tile: rows x kc elements; when kc == K the tile is contiguous
+        {
+            const int per16 = 16 / (int)sizeof(T);
+            const int total = rows * kc;
+            if (kc == K && (total % per16) == 0) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(Ab + m0 * K);
+                uint4 *dst = reinterpret_cast<uint4 *>(As);
+                for (int i = threadIdx.x; i < total / per16; i += kRows) dst[i] = src[i];
+            } else {
+                for (int i = threadIdx.x; i < total; i += kRows) {
+                    const int r = i / kc, kk = i % kc;
+                    As[r * kc + kk] = Ab[(m0 + r) * K + k0 + kk];
+                }
+            }
+        }
+        for (int i = threadIdx.x; i < kc * nc; i += kRows) {
+            const int kk = i / nc, j = i % nc;
+            const T v = Bb[(int64_t)(k0 + kk) * N + n0 + j];
+            if constexpr (DT == TN_C64) Bs[kk][j] = v;
+            else Bs[kk][j] = LpT<DT>::to_f2(v);
+        }
+        __syncthreads();
+        if (threadIdx.x < rows) {
+            for (int kk = 0; kk < kc; ++kk) {
+                float2 a;
+                if constexpr (DT == TN_C64) a = As[threadIdx.x * kc + kk];
+                else a = LpT<DT>::to_f2(As[threadIdx.x * kc + kk]);
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    if (j < nc) {
+                        const float2 bb = Bs[kk][j];
+                        acc[j].x = fmaf(a.x, bb.x, fmaf(-a.y, bb.y, acc[j].x));
+                        acc[j].y = fmaf(a.x, bb.y, fmaf(a.y, bb.x, acc[j].y));
+                    }
+                }
+            }
+        }
+    }
+    if (threadIdx.x >= rows) return;
+    const int64_t m = m0 + threadIdx.x;
+    T *crow = Cb + m * N + n0;
+    if constexpr (DT == TN_C64) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            if (j < nc) crow[j] = acc[j];
+    } else {
+        // power-of-two scaling (exact): e from the operands' recorded maxima
+        int e;
+        if (sr.tmax) e = scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk);
+        else e = sr.fixed_exp;
+        if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+            sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
+        const float s = exp2i(e);
+        float mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            if (j < nc) {
+                const auto h = LpT<DT>::from_f2(make_float2(acc[j].x * s, acc[j].y * s));
+                crow[j] = h;
+                const float2 f = LpT<DT>::to_f2(h);
+                mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+            }
+        if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+    }
+}
+
+template <typename T, int DT>
+static cudaError_t rows_dispatch(const T *A, const T *B, T *C, int lm, int ln, int lk,
+                                 int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                 const ScaleRef &sr, cudaStream_t s) {
+    const int64_t M = (int64_t)1 << lm;
+    const int N = 1 << ln;
+    const int64_t gx = (M + kRows - 1) / kRows;
+    if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
+#define TN_ROWS_CASE(NCV)                                                                   \
+    {                                                                                        \
+        dim3 g((unsigned)gx, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);              \
+        gemm_rows_kernel<T, NCV, DT><<<g, kRows, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc, sr); \
+        break;                                                                               \
+    }
+    switch (N >= 16 ? 16 : N) {
+        case 1: TN_ROWS_CASE(1)
+        case 2: TN_ROWS_CASE(2)
+        case 4: TN_ROWS_CASE(4)
+        case 8: TN_ROWS_CASE(8)
+        default: TN_ROWS_CASE(16)
+    }
+#undef TN_ROWS_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_rows_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
+                                 int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                 cudaStream_t s) {
+    ScaleRef sr{};
+    return rows_dispatch<float2, TN_C64>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+}
+
+cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C, int lm, int ln,
+                                int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                const ScaleRef &sr, cudaStream_t s) {
+    if (dtype == TN_F16)
+        return rows_dispatch<__half2, TN_F16>((const __half2 *)A, (const __half2 *)B, (__half2 *)C,
+                                              lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return rows_dispatch<__nv_bfloat162, TN_BF16>((const __nv_bfloat162 *)A,
+                                                  (const __nv_bfloat162 *)B, (__nv_bfloat162 *)C,
+                                                  lm, ln, lk, batch, sa, sb, sc, sr, s);
+}
+
+// ---------------------------------------------------------- tiled c64 --
+// 64x64 output tile per block of 256 threads, 4x4 complex outputs per
+// thread, K in chunks of 16 staged through shared memory.  Needs M, N >= 64.
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
+    const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C, int lm,
+    int ln, int lk, int64_t sa, int64_t sb, int64_t sc) {
+    constexpr int TM = BM / 16, TN = BN / 16;
+    __shared__ float2 As[BK][BM + 1];
+    __shared__ float2 Bs[BK][BN];
+    const int N = 1 << ln, K = 1 << lk;
+    const int64_t b = blockIdx.z;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const float2 *Ab = A + b * sa + m0 * K;
+    const float2 *Bb = B + b * sb + n0;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float2 acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int i = threadIdx.x; i < BM * BK; i += 256) {
+            const int r = i / BK, kk = i % BK;
+            As[kk][r] = Ab[(int64_t)r * K + k0 + kk];
+        }
+        for (int i = threadIdx.x; i < BK * BN; i += 256) {
+            const int kk = i / BN, c = i % BN;
+            Bs[kk][c] = Bb[(int64_t)(k0 + kk) * N + c];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 a[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, bv[j].x, fmaf(-a[i].y, bv[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(a[i].x, bv[j].y, fmaf(a[i].y, bv[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+    }
+    float2 *Cb = C + b * sc + m0 * N + n0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) Cb[(int64_t)(ty * TM + i) * N + tx + 16 * j] = acc[i][j];
+}
+
+cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
+                                  int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                  int tile, cudaStream_t s) {
+    (void)tile;
+    if (lm < 6 || ln < 6 || lk < 4) return cudaErrorInvalidValue;
+    const int64_t gx = ((int64_t)1 << lm) / 64;
+    if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
+    dim3 g((unsigned)gx, (unsigned)((1 << ln) / 64), (unsigned)batch);
+    gemm_tiled_c64_kernel<64, 64, 16><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- bprep --
+// B [batch][K][N] complex-half -> B' [batch][np][2K] real (K-major rows):
+//   B'[2n  ][2k] =  Re B[k][n],  B'[2n  ][2k+1] = -Im B[k][n]
+//   B'[2n+1][2k] =  Im B[k][n],  B'[2n+1][2k+1] =  Re B[k][n]
+// rows 2N..np-1 are zero.  (Paper Sec. 3.3, Eq. 5: B padded to
+// [B_(real,-imag), B_(imag,real)], the new output mode and the shared
+// real/imag mode both innermost.)
+template <typename H>
+__global__ void bprep_kernel(const H *__restrict__ B, H *__restrict__ Bp, int lk, int ln, int np) {
+    const int K = 1 << lk, N = 1 << ln;
+    const int64_t per = (int64_t)np * 2 * K;
+    const int64_t b = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(i / (2 * K)), col = (int)(i % (2 * K));
+        const int n = row >> 1, co = row & 1, k = col >> 1, ci = col & 1;
+        H v;
+        if (n >= N) {
+            v = H(0.0f);
+        } else {
+            const H *src = B + (b * K + k) * (int64_t)N * 2 + (int64_t)n * 2;
+            const H re = src[0], im = src[1];
+            if (co == 0) v = ci == 0 ? re : __hneg(im);
+            else v = ci == 0 ? im : re;
+        }
+        Bp[b * per + i] = v;
+    }
+}
+
+cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int64_t batch, int np,
+                         cudaStream_t s) {
+    const int64_t per = (int64_t)np * 2 * ((int64_t)1 << lk);
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((per + threads - 1) / threads, 4096);
+    if (batch > 65535) return cudaErrorInvalidValue;
+    dim3 g(blocks, (unsigned)batch);
+    if (dtype == TN_F16)
+        bprep_kernel<__half><<<g, threads, 0, s>>>((const __half *)B, (__half *)Bp, lk, ln, np);
+    else
+        bprep_kernel<__nv_bfloat16><<<g, threads, 0, s>>>((const __nv_bfloat16 *)B,
+                                                          (__nv_bfloat16 *)Bp, lk, ln, np);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- slice sum --
+// amp[j] (+)= sum over batch index t in [t_lo, t_hi), ascending, of
+// F[idx(j, t)] * 2^-E (FP64; one slice added at a time).
+template <typename T, int DT>
+__global__ void slice_sum_kernel(const T *__restrict__ F, const SumOp op, double2 *amps,
+                                 int n_open, int t_lo, int t_hi, int overwrite,
+                                 const int32_t *texp) {
+    const int64_t n = (int64_t)1 << n_open;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int64_t base = 0;
+    for (int t = 0; t < n_open; ++t)
+        if ((j >> t) & 1) base |= (int64_t)1 << op.open_pos[t];
+    const int E = (DT == TN_C64 || !texp) ? 0 : texp[op.meta];
+    double2 a = overwrite ? make_double2(0.0, 0.0) : amps[j];
+    for (int t = t_lo; t < t_hi; ++t) {
+        int64_t idx = base;
+        for (int q = 0; q < op.n_batch; ++q)
+            if ((t >> q) & 1) idx |= (int64_t)1 << op.batch_pos[q];
+        double re, im;
+        if constexpr (DT == TN_C64) {
+            const float2 v = F[idx];
+            re = v.x; im = v.y;
+        } else {
+            const float2 v = LpT<DT>::to_f2(F[idx]);
+            re = ldexp((double)v.x, -E);
+            im = ldexp((double)v.y, -E);
+        }
+        a.x += re;
+        a.y += im;
+    }
+    amps[j] = a;
+}
+
+cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
+                             int t_lo, int t_hi, int overwrite, const int32_t *texp,
+                             cudaStream_t s) {
+    const int64_t n = (int64_t)1 << n_open;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    if (dtype == TN_C64)
+        slice_sum_kernel<float2, TN_C64><<<blocks, threads, 0, s>>>(
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+    else if (dtype == TN_F16)
+        slice_sum_kernel<__half2, TN_F16><<<blocks, threads, 0, s>>>(
+            (const __half2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+    else
+        slice_sum_kernel<__nv_bfloat162, TN_BF16><<<blocks, threads, 0, s>>>(
+            (const __nv_bfloat162 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- metrics --
+// FP64 reductions, deterministic: each block sums a fixed strided subset in
+// a fixed tree order into partials[block][5]; one block then adds the
+// partials in block order.  Sums: |r|^2, |b|^2, |r-b|^2, Re<b,r>, Im<b,r>.
+__device__ __forceinline__ void block_sum5(double v[5], double *sh /* [5][256] */) {
+    for (int q = 0; q < 5; ++q) sh[q * 256 + threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 5; ++q) sh[q * 256 + threadIdx.x] += sh[q * 256 + threadIdx.x + w];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) metrics_partial_kernel(const double2 *r, const double2 *b,
+                                                              int64_t n, double *partials) {
+    __shared__ double sh[5 * 256];
+    double v[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const double2 x = r[i];
+        v[0] += x.x * x.x + x.y * x.y;
+        if (b) {
+            const double2 y = b[i];
+            v[1] += y.x * y.x + y.y * y.y;
+            const double dx = x.x - y.x, dy = x.y - y.y;
+            v[2] += dx * dx + dy * dy;
+            v[3] += y.x * x.x + y.y * x.y;   // Re conj(b) r
+            v[4] += y.x * x.y - y.y * x.x;   // Im conj(b) r
+        }
+    }
+    block_sum5(v, sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) partials[(int64_t)blockIdx.x * 5 + q] = sh[q * 256];
+}
+
+__global__ void __launch_bounds__(256) metrics_final_kernel(const double *partials, int n_blocks,
+                                                            double *out5) {
+    __shared__ double sh[5 * 256];
+    double v[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n_blocks; i += 256)
+        for (int q = 0; q < 5; ++q) v[q] += partials[(int64_t)i * 5 + q];
+    block_sum5(v, sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) out5[q] = sh[q * 256];
+}
+
+cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double *d_out5,
+                           double *d_partials, int n_blocks, cudaStream_t s) {
+    metrics_partial_kernel<<<n_blocks, 256, 0, s>>>(r, b, n, d_partials);
+    metrics_final_kernel<<<1, 256, 0, s>>>(d_partials, n_blocks, d_out5);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ top-k --
+// Post-selection: k rounds; round i finds the first element, in the total
+// order (p descending, index ascending), that comes after the element
+// chosen in round i-1.  One block; p = |amp|^2 in FP64.
+__device__ __forceinline__ bool before(double p1, int64_t i1, double p2, int64_t i2) {
+    return p1 > p2 || (p1 == p2 && i1 < i2);
+}
+
+__global__ void __launch_bounds__(1024) topk_kernel(const double2 *amps, int64_t n, int k,
+                                                    int64_t *out_idx, double *out_prob) {
+    __shared__ double sp[1024];
+    __shared__ int64_t si[1024];
+    double prev_p = INFINITY;
+    int64_t prev_i = -1;
+    for (int round = 0; round < k; ++round) {
+        double bp = -1.0;
+        int64_t bi = -1;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const double2 a = amps[i];
+            // |a|^2 with each product and the sum rounded once (no FMA), so the
+            // selection matches any other FP64 evaluation of re*re + im*im
+            const double p = __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+            if (!before(p, i, prev_p, prev_i) && !(p == prev_p && i == prev_i)) {
+                if (bi < 0 || before(p, i, bp, bi)) { bp = p; bi = i; }
+            }
+        }
+        sp[threadIdx.x] = bp;
+        si[threadIdx.x] = bi;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) {
+                const double p2 = sp[threadIdx.x + w];
+                const int64_t i2 = si[threadIdx.x + w];
+                if (i2 >= 0 && (si[threadIdx.x] < 0 || before(p2, i2, sp[threadIdx.x], si[threadIdx.x]))) {
+                    sp[threadIdx.x] = p2;
+                    si[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        prev_p = sp[0];
+        prev_i = si[0];
+        if (threadIdx.x == 0) {
+            out_idx[round] = prev_i;
+            out_prob[round] = prev_p;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,
+                        cudaStream_t s) {
+    topk_kernel<<<1, 1024, 0, s>>>(amps, n, k, d_idx, d_prob);
+    return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -1,0 +1,80 @@
+// Device kernels of the contraction library: launch wrappers and the
+// parameter blocks the host fills.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace tn {
+
+// Bit-permute transpose of a tensor of 2^rank elements (all modes dim 2).
+// The host precomputes the tile decomposition (see make_perm_params).
+struct PermParams {
+    int32_t rank;
+    int32_t tile_bits;      // bits of the element index covered by one tile
+    int32_t lin;            // low input bits read contiguously
+    int32_t lout;           // low output bits written contiguously
+    int32_t n_outer;        // rank - tile_bits
+    int32_t pad_;
+    int64_t rd_hi_off[32];  // read-order high bits -> input offset
+    int32_t wr_lo_e[32];    // write-order low bits -> read-order index bits
+    int32_t wr_hi_e[32];    // write-order high bits -> read-order index bits
+    int64_t wr_hi_off[32];  // write-order high bits -> output offset
+    int8_t outer_in[kMaxRank], outer_out[kMaxRank];  // tile-id bit k -> in/out position
+};
+
+// perm: output mode i (outermost first) = input mode perm[i].
+PermParams make_perm_params(int rank, const int32_t *perm);
+
+struct ScaleRef {          // power-of-two scaling state (complex-half)
+    const float *tmax;     // per-tensor max |component| of stored values
+    int32_t *texp;         // per-tensor exponent E: true value = stored * 2^-E
+    int32_t meta_a, meta_b, meta_c;
+    int32_t fixed_exp;     // used when tmax == nullptr (tests): e = fixed_exp
+    float *out_max;        // where the epilogue records max |C| (atomicMax)
+};
+
+cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_store, char *ws,
+                             int dtype, int64_t slice_base, float *tmax, int32_t *texp,
+                             cudaStream_t s);
+cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int elem_bytes,
+                           cudaStream_t s);
+cudaError_t launch_gemm_rows_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
+                                 int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                 cudaStream_t s);
+cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
+                                  int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                  int tile, cudaStream_t s);
+cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C, int lm, int ln,
+                                int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                                const ScaleRef &sr, cudaStream_t s);
+cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int64_t batch, int np,
+                         cudaStream_t s);
+cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
+                             int t_lo, int t_hi, int overwrite, const int32_t *texp,
+                             cudaStream_t s);
+cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double *d_out5,
+                           double *d_partials, int n_blocks, cudaStream_t s);
+cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,
+                        cudaStream_t s);
+
+// tcgen05 GEMM (complex-half as real, Eq. 4-5).  Tensor maps are encoded
+// by the host (tc_gemm.cu).
+struct TcGemmDesc {
+    int dtype;             // TN_F16 | TN_BF16
+    const void *A;         // [batch_a][M][2K] real
+    const void *Bp;        // [batch_b][np][2K] real (padded B')
+    void *C;               // [batch][M][N] complex-half
+    int lm, ln, lk;
+    int64_t batch;
+    int batch_a, batch_b;  // 1: operand has the batch dim, 0: broadcast
+    int np;                // padded real columns of B' (>= 16, power of 2)
+};
+bool tc_gemm_supported(int lk, int ln);
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
+                           cudaStream_t s);
+int tc_num_sms();
+
+}  // namespace tn

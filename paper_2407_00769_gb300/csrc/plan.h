@@ -1,0 +1,56 @@
+// The plan object behind the opaque tn_plan_t.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tn {
+
+int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, int cap, Path &path,
+                  std::vector<int> &sliced, std::string &err);
+
+struct Schedule {
+    std::vector<Op> ops;                // phase 0 ops first, then phase 1
+    std::vector<LeafJob> leaf_jobs;
+    std::vector<StepRec> steps;
+    int64_t ws_bytes = 0;               // workspace bytes
+    int n_meta = 0, n_meta_inv = 0;     // meta slots; [0, n_meta_inv) invariant
+    double flops_per_pass = 0, flops_inv = 0;
+    double bytes_per_pass = 0;
+    int n_permutes = 0;
+    int n_steps_inv = 0;
+    int final_tensor = -1;
+    int kernels_per_pass = 0, kernels_inv = 0;
+};
+
+int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
+                   int batch_log2, int dtype, Schedule &out, std::string &err);
+
+}  // namespace tn
+
+struct tn_plan_s {
+    tn::Network net;
+    tn_plan_opts opts{};
+    std::vector<int> sliced;   // edge ids; slice-id bit j <-> sliced[j]
+    int batch_log2 = 0;
+    tn::Path path;
+    tn::Schedule sched;
+    std::vector<tn::cd> leaf_store;     // all leaves, full legs, complex128
+    std::vector<int64_t> leaf_offset;   // element offset of each leaf in the store
+    // device state (created on first contract)
+    bool dev_ready = false;
+    int device = -1;
+    char *d_ws = nullptr;
+    double2 *d_store = nullptr;
+    tn::LeafJob *d_jobs = nullptr;
+    float *d_tmax = nullptr;
+    int32_t *d_texp = nullptr;
+    int32_t *d_err = nullptr;
+    void *h_store_pinned = nullptr;     // pinned copy of the leaf store
+    std::vector<void *> owned;          // allocations to free
+};

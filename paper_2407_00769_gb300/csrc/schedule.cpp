@@ -1,0 +1,410 @@
+// Device schedule of a plan: for every pairwise step, the GEMM form of the
+// einsum (paper Sec. 3.3, Eq. 2-3: reduced modes = the modes both operands
+// share; result modes = the union minus those), the operand layouts and the
+// explicit permutations they need, the workspace buffers, and the kernel.
+//
+// Layout rule.  Each device tensor is stored row-major over an ordered mode
+// list.  The larger operand A must be [batch][M][K] (K innermost, so it is
+// read as a K-major GEMM operand with no copy); if its K modes are not
+// already its innermost modes it is permuted once.  The smaller operand B is
+// brought to [batch][K][N] (same K order as A), and for the tensor-core path
+// padded to B' (Eq. 5).  C is written as [batch][M][N].  When A must be
+// permuted anyway, and for B's N modes, the order is chosen so that the modes
+// the next step will contract end up innermost (fewer permutations later).
+//
+// Slices: bit j of a slice id fixes sliced edge j.  The low `batch_log2`
+// sliced edges are not fixed but carried as batch modes (hyperedges that are
+// never reduced) so 2^batch_log2 slices run in one pass; their sum is taken
+// by the final FP64 kernel.  Steps whose inputs do not depend on the looped
+// slice bits run once per contract call (phase 0).
+#include <algorithm>
+#include <map>
+#include <set>
+
+#include "plan.h"
+
+namespace tn {
+
+namespace {
+
+bool contains(const std::vector<int> &v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); }
+
+std::vector<int> sorted_copy(std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    return v;
+}
+
+// first-fit arena on byte offsets
+struct Arena {
+    std::map<int64_t, int64_t> free_;  // offset -> size
+    int64_t top = 0;
+    static int64_t align(int64_t x) { return (x + 1023) / 1024 * 1024; }
+    int64_t alloc(int64_t bytes) {
+        bytes = align(std::max<int64_t>(bytes, 1));
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const int64_t off = it->first, rem = it->second - bytes;
+                free_.erase(it);
+                if (rem > 0) free_[off + bytes] = rem;
+                return off;
+            }
+        }
+        const int64_t off = top;
+        top += bytes;
+        return off;
+    }
+    void release(int64_t off, int64_t bytes) {
+        bytes = align(std::max<int64_t>(bytes, 1));
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct BufReq {
+    int64_t bytes = 0;
+    int create = -1;     // op index of first write
+    int last = -1;       // op index of last read
+    bool pinned = false; // survives to the end of the call
+    int64_t off = -1;
+};
+
+}  // namespace
+
+int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
+                   int batch_log2, int dtype, Schedule &S, std::string &err) {
+    S = Schedule();
+    const int L = (int)net.leaves.size();
+    const int NS = (int)path.steps.size();
+    const int T = L + NS;
+    const int E = (int)net.edges.size();
+    if (L == 0) { err = "empty network"; return TN_EINVAL; }
+    if (NS != L - 1) { err = "path does not merge every tensor"; return TN_EINVAL; }
+    if (batch_log2 < 0 || batch_log2 > (int)sliced.size() || batch_log2 > 16) {
+        err = "slice_batch_log2 must be in 0..min(16, n_slice_edges)";
+        return TN_EINVAL;
+    }
+    std::vector<int> sbit(E, -1);
+    for (int j = 0; j < (int)sliced.size(); ++j) sbit[sliced[j]] = j;
+    auto looped = [&](int e) { return sbit[e] >= batch_log2; };
+    auto batched = [&](int e) { return sbit[e] >= 0 && sbit[e] < batch_log2; };
+    const int esz = dtype == TN_C64 ? 8 : 4;
+
+    // ---- leg orders, invariance, sets
+    std::vector<std::vector<int>> legs(T), sets(T);
+    std::vector<char> inv(T, 1);
+    for (int l = 0; l < L; ++l) {
+        for (int e : net.leaves[l].legs) {
+            if (looped(e)) inv[l] = 0;
+            else legs[l].push_back(e);
+        }
+        sets[l] = sorted_copy(legs[l]);
+    }
+    std::vector<int> consumer(T, -1);
+    for (int s = 0; s < NS; ++s) {
+        const int a = path.steps[s].first, b = path.steps[s].second;
+        if (a < 0 || b < 0 || a >= L + s || b >= L + s || a == b || consumer[a] >= 0 || consumer[b] >= 0) {
+            err = "malformed path";
+            return TN_EINVAL;
+        }
+        consumer[a] = consumer[b] = s;
+        std::vector<int> sh, out;
+        std::set_intersection(sets[a].begin(), sets[a].end(), sets[b].begin(), sets[b].end(),
+                              std::back_inserter(sh));
+        std::vector<int> un;
+        std::set_union(sets[a].begin(), sets[a].end(), sets[b].begin(), sets[b].end(),
+                       std::back_inserter(un));
+        for (int e : un)
+            if (!(std::binary_search(sh.begin(), sh.end(), e) && !batched(e))) out.push_back(e);
+        sets[L + s] = out;
+        inv[L + s] = inv[a] && inv[b];
+    }
+    const int final_t = NS > 0 ? T - 1 : 0;
+    S.final_tensor = final_t;
+
+    // role of each step: A = operand with more legs (ties: the first)
+    auto a_side = [&](int s) {
+        const int a = path.steps[s].first, b = path.steps[s].second;
+        return sets[b].size() > sets[a].size() ? b : a;
+    };
+    // order `v` so that modes the consumer of tensor t batches come first and
+    // modes it contracts come last (only when t is that step's large operand)
+    auto for_consumer = [&](int t, std::vector<int> v) {
+        const int c = consumer[t];
+        if (c < 0 || a_side(c) != t) return v;
+        const int p = path.steps[c].first == t ? path.steps[c].second : path.steps[c].first;
+        auto key = [&](int e) {
+            const bool sh = std::binary_search(sets[p].begin(), sets[p].end(), e);
+            if (sh && batched(e)) return 0;
+            if (sh) return 2;
+            return 1;
+        };
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return key(x) < key(y); });
+        return v;
+    };
+
+    // ---- meta slots: invariant tensors first
+    std::vector<int> meta(T, -1);
+    int nm = 0;
+    for (int t = 0; t < T; ++t)
+        if (inv[t]) meta[t] = nm++;
+    S.n_meta_inv = nm;
+    for (int t = 0; t < T; ++t)
+        if (!inv[t]) meta[t] = nm++;
+    S.n_meta = nm;
+
+    // ---- ops with symbolic buffers: buffer id t for tensor t, temps after
+    std::vector<BufReq> bufs(T);
+    auto tensor_bytes = [&](int t) { return (int64_t)esz << legs[t].size(); };
+    std::vector<Op> ph[2];
+    auto new_temp = [&](int64_t bytes) {
+        BufReq r;
+        r.bytes = bytes;
+        bufs.push_back(r);
+        return (int)bufs.size() - 1;
+    };
+    // leaf ops
+    for (int phase = 0; phase < 2; ++phase) {
+        Op op;
+        op.kind = OP_LEAF;
+        op.phase = phase;
+        op.leaf_first = (int)S.leaf_jobs.size();
+        for (int l = 0; l < L; ++l) {
+            if ((inv[l] != 0) != (phase == 0)) continue;
+            const Leaf &lf = net.leaves[l];
+            LeafJob j{};
+            const int rin = (int)lf.legs.size();
+            j.rank_in = rin;
+            j.rank_out = (int)legs[l].size();
+            int nf = 0;
+            for (int p = 0; p < rin; ++p) {
+                const int e = lf.legs[p];
+                if (looped(e)) {
+                    j.fixed_pos[nf] = rin - 1 - p;
+                    j.fixed_bit[nf] = sbit[e];
+                    ++nf;
+                }
+            }
+            j.n_fixed = nf;
+            for (int i = 0; i < j.rank_out; ++i) {
+                const int e = legs[l][j.rank_out - 1 - i];
+                const int p = (int)(std::find(lf.legs.begin(), lf.legs.end(), e) - lf.legs.begin());
+                j.keep_pos[i] = rin - 1 - p;
+            }
+            j.src = l;     // fixed up to an element offset by the caller
+            j.dst = l;     // buffer id, replaced by its offset below
+            j.meta = meta[l];
+            bufs[l].bytes = tensor_bytes(l);
+            S.leaf_jobs.push_back(j);
+        }
+        op.leaf_count = (int)S.leaf_jobs.size() - op.leaf_first;
+        if (op.leaf_count > 0) ph[phase].push_back(op);
+    }
+
+    for (int s = 0; s < NS; ++s) {
+        const int a0 = path.steps[s].first, b0 = path.steps[s].second;
+        const int ia = a_side(s), ib = ia == a0 ? b0 : a0;
+        const int c = L + s;
+        const int phase = inv[c] ? 0 : 1;
+        auto &ops = ph[phase];
+        const std::vector<int> &LA = legs[ia], &LB = legs[ib];
+        std::set<int> shared, bset, kset;
+        for (int e : LA)
+            if (contains(LB, e)) {
+                shared.insert(e);
+                if (batched(e)) bset.insert(e);
+                else kset.insert(e);
+            }
+        const int nb = (int)bset.size(), nk = (int)kset.size();
+        bool okA = true;
+        for (int i = 0; i < nb; ++i) okA = okA && bset.count(LA[i]);
+        for (int i = 0; i < nk; ++i) okA = okA && kset.count(LA[LA.size() - 1 - i]);
+        std::vector<int> bo, mo, ko, no;
+        if (okA) {
+            bo.assign(LA.begin(), LA.begin() + nb);
+            mo.assign(LA.begin() + nb, LA.end() - nk);
+            ko.assign(LA.end() - nk, LA.end());
+        } else {
+            for (int e : LA) {
+                if (bset.count(e)) bo.push_back(e);
+                else if (kset.count(e)) ko.push_back(e);
+                else mo.push_back(e);
+            }
+            mo = for_consumer(c, mo);
+        }
+        for (int e : LB)
+            if (!shared.count(e)) no.push_back(e);
+        no = for_consumer(c, no);
+
+        StepRec rec{};
+        rec.a = ia; rec.b = ib; rec.c = c;
+        rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = nk; rec.lb = nb;
+        rec.invariant = inv[c];
+
+        int64_t abuf = ia, bbuf = ib;
+        auto permute_to = [&](int src_t, const std::vector<int> &from, const std::vector<int> &to) {
+            Op op;
+            op.kind = OP_PERM;
+            op.phase = phase;
+            op.perm.rank = (int)to.size();
+            for (int i = 0; i < (int)to.size(); ++i)
+                op.perm.perm[i] = (int)(std::find(from.begin(), from.end(), to[i]) - from.begin());
+            const int tmp = new_temp((int64_t)esz << to.size());
+            op.perm.src = src_t;
+            op.perm.dst = tmp;
+            ops.push_back(op);
+            ++S.n_permutes;
+            const double bytes = 2.0 * (double)((int64_t)esz << to.size());
+            if (phase) S.bytes_per_pass += bytes;
+            return tmp;
+        };
+        if (!okA) {
+            std::vector<int> tgt(bo);
+            tgt.insert(tgt.end(), mo.begin(), mo.end());
+            tgt.insert(tgt.end(), ko.begin(), ko.end());
+            abuf = permute_to(ia, LA, tgt);
+            rec.permute_a = 1;
+        }
+        {
+            std::vector<int> tgt(bo);
+            tgt.insert(tgt.end(), ko.begin(), ko.end());
+            tgt.insert(tgt.end(), no.begin(), no.end());
+            if (tgt != LB) bbuf = permute_to(ib, LB, tgt);
+        }
+        int kernel;
+        if (dtype == TN_C64) kernel = (rec.lm >= 6 && rec.ln >= 6 && rec.lk >= 4) ? GK_C64_TILED : GK_C64_ROWS;
+        else kernel = (rec.lk >= 3 && rec.lk <= 24 && rec.ln <= 24) ? GK_LP_TC : GK_LP_ROWS;
+        rec.kernel = kernel;
+        rec.tile = 0;
+        if (kernel == GK_LP_TC) {
+            Op op;
+            op.kind = OP_BPREP;
+            op.phase = phase;
+            const int np = std::max(16, 2 << rec.ln);
+            op.bprep.src = bbuf;
+            op.bprep.lk = rec.lk;
+            op.bprep.ln = rec.ln;
+            op.bprep.lb = rec.lb;
+            op.bprep.np = np;
+            op.bprep.step = s;
+            const int64_t bpbytes = ((int64_t)np * (2LL << rec.lk) * 2) << rec.lb;
+            const int tmp = new_temp(bpbytes);
+            op.bprep.dst = tmp;
+            ops.push_back(op);
+            if (phase) S.bytes_per_pass += (double)(((int64_t)esz << (rec.lk + rec.ln + rec.lb)) + bpbytes);
+            bbuf = tmp;
+        }
+        legs[c] = bo;
+        legs[c].insert(legs[c].end(), mo.begin(), mo.end());
+        legs[c].insert(legs[c].end(), no.begin(), no.end());
+        bufs[c].bytes = tensor_bytes(c);
+        Op op;
+        op.kind = OP_GEMM;
+        op.phase = phase;
+        op.gemm.a = abuf;
+        op.gemm.b = bbuf;
+        op.gemm.c = c;
+        op.gemm.lm = rec.lm; op.gemm.ln = rec.ln; op.gemm.lk = rec.lk; op.gemm.lb = rec.lb;
+        op.gemm.a_batched = rec.lb > 0;
+        op.gemm.b_batched = rec.lb > 0;
+        op.gemm.meta_a = meta[ia]; op.gemm.meta_b = meta[ib]; op.gemm.meta_c = meta[c];
+        op.gemm.step = s;
+        op.gemm.kernel = kernel;
+        op.gemm.tile = 0;
+        ops.push_back(op);
+        const double fl = 8.0 * std::ldexp(1.0, rec.lm + rec.ln + rec.lk + rec.lb);
+        const double by = (double)(((int64_t)esz << (rec.lm + rec.lk + rec.lb)) +
+                                   ((int64_t)esz << (rec.lk + rec.ln + rec.lb)) +
+                                   ((int64_t)esz << (rec.lm + rec.ln + rec.lb)));
+        if (phase) { S.flops_per_pass += fl; S.bytes_per_pass += by; }
+        else { S.flops_inv += fl; ++S.n_steps_inv; }
+        S.steps.push_back(rec);
+    }
+    // final sum
+    {
+        Op op;
+        op.kind = OP_SUM;
+        op.phase = 1;
+        const auto &F = legs[final_t];
+        const int r = (int)F.size();
+        op.sum.src = final_t;
+        op.sum.rank = r;
+        op.sum.meta = meta[final_t];
+        for (int p = 0; p < r; ++p) {
+            const Edge &ed = net.edges[F[p]];
+            if (ed.open_t >= 0) op.sum.open_pos[ed.open_t] = r - 1 - p;
+            else if (batched(F[p])) op.sum.batch_pos[sbit[F[p]]] = r - 1 - p;
+            else { err = "final tensor has a non-output mode"; return TN_EINVAL; }
+        }
+        if (r != net.n_open + batch_log2) { err = "final tensor misses output modes"; return TN_EINVAL; }
+        op.sum.n_batch = batch_log2;
+        ph[1].push_back(op);
+    }
+
+    // ---- lifetimes over the op sequence (phase 0 then phase 1)
+    S.ops = ph[0];
+    S.ops.insert(S.ops.end(), ph[1].begin(), ph[1].end());
+    const int n_ops = (int)S.ops.size();
+    auto touch_create = [&](int64_t id, int i) {
+        if (bufs[id].create < 0) bufs[id].create = i;
+    };
+    auto touch_read = [&](int64_t id, int i) {
+        bufs[id].last = std::max(bufs[id].last, i);
+        if (S.ops[i].phase == 1 && bufs[id].create >= 0 && S.ops[bufs[id].create].phase == 0)
+            bufs[id].pinned = true;
+    };
+    for (int i = 0; i < n_ops; ++i) {
+        const Op &op = S.ops[i];
+        switch (op.kind) {
+            case OP_LEAF:
+                for (int k = 0; k < op.leaf_count; ++k) touch_create(S.leaf_jobs[op.leaf_first + k].dst, i);
+                break;
+            case OP_PERM: touch_read(op.perm.src, i); touch_create(op.perm.dst, i); break;
+            case OP_BPREP: touch_read(op.bprep.src, i); touch_create(op.bprep.dst, i); break;
+            case OP_GEMM:
+                touch_read(op.gemm.a, i); touch_read(op.gemm.b, i); touch_create(op.gemm.c, i);
+                break;
+            case OP_SUM: touch_read(op.sum.src, i); break;
+        }
+    }
+    Arena arena;
+    std::vector<std::vector<int>> created_at(n_ops), freed_at(n_ops);
+    for (int id = 0; id < (int)bufs.size(); ++id) {
+        if (bufs[id].create < 0) continue;
+        created_at[bufs[id].create].push_back(id);
+        if (!bufs[id].pinned) freed_at[std::max(bufs[id].last, bufs[id].create)].push_back(id);
+    }
+    for (int i = 0; i < n_ops; ++i) {
+        for (int id : created_at[i]) bufs[id].off = arena.alloc(bufs[id].bytes);
+        for (int id : freed_at[i]) arena.release(bufs[id].off, bufs[id].bytes);
+    }
+    S.ws_bytes = std::max<int64_t>(arena.top, 1024);
+    auto off = [&](int64_t id) { return bufs[id].off; };
+    for (LeafJob &j : S.leaf_jobs) j.dst = off(j.dst);
+    for (Op &op : S.ops) {
+        switch (op.kind) {
+            case OP_PERM: op.perm.src = off(op.perm.src); op.perm.dst = off(op.perm.dst); break;
+            case OP_BPREP: op.bprep.src = off(op.bprep.src); op.bprep.dst = off(op.bprep.dst); break;
+            case OP_GEMM:
+                op.gemm.a = off(op.gemm.a); op.gemm.b = off(op.gemm.b); op.gemm.c = off(op.gemm.c);
+                break;
+            case OP_SUM: op.sum.src = off(op.sum.src); break;
+            default: break;
+        }
+        if (op.phase == 1) ++S.kernels_per_pass;
+        else ++S.kernels_inv;
+    }
+    return TN_OK;
+}
+
+}  // namespace tn

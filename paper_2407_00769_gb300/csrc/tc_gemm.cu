@@ -1,0 +1,520 @@
+// Complex-half contraction step on the 5th-generation tensor cores.
+//
+// Paper Sec. 3.3 (Eq. 4-5): the large operand A keeps its interleaved
+// real/imag mode as an extra reduced mode, so A[M][K] complex is read as a
+// real [M][2K] matrix with no copy; the small operand is padded to
+// B'[(n,co)][(k,ci)] = [[Re, -Im], [Im, Re]] (bprep), and ONE real GEMM
+// C'[M][2N] = A'[M][2K] B'^T gives C[M][N] complex, interleaved, exactly the
+// four real products of the complex multiply (8 M N K real flops).
+//
+// Blackwell mapping (sm_103a):
+//   * warp 0      : TMA producer -- cp.async.bulk.tensor tiles of A' and B'
+//                   into a STAGES-deep shared-memory ring (K-major, swizzled),
+//                   completion counted on mbarriers;
+//   * warp 1      : allocates TMEM and issues tcgen05.mma kind::f16
+//                   (M=128, N=BN, K=16 per instruction, FP32 accumulate in
+//                   TMEM), double-buffered accumulators, tcgen05.commit frees
+//                   ring stages and publishes finished tiles;
+//   * warps 2..5  : epilogue -- tcgen05.ld rows out of TMEM, exact 2^e scale,
+//                   round to FP16/BF16, record max |C| for the next step's
+//                   exponent, store interleaved complex-half rows.
+// Persistent: one CTA per SM walks tiles (batch, m-tile, n-tile).
+// Every mbarrier wait is bounded by wall time (globaltimer); on expiry the
+// CTA records an error, drains, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace tn {
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: returns false (and raises the CTA abort flag) on timeout or
+// when another role already aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// K-major shared-memory matrix descriptor (tcgen05): start address, leading
+// byte offset (unused for swizzled K-major), stride byte offset = 8 rows,
+// descriptor version 1, swizzle mode.
+template <int BK>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    constexpr uint32_t row_bytes = BK * 2;             // one swizzle row
+    constexpr uint32_t sbo = 8 * row_bytes;            // 8-row core-matrix group
+    constexpr uint64_t layout = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // 128B / 64B / 32B
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                            // LBO (16 B, ignored)
+    d |= (uint64_t)(sbo >> 4) << 32;
+    d |= (uint64_t)1 << 46;                            // version
+    d |= layout << 61;
+    return d;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int scale_exp_tc(float maxa, float maxb, int lk) {
+    const float t = 2.0f * maxa * maxb;
+    if (!(t > 0.0f) || !isfinite(t)) return 0;
+    int x;
+    const float f = frexpf(t, &x);
+    const int c = (f == 0.5f) ? x - 1 : x;
+    int e = 14 - lk - c;
+    return max(-120, min(120, e));
+}
+
+struct TcArgs {
+    void *C;
+    int64_t M;
+    int64_t n_mt;          // m tiles per batch
+    int n_nt;              // n tiles
+    int64_t batch;
+    int64_t tiles;
+    int N;                 // complex columns
+    int lk;
+    int nk;                // K chunks
+    int dtype;
+    int batch_a, batch_b;
+    ScaleRef sr;
+    int32_t *err;
+};
+
+template <int BN, int BK, int STAGES>
+struct TcSmem {
+    static constexpr int a_bytes = 128 * BK * 2;
+    static constexpr int b_bytes = BN * BK * 2;
+    static constexpr int stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
+    static constexpr int ring = STAGES * stage_bytes;
+    static constexpr int bars = (2 * STAGES + 4) * 8;
+    static constexpr int total = 1024 + ring + bars + 16;   // + alignment slack
+};
+
+template <int BN, int BK, int STAGES>
+__global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB,
+                                                         const TcArgs args) {
+    using S = TcSmem<BN, BK, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + S::ring);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint64_t *acce = accf + 2;
+    volatile uint32_t *tmem_slot = (volatile uint32_t *)(acce + 2);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr uint32_t tmem_cols = (2 * BN < 32) ? 32 : 2 * BN;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int8_t armed[STAGES];   // phase parity of the last load issued per stage
+            for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            for (int64_t t = blockIdx.x; t < args.tiles && ok; t += gridDim.x) {
+                const int nt = (int)(t % args.n_nt);
+                const int64_t rest = t / args.n_nt;
+                const int64_t mt = rest % args.n_mt;
+                const int64_t b = rest / args.n_mt;
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
+                    uint8_t *sa = smem + stage * S::stage_bytes;
+                    uint8_t *sb = sa + S::a_bytes;
+                    mbar_expect_tx(&full[stage], S::a_bytes + S::b_bytes);
+                    tma_load_3d(sa, &tmA, &full[stage], kc * BK, (int)(mt * 128),
+                                args.batch_a ? (int)b : 0);
+                    tma_load_3d(sb, &tmB, &full[stage], kc * BK, nt * BN, args.batch_b ? (int)b : 0);
+                    armed[stage] = (int8_t)phase;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (!ok) {
+                // drain: only the last STAGES loads can still be in flight;
+                // wait (bounded) until each has landed before shared memory goes
+                for (int s = 0; s < STAGES; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&full[s], (uint32_t)armed[s]) &&
+                           globaltimer() - t0 < kWaitLimitNs / 4) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------- MMA issue --
+        if (lane == 0) {
+            uint32_t idesc = 0;
+            idesc |= 1u << 4;                                  // D = F32
+            const uint32_t fmt = args.dtype == TN_BF16 ? 1u : 0u;
+            idesc |= fmt << 7;                                 // A format
+            idesc |= fmt << 10;                                // B format
+            idesc |= (uint32_t)(BN >> 3) << 17;                // N
+            idesc |= (uint32_t)(128 >> 4) << 24;               // M
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < args.tiles && ok; t += gridDim.x) {
+                if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
+                    const uint32_t b_addr = a_addr + S::a_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = smem_desc<BK>(a_addr + kk * 32);
+                        const uint64_t bd = smem_desc<BK>(b_addr + kk * 32);
+                        tc_mma(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc_commit(&empty[stage]);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                tc_commit(&accf[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue --
+        const int q = warp & 3;                 // TMEM lane quadrant of this warp
+        const int row = q * 32 + lane;
+        int e;
+        if (args.sr.tmax)
+            e = scale_exp_tc(args.sr.tmax[args.sr.meta_a], args.sr.tmax[args.sr.meta_b], args.lk);
+        else
+            e = args.sr.fixed_exp;
+        if (args.sr.texp && blockIdx.x == 0 && threadIdx.x == 64)
+            args.sr.texp[args.sr.meta_c] = args.sr.texp[args.sr.meta_a] + args.sr.texp[args.sr.meta_b] + e;
+        const float sc = __int_as_float((127 + e) << 23);
+        float mx = 0.f;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t t = blockIdx.x; t < args.tiles; t += gridDim.x) {
+            const int nt = (int)(t % args.n_nt);
+            const int64_t rest = t / args.n_nt;
+            const int64_t mt = rest % args.n_mt;
+            const int64_t b = rest / args.n_mt;
+            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
+            tc_fence_after();
+            const int64_t m = mt * 128 + row;
+            const int col0 = nt * BN;                          // real column of this tile
+            const int valid_real = min(BN, 2 * args.N - col0);  // warp-uniform
+            for (int c = 0; c < valid_real; c += 16) {
+                uint32_t r[16];
+                tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                tmem_wait_ld();
+                if (m < args.M) {
+                    const int nreal = min(16, valid_real - c);   // 2, 4, 8 or 16
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float re = __uint_as_float(r[2 * j]) * sc;
+                        const float im = __uint_as_float(r[2 * j + 1]) * sc;
+                        float2 back;
+                        if (args.dtype == TN_BF16) {
+                            __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                            back = __bfloat1622float2(h);
+                        } else {
+                            __half2 h = __floats2half2_rn(re, im);
+                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                            back = __half22float2(h);
+                        }
+                        if (2 * j < nreal) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
+                    }
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) +
+                                    (b * args.M + m) * (int64_t)args.N + (col0 + c) / 2;
+                    if (nreal == 16) {
+                        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        reinterpret_cast<uint4 *>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    } else if (nreal == 8) {
+                        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    } else if (nreal == 4) {
+                        reinterpret_cast<uint2 *>(dst)[0] = make_uint2(packed[0], packed[1]);
+                    } else {
+                        dst[0] = packed[0];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[acc]);
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        if (lane == 0 && args.sr.out_max)
+            atomicMax(reinterpret_cast<int *>(args.sr.out_max), __float_as_int(mx));
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0 && args.err) atomicExch(args.err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------ host side --
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    });
+    return fn;
+}
+
+bool encode_3d(CUtensorMap *m, int dtype, const void *base, uint64_t inner, uint64_t rows,
+               uint64_t depth, uint32_t box_inner, uint32_t box_rows) {
+    EncodeFn enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {inner, rows, depth};
+    const cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+    const cuuint32_t box[3] = {box_inner, box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                    : CU_TENSOR_MAP_SWIZZLE_32B;
+    const CUtensorMapDataType dt =
+        dtype == TN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int BK>
+struct TcCfg {
+    static constexpr int stage_bytes = (128 * BK * 2 + BN * BK * 2 + 1023) / 1024 * 1024;
+    static constexpr int stages0 = (196 * 1024) / stage_bytes;
+    static constexpr int STAGES = stages0 > 12 ? 12 : (stages0 < 2 ? 2 : stages0);
+};
+
+template <int BN, int BK>
+cudaError_t run_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, cudaStream_t s) {
+    constexpr int ST = TcCfg<BN, BK>::STAGES;
+    using S = TcSmem<BN, BK, ST>;
+    auto kern = gemm_tc_kernel<BN, BK, ST>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::total);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
+    kern<<<(unsigned)grid, 192, S::total, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t run_tc_bn(int bn, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
+                      cudaStream_t s) {
+    switch (bn) {
+        case 16: return run_tc<16, BK>(ma, mb, a, s);
+        case 32: return run_tc<32, BK>(ma, mb, a, s);
+        case 64: return run_tc<64, BK>(ma, mb, a, s);
+        case 128: return run_tc<128, BK>(ma, mb, a, s);
+        case 256: return run_tc<256, BK>(ma, mb, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int tc_num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
+
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
+    if (!tc_gemm_supported(d.lk, d.ln)) return cudaErrorInvalidValue;
+    const int kreal = 2 << d.lk;                 // 2K
+    const int bk = kreal >= 64 ? 64 : kreal;     // 16, 32 or 64
+    const int bn = d.np >= 256 ? 256 : d.np;     // 16 .. 256
+    const int64_t M = (int64_t)1 << d.lm;
+    CUtensorMap ma, mb;
+    if (!encode_3d(&ma, d.dtype, d.A, (uint64_t)kreal, (uint64_t)M,
+                   (uint64_t)(d.batch_a ? d.batch : 1), bk, 128))
+        return cudaErrorInvalidValue;
+    if (!encode_3d(&mb, d.dtype, d.Bp, (uint64_t)kreal, (uint64_t)d.np,
+                   (uint64_t)(d.batch_b ? d.batch : 1), bk, bn))
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    a.C = d.C;
+    a.M = M;
+    a.n_mt = (M + 127) / 128;
+    a.n_nt = d.np / bn;
+    a.batch = d.batch;
+    a.tiles = a.n_mt * a.n_nt * d.batch;
+    a.N = 1 << d.ln;
+    a.lk = d.lk;
+    a.nk = kreal / bk;
+    a.dtype = d.dtype;
+    a.batch_a = d.batch_a;
+    a.batch_b = d.batch_b;
+    a.sr = sr;
+    a.err = d_err;
+    switch (bk) {
+        case 16: return run_tc_bn<16>(bn, ma, mb, a, s);
+        case 32: return run_tc_bn<32>(bn, ma, mb, a, s);
+        default: return run_tc_bn<64>(bn, ma, mb, a, s);
+    }
+}
+
+}  // namespace tn

@@ -1,0 +1,170 @@
+"""End-to-end parity of tn_contract / tn_sample / tn_metrics against the FP64
+oracle (state vector; per-slice values from wire projectors).
+
+Tolerances: complex64 path rel-L2 <= 1e-5; complex-half (FP16) path
+rel-L2 <= 5e-3 and fidelity >= 0.999; BF16 (8 mantissa bits) is measured
+against a looser 3e-2 bound and reported."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
+import rqcgen  # noqa: E402
+import paper_2407_00769_gb300 as tn  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+TOL = {tn.C64: 1e-5, tn.F16: 5e-3, tn.BF16: 3e-2}
+
+
+def check(got, want, dtype):
+    got = got.cpu().numpy() if hasattr(got, "cpu") else got
+    e = oracle.rel_l2(got, want)
+    f = oracle.fidelity(want, got)
+    assert e <= TOL[dtype], (tn.DTYPE_NAMES[dtype], e)
+    if dtype == tn.F16:
+        assert f >= 0.999, f
+    return e, f
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16, tn.BF16])
+def test_grid_12q_all_amplitudes(dtype):
+    c, q = rqcgen.grid_12q()
+    want = oracle.amplitudes(c, q)
+    p = tn.Plan(c, q, dtype=dtype)
+    check(p.contract(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+@pytest.mark.parametrize("rows,cols,cycles,seed,n_open", [(2, 2, 3, 1, 4), (1, 2, 2, 3, 1),
+                                                          (3, 3, 6, 2, 0), (4, 4, 10, 7, 6)])
+def test_small_and_degenerate_circuits(dtype, rows, cols, cycles, seed, n_open):
+    c, q = rqcgen.small_grid(rows, cols, cycles, seed=seed, n_open=n_open)
+    want = oracle.amplitudes(c, q)
+    p = tn.Plan(c, q, dtype=dtype)
+    check(p.contract(), want, dtype)
+
+
+def test_qubit_without_two_qubit_gates():
+    # a qubit that no coupler touches becomes its own rank-1 / rank-0 leaf
+    c, _ = rqcgen.small_grid(2, 3, 5, seed=4, n_open=0)
+    keep = (c.q1 < 0) | ~((c.q0 == 5) | (c.q1 == 5))
+    cc = rqcgen.Circuit(c.n_qubits, c.q0[keep], c.q1[keep], c.mats[keep])
+    for opens in ([5], [0, 5], [1]):
+        q = rqcgen.make_query(cc.n_qubits, opens, seed=3)
+        want = oracle.amplitudes(cc, q)
+        check(tn.Plan(cc, q, dtype=tn.C64).contract(), want, tn.C64)
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+def test_per_slice_values_match_projected_oracle(dtype):
+    c, q = rqcgen.small_grid(4, 4, 10, seed=7, n_open=6)
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=3, trials=2)
+    edges = p.sliced_edges()
+    full = oracle.amplitudes(c, q)
+    total = None
+    for s in range(8):
+        got = p.contract(s, 1).cpu().numpy()
+        want = oracle.amplitudes(c, q, oracle.slice_projectors(edges, s))
+        if np.linalg.norm(want) > 1e-3 * np.linalg.norm(full):
+            assert oracle.rel_l2(got, want) <= TOL[dtype]
+        total = got if total is None else total + got
+    check(total, full, dtype)
+    check(p.contract(), full, dtype)
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+def test_slice_batching_matches(dtype):
+    c, q = rqcgen.small_grid(4, 5, 12, seed=8, n_open=6)
+    full = oracle.amplitudes(c, q)
+    ref = tn.Plan(c, q, dtype=dtype, n_slice_edges=4).contract()
+    for b in (1, 2, 4):
+        p = tn.Plan(c, q, dtype=dtype, n_slice_edges=4, slice_batch_log2=b)
+        got = p.contract()
+        check(got, full, dtype)
+        # partial, unaligned range: slices 3..12
+        part = p.contract(3, 10).cpu().numpy()
+        edges = p.sliced_edges()
+        want = oracle.sliced_amplitudes(c, q, edges, range(3, 13))
+        assert oracle.rel_l2(part, want) <= TOL[dtype]
+    assert oracle.rel_l2(got.cpu().numpy(), ref.cpu().numpy()) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+def test_split_ranges_bit_identical(dtype):
+    c, q = rqcgen.small_grid(4, 4, 10, seed=9, n_open=5)
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=4)
+    whole = p.contract(0, 16).cpu().numpy()
+    out = p.contract(0, 5)
+    p.contract(5, 7, out=out, accumulate=True)
+    p.contract(12, 4, out=out, accumulate=True)
+    assert np.array_equal(out.cpu().numpy(), whole)
+    again = p.contract(0, 16).cpu().numpy()
+    assert np.array_equal(again, whole)   # deterministic re-run
+
+
+def test_contract_host_matches_device():
+    c, q = rqcgen.small_grid(4, 4, 10, seed=9, n_open=5)
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=2)
+    d = p.contract().cpu().numpy()
+    h, rep = p.contract_host(report=True)
+    assert np.array_equal(h, d)
+    assert rep["slices"] == 4 and rep["kernels"] > 0
+
+
+def test_sample_and_metrics_match_oracle():
+    c, q = rqcgen.small_grid(4, 5, 14, seed=21, n_open=10)
+    want = oracle.amplitudes(c, q)
+    p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=2)
+    amps = p.contract()
+    for k in (1, 5, 64):
+        idx, prob = tn.sample(amps, k)
+        widx, wprob = oracle.topk(amps.cpu().numpy(), k)
+        assert np.array_equal(idx, widx)
+        assert np.array_equal(prob, wprob)
+        oidx, _ = oracle.topk(want, k)
+        assert set(idx[:1]) == set(oidx[:1])
+    ref = torch.from_numpy(want).cuda()
+    m = tn.metrics(amps, ref, n_qubits=c.n_qubits)
+    got = amps.cpu().numpy()
+    assert abs(m["norm2"] - np.vdot(got, got).real) <= 1e-12 * m["norm2"]
+    assert abs(m["rel_l2"] - oracle.rel_l2(got, want)) <= 1e-9
+    assert abs(m["fidelity"] - oracle.fidelity(want, got)) <= 1e-12
+    x = oracle.linear_xeb(np.abs(got) ** 2, c.n_qubits)
+    assert abs(m["xeb"] - x) <= 1e-9 * max(1, abs(x))
+
+
+def test_sample_ties_go_to_lower_index():
+    a = np.zeros(16, dtype=np.complex128)
+    a[[3, 7, 9]] = [1j, -1, 1]
+    a[12] = 0.5
+    idx, prob = tn.sample(torch.from_numpy(a).cuda(), 4)
+    assert idx.tolist() == [3, 7, 9, 12] and prob.tolist() == [1, 1, 1, 0.25]
+
+
+def _golden(name):
+    path = os.path.join(GOLD, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated (tests/golden/make_golden.py)")
+    vals = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        _, re_, im_ = line.split()
+        vals.append(complex(float(re_), float(im_)))
+    return np.array(vals)
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16, tn.BF16])
+def test_grid_30q_sliced_full_size(dtype):
+    # the 30-qubit, 14-cycle workload: 8 sliced edges (256 slices), 1024
+    # correlated amplitudes, against the FP64 state vector on 2^30 amplitudes
+    want = _golden("grid5x6_14c_amps.txt")
+    c, q = rqcgen.grid_30q()
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=8, trials=4)
+    got = p.contract()
+    e, f = check(got, want, dtype)
+    print(f"grid30 {tn.DTYPE_NAMES[dtype]}: rel_l2={e:.3e} fidelity={f:.6f}")

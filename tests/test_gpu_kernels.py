@@ -1,0 +1,206 @@
+"""Single-kernel parity through the C ABI: bit-exact permutations, complex
+GEMMs (complex64 SIMT, complex-half rows, tcgen05 tensor cores) against FP64
+products of the same (rounded) inputs, and the paper's worked complex-half
+example (Sec. 3.3) through the tensor-core path."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import paper_2407_00769_gb300 as tn  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ------------------------------------------------------------------ permute
+@pytest.mark.parametrize("elem", [4, 8])
+def test_permute_all_small_ranks(elem):
+    dt = np.int32 if elem == 4 else np.int64
+    for r in range(0, 6):
+        x = np.arange(1 << r, dtype=dt) * 7 + 3
+        xd = dev(x)
+        for perm in itertools.permutations(range(r)):
+            out = tn.permute(xd, list(perm), elem_bytes=elem)
+            want = np.transpose(x.reshape([2] * r), perm).reshape(-1) if r else x
+            assert np.array_equal(out.cpu().numpy(), want), (r, perm)
+
+
+@pytest.mark.parametrize("r", [6, 9, 11, 12, 16, 20])
+def test_permute_random(r):
+    rng = np.random.default_rng(r)
+    for elem, dt in ((4, np.int32), (8, np.int64)):
+        x = rng.integers(-2**31, 2**31 - 1, size=1 << r).astype(dt)
+        xd = dev(x)
+        for _ in range(4):
+            perm = list(rng.permutation(r))
+            out = tn.permute(xd, perm, elem_bytes=elem)
+            want = np.transpose(x.reshape([2] * r), perm).reshape(-1)
+            assert np.array_equal(out.cpu().numpy(), want), perm
+
+
+def test_permute_large_reversal():
+    r = 24
+    x = torch.arange(1 << r, dtype=torch.int32, device="cuda")
+    perm = list(range(r))[::-1]
+    out = tn.permute(x, perm).cpu().numpy()
+    idx = np.arange(1 << r, dtype=np.int64)
+    rev = np.zeros_like(idx)
+    for b in range(r):
+        rev |= ((idx >> b) & 1) << (r - 1 - b)
+    assert np.array_equal(out, rev.astype(np.int32))
+
+
+# --------------------------------------------------------------------- gemm
+def crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def to_c64(z):
+    return z.astype(np.complex64)
+
+
+def half_pairs(z, np_dtype=np.float16):
+    r = np.empty(z.shape + (2,), dtype=np_dtype)
+    r[..., 0] = z.real
+    r[..., 1] = z.imag
+    return r
+
+
+def from_pairs(a):
+    a = a.astype(np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def bf16_round(z):
+    t = torch.from_numpy(np.stack([z.real, z.imag], -1).astype(np.float32)).to(torch.bfloat16)
+    return t
+
+
+def ref_gemm(a, b):
+    return np.matmul(a.astype(np.complex128), b.astype(np.complex128))
+
+
+def bound(a, b, K):
+    return np.matmul(np.abs(a), np.abs(b))
+
+
+C64_SHAPES = [(1, 1, 1), (3, 2, 4), (128, 4, 4), (1000, 8, 16), (4096, 2, 1), (64, 64, 16),
+              (256, 128, 64), (128, 16, 256), (2, 256, 2)]
+
+
+@pytest.mark.parametrize("M,N,K", C64_SHAPES)
+@pytest.mark.parametrize("batch", [1, 3])
+def test_gemm_c64(M, N, K, batch):
+    M = 1 << int(np.ceil(np.log2(M)))
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    a = to_c64(crandn(rng, batch, M, K))
+    b = to_c64(crandn(rng, batch, K, N))
+    c = torch.zeros(batch, M, N, dtype=torch.complex64, device="cuda")
+    for kernel in (-1, 0, 1):
+        if kernel == 1 and not (M >= 64 and N >= 64 and K >= 16):
+            continue
+        tn.gemm(tn.C64, dev(a), dev(b), c, M, N, K, batch=batch, batch_a=True, batch_b=True,
+                kernel=kernel)
+        got = c.cpu().numpy()
+        want = ref_gemm(a, b)
+        err = np.abs(got - want)
+        assert np.all(err <= 1e-6 * bound(a, b, K) * max(1, np.sqrt(K)) + 1e-30), kernel
+
+
+def test_gemm_c64_broadcast_b():
+    rng = np.random.default_rng(5)
+    M, N, K, batch = 256, 8, 8, 4
+    a = to_c64(crandn(rng, batch, M, K))
+    b = to_c64(crandn(rng, K, N))
+    c = torch.zeros(batch, M, N, dtype=torch.complex64, device="cuda")
+    tn.gemm(tn.C64, dev(a), dev(b), c, M, N, K, batch=batch, batch_a=True, batch_b=False)
+    assert np.allclose(c.cpu().numpy(), ref_gemm(a, b[None]), rtol=1e-5, atol=1e-5)
+
+
+LP_SHAPES = [(1, 1, 8), (2, 4, 8), (128, 8, 8), (256, 16, 16), (4096, 4, 32), (1024, 128, 64),
+             (512, 256, 512), (256, 1, 1024), (64, 64, 8), (8192, 2, 8), (256, 512, 64)]
+
+
+def _lp_case(dtype, M, N, K, batch, kernel, ba=True, bb=True, seed=0):
+    rng = np.random.default_rng(seed + M * 13 + N * 5 + K)
+    a = crandn(rng, batch if ba else 1, M, K)
+    b = crandn(rng, batch if bb else 1, K, N) / np.sqrt(K)
+    if dtype == tn.F16:
+        ah, bh = half_pairs(a), half_pairs(b)
+        ad, bd = dev(ah), dev(bh)
+        ar, br = from_pairs(ah), from_pairs(bh)
+        unit = 2.0 ** -11
+    else:
+        ad, bd = bf16_round(a).cuda(), bf16_round(b).cuda()
+        ar = ad.float().cpu().numpy().astype(np.float64)
+        ar = ar[..., 0] + 1j * ar[..., 1]
+        br = bd.float().cpu().numpy().astype(np.float64)
+        br = br[..., 0] + 1j * br[..., 1]
+        unit = 2.0 ** -8
+    c = torch.zeros(batch, M, N, 2, dtype=torch.float16 if dtype == tn.F16 else torch.bfloat16,
+                    device="cuda")
+    mx = torch.zeros(1, dtype=torch.float32, device="cuda")
+    tn.gemm(dtype, ad, bd, c, M, N, K, batch=batch, batch_a=ba, batch_b=bb, scale_exp=3,
+            kernel=kernel, out_max=mx)
+    got = c.float().cpu().numpy().astype(np.float64)
+    got = got[..., 0] + 1j * got[..., 1]
+    want = ref_gemm(np.broadcast_to(ar, (batch, M, K)), np.broadcast_to(br, (batch, K, N))) * 8.0
+    mag = 8.0 * np.matmul(np.abs(np.broadcast_to(ar, (batch, M, K))), np.abs(np.broadcast_to(br, (batch, K, N))))
+    tol = 2 * unit * np.abs(want) + 1e-6 * mag + 1e-30
+    assert np.all(np.abs(got - want) <= tol), (np.max(np.abs(got - want) / (np.abs(want) + 1e-9)))
+    gmax = max(np.abs(got.real).max(), np.abs(got.imag).max())
+    assert abs(mx.item() - gmax) <= 1e-6 * gmax
+
+
+@pytest.mark.parametrize("M,N,K", LP_SHAPES)
+def test_gemm_f16_tensor_cores(M, N, K):
+    _lp_case(tn.F16, M, N, K, 1, 3)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 8, 8), (1024, 128, 64), (512, 256, 512)])
+def test_gemm_bf16_tensor_cores(M, N, K):
+    _lp_case(tn.BF16, M, N, K, 1, 3)
+
+
+@pytest.mark.parametrize("ba,bb", [(True, True), (True, False), (False, True)])
+def test_gemm_f16_tensor_cores_batched(ba, bb):
+    _lp_case(tn.F16, 256, 16, 32, 3, 3, ba, bb)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 4, 2), (300, 16, 4), (1024, 64, 1), (256, 8, 64)])
+def test_gemm_f16_rows(M, N, K):
+    M = 1 << int(np.ceil(np.log2(M)))
+    _lp_case(tn.F16, M, N, K, 2, 2)
+
+
+def _read_example():
+    vals = {}
+    for line in open(os.path.join(GOLD, "complex_half_example.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = [float(x) for x in v.split()]
+    return vals
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_paper_worked_example(kernel):
+    # a1a2,b1 -> a1b1 with A = [(1+2i), (3+4i)], B = [(5+6i)]: the paper's
+    # integer example, exact in FP16; embedded in a K = 8 step (zeros) so the
+    # tensor-core path (K >= 8) runs it too.
+    g = _read_example()
+    M, N, K = 2, 1, 8
+    A = np.zeros((M, K, 2), dtype=np.float16)
+    A[0, 0] = g["A_complex"][0:2]
+    A[1, 0] = g["A_complex"][2:4]
+    B = np.zeros((K, N, 2), dtype=np.float16)
+    B[0, 0] = g["B_complex"]
+    C = torch.zeros(M, N, 2, dtype=torch.float16, device="cuda")
+    tn.gemm(tn.F16, dev(A), dev(B), C, M, N, K, scale_exp=0, kernel=kernel)
+    assert C.float().cpu().numpy().reshape(-1).tolist() == g["C_complex"]

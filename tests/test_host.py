@@ -1,0 +1,137 @@
+"""Host-side checks of the library that need no GPU: it loads, exports every
+symbol include/tn.h declares, and its planner obeys the paper's GEMM
+condition (Sec. 3.3, Eq. 2-3) and the slicing/memory invariants."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import rqcgen
+import paper_2407_00769_gb300 as tn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "tn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = tn.lib()
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) == set(tn.EXPORTED)
+
+
+def test_strerror_codes():
+    L = tn.lib()
+    assert L.tn_strerror(0) == b"ok"
+    assert L.tn_strerror(4) == b"device wait timed out"
+
+
+def _plan(circuit, query, **kw):
+    kw.setdefault("torch_allocator", False)
+    return tn.Plan(circuit, query, **kw)
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+@pytest.mark.parametrize("slices,batch", [(0, 0), (3, 0), (3, 2)])
+def test_plan_steps_are_pure_gemms(dtype, slices, batch):
+    # Eq. 2-3: every step's result has exactly the modes of A and B minus the
+    # reduced ones; the sizes each tensor is produced with and consumed with
+    # must agree, and the last tensor holds the open modes (+ batch modes).
+    c, q = rqcgen.small_grid(4, 4, 10, seed=3, n_open=5)
+    p = _plan(c, q, dtype=dtype, n_slice_edges=slices, slice_batch_log2=batch)
+    info = p.info()
+    steps = p.steps()
+    assert info["n_steps"] == info["n_leaves"] - 1 == len(steps)
+    size = {}
+    for s in steps:
+        la = s["log2_batch"] + s["log2_m"] + s["log2_k"]
+        lb = s["log2_batch"] + s["log2_k"] + s["log2_n"]
+        for t, l in ((s["a"], la), (s["b"], lb)):
+            if t in size:
+                assert size[t] == l
+        size[s["c"]] = s["log2_batch"] + s["log2_m"] + s["log2_n"]
+        assert size[s["c"]] <= info["max_log2_elems"] + batch
+        # A is the larger operand
+        assert la >= lb
+    assert size[steps[-1]["c"]] == info["n_open"] + batch
+
+
+def test_slicing_hits_count_and_reduces_width():
+    c, q = rqcgen.small_grid(4, 5, 12, seed=4, n_open=6)
+    w0 = _plan(c, q, n_slice_edges=0).info()["max_log2_elems"]
+    for s in (1, 3, 5):
+        i = _plan(c, q, n_slice_edges=s).info()
+        assert i["n_slice_edges"] == s and i["n_slices"] == 1 << s
+        assert i["max_log2_elems"] <= w0
+
+
+def test_cap_mode_reaches_cap():
+    c, q = rqcgen.small_grid(4, 5, 12, seed=4, n_open=6)
+    w0 = _plan(c, q, n_slice_edges=0).info()["max_log2_elems"]
+    cap = w0 - 3
+    i = _plan(c, q, n_slice_edges=-1, max_log2_elems=cap).info()
+    assert i["max_log2_elems"] <= cap and i["n_slice_edges"] >= 1
+
+
+def test_sliced_edges_are_two_qubit_wires():
+    c, q = rqcgen.small_grid(4, 4, 10, seed=3, n_open=5)
+    p = _plan(c, q, n_slice_edges=4)
+    for qb, g in p.sliced_edges():
+        assert c.q1[g] >= 0 and qb in (c.q0[g], c.q1[g])
+        # the wire continues into a later two-qubit gate (internal edge)
+        later = [h for h in range(g + 1, c.n_gates) if c.q1[h] >= 0 and qb in (c.q0[h], c.q1[h])]
+        assert later
+
+
+def test_workspace_covers_largest_intermediate():
+    c, q = rqcgen.small_grid(4, 5, 12, seed=4, n_open=6)
+    for dt, esz in ((tn.C64, 8), (tn.F16, 4)):
+        i = _plan(c, q, dtype=dt, n_slice_edges=2).info()
+        assert i["workspace_bytes"] >= esz << i["max_log2_elems"]
+
+
+def test_plan_is_deterministic():
+    c, q = rqcgen.small_grid(4, 5, 12, seed=4, n_open=6)
+    a = _plan(c, q, n_slice_edges=3, trials=3, seed=9)
+    b = _plan(c, q, n_slice_edges=3, trials=3, seed=9)
+    assert a.sliced_edges() == b.sliced_edges() and a.steps() == b.steps()
+
+
+def test_rejects_bad_inputs():
+    c, q = rqcgen.small_grid(3, 3, 4, seed=1, n_open=3)
+    bad = rqcgen.Circuit(c.n_qubits, c.q0.copy(), c.q1.copy(), c.mats.copy())
+    bad.q0[5] = 99
+    with pytest.raises(tn.TnError) as e:
+        _plan(bad, q)
+    assert e.value.code == tn.TN_EINVAL
+    q2 = rqcgen.Query(np.array([5, 2], dtype=np.int32), q.fixed_bits)
+    with pytest.raises(tn.TnError):
+        _plan(c, q2)  # not ascending
+    with pytest.raises(tn.TnError):
+        _plan(c, q, dtype=7)
+    with pytest.raises(tn.TnError):
+        _plan(c, q, n_slice_edges=1, slice_batch_log2=2)
+    nan = rqcgen.Circuit(c.n_qubits, c.q0.copy(), c.q1.copy(), c.mats.copy())
+    nan.mats[0, 0, 0] = np.nan
+    with pytest.raises(tn.TnError):
+        _plan(nan, q)
+
+
+def test_workload_plans():
+    # the 30-qubit workload: 8 sliced edges, 256 slices, 1024 amplitudes
+    c, q = rqcgen.grid_30q()
+    i = _plan(c, q, n_slice_edges=8, trials=4).info()
+    assert i["n_slices"] == 256 and i["n_open"] == 10 and i["n_leaves"] == 172
+    # the 53-qubit workload: sliced until each slice's largest tensor <= 2^30
+    c, q = rqcgen.grid_53q()
+    i = _plan(c, q, n_slice_edges=-1, max_log2_elems=30, trials=2).info()
+    assert i["max_log2_elems"] <= 30 and i["n_open"] == 12
