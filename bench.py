@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the sliced tensor-network contraction on GB300.
+
+Workload: the 30-qubit 5x6-grid, 14-cycle synthetic Sycamore-shaped random
+circuit, greedy path sliced on 8 edges (256 slices), 1024 correlated
+amplitudes (qubits 20..29 open).  One step = the whole hot path once: every
+slice decoded, permuted, contracted (GEMMs), rescaled, summed in FP64, then
+top-1 post-selection.  Metric: contraction TFLOP/s (8 M N K real flops per
+step, summed over the plan) and slices/s; the FP16 tensor-core path is the
+headline, the complex64 path is measured beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f16|bf16|c64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, same metric
+
+N > 1 runs under torch.distributed.run: each rank contracts a contiguous
+share of the 256 slices and the FP64 amplitude vectors are summed with one
+NCCL all-reduce (strong scaling over a fixed job).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contraction TFLOPS & slices/s, FP16 vs complex64 path, at rel-L2 <=5e-3 vs FP64"
+WORKLOAD = ("grid5x6-14c: 30-qubit 5x6 random circuit, 14 cycles, greedy path sliced on 8 edges "
+            "(256 slices), 1024 correlated amplitudes (qubits 20-29 open)")
+N_SLICE_EDGES = 8
+PATH_TRIALS = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f16", choices=["f16", "bf16", "c64"])
+    ap.add_argument("--slice-batch", type=int, default=8,
+                    help="log2 of the slices run together in one pass (carried as a batch mode)")
+    ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def read_golden():
+    path = os.path.join(ROOT, "tests", "golden", "grid5x6_14c_amps.txt")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+    vals = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        _, a, b = line.split()
+        vals.append(complex(float(a), float(b)))
+    return np.array(vals)
+
+
+# ------------------------------------------------------------- oracle leg
+def oracle_sample(seconds_target=15.0, max_gates=None):
+    """Time the FP64 state-vector oracle on a bounded prefix of the 30-qubit
+    circuit; return (estimated seconds for the whole circuit, sample text,
+    threads)."""
+    import numpy as np
+    import oracle
+    import rqcgen
+    c, _ = rqcgen.grid_30q()
+    oracle.build()
+    threads = oracle.threads()
+
+    def run(g):
+        sub = rqcgen.Circuit(c.n_qubits, c.q0[:g], c.q1[:g], c.mats[:g])
+        t = time.perf_counter()
+        oracle.state_vector(sub)
+        return time.perf_counter() - t
+
+    t_init = run(0)                      # allocation + |0> initialisation
+    probe = 8
+    t_probe = run(probe) - t_init
+    per_gate = max(t_probe / probe, 1e-6)
+    g = int(max(probe, min(c.n_gates, (seconds_target - t_init) / per_gate)))
+    if max_gates:
+        g = min(g, max_gates)
+    t = run(g)
+    per_gate = (t - t_init) / g
+    full = t_init + per_gate * c.n_gates
+    return full, (f"FP64 state vector of the 30-qubit circuit (2^30 amplitudes, 16 GiB), first "
+                  f"{g} of {c.n_gates} gates timed ({t:.1f} s), scaled to all gates"), threads
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import rqcgen
+    import paper_2407_00769_gb300 as tn
+    c, q = rqcgen.grid_30q()
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                   slice_batch_log2=args.slice_batch, torch_allocator=False)
+    info = plan.info()
+    job_flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
+    oracle.build()
+    per_step = []
+    gates_per_step = None
+    sub_t = None
+    for i in range(args.warmup + args.steps):
+        full, sample, threads = oracle_sample(seconds_target=8.0, max_gates=gates_per_step)
+        if i >= args.warmup:
+            per_step.append(full)
+        sub_t = sample
+    est = statistics.mean(per_step)
+    value = job_flops / est / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "slices": info["n_slices"],
+                       "flops_per_job": job_flops},
+            "slices_per_s": info["n_slices"] / est,
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads,
+                             "kind": "oracle", "sample": sub_t},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import rqcgen
+    import paper_2407_00769_gb300 as tn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dtype = {"f16": tn.F16, "bf16": tn.BF16, "c64": tn.C64}[args.dtype]
+
+    c, q = rqcgen.grid_30q()
+    sb = args.slice_batch if world == 1 else 0
+    plan = tn.Plan(c, q, dtype=dtype, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                   slice_batch_log2=sb)
+    info = plan.info()
+    n_slices = info["n_slices"]
+    lo = rank * n_slices // world
+    hi = (rank + 1) * n_slices // world
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.contract(lo, hi - lo, out=amps)
+        if world > 1:
+            dist.all_reduce(amps.view(torch.float64))
+        return tn.sample(amps, 1)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    barrier()
+
+    # timed region: per step flush L2 (outside the events), then events
+    # around the step; inside it, each launch of the tensor-core GEMM is
+    # bracketed by its own event pair (the roofline's kernel)
+    plan.profile(["gemm_tc"] if dtype != tn.C64 else ["gemm_c64"])
+    clocks = Clocks(local) if rank == 0 else None
+    times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop() if clocks else None
+    prof_live = plan.profile_read()
+    # one more step with every kernel class timed, for the breakdown
+    plan.profile(tn.KC_NAMES)
+    flush.zero_()
+    step()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(None)
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    job_flops = info["flops_per_slice"] * n_slices + info["flops_invariant"] * world
+    launches_per_step = sum(v["launches"] for v in prof.values()) + 1
+
+    # accuracy of the timed path against the FP64 reference amplitudes
+    gold = read_golden()
+    acc = {}
+    if gold is not None:
+        ref = torch.from_numpy(gold).to(dev)
+        m = tn.metrics(amps, ref, n_qubits=c.n_qubits)
+        acc = {"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    # dominant kernel class by time (breakdown step); its achieved rate is
+    # taken from the launches timed live inside the timed region when that
+    # class was instrumented there
+    name = max(prof.items(), key=lambda kv: kv[1]["ms"])[0]
+    st = prof_live.get(name)
+    live = st is not None
+    if not live:
+        st = prof[name]
+        nsteps = 1
+    else:
+        nsteps = args.steps
+    avg_ms = st["ms"] / st["launches"]
+    if name == "gemm_tc":
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = st["flops"] / (st["ms"] * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak_note = f"{peak_src} bf16 sustained (FP16 dense rate = BF16 rate)"
+    elif name == "gemm_c64":
+        bound, unit = "alu", "TFLOP/s"
+        achieved = st["flops"] / (st["ms"] * 1e-3) / 1e12
+        # FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak_note = "FP32 CUDA-core FMA peak 152 SM x 128 lanes x 2 flop x 2070 MHz"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = st["bytes"] / (st["ms"] * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs")
+        peak_note = f"{peak_src} HBM copy bandwidth"
+    total_prof_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "timed_live": live, "launches_per_step": st["launches"] // nsteps,
+                "avg_launch_ms": avg_ms, "peak_source": peak_note,
+                "share_of_kernel_time": prof[name]["ms"] / total_prof_ms,
+                "per_class": {k: {"launches": v["launches"], "ms_per_step": v["ms"],
+                                  "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9,
+                                  "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
+                              for k, v in prof.items()}}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tr = json.load(open(traffic_file))
+            if tr.get("kernel") == name and tr.get("dtype") == args.dtype:
+                roofline["traffic"] = tr.get("bytes_per_launch")
+        except Exception:
+            pass
+
+    line = {"metric": METRIC, "value": job_flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "slices": n_slices, "flops_per_job": job_flops,
+                       "max_log2_elems": info["max_log2_elems"], "steps_per_slice": info["n_steps"],
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "parallelism": f"slices split over {world} GPU(s)",
+                       "slice_batch_log2": sb},
+            "slices_per_s": n_slices / (ms * 1e-3), **acc,
+            "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
+    if clk:
+        line["clocks"] = clk
+
+    # complex64 path on the same workload (fewer steps: it is the slow path)
+    if not args.no_c64 and dtype != tn.C64 and world == 1:
+        p64 = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                      slice_batch_log2=sb)
+        a64 = torch.zeros_like(amps)
+        p64.contract(0, n_slices, out=a64)
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p64.contract(0, n_slices, out=a64)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        m64 = statistics.mean(tt)
+        i64 = p64.info()
+        f64 = i64["flops_per_slice"] * n_slices + i64["flops_invariant"]
+        c64 = {"tflops": f64 / (m64 * 1e-3) / 1e12, "slices_per_s": n_slices / (m64 * 1e-3),
+               "ms_per_step": m64}
+        if gold is not None:
+            m = tn.metrics(a64, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
+            c64.update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]})
+        line["c64"] = c64
+        line["speedup_vs_c64"] = m64 / ms
+        del p64, a64
+
+    # end to end through the public API from host memory (leaves uploaded,
+    # amplitudes downloaded, every step)
+    if not args.no_e2e and world == 1:
+        plan.contract_host()
+        tt = []
+        for _ in range(max(2, args.steps)):
+            t0 = time.perf_counter()
+            h = plan.contract_host()
+            tt.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(tt)
+        leaf_bytes = info.get("leaf_bytes", 0)
+        line["e2e"] = {"value": job_flops / e2e_s / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": leaf_bytes, "d2h_bytes_per_step": int(h.nbytes),
+                       "ms_per_step": e2e_s * 1e3}
+
+    if not args.no_cpu_baseline and world == 1:
+        full, sample, threads = oracle_sample()
+        line["cpu_baseline"] = {"value": job_flops / full / 1e12, "unit": "TFLOP/s",
+                                "cores": threads, "kind": "oracle", "sample": sample,
+                                "est_seconds_per_step": full}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

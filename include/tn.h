@@ -118,6 +118,7 @@ typedef struct {
     int64_t workspace_bytes;      /* device workspace of the plan                */
     int32_t n_permutes;           /* explicit permutations per slice             */
     int32_t dtype;
+    int64_t leaf_bytes;           /* host->device bytes of the leaf tensors      */
 } tn_plan_stats;
 
 typedef struct {
@@ -216,6 +217,30 @@ int tn_metrics(const double *d_amps, const double *d_ref, int64_t n, int32_t n_q
 
 void tn_plan_destroy(tn_plan_t *plan);
 
+/* ---- per-kernel timing (measurement, not for production runs) ---- */
+#define TN_KC_LEAF 0        /* leaf preparation / slice decoding            */
+#define TN_KC_PERMUTE 1     /* bit-permute transposes                       */
+#define TN_KC_BPREP 2       /* B' padding for the tensor-core path          */
+#define TN_KC_GEMM_TC 3     /* tcgen05 complex-as-real GEMM                 */
+#define TN_KC_GEMM_LP 4     /* complex-half GEMM on CUDA cores              */
+#define TN_KC_GEMM_C64 5    /* complex64 GEMMs on CUDA cores                */
+#define TN_KC_SUM 6         /* FP64 cross-slice sum                          */
+#define TN_KC_COUNT 7
+
+typedef struct {
+    int64_t launches;
+    double ms;        /* summed CUDA-event durations of those launches       */
+    double flops;     /* algorithmic real flops (8 M N K per GEMM)            */
+    double bytes;     /* algorithmic bytes: operands read + result written   */
+} tn_kernel_stats;
+
+/* Record a CUDA event pair around every later launch of the kernel classes
+ * in class_mask (bit TN_KC_*) made by tn_contract on this plan; 0 turns it
+ * off.  Resets the counters. */
+int tn_profile(tn_plan_t *plan, uint32_t class_mask);
+/* Synchronize on the recorded events and return TN_KC_COUNT entries. */
+int tn_profile_read(tn_plan_t *plan, tn_kernel_stats *out);
+
 /* ---- single-kernel entry points (used by tests; same kernels as above) ---- */
 
 /*
@@ -233,9 +258,9 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  * B[b][K][N] on interleaved complex data (row-major; batch stride 0 for a
  * broadcast operand: pass batch_a / batch_b = 0 for no batch mode).
  *   dtype TN_C64: A, B, C complex64, FP32 accumulation; scale ignored.
- *   dtype TN_F16/TN_BF16: A, C complex-half; B complex64 (small operand, padded
- *   on the device to the real 2K x 2N form of Eq. 4-5); FP32 accumulation; C
- *   is multiplied by 2^scale_exp before rounding.
+ *   dtype TN_F16/TN_BF16: A, B, C complex-half (B is padded on the device to
+ *   the real 2K x 2N form of Eq. 4-5 for the tensor-core variant); FP32
+ *   accumulation; C is multiplied by 2^scale_exp before rounding.
  * kernel: -1 = automatic; otherwise a variant index (tests).
  * out_max: optional device float, receives max |component| of the stored C.
  */

@@ -32,7 +32,9 @@ EXPORTED = [
     "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
+    "tn_profile", "tn_profile_read",
 ]
+KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum"]
 
 
 class TnError(RuntimeError):
@@ -76,13 +78,19 @@ class PlanStats(ctypes.Structure):
                 ("max_log2_elems", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
                 ("flops_per_slice", ctypes.c_double), ("flops_invariant", ctypes.c_double),
                 ("bytes_per_slice", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
-                ("n_permutes", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+                ("n_permutes", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("leaf_bytes", ctypes.c_int64)]
 
 
 class ContractReport(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("slices", ctypes.c_int64),
                 ("kernels", ctypes.c_int32), ("min_exp", ctypes.c_int32),
                 ("max_exp", ctypes.c_int32)]
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class StepInfo(ctypes.Structure):
@@ -130,6 +138,8 @@ def lib():
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
         L.tn_gemm.argtypes = [i32, vp, vp, vp, i64, i64, i64, i64, i32, i32, i32, i32, vp, vp]
+        L.tn_profile.argtypes = [vp, ctypes.c_uint32]
+        L.tn_profile_read.argtypes = [vp, ctypes.POINTER(KernelStats)]
         L.tn_strerror.argtypes = [ctypes.c_int]
         L.tn_strerror.restype = ctypes.c_char_p
         L.tn_last_error.argtypes = []
@@ -289,6 +299,19 @@ class Plan:
         if report:
             return out, {f: getattr(rep, f) for f, _ in ContractReport._fields_}
         return out
+
+    def profile(self, classes=None):
+        """Start per-kernel-class event timing (names from KC_NAMES; None: off)."""
+        mask = 0
+        for c in classes or []:
+            mask |= 1 << KC_NAMES.index(c)
+        _check(lib().tn_profile(self._h, mask))
+
+    def profile_read(self) -> dict:
+        arr = (KernelStats * len(KC_NAMES))()
+        _check(lib().tn_profile_read(self._h, arr))
+        return {KC_NAMES[i]: {f: getattr(arr[i], f) for f, _ in KernelStats._fields_}
+                for i in range(len(KC_NAMES)) if arr[i].launches}
 
     def contract_host(self, slice_begin: int = 0, slice_count: Optional[int] = None, stream=None,
                       report: bool = False):

@@ -82,8 +82,73 @@ int ensure_device(tn_plan_s *P) {
     return TN_OK;
 }
 
+// kernel class and algorithmic flops / bytes of one op
+int op_class(const tn_plan_s *P, const Op &op, double &flops, double &bytes) {
+    const int dtype = P->opts.dtype;
+    const double esz = dtype == TN_C64 ? 8 : 4;
+    flops = 0;
+    bytes = 0;
+    switch (op.kind) {
+        case OP_LEAF: {
+            for (int k = 0; k < op.leaf_count; ++k) {
+                const LeafJob &j = P->sched.leaf_jobs[op.leaf_first + k];
+                bytes += std::ldexp(16.0, j.rank_out) + std::ldexp(esz, j.rank_out);
+            }
+            return TN_KC_LEAF;
+        }
+        case OP_PERM: bytes = 2 * std::ldexp(esz, op.perm.rank); return TN_KC_PERMUTE;
+        case OP_BPREP: {
+            const double b = std::ldexp(1.0, op.bprep.lb);
+            bytes = b * (std::ldexp(esz, op.bprep.lk + op.bprep.ln) + (double)op.bprep.np * std::ldexp(4.0, op.bprep.lk));
+            return TN_KC_BPREP;
+        }
+        case OP_GEMM: {
+            const GemmOp &g = op.gemm;
+            flops = 8.0 * std::ldexp(1.0, g.lm + g.ln + g.lk + g.lb);
+            const double bsz = g.kernel == GK_LP_TC
+                                   ? std::max(16.0, std::ldexp(2.0, g.ln)) * std::ldexp(4.0, g.lk)
+                                   : std::ldexp(esz, g.lk + g.ln);
+            bytes = std::ldexp(1.0, g.lb) * (std::ldexp(esz, g.lm + g.lk) + bsz + std::ldexp(esz, g.lm + g.ln));
+            if (g.kernel == GK_LP_TC) return TN_KC_GEMM_TC;
+            if (g.kernel == GK_LP_ROWS) return TN_KC_GEMM_LP;
+            return TN_KC_GEMM_C64;
+        }
+        case OP_SUM: bytes = std::ldexp(esz, op.sum.rank); return TN_KC_SUM;
+    }
+    return -1;
+}
+
+cudaEvent_t take_event(tn_plan_s *P) {
+    if (!P->ev_pool.empty()) {
+        cudaEvent_t e = P->ev_pool.back();
+        P->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, int t_lo, int t_hi,
+               int overwrite, cudaStream_t s, int &launches);
+
 int run_op(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, int t_lo, int t_hi,
            int overwrite, cudaStream_t s, int &launches) {
+    if (!P->prof_mask) return run_op_raw(P, op, slice_base, amps, t_lo, t_hi, overwrite, s, launches);
+    double fl, by;
+    const int cls = op_class(P, op, fl, by);
+    if (cls < 0 || !((P->prof_mask >> cls) & 1))
+        return run_op_raw(P, op, slice_base, amps, t_lo, t_hi, overwrite, s, launches);
+    tn_plan_s::ProfRec r{cls, take_event(P), take_event(P), fl, by};
+    cudaEventRecord(r.e0, s);
+    const int rc = run_op_raw(P, op, slice_base, amps, t_lo, t_hi, overwrite, s, launches);
+    cudaEventRecord(r.e1, s);
+    P->prof.push_back(r);
+    return rc;
+}
+
+int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, int t_lo, int t_hi,
+               int overwrite, cudaStream_t s, int &launches) {
     const int dtype = P->opts.dtype;
     const int esz = dtype == TN_C64 ? 8 : 4;
     char *ws = P->d_ws;
@@ -254,6 +319,7 @@ int tn_plan_info(const tn_plan_t *P, tn_plan_stats *s) {
     s->workspace_bytes = P->sched.ws_bytes;
     s->n_permutes = P->sched.n_permutes;
     s->dtype = P->opts.dtype;
+    s->leaf_bytes = (int64_t)P->leaf_store.size() * 16;
     return TN_OK;
 }
 
@@ -432,9 +498,40 @@ int tn_metrics(const double *d_amps, const double *d_ref, int64_t n, int32_t n_q
     return TN_OK;
 }
 
+int tn_profile(tn_plan_t *P, uint32_t class_mask) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    for (auto &r : P->prof) {
+        P->ev_pool.push_back(r.e0);
+        P->ev_pool.push_back(r.e1);
+    }
+    P->prof.clear();
+    P->prof_mask = class_mask & ((1u << TN_KC_COUNT) - 1);
+    return TN_OK;
+}
+
+int tn_profile_read(tn_plan_t *P, tn_kernel_stats *out) {
+    if (!P || !out) return fail(TN_EINVAL, "NULL argument");
+    for (int c = 0; c < TN_KC_COUNT; ++c) out[c] = tn_kernel_stats{0, 0.0, 0.0, 0.0};
+    for (auto &r : P->prof) {
+        TN_CUDA(cudaEventSynchronize(r.e1), "event sync");
+        float ms = 0;
+        TN_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1), "event time");
+        out[r.cls].launches += 1;
+        out[r.cls].ms += ms;
+        out[r.cls].flops += r.flops;
+        out[r.cls].bytes += r.bytes;
+    }
+    return TN_OK;
+}
+
 void tn_plan_destroy(tn_plan_t *P) {
     if (!P) return;
     if (P->dev_ready) cudaDeviceSynchronize();
+    for (auto &r : P->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (auto e : P->ev_pool) cudaEventDestroy(e);
     plan_dev_free_all(P);
     if (P->h_store_pinned) cudaFreeHost(P->h_store_pinned);
     delete P;

@@ -52,5 +52,10 @@ struct tn_plan_s {
     int32_t *d_texp = nullptr;
     int32_t *d_err = nullptr;
     void *h_store_pinned = nullptr;     // pinned copy of the leaf store
+    // per-kernel-class event timing (tn_profile)
+    uint32_t prof_mask = 0;
+    struct ProfRec { int cls; cudaEvent_t e0, e1; double flops, bytes; };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
     std::vector<void *> owned;          // allocations to free
 };
