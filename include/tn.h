@@ -10,9 +10,9 @@
  * "breaking edges" (Sec. 3, Innovations; Sec. 3.1) -- and each slice is
  * contracted as a sequence of pairwise steps, each one index permutation
  * followed by a matrix multiplication (Sec. 3.1, device level; Sec. 3.3,
- * Eq. 2-3: a pairwise einsum is a pure GEMM when its reduced modes are the
+ * Eq. 3-4: a pairwise einsum is a pure GEMM when its reduced modes are the
  * modes the two operands share).  Slice results are summed in FP64.  Low-
- * precision steps use the complex-as-real layout of Sec. 3.3 (Eq. 4-5): the
+ * precision steps use the complex-as-real layout of Sec. 3.3 (Eq. 5-6): the
  * large operand keeps its interleaved real/imag mode as an extra reduced mode
  * and the small operand is padded to [[Re, -Im], [Im, Re]], so one real GEMM
  * with K -> 2K and N -> 2N does the complex product.  Post-selection keeps the
@@ -208,7 +208,7 @@ int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
 /*
  * tn_metrics: FP64 reductions on the device over n complex128 amplitudes:
  * out[0] = sum |r|^2, out[1] = rel-L2 ||r - b|| / ||b||, out[2] = fidelity
- * |<b,r>|^2 / (||b||^2 ||r||^2) (Sec. 4.2, Eq. 9, conjugate-linear inner
+ * |<b,r>|^2 / (||b||^2 ||r||^2) (Sec. 4.2, Eq. 8, conjugate-linear inner
  * product), out[3] = linear XEB 2^n_qubits * mean |r|^2 - 1 of the n entries.
  * d_ref may be NULL (then out[1], out[2] are NaN).  out: host, 4 doubles.
  */
@@ -259,7 +259,7 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  * broadcast operand: pass batch_a / batch_b = 0 for no batch mode).
  *   dtype TN_C64: A, B, C complex64, FP32 accumulation; scale ignored.
  *   dtype TN_F16/TN_BF16: A, B, C complex-half (B is padded on the device to
- *   the real 2K x 2N form of Eq. 4-5 for the tensor-core variant); FP32
+ *   the real 2K x 2N form of Eq. 6 for the tensor-core variant); FP32
  *   accumulation; C is multiplied by 2^scale_exp before rounding.
  * kernel: -1 = automatic; otherwise a variant index (tests).
  * out_max: optional device float, receives max |component| of the stored C.

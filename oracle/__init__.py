@@ -11,8 +11,8 @@ Contents
     (paper Sec. 3.1: sub-networks from broken edges).      -> oracle/sv.c
   * bruteforce_state: product of full 2^n x 2^n gate matrices (n <= 8).
   * complex_as_real_einsum: the paper's complex-half einsum extension
-    (Sec. 3.3, Eq. 4-5), FP64, pinned by the paper's worked example.
-  * rel_l2, fidelity (Eq. 9), linear_xeb, topk (post-selection, Sec. 1/2).
+    (Sec. 3.3, Eq. 5-6), FP64, pinned by the paper's worked example.
+  * rel_l2, fidelity (Eq. 8), linear_xeb, topk (post-selection, Sec. 1/2).
 """
 from __future__ import annotations
 
@@ -153,7 +153,7 @@ def bruteforce_state(circuit) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Complex-half einsum extension (paper Sec. 3.3, Eq. 4-5)
+# Complex-half einsum extension (paper Sec. 3.3, Eq. 5-6)
 # --------------------------------------------------------------------------
 
 def pad_b(b: np.ndarray) -> np.ndarray:
@@ -177,7 +177,7 @@ def complex_as_real_einsum(eq: str, a_real: np.ndarray, b: np.ndarray) -> np.nda
     """Evaluate the complex einsum ``eq`` ("A,B->C", single-letter modes) the
     paper's way: A is given as real with its real/imag mode last, B is padded
     to B' (``pad_b``), and one real einsum runs over the modified equation
-    "A r, o B r -> C o" (Eq. 5).  Returns C real with its real/imag mode last.
+    "A r, o B r -> C o" (Eq. 6).  Returns C real with its real/imag mode last.
     """
     lhs, out = eq.replace(" ", "").split("->")
     ea, eb = lhs.split(",")
@@ -200,7 +200,7 @@ def rel_l2(result: np.ndarray, reference: np.ndarray) -> float:
 
 
 def fidelity(reference: np.ndarray, result: np.ndarray) -> float:
-    """Eq. 9 read for complex vectors: |<b, r>|^2 / (||b||^2 ||r||^2) with the
+    """Eq. 8 read for complex vectors: |<b, r>|^2 / (||b||^2 ||r||^2) with the
     conjugate-linear inner product <b, r> = sum conj(b) r."""
     b = np.asarray(reference, dtype=np.complex128).ravel()
     r = np.asarray(result, dtype=np.complex128).ravel()

@@ -441,7 +441,7 @@ cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, i
 // B [batch][K][N] complex-half -> B' [batch][np][2K] real (K-major rows):
 //   B'[2n  ][2k] =  Re B[k][n],  B'[2n  ][2k+1] = -Im B[k][n]
 //   B'[2n+1][2k] =  Im B[k][n],  B'[2n+1][2k+1] =  Re B[k][n]
-// rows 2N..np-1 are zero.  (Paper Sec. 3.3, Eq. 5: B padded to
+// rows 2N..np-1 are zero.  (Paper Sec. 3.3, Eq. 6: B padded to
 // [B_(real,-imag), B_(imag,real)], the new output mode and the shared
 // real/imag mode both innermost.)
 template <typename H>

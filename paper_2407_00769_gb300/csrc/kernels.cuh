@@ -60,7 +60,7 @@ cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double
 cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,
                         cudaStream_t s);
 
-// tcgen05 GEMM (complex-half as real, Eq. 4-5).  Tensor maps are encoded
+// tcgen05 GEMM (complex-half as real, Eq. 5-6).  Tensor maps are encoded
 // by the host (tc_gemm.cu).
 struct TcGemmDesc {
     int dtype;             // TN_F16 | TN_BF16

@@ -1,5 +1,5 @@
 // Device schedule of a plan: for every pairwise step, the GEMM form of the
-// einsum (paper Sec. 3.3, Eq. 2-3: reduced modes = the modes both operands
+// einsum (paper Sec. 3.3, Eq. 3-4: reduced modes = the modes both operands
 // share; result modes = the union minus those), the operand layouts and the
 // explicit permutations they need, the workspace buffers, and the kernel.
 //
@@ -8,7 +8,7 @@
 // read as a K-major GEMM operand with no copy); if its K modes are not
 // already its innermost modes it is permuted once.  The smaller operand B is
 // brought to [batch][K][N] (same K order as A), and for the tensor-core path
-// padded to B' (Eq. 5).  C is written as [batch][M][N].  When A must be
+// padded to B' (Eq. 6).  C is written as [batch][M][N].  When A must be
 // permuted anyway, and for B's N modes, the order is chosen so that the modes
 // the next step will contract end up innermost (fewer permutations later).
 //

@@ -1,6 +1,6 @@
 // Complex-half contraction step on the 5th-generation tensor cores.
 //
-// Paper Sec. 3.3 (Eq. 4-5): the large operand A keeps its interleaved
+// Paper Sec. 3.3 (Eq. 5-6): the large operand A keeps its interleaved
 // real/imag mode as an extra reduced mode, so A[M][K] complex is read as a
 // real [M][2K] matrix with no copy; the small operand is padded to
 // B'[(n,co)][(k,ci)] = [[Re, -Im], [Im, Re]] (bprep), and ONE real GEMM

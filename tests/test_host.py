@@ -1,6 +1,6 @@
 """Host-side checks of the library that need no GPU: it loads, exports every
 symbol include/tn.h declares, and its planner obeys the paper's GEMM
-condition (Sec. 3.3, Eq. 2-3) and the slicing/memory invariants."""
+condition (Sec. 3.3: reduced modes = shared modes, stated after Eq. 3; result modes, Eq. 4) and the slicing/memory invariants."""
 import ctypes
 import os
 import re
@@ -43,7 +43,7 @@ def _plan(circuit, query, **kw):
 @pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
 @pytest.mark.parametrize("slices,batch", [(0, 0), (3, 0), (3, 2)])
 def test_plan_steps_are_pure_gemms(dtype, slices, batch):
-    # Eq. 2-3: every step's result has exactly the modes of A and B minus the
+    # Eq. 3-4: every step's result has exactly the modes of A and B minus the
     # reduced ones; the sizes each tensor is produced with and consumed with
     # must agree, and the last tensor holds the open modes (+ batch modes).
     c, q = rqcgen.small_grid(4, 4, 10, seed=3, n_open=5)
