@@ -206,6 +206,32 @@ int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
               double *out_prob, void *stream);
 
 /*
+ * tn_sample_noalloc: tn_sample for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment variant.
+ * tn_sample allocates a small device buffer for the k results on every
+ * call; a caller inside a host application that owns all device memory
+ * through its own pool, or a latency-critical thread that must not enter
+ * the CUDA allocator (cudaMalloc/cudaFree can synchronize the device),
+ * cannot.  This call allocates nothing: its scratch is a fixed array in
+ * device global memory of TN_SAMPLE_NOALLOC_MAX_K indices and probabilities
+ * (16 KiB), present on every GPU that loads the library until the process
+ * exits.  Same arguments, results and ordering as tn_sample.
+ *   - k > TN_SAMPLE_NOALLOC_MAX_K is rejected with TN_EINVAL (use tn_sample).
+ *   - The first call on a device looks up the array's device address
+ *     (set-up, once per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls on a device share the one array and it keeps the last
+ *     call's contents; calls that overlap on the GPU (different streams or
+ *     threads without ordering between them) race and may return each
+ *     other's results.  Each call writes every entry it reads back, so
+ *     nothing has to start at zero.
+ * Synchronizes `stream`.
+ */
+#define TN_SAMPLE_NOALLOC_MAX_K 1024
+int tn_sample_noalloc(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
+                      double *out_prob, void *stream);
+
+/*
  * tn_metrics: FP64 reductions on the device over n complex128 amplitudes:
  * out[0] = sum |r|^2, out[1] = rel-L2 ||r - b|| / ||b||, out[2] = fidelity
  * |<b,r>|^2 / (||b||^2 ||r||^2) (Sec. 4.2, Eq. 8, conjugate-linear inner

@@ -32,7 +32,7 @@ EXPORTED = [
     "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
-    "tn_profile", "tn_profile_read",
+    "tn_profile", "tn_profile_read", "tn_sample_noalloc",
 ]
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum"]
 
@@ -134,6 +134,7 @@ def lib():
         L.tn_contract_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
         L.tn_sample.argtypes = [vp, i32, i32, vp, vp, vp]
         L.tn_metrics.argtypes = [vp, vp, i64, i32, vp, vp]
+        L.tn_sample_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
@@ -347,6 +348,19 @@ def sample(amps, k: int = 1, stream=None):
     prob = np.zeros(k, dtype=np.float64)
     _check(lib().tn_sample(amps.data_ptr(), n_open, int(k), idx.ctypes.data, prob.ctypes.data,
                            _stream_ptr(stream)))
+    return idx, prob
+
+
+def sample_noalloc(amps, k: int = 1, stream=None):
+    """tn_sample without device allocation (k <= 1024; see include/tn.h)."""
+    n = amps.numel()
+    n_open = n.bit_length() - 1
+    if (1 << n_open) != n:
+        raise ValueError("amplitude count must be a power of two")
+    idx = np.zeros(k, dtype=np.int64)
+    prob = np.zeros(k, dtype=np.float64)
+    _check(lib().tn_sample_noalloc(amps.data_ptr(), n_open, int(k), idx.ctypes.data,
+                                   prob.ctypes.data, _stream_ptr(stream)))
     return idx, prob
 
 

@@ -230,6 +230,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
 
 }  // namespace
 
+int tn::record_error(int code, const std::string &msg) { return fail(code, msg); }
+
 extern "C" {
 
 void tn_plan_opts_default(tn_plan_opts *o) {

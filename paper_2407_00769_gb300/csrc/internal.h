@@ -116,6 +116,10 @@ struct Op {
     SumOp sum{};
 };
 
+// Record `msg` as the calling thread's last error (tn_last_error) and
+// return `code`.
+int record_error(int code, const std::string &msg);
+
 // Per-step record for inspection.
 struct StepRec {
     int a, b, c;
