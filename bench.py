@@ -47,7 +47,55 @@ def parse():
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute"],
+                    help="time one kernel on one shape instead (profiling aid)")
+    ap.add_argument("--lm", type=int, default=14)
+    ap.add_argument("--ln", type=int, default=14)
+    ap.add_argument("--lk", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--rank", type=int, default=28)
     return ap.parse_args()
+
+
+def kernel_case(args):
+    """One kernel on one shape: the dominant step shape of the workload's
+    tensor-core GEMM (default M = N = 2^14, K = 2^12 complex) or a rank-r
+    bit-permute transpose (reversal of the mode order)."""
+    import torch
+    import paper_2407_00769_gb300 as tn
+    torch.cuda.set_device(0)
+    if args.case == "gemm_tc":
+        M, N, K, b = 1 << args.lm, 1 << args.ln, 1 << args.lk, args.batch
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = (torch.randn(b, M, K, 2, device="cuda", generator=g) * 0.5).half()
+        B = (torch.randn(b, K, N, 2, device="cuda", generator=g) / (K ** 0.5)).half()
+        C = torch.empty(b, M, N, 2, dtype=torch.float16, device="cuda")
+        run = lambda: tn.gemm(tn.F16, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
+                              scale_exp=0, kernel=3)
+        work, unit = 8.0 * M * N * K * b, "TFLOP/s"
+    else:
+        r = args.rank
+        x = torch.empty(1 << r, dtype=torch.int32, device="cuda").random_()
+        y = torch.empty_like(x)
+        perm = list(range(r))[::-1]
+        run = lambda: tn.permute(x, perm, out=y)
+        work, unit = 2.0 * 4 * (1 << r), "GB/s"
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    rate = work / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+    print(json.dumps({"case": args.case, "ms": ms, "rate": rate, "unit": unit,
+                      "shape": vars(args)}), flush=True)
 
 
 def load_peaks():
@@ -192,6 +240,8 @@ def reference_arm(args):
 # --------------------------------------------------------------- our arm
 def main():
     args = parse()
+    if args.case:
+        return kernel_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     import numpy as np

@@ -137,6 +137,7 @@ typedef struct {
     int32_t slice_invariant;
     int32_t kernel;               /* which GEMM kernel variant runs this step    */
     int32_t tile;                 /* tile configuration index                    */
+    int32_t permute_b;            /* 1 if B is permuted before the GEMM          */
 } tn_step_info;
 
 /*

@@ -98,7 +98,8 @@ class StepInfo(ctypes.Structure):
                 ("log2_m", ctypes.c_int32), ("log2_n", ctypes.c_int32),
                 ("log2_k", ctypes.c_int32), ("log2_batch", ctypes.c_int32),
                 ("permute_a", ctypes.c_int32), ("slice_invariant", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("permute_b", ctypes.c_int32)]
 
 
 _lib = None

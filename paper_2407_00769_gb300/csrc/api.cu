@@ -166,8 +166,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             break;
         }
         case OP_BPREP:
-            e = launch_bprep(dtype, ws + op.bprep.src, ws + op.bprep.dst, op.bprep.lk, op.bprep.ln,
-                             (int64_t)1 << op.bprep.lb, op.bprep.np, s);
+            e = launch_bprep_perm(ws + op.bprep.src, ws + op.bprep.dst, op.bprep.rank, op.bprep.perm,
+                                  op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, s);
             ++launches;
             break;
         case OP_GEMM: {
@@ -342,6 +342,7 @@ int tn_plan_step(const tn_plan_t *P, int32_t i, tn_step_info *out) {
     out->a = r.a; out->b = r.b; out->c = r.c;
     out->log2_m = r.lm; out->log2_n = r.ln; out->log2_k = r.lk; out->log2_batch = r.lb;
     out->permute_a = r.permute_a;
+    out->permute_b = r.permute_b;
     out->slice_invariant = r.invariant;
     out->kernel = r.kernel;
     out->tile = r.tile;

@@ -92,9 +92,11 @@ struct GemmOp {
 };
 
 struct BprepOp {
-    int64_t src, dst;     // [batch][K][N] complex-half -> [batch][N'][K'] real
+    int64_t src, dst;     // B (stored mode order) -> B' [batch][N'][K'] real
     int32_t lk, ln, lb, step;
     int32_t np;           // padded N' (real columns, >= 16)
+    int32_t rank;         // modes of B
+    int32_t perm[kMaxRank];  // [batch][N][K] order: output mode i = stored mode perm[i]
 };
 
 struct SumOp {
@@ -124,7 +126,7 @@ int record_error(int code, const std::string &msg);
 struct StepRec {
     int a, b, c;
     int lm, ln, lk, lb;
-    int permute_a;
+    int permute_a, permute_b;
     int invariant;
     int kernel, tile;
 };

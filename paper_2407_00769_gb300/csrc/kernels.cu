@@ -213,10 +213,126 @@ __global__ void __launch_bounds__(256) permute_kernel(const T *__restrict__ in, 
     }
 }
 
+// Fast path for tensors of rank >= 10: the tile is always 2^10 elements
+// (32 contiguous input elements x 32 contiguous output elements), and the
+// position of an element inside its tile is the same for every tile, so
+// each thread works out once where its 4 elements come from and go to; per
+// tile only the tile's base offsets change (from 8-bit lookup tables).  Each
+// thread moves its 4 elements with one 16-byte (4-byte elements) or two
+// (8-byte elements) vector loads and stores.  Persistent over tiles.
+//
+// EXPAND (complex-half only): instead of the permuted tensor, write the
+// padded real operand of the tensor-core GEMM (Sec. 3.3, Eq. 6): the
+// permuted order is [batch][N][K] complex and element (b, n, k) = (re, im)
+// goes to B'[b][2n][k] = (re, -im) and B'[b][2n+1][k] = (im, re) (pairs of
+// halves; np rows per batch).
+struct ExpandArgs {
+    int32_t lk, ln, np;
+};
+
+template <typename T, bool EXPAND>
+__global__ void __launch_bounds__(256) permute_tiled_kernel(const T *__restrict__ in,
+                                                            void *__restrict__ out_,
+                                                            const __grid_constant__ PermParams p,
+                                                            int64_t ntiles, ExpandArgs ex) {
+    __shared__ T tile[1024 + 32];
+    __shared__ int64_t s_bin[4][256], s_bout[4][256];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        const int level = i >> 8, v = i & 255;
+        int64_t bi = 0, bo = 0;
+        for (int b = 0; b < 8; ++b) {
+            const int k = level * 8 + b;
+            if (k < p.n_outer && ((v >> b) & 1)) {
+                bi |= (int64_t)1 << p.outer_in[k];
+                bo |= (int64_t)1 << p.outer_out[k];
+            }
+        }
+        s_bin[level][v] = bi;
+        s_bout[level][v] = bo;
+    }
+    // this thread's 4 elements: read-order e0..e0+3, write-order f0..f0+3
+    const int e0 = threadIdx.x * 4;
+    const int64_t in_off = (e0 & 31) + p.rd_hi_off[e0 >> 5];
+    int rd_slot[4], wr_slot[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        rd_slot[j] = (e0 + j) + ((e0 + j) >> 5);
+        const int f = e0 + j;
+        const int e = p.wr_lo_e[f & 31] | p.wr_hi_e[f >> 5];
+        wr_slot[j] = e + (e >> 5);
+    }
+    const int64_t out_off = (e0 & 31) + p.wr_hi_off[e0 >> 5];
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t bin = s_bin[0][t & 255] + s_bin[1][(t >> 8) & 255] +
+                            s_bin[2][(t >> 16) & 255] + s_bin[3][(t >> 24) & 255];
+        const int64_t bout = s_bout[0][t & 255] + s_bout[1][(t >> 8) & 255] +
+                             s_bout[2][(t >> 16) & 255] + s_bout[3][(t >> 24) & 255];
+        T v[4];
+        if constexpr (sizeof(T) == 4) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else {
+            const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
+            const uint4 y = *reinterpret_cast<const uint4 *>(in + bin + in_off + 2);
+            v[0] = make_uint2(x.x, x.y); v[1] = make_uint2(x.z, x.w);
+            v[2] = make_uint2(y.x, y.y); v[3] = make_uint2(y.z, y.w);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tile[rd_slot[j]] = v[j];
+        __syncthreads();
+        T w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = tile[wr_slot[j]];
+        const int64_t f = bout + out_off;
+        if constexpr (EXPAND) {
+            const int K = 1 << ex.lk;
+            const int64_t k0 = f & (K - 1);
+            const int64_t n = (f >> ex.lk) & ((1 << ex.ln) - 1);
+            const int64_t b = f >> (ex.lk + ex.ln);
+            uint32_t *o = reinterpret_cast<uint32_t *>(out_);
+            const int64_t row0 = b * ex.np + 2 * n;
+            uint4 r0, r1;
+            // (re, -im): flip the sign bit of the high half; (im, re): swap halves
+            r0.x = w[0] ^ 0x80000000u; r0.y = w[1] ^ 0x80000000u;
+            r0.z = w[2] ^ 0x80000000u; r0.w = w[3] ^ 0x80000000u;
+            r1.x = __byte_perm(w[0], 0, 0x1032); r1.y = __byte_perm(w[1], 0, 0x1032);
+            r1.z = __byte_perm(w[2], 0, 0x1032); r1.w = __byte_perm(w[3], 0, 0x1032);
+            *reinterpret_cast<uint4 *>(o + row0 * K + k0) = r0;
+            *reinterpret_cast<uint4 *>(o + (row0 + 1) * K + k0) = r1;
+        } else {
+            T *out = reinterpret_cast<T *>(out_);
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
+                *reinterpret_cast<uint4 *>(out + f + 2) = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static int64_t permute_grid(int64_t ntiles) {
+    return std::min<int64_t>(ntiles, (int64_t)tc_num_sms() * 8);
+}
+
 cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int elem_bytes,
                            cudaStream_t s) {
     const int64_t blocks = (int64_t)1 << pp.n_outer;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (pp.tile_bits == 10 && pp.lin == 5 && pp.lout == 5 && pp.n_outer <= 32) {
+        const ExpandArgs ex{0, 0, 0};
+        if (elem_bytes == 4)
+            permute_tiled_kernel<uint32_t, false><<<(unsigned)permute_grid(blocks), 256, 0, s>>>(
+                (const uint32_t *)in, out, pp, blocks, ex);
+        else if (elem_bytes == 8)
+            permute_tiled_kernel<uint2, false><<<(unsigned)permute_grid(blocks), 256, 0, s>>>(
+                (const uint2 *)in, out, pp, blocks, ex);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     const int threads = std::min(256, 1 << pp.tile_bits);
     if (elem_bytes == 4)
         permute_kernel<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(
@@ -225,6 +341,60 @@ cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int 
         permute_kernel<uint2><<<(unsigned)blocks, threads, 0, s>>>((const uint2 *)in, (uint2 *)out, pp);
     else
         return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// B (complex-half, any mode order) -> B' in one pass.  `pp` permutes B's
+// stored modes into [batch][N][K] order.  Tensors of rank >= 10 with K >= 4
+// use the tiled EXPAND kernel; smaller ones a direct gather.
+__global__ void bprep_gather_kernel(const uint32_t *__restrict__ B, uint32_t *__restrict__ Bp,
+                                    int lk, int ln, int lb, int np, const __grid_constant__ PermParams p,
+                                    int rank) {
+    // target complex index bits: [batch][N][K], LSB = k bit 0.  For target
+    // bit i the input bit position is in_pos = r-1-perm[r-1-i].
+    const int K = 1 << lk, N = 1 << ln;
+    const int64_t total = ((int64_t)np * K) << lb;    // uint32 pairs of B'
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % K);
+        const int64_t row = i / K;
+        const int rr = (int)(row % np);
+        const int64_t b = row / np;
+        const int n = rr >> 1, co = rr & 1;
+        uint32_t v = 0;
+        if (n < N) {
+            const int64_t tidx = ((b * N + n) << lk) | k;
+            int64_t src = 0;
+            for (int t = 0; t < rank; ++t)
+                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
+            const uint32_t x = B[src];
+            v = co == 0 ? (x ^ 0x80000000u) : __byte_perm(x, 0, 0x1032);
+        }
+        Bp[i] = v;
+    }
+}
+
+cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
+                              int lb, int np, cudaStream_t s) {
+    const ExpandArgs ex{lk, ln, np};
+    if (rank >= 10 && lk >= 2 && np == 2 << ln) {
+        const PermParams pp = make_perm_params(rank, perm);
+        if (pp.tile_bits == 10 && pp.lin == 5 && pp.lout == 5 && pp.n_outer <= 32) {
+            const int64_t blocks = (int64_t)1 << pp.n_outer;
+            permute_tiled_kernel<uint32_t, true><<<(unsigned)permute_grid(blocks), 256, 0, s>>>(
+                (const uint32_t *)B, Bp, pp, blocks, ex);
+            return cudaGetLastError();
+        }
+    }
+    // direct gather: outer_in[t] = input bit position of target bit t
+    PermParams g;
+    std::memset(&g, 0, sizeof(g));
+    for (int i = 0; i < rank; ++i) g.outer_in[rank - 1 - i] = (int8_t)(rank - 1 - perm[i]);
+    const int64_t total = ((int64_t)np << lk) << lb;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 8192);
+    bprep_gather_kernel<<<blocks, threads, 0, s>>>((const uint32_t *)B, (uint32_t *)Bp, lk, ln, lb,
+                                                   np, g, rank);
     return cudaGetLastError();
 }
 

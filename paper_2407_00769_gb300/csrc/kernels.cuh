@@ -52,6 +52,10 @@ cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C
                                 const ScaleRef &sr, cudaStream_t s);
 cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int64_t batch, int np,
                          cudaStream_t s);
+// B in any mode order -> B' in one pass (perm: output mode i of the
+// [batch][N][K] order = stored mode perm[i]); complex-half only.
+cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
+                              int lb, int np, cudaStream_t s);
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
                              int t_lo, int t_hi, int overwrite, const int32_t *texp,
                              cudaStream_t s);

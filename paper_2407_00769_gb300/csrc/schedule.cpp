@@ -275,18 +275,17 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             abuf = permute_to(ia, LA, tgt);
             rec.permute_a = 1;
         }
-        {
-            std::vector<int> tgt(bo);
-            tgt.insert(tgt.end(), ko.begin(), ko.end());
-            tgt.insert(tgt.end(), no.begin(), no.end());
-            if (tgt != LB) bbuf = permute_to(ib, LB, tgt);
-        }
         int kernel;
         if (dtype == TN_C64) kernel = (rec.lm >= 6 && rec.ln >= 6 && rec.lk >= 4) ? GK_C64_TILED : GK_C64_ROWS;
         else kernel = (rec.lk >= 3 && rec.lk <= 24 && rec.ln <= 24) ? GK_LP_TC : GK_LP_ROWS;
         rec.kernel = kernel;
         rec.tile = 0;
         if (kernel == GK_LP_TC) {
+            // B goes straight from its stored order to the padded B' of
+            // Eq. 6 ([batch][N][K] complex expanded to real rows) in one pass
+            std::vector<int> tgt(bo);
+            tgt.insert(tgt.end(), no.begin(), no.end());
+            tgt.insert(tgt.end(), ko.begin(), ko.end());
             Op op;
             op.kind = OP_BPREP;
             op.phase = phase;
@@ -297,12 +296,23 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             op.bprep.lb = rec.lb;
             op.bprep.np = np;
             op.bprep.step = s;
+            op.bprep.rank = (int)tgt.size();
+            for (int i = 0; i < (int)tgt.size(); ++i)
+                op.bprep.perm[i] = (int)(std::find(LB.begin(), LB.end(), tgt[i]) - LB.begin());
             const int64_t bpbytes = ((int64_t)np * (2LL << rec.lk) * 2) << rec.lb;
             const int tmp = new_temp(bpbytes);
             op.bprep.dst = tmp;
             ops.push_back(op);
             if (phase) S.bytes_per_pass += (double)(((int64_t)esz << (rec.lk + rec.ln + rec.lb)) + bpbytes);
             bbuf = tmp;
+        } else {
+            std::vector<int> tgt(bo);
+            tgt.insert(tgt.end(), ko.begin(), ko.end());
+            tgt.insert(tgt.end(), no.begin(), no.end());
+            if (tgt != LB) {
+                bbuf = permute_to(ib, LB, tgt);
+                rec.permute_b = 1;
+            }
         }
         legs[c] = bo;
         legs[c].insert(legs[c].end(), mo.begin(), mo.end());

@@ -171,9 +171,28 @@ struct TcArgs {
     int nk;                // K chunks
     int dtype;
     int batch_a, batch_b;
+    int gm;                // m tiles per raster group
     ScaleRef sr;
     int32_t *err;
 };
+
+// Tile t -> (batch, m tile, n tile).  Tiles go in groups of `gm` m-tiles:
+// inside a group the m index runs fastest, so the tiles in flight at once
+// cover about gm m-tiles x (SMs / gm) n-tiles, whose A rows and B' columns
+// fit in L2 together; A and B' are then read from DRAM about once per group
+// instead of once per m-tile.
+__device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt,
+                                            int &nt) {
+    const int64_t per_batch = a.n_mt * a.n_nt;
+    b = t / per_batch;
+    const int64_t r = t - b * per_batch;
+    const int64_t span = (int64_t)a.gm * a.n_nt;
+    const int64_t g = r / span;
+    const int64_t in = r - g * span;
+    const int64_t gm = min((int64_t)a.gm, a.n_mt - g * a.gm);
+    mt = g * a.gm + in % gm;
+    nt = (int)(in / gm);
+}
 
 template <int BN, int BK, int STAGES>
 struct TcSmem {
@@ -240,10 +259,9 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             int8_t armed[STAGES];   // phase parity of the last load issued per stage
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
             for (int64_t t = blockIdx.x; t < args.tiles && ok; t += gridDim.x) {
-                const int nt = (int)(t % args.n_nt);
-                const int64_t rest = t / args.n_nt;
-                const int64_t mt = rest % args.n_mt;
-                const int64_t b = rest / args.n_mt;
+                int64_t b, mt;
+                int nt;
+                tile_coords(args, t, b, mt, nt);
                 for (int kc = 0; kc < args.nk; ++kc) {
                     if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
                     uint8_t *sa = smem + stage * S::stage_bytes;
@@ -323,10 +341,9 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int64_t t = blockIdx.x; t < args.tiles; t += gridDim.x) {
-            const int nt = (int)(t % args.n_nt);
-            const int64_t rest = t / args.n_nt;
-            const int64_t mt = rest % args.n_mt;
-            const int64_t b = rest / args.n_mt;
+            int64_t b, mt;
+            int nt;
+            tile_coords(args, t, b, mt, nt);
             if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
             tc_fence_after();
             const int64_t m = mt * 128 + row;
@@ -508,6 +525,11 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.dtype = d.dtype;
     a.batch_a = d.batch_a;
     a.batch_b = d.batch_b;
+    {
+        // keep a group's A rows (gm x 128 x 2K halves) within ~48 MB of L2
+        const int64_t per_mtile = (int64_t)128 * kreal * 2;
+        a.gm = (int)std::max<int64_t>(1, std::min<int64_t>(16, (48ll << 20) / per_mtile));
+    }
     a.sr = sr;
     a.err = d_err;
     switch (bk) {
