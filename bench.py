@@ -265,8 +265,9 @@ def main():
                    slice_batch_log2=sb)
     info = plan.info()
     n_slices = info["n_slices"]
-    lo = rank * n_slices // world
-    hi = (rank + 1) * n_slices // world
+    from paper_2407_00769_gb300 import shard
+    lo, cnt = shard.slice_range(rank, world, n_slices)
+    hi = lo + cnt
     amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -274,7 +275,7 @@ def main():
     def step():
         plan.contract(lo, hi - lo, out=amps)
         if world > 1:
-            dist.all_reduce(amps.view(torch.float64))
+            shard.allreduce_amplitudes(amps)
         return tn.sample(amps, 1)
 
     def barrier():
@@ -374,12 +375,19 @@ def main():
                                   "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9,
                                   "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
                               for k, v in prof.items()}}
+    # DRAM traffic per launch from the committed ncu capture, only while the
+    # kernel source is the one that was captured
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_file):
         try:
+            import hashlib
             tr = json.load(open(traffic_file))
-            if tr.get("kernel") == name and tr.get("dtype") == args.dtype:
+            src = os.path.join(ROOT, "paper_2407_00769_gb300", "csrc", "tc_gemm.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            if (tr.get("kernel") == name and tr.get("dtype") == args.dtype
+                    and tr.get("kernel_sha256_16") == sha and sb == 8):
                 roofline["traffic"] = tr.get("bytes_per_launch")
+                roofline["traffic_source"] = tr.get("source")
         except Exception:
             pass
 

@@ -189,10 +189,31 @@ int tn_contract_host(tn_plan_t *plan, int64_t slice_begin, int64_t slice_count,
                      double *h_amps, void *stream, tn_contract_report *rep);
 
 /*
- * tn_contract_batch: contract every slice of n independent plans (uneven
- * circuits) and write each one's amplitudes to d_amps[i] (device), in one
- * captured CUDA graph.  Plans must share dtype.
+ * tn_plan_set_graph: when enable != 0, tn_contract captures its launches
+ * into a CUDA graph the first time it is called with a given (slice range,
+ * d_amps, accumulate, stream) and replays the graph on later identical
+ * calls.  Needs a non-default stream (on the legacy default stream the
+ * launches are issued directly).  Off by default.
  */
+int tn_plan_set_graph(tn_plan_t *plan, int enable);
+
+/*
+ * Batched launch of many independent plans (e.g. uneven circuits): every
+ * slice of plans[i] is contracted into d_amps[i] (device, 2^n_open_i
+ * complex128, overwritten).  tn_batch_create sets up each plan's device
+ * state, spreads the plans over n_streams side streams (largest work first,
+ * to the least loaded stream) and captures all their launches into one CUDA
+ * graph; tn_batch_run replays that graph on `stream` (rep: optional timing,
+ * synchronizes).  Plans must share dtype, have profiling off, and not be
+ * used elsewhere while the batch exists.
+ */
+typedef struct tn_batch_s tn_batch_t;
+int tn_batch_create(tn_plan_t *const *plans, int32_t n, double *const *d_amps, int32_t n_streams,
+                    tn_batch_t **out);
+int tn_batch_run(tn_batch_t *batch, void *stream, tn_contract_report *rep);
+void tn_batch_destroy(tn_batch_t *batch);
+
+/* One-shot form: create (16 streams), run once, synchronize, destroy. */
 int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps, void *stream);
 
 /*
@@ -244,6 +265,67 @@ int tn_metrics(const double *d_amps, const double *d_ref, int64_t n, int32_t n_q
 
 void tn_plan_destroy(tn_plan_t *plan);
 
+/* ---- autotuner (tile choice per step) ---- */
+
+/* One timing taken by the autotuner: a GEMM step under one (kernel, tile)
+ * configuration, or a permutation. */
+typedef struct {
+    int32_t kind;          /* 0: GEMM step, 1: permutation                    */
+    int32_t lm, ln, lk, lb;/* log2 M, N, K, batch (GEMM); lm = rank (perm)     */
+    int32_t dtype;
+    int32_t kernel;        /* GEMM kernel variant (perm: -1)                   */
+    int32_t tile;          /* tile configuration (perm: stride class 0..5 =
+                              low output bits that stay low input bits)       */
+    double ms;             /* CUDA-event time of one launch                    */
+} tn_tune_record;
+
+/*
+ * tn_plan_tune: exhaustive autotuning.  Runs the slice-invariant ops and one
+ * pass of the per-slice ops on slice 0's data; every GEMM step is launched
+ * under each legal (kernel, tile) configuration, timed with CUDA events, and
+ * the fastest is kept for later tn_contract calls; every permutation is
+ * timed once.  All timings are kept as records.  Synchronizes.  Plans with
+ * tile_policy TN_TILE_EXHAUSTIVE tune themselves on their first tn_contract.
+ */
+int tn_plan_tune(tn_plan_t *plan, void *stream);
+
+/* Copy up to `capacity` autotuner records; *n_total receives how many exist. */
+int tn_tune_records(const tn_plan_t *plan, tn_tune_record *out, int32_t capacity, int32_t *n_total);
+
+/* ---- learned cost model ----
+ * A small MLP (TN_COST_NFEAT inputs -> 3 hidden ReLU layers -> 1) predicting
+ * log2 of a step's time in microseconds from its shape features; trained on
+ * the GPU by the library's own forward/backward/Adam kernels on autotuner
+ * records; used by TN_TILE_LEARNED plans to pick each GEMM step's (kernel,
+ * tile) without timing, and to compare plans by predicted time.  FP32. */
+#define TN_COST_NFEAT 26
+typedef struct tn_cost_model_s tn_cost_model_t;
+int tn_cost_model_create(int32_t hidden, uint64_t seed, tn_cost_model_t **out);
+void tn_cost_model_destroy(tn_cost_model_t *model);
+/* Get (set = 0) or set (set = 1) the flat FP32 parameter vector
+ * [W1, b1, W2, b2, W3, b3, W4, b4], each W row-major (inputs x outputs);
+ * *n_params receives its length.  Setting resets the Adam state. */
+int tn_cost_model_params(tn_cost_model_t *model, float *h_params, int64_t capacity, int64_t *n_params,
+                         int32_t set);
+/* Mean-squared-error loss of n samples (h_x: n x TN_COST_NFEAT, h_t: n) and
+ * its gradient with respect to every parameter (h_grad, may be NULL). */
+int tn_cost_model_grad(tn_cost_model_t *model, const float *h_x, const float *h_t, int32_t n,
+                       float *h_grad, double *loss, void *stream);
+/* Adam on shuffled minibatches (splitmix64(seed) order), `epochs` passes. */
+int tn_cost_model_train(tn_cost_model_t *model, const float *h_x, const float *h_t, int64_t n,
+                        int32_t epochs, int32_t batch, float lr, uint64_t seed, double *final_loss,
+                        void *stream);
+int tn_cost_model_predict(tn_cost_model_t *model, const float *h_x, int64_t n, float *h_y,
+                          void *stream);
+/* Feature rows (n x TN_COST_NFEAT) of autotuner records. */
+int tn_cost_features(const tn_tune_record *recs, int32_t n, float *out);
+/* Attach a model to a plan: with tile_policy TN_TILE_LEARNED the first
+ * tn_contract picks every GEMM step's configuration by predicted time. */
+int tn_plan_set_cost_model(tn_plan_t *plan, tn_cost_model_t *model);
+/* Predicted milliseconds of contracting every slice of the plan (GEMM
+ * steps under their current configuration + permutations). */
+int tn_plan_predict_ms(tn_plan_t *plan, tn_cost_model_t *model, double *ms, void *stream);
+
 /* ---- per-kernel timing (measurement, not for production runs) ---- */
 #define TN_KC_LEAF 0        /* leaf preparation / slice decoding            */
 #define TN_KC_PERMUTE 1     /* bit-permute transposes                       */
@@ -294,6 +376,17 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,
             int64_t K, int64_t batch, int32_t batch_a, int32_t batch_b, int32_t scale_exp,
             int32_t kernel, float *out_max, void *stream);
+
+/*
+ * tn_selftest_wait_timeout: failure-detection self-test.  Launches one small
+ * tensor-core GEMM whose TMA producer is told to issue nothing, so the MMA
+ * warp's bounded mbarrier wait runs out (about 2 s); the kernel then records
+ * an error word, frees its tensor memory and returns.  Returns TN_ETIMEOUT
+ * when the timeout was detected and reported (the expected outcome; the CUDA
+ * context stays usable), TN_OK if not, TN_ECUDA on a CUDA error.
+ * Synchronizes `stream`; allocates a few KiB of device memory.
+ */
+int tn_selftest_wait_timeout(void *stream);
 
 const char *tn_strerror(int code);
 const char *tn_last_error(void);

@@ -32,7 +32,9 @@ EXPORTED = [
     "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
-    "tn_profile", "tn_profile_read", "tn_sample_noalloc",
+    "tn_profile", "tn_profile_read", "tn_sample_noalloc", "tn_selftest_wait_timeout",
+    "tn_plan_set_graph", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
+    "tn_plan_tune", "tn_tune_records",
 ]
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum"]
 
@@ -93,6 +95,12 @@ class KernelStats(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+class TuneRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("lm", ctypes.c_int32), ("ln", ctypes.c_int32),
+                ("lk", ctypes.c_int32), ("lb", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 class StepInfo(ctypes.Structure):
     _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32),
                 ("log2_m", ctypes.c_int32), ("log2_n", ctypes.c_int32),
@@ -136,6 +144,15 @@ def lib():
         L.tn_sample.argtypes = [vp, i32, i32, vp, vp, vp]
         L.tn_metrics.argtypes = [vp, vp, i64, i32, vp, vp]
         L.tn_sample_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.tn_selftest_wait_timeout.argtypes = [vp]
+        L.tn_plan_set_graph.argtypes = [vp, ctypes.c_int]
+        L.tn_plan_tune.argtypes = [vp, vp]
+        L.tn_tune_records.argtypes = [vp, ctypes.POINTER(TuneRecord), i32, ctypes.POINTER(i32)]
+        L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i32,
+                                      ctypes.POINTER(vp)]
+        L.tn_batch_run.argtypes = [vp, vp, ctypes.POINTER(ContractReport)]
+        L.tn_batch_destroy.argtypes = [vp]
+        L.tn_batch_destroy.restype = None
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
@@ -147,7 +164,8 @@ def lib():
         L.tn_last_error.argtypes = []
         L.tn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
-            if name not in ("tn_plan_opts_default", "tn_plan_destroy", "tn_strerror", "tn_last_error"):
+            if name not in ("tn_plan_opts_default", "tn_plan_destroy", "tn_strerror", "tn_last_error",
+                            "tn_batch_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -302,6 +320,22 @@ class Plan:
             return out, {f: getattr(rep, f) for f, _ in ContractReport._fields_}
         return out
 
+    def tune(self, stream=None):
+        """Exhaustive autotuning of every GEMM step's (kernel, tile)."""
+        _check(lib().tn_plan_tune(self._h, _stream_ptr(stream)))
+
+    def tune_records(self):
+        """Every timing the autotuner took, as a list of dicts."""
+        n = ctypes.c_int32(0)
+        _check(lib().tn_tune_records(self._h, None, 0, ctypes.byref(n)))
+        arr = (TuneRecord * max(1, n.value))()
+        _check(lib().tn_tune_records(self._h, arr, n.value, ctypes.byref(n)))
+        return [{f: getattr(arr[i], f) for f, _ in TuneRecord._fields_} for i in range(n.value)]
+
+    def set_graph(self, enable: bool = True):
+        """Capture tn_contract calls into a CUDA graph and replay identical ones."""
+        _check(lib().tn_plan_set_graph(self._h, 1 if enable else 0))
+
     def profile(self, classes=None):
         """Start per-kernel-class event timing (names from KC_NAMES; None: off)."""
         mask = 0
@@ -332,11 +366,43 @@ class Plan:
 
 
 def contract_batch(plans, outs, stream=None):
+    """One-shot batched contraction of independent plans (one CUDA graph)."""
     n = len(plans)
     hs = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     ds = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     _check(lib().tn_contract_batch(hs, n, ds, _stream_ptr(stream)))
     return outs
+
+
+class Batch:
+    """Many independent plans captured into one CUDA graph (tn_batch_*);
+    run() replays it.  Keeps the plans and output tensors alive."""
+
+    def __init__(self, plans, outs, n_streams: int = 16):
+        self.plans, self.outs = list(plans), list(outs)
+        n = len(self.plans)
+        hs = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        ds = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        h = ctypes.c_void_p()
+        _check(lib().tn_batch_create(hs, n, ds, int(n_streams), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None, report: bool = False):
+        rep = ContractReport() if report else None
+        _check(lib().tn_batch_run(self._h, _stream_ptr(stream),
+                                  ctypes.byref(rep) if rep is not None else None))
+        if report:
+            return {f: getattr(rep, f) for f, _ in ContractReport._fields_}
+        return None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().tn_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
 
 
 def sample(amps, k: int = 1, stream=None):

@@ -78,6 +78,8 @@ int ensure_device(tn_plan_s *P) {
         TN_CUDA(cudaMemcpy(P->d_jobs, S.leaf_jobs.data(), S.leaf_jobs.size() * sizeof(LeafJob),
                            cudaMemcpyHostToDevice),
                 "upload leaf jobs");
+    TN_CUDA(tc_prepare(), "tensor-core kernel attributes");
+    tc_num_sms();
     P->dev_ready = true;
     return TN_OK;
 }
@@ -207,6 +209,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.batch_a = g.lb > 0;
                     d.batch_b = g.lb > 0;
                     d.np = std::max(16, 2 << g.ln);
+                    d.bn = tc_tile_bn(g.tile);
+                    d.gm = tc_tile_gm(g.tile);
                     e = launch_gemm_tc(d, sr, P->d_err, s);
                     break;
                 }
@@ -225,6 +229,201 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             return fail(TN_EINVAL, "unknown op");
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return TN_OK;
+}
+
+// Legal (kernel, tile) configurations of a GEMM op.
+std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
+    std::vector<std::pair<int, int>> c;
+    if (g.kernel == GK_C64_ROWS || g.kernel == GK_C64_TILED) {
+        c.push_back({GK_C64_ROWS, 0});
+        if (g.lm >= 6 && g.ln >= 6 && g.lk >= 4) c.push_back({GK_C64_TILED, 0});
+    } else if (g.kernel == GK_LP_ROWS) {
+        c.push_back({GK_LP_ROWS, 0});
+    } else {
+        const int np = std::max(16, 2 << g.ln);
+        const int bn_max = std::min(np, 256);
+        std::vector<int> bn_codes;
+        for (int code = 1; code <= 4; ++code)
+            if (kTcBn[code] <= bn_max && (int)bn_codes.size() < 3) bn_codes.push_back(code);
+        if (bn_codes.empty()) bn_codes.push_back(0);
+        const int64_t n_mt = std::max<int64_t>(1, ((int64_t)1 << g.lm) / 128);
+        std::vector<int> gm_codes;
+        if (n_mt > 4) {
+            for (int code = 1; code <= 4; ++code)
+                if (kTcGm[code] <= 2 * n_mt) gm_codes.push_back(code);
+        }
+        if (gm_codes.empty()) gm_codes.push_back(0);
+        for (int b : bn_codes)
+            for (int m : gm_codes) c.push_back({GK_LP_TC, b | (m << 4)});
+    }
+    return c;
+}
+
+int perm_stride_class(const PermOp &p) {
+    // how many of the 5 lowest output bits come from the 5 lowest input bits
+    const int r = p.rank;
+    int cls = 0;
+    for (int ob = 0; ob < std::min(5, r); ++ob) {
+        const int i = r - 1 - ob;              // output mode index
+        const int in_bit = r - 1 - p.perm[i];
+        if (in_bit < 5) ++cls;
+    }
+    return cls;
+}
+
+// Time one launch of an op (events around it on stream s).
+int time_op(tn_plan_s *P, const Op &op, int64_t slice_base, cudaStream_t s, double &ms) {
+    cudaEvent_t e0 = take_event(P), e1 = take_event(P);
+    int launches = 0;
+    TN_CUDA(cudaEventRecord(e0, s), "event");
+    const int rc = run_op_raw(P, op, slice_base, nullptr, 0, 0, 0, s, launches);
+    TN_CUDA(cudaEventRecord(e1, s), "event");
+    if (rc != TN_OK) return rc;
+    TN_CUDA(cudaEventSynchronize(e1), "event sync");
+    float f = 0;
+    cudaEventElapsedTime(&f, e0, e1);
+    P->ev_pool.push_back(e0);
+    P->ev_pool.push_back(e1);
+    ms = f;
+    return TN_OK;
+}
+
+int tune_plan(tn_plan_s *P, cudaStream_t s) {
+    Schedule &S = P->sched;
+    const int dtype = P->opts.dtype;
+    TN_CUDA(cudaMemsetAsync(P->d_err, 0, 4, s), "memset");
+    if (dtype != TN_C64) {
+        TN_CUDA(cudaMemsetAsync(P->d_tmax, 0, (size_t)S.n_meta * 4, s), "memset");
+        TN_CUDA(cudaMemsetAsync(P->d_texp, 0, (size_t)S.n_meta * 4, s), "memset");
+    }
+    for (int phase = 0; phase < 2; ++phase)
+        for (Op &op : S.ops) {
+            if (op.phase != phase || op.kind == OP_SUM) continue;
+            if (op.kind == OP_GEMM) {
+                GemmOp &g = op.gemm;
+                double best = 1e30;
+                std::pair<int, int> pick{g.kernel, g.tile};
+                for (const auto &cand : gemm_candidates(g)) {
+                    Op trial = op;
+                    trial.gemm.kernel = cand.first;
+                    trial.gemm.tile = cand.second;
+                    double ms = 0, ms2 = 0;
+                    int rc = time_op(P, trial, 0, s, ms);       // warm
+                    if (rc == TN_OK) rc = time_op(P, trial, 0, s, ms2);
+                    if (rc != TN_OK) return rc;
+                    ms = std::min(ms, ms2);
+                    P->tune_recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, dtype, cand.first,
+                                                          cand.second, ms});
+                    if (ms < best) { best = ms; pick = cand; }
+                }
+                g.kernel = pick.first;
+                g.tile = pick.second;
+                // leave C as the chosen configuration writes it
+                double ms = 0;
+                const int rc = time_op(P, op, 0, s, ms);
+                if (rc != TN_OK) return rc;
+            } else {
+                double ms = 0;
+                const int rc = time_op(P, op, 0, s, ms);
+                if (rc != TN_OK) return rc;
+                if (op.kind == OP_PERM)
+                    P->tune_recs.push_back(tn_tune_record{1, op.perm.rank, 0, 0, 0, dtype, -1,
+                                                          perm_stride_class(op.perm), ms});
+            }
+        }
+    // keep the per-step records (tn_plan_step) in line with the choices
+    for (const Op &op : S.ops)
+        if (op.kind == OP_GEMM && op.gemm.step >= 0 && op.gemm.step < (int)S.steps.size()) {
+            S.steps[op.gemm.step].kernel = op.gemm.kernel;
+            S.steps[op.gemm.step].tile = op.gemm.tile;
+        }
+    P->tuned = true;
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    int32_t herr = 0;
+    TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
+    if (herr) return fail(TN_ETIMEOUT, "a bounded device wait gave up while tuning");
+    return TN_OK;
+}
+
+void cost_features(const tn_tune_record &r, float *f) {
+    for (int i = 0; i < TN_COST_NFEAT; ++i) f[i] = 0.0f;
+    const double esz = r.dtype == TN_C64 ? 8.0 : 4.0;
+    if (r.dtype >= 0 && r.dtype <= 2) f[6 + r.dtype] = 1.0f;
+    if (r.kind == 0) {
+        f[0] = r.lm / 32.0f;
+        f[1] = r.ln / 32.0f;
+        f[2] = r.lk / 32.0f;
+        f[3] = r.lb / 16.0f;
+        f[4] = (r.lm + r.ln + r.lk + r.lb) / 64.0f;
+        const double bytes = esz * (std::ldexp(1.0, r.lm + r.lk + r.lb) + std::ldexp(1.0, r.lk + r.ln + r.lb) +
+                                    std::ldexp(1.0, r.lm + r.ln + r.lb));
+        f[5] = (float)(std::log2(bytes) / 40.0);
+        if (r.kernel >= 0 && r.kernel <= 3) f[10 + r.kernel] = 1.0f;
+        if (r.kernel == GK_LP_TC) {
+            const int bc = r.tile & 15, gc = (r.tile >> 4) & 15;
+            if (bc < 5) f[14 + bc] = 1.0f;
+            if (gc < 5) f[19 + gc] = 1.0f;
+        }
+    } else {
+        f[9] = 1.0f;
+        f[5] = (float)(std::log2(2.0 * esz * std::ldexp(1.0, r.lm)) / 40.0);
+        f[24] = r.tile / 5.0f;
+        f[25] = r.lm / 40.0f;
+    }
+}
+
+int predict_records(tn_cost_model_t *M, const std::vector<tn_tune_record> &recs, std::vector<float> &ms,
+                    cudaStream_t s) {
+    std::vector<float> x(recs.size() * TN_COST_NFEAT), y(recs.size());
+    for (size_t i = 0; i < recs.size(); ++i) cost_features(recs[i], &x[i * TN_COST_NFEAT]);
+    const int rc = tn_cost_model_predict(M, x.data(), (int64_t)recs.size(), y.data(), s);
+    if (rc != TN_OK) return rc;
+    ms.resize(recs.size());
+    for (size_t i = 0; i < recs.size(); ++i) ms[i] = std::exp2(y[i]) * 1e-3f;   // log2 us -> ms
+    return TN_OK;
+}
+
+int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
+    Schedule &S = P->sched;
+    std::vector<tn_tune_record> recs;
+    std::vector<std::pair<int, std::pair<int, int>>> who;   // op index, candidate
+    for (int i = 0; i < (int)S.ops.size(); ++i) {
+        const Op &op = S.ops[i];
+        if (op.kind != OP_GEMM) continue;
+        const GemmOp &g = op.gemm;
+        for (const auto &cand : gemm_candidates(g)) {
+            recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second, 0});
+            who.push_back({i, cand});
+        }
+    }
+    std::vector<float> ms;
+    if (!recs.empty()) {
+        const int rc = predict_records(M, recs, ms, s);
+        if (rc != TN_OK) return rc;
+    }
+    std::vector<float> best(S.ops.size(), 1e30f);
+    for (size_t k = 0; k < recs.size(); ++k) {
+        const int i = who[k].first;
+        if (ms[k] < best[i]) {
+            best[i] = ms[k];
+            S.ops[i].gemm.kernel = who[k].second.first;
+            S.ops[i].gemm.tile = who[k].second.second;
+        }
+    }
+    for (const Op &op : S.ops)
+        if (op.kind == OP_GEMM && op.gemm.step >= 0 && op.gemm.step < (int)S.steps.size()) {
+            S.steps[op.gemm.step].kernel = op.gemm.kernel;
+            S.steps[op.gemm.step].tile = op.gemm.tile;
+        }
+    P->tuned = true;
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
     return TN_OK;
 }
 
@@ -349,31 +548,16 @@ int tn_plan_step(const tn_plan_t *P, int32_t i, tn_step_info *out) {
     return TN_OK;
 }
 
-int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *d_amps,
-                int accumulate, void *stream, tn_contract_report *rep) {
-    if (!P) return fail(TN_EINVAL, "NULL plan");
-    const int64_t n_slices = (int64_t)1 << P->sliced.size();
-    if (slice_begin < 0 || slice_count < 0 || slice_begin + slice_count > n_slices)
-        return fail(TN_EINVAL, "slice range outside [0, n_slices)");
-    if (!d_amps) return fail(TN_EINVAL, "d_amps is NULL");
-    int rc = ensure_device(P);
-    if (rc != TN_OK) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n_amps = (int64_t)1 << P->net.n_open;
-    if (slice_count == 0) {
-        if (!accumulate) TN_CUDA(cudaMemsetAsync(d_amps, 0, n_amps * 16, s), "memset");
-        if (rep) std::memset(rep, 0, sizeof(*rep));
-        return TN_OK;
-    }
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (rep) {
-        TN_CUDA(cudaEventCreate(&ev0), "event");
-        TN_CUDA(cudaEventCreate(&ev1), "event");
-        TN_CUDA(cudaEventRecord(ev0, s), "event");
-    }
+}  // extern "C"
+
+namespace {
+
+// Issue every op of one tn_contract call on stream s (no synchronization).
+int enqueue_contract(tn_plan_s *P, int64_t slice_begin, int64_t slice_count, double *d_amps,
+                     int accumulate, cudaStream_t s, int &launches) {
     const Schedule &S = P->sched;
     const bool lp = P->opts.dtype != TN_C64;
-    int launches = 0;
+    int rc;
     TN_CUDA(cudaMemsetAsync(P->d_err, 0, 4, s), "memset");
     if (lp) {
         TN_CUDA(cudaMemsetAsync(P->d_tmax, 0, (size_t)S.n_meta * 4, s), "memset");
@@ -400,6 +584,150 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
                 if (rc != TN_OK) return rc;
             }
     }
+    return TN_OK;
+}
+
+int64_t plan_passes(const tn_plan_s *P, int64_t slice_begin, int64_t slice_count) {
+    const int64_t bsize = (int64_t)1 << P->batch_log2;
+    const int64_t first = slice_begin / bsize * bsize;
+    const int64_t last = (slice_begin + slice_count - 1) / bsize * bsize;
+    return (last - first) / bsize + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tn_plan_tune(tn_plan_t *P, void *stream) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    if (P->prof_mask) return fail(TN_EINVAL, "profiling must be off while tuning");
+    int rc = ensure_device(P);
+    if (rc != TN_OK) return rc;
+    return tune_plan(P, (cudaStream_t)stream);
+}
+
+int tn_tune_records(const tn_plan_t *P, tn_tune_record *out, int32_t capacity, int32_t *n_total) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    if (n_total) *n_total = (int32_t)P->tune_recs.size();
+    for (int i = 0; i < (int)P->tune_recs.size() && i < capacity && out; ++i) out[i] = P->tune_recs[i];
+    return TN_OK;
+}
+
+int tn_cost_features(const tn_tune_record *recs, int32_t n, float *out) {
+    if (n < 0 || (n > 0 && (!recs || !out))) return fail(TN_EINVAL, "bad argument");
+    for (int i = 0; i < n; ++i) cost_features(recs[i], out + (size_t)i * TN_COST_NFEAT);
+    return TN_OK;
+}
+
+int tn_plan_set_cost_model(tn_plan_t *P, tn_cost_model_t *M) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    P->cost_model = M;
+    return TN_OK;
+}
+
+int tn_plan_predict_ms(tn_plan_t *P, tn_cost_model_t *M, double *out_ms, void *stream) {
+    if (!P || !M || !out_ms) return fail(TN_EINVAL, "NULL argument");
+    const Schedule &S = P->sched;
+    std::vector<tn_tune_record> recs;
+    std::vector<int> phase;
+    for (const Op &op : S.ops) {
+        if (op.kind == OP_GEMM)
+            recs.push_back(tn_tune_record{0, op.gemm.lm, op.gemm.ln, op.gemm.lk, op.gemm.lb, P->opts.dtype,
+                                          op.gemm.kernel, op.gemm.tile, 0});
+        else if (op.kind == OP_PERM)
+            recs.push_back(tn_tune_record{1, op.perm.rank, 0, 0, 0, P->opts.dtype, -1,
+                                          perm_stride_class(op.perm), 0});
+        else
+            continue;
+        phase.push_back(op.phase);
+    }
+    std::vector<float> ms;
+    if (!recs.empty()) {
+        const int rc = predict_records(M, recs, ms, (cudaStream_t)stream);
+        if (rc != TN_OK) return rc;
+    }
+    const double passes = (double)plan_passes(P, 0, (int64_t)1 << P->sliced.size());
+    double t = 0;
+    for (size_t i = 0; i < recs.size(); ++i) t += phase[i] ? passes * ms[i] : ms[i];
+    *out_ms = t;
+    return TN_OK;
+}
+
+int tn_plan_set_graph(tn_plan_t *P, int enable) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    P->use_graph = enable != 0;
+    if (!P->use_graph && P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    return TN_OK;
+}
+
+int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *d_amps,
+                int accumulate, void *stream, tn_contract_report *rep) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    const int64_t n_slices = (int64_t)1 << P->sliced.size();
+    if (slice_begin < 0 || slice_count < 0 || slice_begin + slice_count > n_slices)
+        return fail(TN_EINVAL, "slice range outside [0, n_slices)");
+    if (!d_amps) return fail(TN_EINVAL, "d_amps is NULL");
+    int rc = ensure_device(P);
+    if (rc != TN_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!P->tuned && P->opts.tile_policy == TN_TILE_EXHAUSTIVE && P->prof_mask == 0) {
+        rc = tune_plan(P, s);
+        if (rc != TN_OK) return rc;
+    }
+    if (!P->tuned && P->opts.tile_policy == TN_TILE_LEARNED && P->cost_model) {
+        rc = choose_by_model(P, P->cost_model, s);
+        if (rc != TN_OK) return rc;
+    }
+    const int64_t n_amps = (int64_t)1 << P->net.n_open;
+    if (slice_count == 0) {
+        if (!accumulate) TN_CUDA(cudaMemsetAsync(d_amps, 0, n_amps * 16, s), "memset");
+        if (rep) std::memset(rep, 0, sizeof(*rep));
+        return TN_OK;
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (rep) {
+        TN_CUDA(cudaEventCreate(&ev0), "event");
+        TN_CUDA(cudaEventCreate(&ev1), "event");
+        TN_CUDA(cudaEventRecord(ev0, s), "event");
+    }
+    const Schedule &S = P->sched;
+    int launches = 0;
+    const bool graph = P->use_graph && s != nullptr && s != cudaStreamLegacy &&
+                       s != cudaStreamPerThread && P->prof_mask == 0;
+    if (graph) {
+        const tn_plan_s::GraphKey key{slice_begin, slice_count, d_amps, accumulate, s};
+        if (!P->graph_exec || !(P->graph_key == key)) {
+            if (P->graph_exec) {
+                cudaGraphExecDestroy(P->graph_exec);
+                P->graph_exec = nullptr;
+            }
+            TN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+            rc = enqueue_contract(P, slice_begin, slice_count, d_amps, accumulate, s, launches);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            if (rc != TN_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ec != cudaSuccess) return cuda_fail(ec, "end capture");
+            const cudaError_t ei = cudaGraphInstantiate(&P->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                P->graph_exec = nullptr;
+                return cuda_fail(ei, "graph instantiate");
+            }
+            P->graph_key = key;
+            P->graph_launches = launches;
+        }
+        TN_CUDA(cudaGraphLaunch(P->graph_exec, s), "graph launch");
+        launches = P->graph_launches;
+    } else {
+        rc = enqueue_contract(P, slice_begin, slice_count, d_amps, accumulate, s, launches);
+        if (rc != TN_OK) return rc;
+    }
     if (rep) {
         TN_CUDA(cudaEventRecord(ev1, s), "event");
         TN_CUDA(cudaEventSynchronize(ev1), "sync");
@@ -409,8 +737,7 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
         cudaEventDestroy(ev1);
         std::memset(rep, 0, sizeof(*rep));
         rep->ms = ms;
-        const int64_t passes = (last - first) / bsize + 1;
-        rep->flops = S.flops_inv + S.flops_per_pass * (double)passes;
+        rep->flops = S.flops_inv + S.flops_per_pass * (double)plan_passes(P, slice_begin, slice_count);
         rep->slices = slice_count;
         rep->kernels = launches;
         int32_t herr = 0;
@@ -442,17 +769,134 @@ int tn_contract_host(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, dou
     return rc;
 }
 
-int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps, void *stream) {
-    if (n < 0 || (n > 0 && (!plans || !d_amps))) return fail(TN_EINVAL, "bad batch");
+struct tn_batch_s {
+    std::vector<tn_plan_s *> plans;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    double flops = 0;
+    int64_t slices = 0;
+};
+
+int tn_batch_create(tn_plan_t *const *plans, int32_t n, double *const *d_amps, int32_t n_streams,
+                    tn_batch_t **out) {
+    if (!out || n < 1 || !plans || !d_amps) return fail(TN_EINVAL, "bad batch");
+    *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (!plans[i] || plans[i]->opts.dtype != plans[0]->opts.dtype)
-            return fail(TN_EINVAL, "plans must be non-NULL and share dtype");
+        if (!plans[i] || !d_amps[i] || plans[i]->opts.dtype != plans[0]->opts.dtype)
+            return fail(TN_EINVAL, "plans and outputs must be non-NULL; plans must share dtype");
+    if (n_streams < 1) n_streams = 1;
+    n_streams = std::min(n_streams, std::min(n, 64));
     for (int i = 0; i < n; ++i) {
-        const int64_t ns = (int64_t)1 << plans[i]->sliced.size();
-        const int rc = tn_contract(plans[i], 0, ns, d_amps[i], 0, stream, nullptr);
+        const int rc = ensure_device(plans[i]);
         if (rc != TN_OK) return rc;
+        if (plans[i]->prof_mask) return fail(TN_EINVAL, "profiling must be off for a batch");
+    }
+    // longest-processing-time assignment of plans to side streams by flops
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto work = [&](int i) {
+        const tn_plan_s *P = plans[i];
+        return P->sched.flops_inv + P->sched.flops_per_pass * (double)plan_passes(P, 0, (int64_t)1 << P->sliced.size()) + 1.0;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(n_streams, 0.0);
+    std::vector<std::vector<int>> assign(n_streams);
+    for (int i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[k].push_back(i);
+        load[k] += work(i);
+    }
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> side(n_streams, nullptr);
+    std::vector<cudaEvent_t> ev(n_streams + 1, nullptr);
+    auto cleanup = [&]() {
+        for (auto x : side) if (x) cudaStreamDestroy(x);
+        for (auto e : ev) if (e) cudaEventDestroy(e);
+        if (origin) cudaStreamDestroy(origin);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    for (int k = 0; k < n_streams && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking);
+    for (int k = 0; k <= n_streams && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "batch streams"); }
+    tn_batch_s *B = new tn_batch_s();
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { delete B; cleanup(); return cuda_fail(e, "begin capture"); }
+    cudaEventRecord(ev[n_streams], origin);
+    int rc = TN_OK;
+    for (int k = 0; k < n_streams && rc == TN_OK; ++k) {
+        cudaStreamWaitEvent(side[k], ev[n_streams], 0);
+        for (int i : assign[k]) {
+            tn_plan_s *P = plans[i];
+            const int64_t ns = (int64_t)1 << P->sliced.size();
+            rc = enqueue_contract(P, 0, ns, d_amps[i], 0, side[k], B->launches);
+            if (rc != TN_OK) break;
+            B->flops += P->sched.flops_inv + P->sched.flops_per_pass * (double)plan_passes(P, 0, ns);
+            B->slices += ns;
+        }
+        cudaEventRecord(ev[k], side[k]);
+        cudaStreamWaitEvent(origin, ev[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(origin, &g);
+    if (rc == TN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cleanup();
+    if (rc != TN_OK) { delete B; return rc; }
+    if (e != cudaSuccess) { delete B; return cuda_fail(e, "batch graph"); }
+    B->plans.assign(plans, plans + n);
+    *out = B;
+    return TN_OK;
+}
+
+int tn_batch_run(tn_batch_t *B, void *stream, tn_contract_report *rep) {
+    if (!B || !B->exec) return fail(TN_EINVAL, "NULL batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (rep) {
+        TN_CUDA(cudaEventCreate(&ev0), "event");
+        TN_CUDA(cudaEventCreate(&ev1), "event");
+        TN_CUDA(cudaEventRecord(ev0, s), "event");
+    }
+    TN_CUDA(cudaGraphLaunch(B->exec, s), "graph launch");
+    if (rep) {
+        TN_CUDA(cudaEventRecord(ev1, s), "event");
+        TN_CUDA(cudaEventSynchronize(ev1), "sync");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        std::memset(rep, 0, sizeof(*rep));
+        rep->ms = ms;
+        rep->flops = B->flops;
+        rep->slices = B->slices;
+        rep->kernels = B->launches;
+        for (tn_plan_s *P : B->plans) {
+            int32_t herr = 0;
+            TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
+            if (herr) return fail(TN_ETIMEOUT, "a bounded device wait gave up");
+        }
     }
     return TN_OK;
+}
+
+void tn_batch_destroy(tn_batch_t *B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    delete B;
+}
+
+int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps, void *stream) {
+    if (n == 0) return TN_OK;
+    tn_batch_t *B = nullptr;
+    int rc = tn_batch_create(plans, n, d_amps, 16, &B);
+    if (rc != TN_OK) return rc;
+    rc = tn_batch_run(B, stream, nullptr);
+    if (rc == TN_OK) {
+        const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch sync");
+    }
+    tn_batch_destroy(B);
+    return rc;
 }
 
 int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx, double *out_prob,
@@ -530,6 +974,7 @@ int tn_profile_read(tn_plan_t *P, tn_kernel_stats *out) {
 void tn_plan_destroy(tn_plan_t *P) {
     if (!P) return;
     if (P->dev_ready) cudaDeviceSynchronize();
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     for (auto &r : P->prof) {
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
@@ -618,6 +1063,39 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
     }
     if (e != cudaSuccess) return cuda_fail(e, "tn_gemm");
     return TN_OK;
+}
+
+int tn_selftest_wait_timeout(void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int lm = 7, ln = 3, lk = 3, np = 16;
+    void *A = nullptr, *Bp = nullptr, *C = nullptr;
+    int32_t *err = nullptr;
+    cudaError_t e = cudaMalloc(&A, (size_t)(4 << (lm + lk)));
+    if (e == cudaSuccess) e = cudaMalloc(&Bp, (size_t)np * (2 << lk) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&C, (size_t)(4 << (lm + ln)));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&err, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
+    int32_t herr = 0;
+    if (e == cudaSuccess) {
+        TcGemmDesc d;
+        d.dtype = TN_F16;
+        d.A = A; d.Bp = Bp; d.C = C;
+        d.lm = lm; d.ln = ln; d.lk = lk;
+        d.batch = 1; d.batch_a = 0; d.batch_b = 0;
+        d.np = np;
+        d.withhold = 1;
+        ScaleRef sr{};
+        e = launch_gemm_tc(d, sr, err, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(A);
+    cudaFree(Bp);
+    cudaFree(C);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "tn_selftest_wait_timeout");
+    if (herr) return fail(TN_ETIMEOUT, "bounded wait gave up as intended; the kernel returned");
+    return fail(TN_OK, "no timeout was reported");
 }
 
 const char *tn_strerror(int code) {

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) permute_tiled_kernel(const T *__restrict_
                                                             void *__restrict__ out_,
                                                             const __grid_constant__ PermParams p,
                                                             int64_t ntiles, ExpandArgs ex) {
-    __shared__ T tile[1024 + 32];
+    __shared__ T tile[2][1024 + 32];
     __shared__ int64_t s_bin[4][256], s_bout[4][256];
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
         const int level = i >> 8, v = i & 255;
@@ -263,50 +263,67 @@ __global__ void __launch_bounds__(256) permute_tiled_kernel(const T *__restrict_
     }
     const int64_t out_off = (e0 & 31) + p.wr_hi_off[e0 >> 5];
     __syncthreads();
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t bin = s_bin[0][t & 255] + s_bin[1][(t >> 8) & 255] +
-                            s_bin[2][(t >> 16) & 255] + s_bin[3][(t >> 24) & 255];
-        const int64_t bout = s_bout[0][t & 255] + s_bout[1][(t >> 8) & 255] +
-                             s_bout[2][(t >> 16) & 255] + s_bout[3][(t >> 24) & 255];
-        T v[4];
-        if constexpr (sizeof(T) == 4) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
-            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-        } else {
-            const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
-            const uint4 y = *reinterpret_cast<const uint4 *>(in + bin + in_off + 2);
-            v[0] = make_uint2(x.x, x.y); v[1] = make_uint2(x.z, x.w);
-            v[2] = make_uint2(y.x, y.y); v[3] = make_uint2(y.z, y.w);
+    // two tiles per iteration (two 16-byte loads in flight per thread)
+    for (int64_t t0 = blockIdx.x; t0 < ntiles; t0 += 2 * (int64_t)gridDim.x) {
+        const int64_t t1 = t0 + gridDim.x;
+        const bool has1 = t1 < ntiles;
+        T v[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t t = h ? t1 : t0;
+            if (h && !has1) break;
+            const int64_t bin = s_bin[0][t & 255] + s_bin[1][(t >> 8) & 255] +
+                                s_bin[2][(t >> 16) & 255] + s_bin[3][(t >> 24) & 255];
+            if constexpr (sizeof(T) == 4) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
+                v[h][0] = x.x; v[h][1] = x.y; v[h][2] = x.z; v[h][3] = x.w;
+            } else {
+                const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
+                const uint4 y = *reinterpret_cast<const uint4 *>(in + bin + in_off + 2);
+                v[h][0] = make_uint2(x.x, x.y); v[h][1] = make_uint2(x.z, x.w);
+                v[h][2] = make_uint2(y.x, y.y); v[h][3] = make_uint2(y.z, y.w);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) tile[rd_slot[j]] = v[j];
-        __syncthreads();
-        T w[4];
+        for (int h = 0; h < 2; ++h) {
+            if (h && !has1) break;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) w[j] = tile[wr_slot[j]];
-        const int64_t f = bout + out_off;
-        if constexpr (EXPAND) {
-            const int K = 1 << ex.lk;
-            const int64_t k0 = f & (K - 1);
-            const int64_t n = (f >> ex.lk) & ((1 << ex.ln) - 1);
-            const int64_t b = f >> (ex.lk + ex.ln);
-            uint32_t *o = reinterpret_cast<uint32_t *>(out_);
-            const int64_t row0 = b * ex.np + 2 * n;
-            uint4 r0, r1;
-            // (re, -im): flip the sign bit of the high half; (im, re): swap halves
-            r0.x = w[0] ^ 0x80000000u; r0.y = w[1] ^ 0x80000000u;
-            r0.z = w[2] ^ 0x80000000u; r0.w = w[3] ^ 0x80000000u;
-            r1.x = __byte_perm(w[0], 0, 0x1032); r1.y = __byte_perm(w[1], 0, 0x1032);
-            r1.z = __byte_perm(w[2], 0, 0x1032); r1.w = __byte_perm(w[3], 0, 0x1032);
-            *reinterpret_cast<uint4 *>(o + row0 * K + k0) = r0;
-            *reinterpret_cast<uint4 *>(o + (row0 + 1) * K + k0) = r1;
-        } else {
-            T *out = reinterpret_cast<T *>(out_);
-            if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int j = 0; j < 4; ++j) tile[h][rd_slot[j]] = v[h][j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t t = h ? t1 : t0;
+            if (h && !has1) break;
+            const int64_t bout = s_bout[0][t & 255] + s_bout[1][(t >> 8) & 255] +
+                                 s_bout[2][(t >> 16) & 255] + s_bout[3][(t >> 24) & 255];
+            T w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = tile[h][wr_slot[j]];
+            const int64_t f = bout + out_off;
+            if constexpr (EXPAND) {
+                const int K = 1 << ex.lk;
+                const int64_t k0 = f & (K - 1);
+                const int64_t n = (f >> ex.lk) & ((1 << ex.ln) - 1);
+                const int64_t b = f >> (ex.lk + ex.ln);
+                uint32_t *o = reinterpret_cast<uint32_t *>(out_);
+                const int64_t row0 = b * ex.np + 2 * n;
+                uint4 r0, r1;
+                // (re, -im): flip the sign bit of the high half; (im, re): swap halves
+                r0.x = w[0] ^ 0x80000000u; r0.y = w[1] ^ 0x80000000u;
+                r0.z = w[2] ^ 0x80000000u; r0.w = w[3] ^ 0x80000000u;
+                r1.x = __byte_perm(w[0], 0, 0x1032); r1.y = __byte_perm(w[1], 0, 0x1032);
+                r1.z = __byte_perm(w[2], 0, 0x1032); r1.w = __byte_perm(w[3], 0, 0x1032);
+                *reinterpret_cast<uint4 *>(o + row0 * K + k0) = r0;
+                *reinterpret_cast<uint4 *>(o + (row0 + 1) * K + k0) = r1;
             } else {
-                *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
-                *reinterpret_cast<uint4 *>(out + f + 2) = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
+                T *out = reinterpret_cast<T *>(out_);
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+                    *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
+                    *reinterpret_cast<uint4 *>(out + f + 2) = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
+                }
             }
         }
         __syncthreads();

@@ -75,10 +75,21 @@ struct TcGemmDesc {
     int64_t batch;
     int batch_a, batch_b;  // 1: operand has the batch dim, 0: broadcast
     int np;                // padded real columns of B' (>= 16, power of 2)
+    int withhold = 0;      // self-test: the TMA producer issues nothing
+    int bn = 0;            // N-tile width in real columns (0: min(np, 256))
+    int gm = 0;            // m tiles per raster group (0: from the L2 budget)
 };
+
+// Tile configuration of a tensor-core step: (bn, gm) packed as
+// bn_code | gm_code << 4 (code 0 = automatic choice).
+constexpr int kTcBn[5] = {0, 256, 128, 64, 32};
+constexpr int kTcGm[6] = {0, 4, 8, 16, 32, 64};
+inline int tc_tile_bn(int tile) { return kTcBn[(tile & 15) < 5 ? (tile & 15) : 0]; }
+inline int tc_tile_gm(int tile) { return kTcGm[((tile >> 4) & 15) < 6 ? ((tile >> 4) & 15) : 0]; }
 bool tc_gemm_supported(int lk, int ln);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);
 int tc_num_sms();
+cudaError_t tc_prepare();
 
 }  // namespace tn

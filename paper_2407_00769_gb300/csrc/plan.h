@@ -58,4 +58,24 @@ struct tn_plan_s {
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<void *> owned;          // allocations to free
+    // CUDA graph of the last captured tn_contract call (tn_plan_set_graph)
+    bool use_graph = false;
+    struct GraphKey {
+        int64_t begin, count;
+        double *amps;
+        int accumulate;
+        cudaStream_t stream;
+        bool operator==(const GraphKey &o) const {
+            return begin == o.begin && count == o.count && amps == o.amps &&
+                   accumulate == o.accumulate && stream == o.stream;
+        }
+    };
+    GraphKey graph_key{};
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_launches = 0;
+    // autotuner: chosen (kernel, tile) per GEMM op live in sched.ops; every
+    // timing taken is kept as a record (the cost model's training data)
+    bool tuned = false;
+    std::vector<tn_tune_record> tune_recs;
+    struct tn_cost_model_s *cost_model = nullptr;
 };

@@ -172,6 +172,7 @@ struct TcArgs {
     int dtype;
     int batch_a, batch_b;
     int gm;                // m tiles per raster group
+    int withhold;          // self-test: issue no loads, so consumers' waits run out
     ScaleRef sr;
     int32_t *err;
 };
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer --
-        if (lane == 0) {
+        if (lane == 0 && !args.withhold) {
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -456,16 +457,28 @@ struct TcCfg {
 };
 
 template <int BN, int BK>
+cudaError_t set_attr() {
+    constexpr int ST = TcCfg<BN, BK>::STAGES;
+    using S = TcSmem<BN, BK, ST>;
+    return cudaFuncSetAttribute(gemm_tc_kernel<BN, BK, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                S::total);
+}
+
+template <int BK>
+cudaError_t set_attr_bn() {
+    cudaError_t e = set_attr<16, BK>();
+    if (e == cudaSuccess) e = set_attr<32, BK>();
+    if (e == cudaSuccess) e = set_attr<64, BK>();
+    if (e == cudaSuccess) e = set_attr<128, BK>();
+    if (e == cudaSuccess) e = set_attr<256, BK>();
+    return e;
+}
+
+template <int BN, int BK>
 cudaError_t run_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, cudaStream_t s) {
     constexpr int ST = TcCfg<BN, BK>::STAGES;
     using S = TcSmem<BN, BK, ST>;
     auto kern = gemm_tc_kernel<BN, BK, ST>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::total);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
     kern<<<(unsigned)grid, 192, S::total, s>>>(ma, mb, a);
     return cudaGetLastError();
@@ -497,13 +510,35 @@ int tc_num_sms() {
     return n;
 }
 
+// Set the dynamic shared-memory limit of every tensor-core GEMM variant on
+// the current device (must happen outside any stream capture).
+cudaError_t tc_prepare() {
+    static int done_mask = 0;  // one bit per device (first 31)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 31 && ((done_mask >> dev) & 1)) return cudaSuccess;
+    cudaError_t e = set_attr_bn<16>();
+    if (e == cudaSuccess) e = set_attr_bn<32>();
+    if (e == cudaSuccess) e = set_attr_bn<64>();
+    if (e == cudaSuccess && dev < 31) done_mask |= 1 << dev;
+    return e;
+}
+
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
     if (!tc_gemm_supported(d.lk, d.ln)) return cudaErrorInvalidValue;
+    {
+        const cudaError_t e = tc_prepare();
+        if (e != cudaSuccess) return e;
+    }
     const int kreal = 2 << d.lk;                 // 2K
     const int bk = kreal >= 64 ? 64 : kreal;     // 16, 32 or 64
-    const int bn = d.np >= 256 ? 256 : d.np;     // 16 .. 256
+    int bn = d.np >= 256 ? 256 : d.np;           // 16 .. 256
+    if (d.bn > 0) {
+        if ((d.bn & (d.bn - 1)) != 0 || d.bn < 16 || d.bn > 256) return cudaErrorInvalidValue;
+        bn = d.bn < bn ? d.bn : bn;
+    }
     const int64_t M = (int64_t)1 << d.lm;
     CUtensorMap ma, mb;
     if (!encode_3d(&ma, d.dtype, d.A, (uint64_t)kreal, (uint64_t)M,
@@ -525,7 +560,10 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.dtype = d.dtype;
     a.batch_a = d.batch_a;
     a.batch_b = d.batch_b;
-    {
+    a.withhold = d.withhold;
+    if (d.gm > 0) {
+        a.gm = d.gm;
+    } else {
         // keep a group's A rows (gm x 128 x 2K halves) within ~48 MB of L2
         const int64_t per_mtile = (int64_t)128 * kreal * 2;
         a.gm = (int)std::max<int64_t>(1, std::min<int64_t>(16, (48ll << 20) / per_mtile));

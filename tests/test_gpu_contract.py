@@ -173,3 +173,45 @@ def test_grid_30q_sliced_full_size(dtype, batch):
     got = p.contract()
     e, f = check(got, want, dtype)
     print(f"grid30 {tn.DTYPE_NAMES[dtype]} batch 2^{batch}: rel_l2={e:.3e} fidelity={f:.6f}")
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+def test_graph_replay_matches_direct_launches(dtype):
+    c, q = rqcgen.small_grid(4, 5, 12, seed=8, n_open=6)
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=4, slice_batch_log2=2)
+    direct = p.contract().cpu().numpy()
+    p.set_graph(True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        out = torch.zeros(1 << q.n_open, dtype=torch.complex128, device="cuda")
+        for _ in range(3):   # capture, then two replays
+            p.contract(out=out, stream=s)
+        s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), direct)
+    # a different range recaptures
+    with torch.cuda.stream(s):
+        part = p.contract(2, 9, stream=s)
+        s.synchronize()
+    p.set_graph(False)
+    assert np.array_equal(part.cpu().numpy(), p.contract(2, 9).cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
+def test_batch_of_uneven_circuits(dtype):
+    items = rqcgen.uneven_batch(count=12, seed=44, n_min=9, n_max=16, c_min=6, c_max=12)
+    plans = [tn.Plan(c, q, dtype=dtype, n_slice_edges=(1 if i % 3 == 0 else 0)) for i, (c, q) in
+             enumerate(items)]
+    outs = [torch.zeros(64, dtype=torch.complex128, device="cuda") for _ in items]
+    b = tn.Batch(plans, outs, n_streams=4)
+    s = torch.cuda.Stream()
+    rep = None
+    for _ in range(2):
+        rep = b.run(stream=s, report=True)
+    assert rep["slices"] == sum(p.info()["n_slices"] for p in plans)
+    for (c, q), o in zip(items, outs):
+        check(o, oracle.amplitudes(c, q), dtype)
+    # the one-shot form agrees
+    outs2 = [torch.zeros(64, dtype=torch.complex128, device="cuda") for _ in items]
+    tn.contract_batch(plans, outs2)
+    for o, o2 in zip(outs, outs2):
+        assert np.array_equal(o.cpu().numpy(), o2.cpu().numpy())

@@ -204,3 +204,13 @@ def test_paper_worked_example(kernel):
     C = torch.zeros(M, N, 2, dtype=torch.float16, device="cuda")
     tn.gemm(tn.F16, dev(A), dev(B), C, M, N, K, scale_exp=0, kernel=kernel)
     assert C.float().cpu().numpy().reshape(-1).tolist() == g["C_complex"]
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    # the tensor-core GEMM's producer is told to issue nothing: the MMA
+    # warp's mbarrier wait must give up (~2 s), report, free TMEM, return
+    L = tn.lib()
+    rc = L.tn_selftest_wait_timeout(torch.cuda.current_stream().cuda_stream)
+    assert rc == tn.TN_ETIMEOUT, L.tn_last_error()
+    # the context is still usable: a normal tensor-core GEMM is correct
+    _lp_case(tn.F16, 256, 16, 32, 1, 3)
