@@ -42,11 +42,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f16", choices=["f16", "bf16", "c64"])
+    ap.add_argument("--tile-policy", default="exhaustive", choices=["fixed", "exhaustive"],
+                    help="tile choice per GEMM step (exhaustive: autotuned in the first warm-up step)")
     ap.add_argument("--slice-batch", type=int, default=8,
                     help="log2 of the slices run together in one pass (carried as a batch mode)")
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--legs", default="grid53,batch256",
+                    help="extra workloads timed after the main line (comma list, or 'none')")
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute"],
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--lm", type=int, default=14)
@@ -237,6 +241,89 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ extra legs
+def _timed(fn, stream, flush, reps=1):
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def leg_grid53(tn, torch, dev, flush, stream, peaks):
+    """Large-slice workload: 53-qubit 6x9-minus-one grid, 12 cycles, each
+    slice's largest intermediate <= 2^30 elements; slices 0..63 in one call
+    (8 slices per pass, batched), FP16 tensor cores."""
+    import rqcgen
+    c, q = rqcgen.grid_53q()
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=1,
+                   slice_batch_log2=3)
+    info = plan.info()
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    n = 64
+    plan.contract(0, n, out=amps)
+    torch.cuda.synchronize()
+    plan.profile(["gemm_tc"])
+    ms = _timed(lambda: plan.contract(0, n, out=amps), stream, flush)
+    prof = plan.profile_read()
+    plan.profile(None)
+    flops = info["flops_per_slice"] * n + info["flops_invariant"]
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    g = prof.get("gemm_tc", {"flops": 0, "ms": 1})
+    tf = flops / (ms * 1e-3) / 1e12
+    out = {"workload": "grid6x9m1-12c: 53 qubits, 12 cycles, 21 sliced edges (cap 2^30 elements "
+                       "per slice), slices 0-63 (8 per pass), 4096 amplitudes",
+           "slices": n, "ms": ms, "tflops": tf, "slices_per_s": n / (ms * 1e-3),
+           "frac_of_dense_fp16_peak": tf / peak,
+           "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12,
+           "gemm_tc_share": g["ms"] / ms, "max_log2_elems": info["max_log2_elems"],
+           "peak_tflops": peak}
+    del plan, amps
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_batch256(tn, torch, dev, flush, stream):
+    """256 independent uneven circuits (16-28 qubits, 8-16 cycles, 64
+    amplitudes each), FP16, one CUDA graph over 16 streams; tile choices
+    from an autotuner cache built by tuning every 32nd plan."""
+    import time as _t
+    import rqcgen
+    items = rqcgen.uneven_batch()
+    t0 = _t.perf_counter()
+    plans = [tn.plan_within_budget(c, q, dtype=tn.F16) for c, q in items]
+    t_plan = _t.perf_counter() - t0
+    recs = []
+    for p in plans[::32]:
+        p.tune()
+        recs += p.tune_records()
+    for p in plans:
+        p.apply_tuning(recs)
+    outs = [torch.zeros(64, dtype=torch.complex128, device=dev) for _ in plans]
+    t0 = _t.perf_counter()
+    b = tn.Batch(plans, outs, n_streams=16)
+    t_capture = _t.perf_counter() - t0
+    rep = b.run(stream=stream, report=True)
+    ms = _timed(lambda: b.run(stream=stream), stream, flush, reps=2)
+    out = {"workload": "256 uneven circuits (16-28 qubits, 8-16 cycles), 64 amplitudes each",
+           "circuits": len(plans), "ms": ms, "circuits_per_s": len(plans) / (ms * 1e-3),
+           "amplitudes_per_s": 64 * len(plans) / (ms * 1e-3),
+           "tflops": rep["flops"] / (ms * 1e-3) / 1e12, "slices": rep["slices"],
+           "kernels_in_graph": rep["kernels"], "plan_s": t_plan, "graph_capture_s": t_capture,
+           "tuned_plans": len(plans[::32])}
+    del b, plans, outs
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -261,8 +348,9 @@ def main():
 
     c, q = rqcgen.grid_30q()
     sb = args.slice_batch if world == 1 else 0
+    policy = tn.TILE_EXHAUSTIVE if args.tile_policy == "exhaustive" else tn.TILE_FIXED
     plan = tn.Plan(c, q, dtype=dtype, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
-                   slice_batch_log2=sb)
+                   slice_batch_log2=sb, tile_policy=policy)
     info = plan.info()
     n_slices = info["n_slices"]
     from paper_2407_00769_gb300 import shard
@@ -399,7 +487,7 @@ def main():
                        "max_log2_elems": info["max_log2_elems"], "steps_per_slice": info["n_steps"],
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "parallelism": f"slices split over {world} GPU(s)",
-                       "slice_batch_log2": sb},
+                       "slice_batch_log2": sb, "tile_policy": args.tile_policy},
             "slices_per_s": n_slices / (ms * 1e-3), **acc,
             "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
     if clk:
@@ -448,6 +536,15 @@ def main():
         line["e2e"] = {"value": job_flops / e2e_s / 1e12, "unit": "TFLOP/s",
                        "h2d_bytes_per_step": leaf_bytes, "d2h_bytes_per_step": int(h.nbytes),
                        "ms_per_step": e2e_s * 1e3}
+
+    legs = [x for x in args.legs.split(",") if x and x != "none"] if world == 1 else []
+    del plan
+    torch.cuda.empty_cache()
+    side = torch.cuda.Stream()
+    if "grid53" in legs:
+        line["grid53"] = leg_grid53(tn, torch, dev, flush, stream, peaks)
+    if "batch256" in legs:
+        line["batch256"] = leg_batch256(tn, torch, dev, flush, side)
 
     if not args.no_cpu_baseline and world == 1:
         full, sample, threads = oracle_sample()

@@ -92,6 +92,11 @@ typedef struct {
     int32_t slice_batch_log2; /* run 2^this consecutive slices in one pass, the
                                  batch carried as an extra tensor mode (>= 0)    */
     int32_t tile_policy;      /* TN_TILE_*                                       */
+    int32_t small_log2;       /* complex-half plans: tensors of at most
+                                 2^small_log2 elements are stored complex64
+                                 (0: default 16; > 40: every tensor)            */
+    int32_t no_tensor_cores;  /* 1: complex-half steps on CUDA cores only
+                                 (validation of the tensor-core path)           */
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *ctx);
@@ -138,6 +143,9 @@ typedef struct {
     int32_t kernel;               /* which GEMM kernel variant runs this step    */
     int32_t tile;                 /* tile configuration index                    */
     int32_t permute_b;            /* 1 if B is permuted before the GEMM          */
+    int32_t scale_headroom;       /* calibrated extra 2^e of the step's output   */
+    int32_t storage;              /* bit 0: A, bit 1: B, bit 2: C stored
+                                     complex-half (else complex64)               */
 } tn_step_info;
 
 /*
@@ -276,6 +284,8 @@ typedef struct {
     int32_t kernel;        /* GEMM kernel variant (perm: -1)                   */
     int32_t tile;          /* tile configuration (perm: stride class 0..5 =
                               low output bits that stay low input bits)       */
+    int32_t step;          /* plan step of a GEMM record (perm: -1)            */
+    int32_t pad_;
     double ms;             /* CUDA-event time of one launch                    */
 } tn_tune_record;
 
@@ -288,6 +298,12 @@ typedef struct {
  * tile_policy TN_TILE_EXHAUSTIVE tune themselves on their first tn_contract.
  */
 int tn_plan_tune(tn_plan_t *plan, void *stream);
+
+/* Autotuner cache: for every GEMM step of `plan`, pick the fastest
+ * configuration among `recs` (records from tuning other plans) whose
+ * signature -- (log2 M, N, K, batch), dtype and kernel family -- matches
+ * the step; steps without a matching record keep their configuration. */
+int tn_plan_apply_tuning(tn_plan_t *plan, const tn_tune_record *recs, int32_t n);
 
 /* Copy up to `capacity` autotuner records; *n_total receives how many exist. */
 int tn_tune_records(const tn_plan_t *plan, tn_tune_record *out, int32_t capacity, int32_t *n_total);

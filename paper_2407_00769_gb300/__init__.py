@@ -35,7 +35,11 @@ EXPORTED = [
     "tn_profile", "tn_profile_read", "tn_sample_noalloc", "tn_selftest_wait_timeout",
     "tn_plan_set_graph", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
     "tn_plan_tune", "tn_tune_records",
+    "tn_cost_model_create", "tn_cost_model_destroy", "tn_cost_model_params", "tn_cost_model_grad",
+    "tn_cost_model_train", "tn_cost_model_predict", "tn_cost_features", "tn_plan_set_cost_model",
+    "tn_plan_predict_ms", "tn_plan_apply_tuning",
 ]
+COST_NFEAT = 26
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum"]
 
 
@@ -68,7 +72,9 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("max_log2_elems", ctypes.c_int32),
                 ("n_slice_edges", ctypes.c_int32), ("path_seed", ctypes.c_uint64),
                 ("path_trials", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
-                ("tile_policy", ctypes.c_int32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("tile_policy", ctypes.c_int32), ("small_log2", ctypes.c_int32),
+                ("no_tensor_cores", ctypes.c_int32),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -98,7 +104,8 @@ class KernelStats(ctypes.Structure):
 class TuneRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("lm", ctypes.c_int32), ("ln", ctypes.c_int32),
                 ("lk", ctypes.c_int32), ("lb", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32), ("ms", ctypes.c_double)]
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32), ("step", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 class StepInfo(ctypes.Structure):
@@ -107,7 +114,8 @@ class StepInfo(ctypes.Structure):
                 ("log2_k", ctypes.c_int32), ("log2_batch", ctypes.c_int32),
                 ("permute_a", ctypes.c_int32), ("slice_invariant", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("permute_b", ctypes.c_int32)]
+                ("permute_b", ctypes.c_int32), ("scale_headroom", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
 
 
 _lib = None
@@ -147,6 +155,19 @@ def lib():
         L.tn_selftest_wait_timeout.argtypes = [vp]
         L.tn_plan_set_graph.argtypes = [vp, ctypes.c_int]
         L.tn_plan_tune.argtypes = [vp, vp]
+        L.tn_plan_apply_tuning.argtypes = [vp, ctypes.POINTER(TuneRecord), i32]
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L.tn_cost_model_create.argtypes = [i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        L.tn_cost_model_destroy.argtypes = [vp]
+        L.tn_cost_model_destroy.restype = None
+        L.tn_cost_model_params.argtypes = [vp, f32p, i64, ctypes.POINTER(i64), i32]
+        L.tn_cost_model_grad.argtypes = [vp, f32p, f32p, i32, f32p, ctypes.POINTER(ctypes.c_double), vp]
+        L.tn_cost_model_train.argtypes = [vp, f32p, f32p, i64, i32, i32, ctypes.c_float,
+                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), vp]
+        L.tn_cost_model_predict.argtypes = [vp, f32p, i64, f32p, vp]
+        L.tn_cost_features.argtypes = [ctypes.POINTER(TuneRecord), i32, f32p]
+        L.tn_plan_set_cost_model.argtypes = [vp, vp]
+        L.tn_plan_predict_ms.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), vp]
         L.tn_tune_records.argtypes = [vp, ctypes.POINTER(TuneRecord), i32, ctypes.POINTER(i32)]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i32,
                                       ctypes.POINTER(vp)]
@@ -165,7 +186,7 @@ def lib():
         L.tn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("tn_plan_opts_default", "tn_plan_destroy", "tn_strerror", "tn_last_error",
-                            "tn_batch_destroy"):
+                            "tn_batch_destroy", "tn_cost_model_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -239,7 +260,8 @@ class Plan:
     def __init__(self, circuit, query, dtype: int = F16, max_log2_elems: int = 0,
                  n_slice_edges: int = 0, seed: int = 1, trials: int = 1,
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, small_log2: int = 0,
+                 no_tensor_cores: bool = False):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
@@ -252,6 +274,8 @@ class Plan:
         opts.path_trials = int(trials)
         opts.slice_batch_log2 = int(slice_batch_log2)
         opts.tile_policy = int(tile_policy)
+        opts.small_log2 = int(small_log2)
+        opts.no_tensor_cores = 1 if no_tensor_cores else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()
@@ -324,6 +348,15 @@ class Plan:
         """Exhaustive autotuning of every GEMM step's (kernel, tile)."""
         _check(lib().tn_plan_tune(self._h, _stream_ptr(stream)))
 
+    def apply_tuning(self, records):
+        """Reuse other plans' autotuner records (same step signatures)."""
+        n = len(records)
+        arr = (TuneRecord * max(1, n))()
+        for i, r in enumerate(records):
+            for f, _ in TuneRecord._fields_:
+                setattr(arr[i], f, r.get(f, 0))
+        _check(lib().tn_plan_apply_tuning(self._h, arr, n))
+
     def tune_records(self):
         """Every timing the autotuner took, as a list of dicts."""
         n = ctypes.c_int32(0)
@@ -331,6 +364,16 @@ class Plan:
         arr = (TuneRecord * max(1, n.value))()
         _check(lib().tn_tune_records(self._h, arr, n.value, ctypes.byref(n)))
         return [{f: getattr(arr[i], f) for f, _ in TuneRecord._fields_} for i in range(n.value)]
+
+    def set_cost_model(self, model):
+        """Attach a CostModel (used by tile_policy=TILE_LEARNED)."""
+        _check(lib().tn_plan_set_cost_model(self._h, model.handle if model else None))
+        self._model = model
+
+    def predict_ms(self, model, stream=None) -> float:
+        out = ctypes.c_double(0)
+        _check(lib().tn_plan_predict_ms(self._h, model.handle, ctypes.byref(out), _stream_ptr(stream)))
+        return out.value
 
     def set_graph(self, enable: bool = True):
         """Capture tn_contract calls into a CUDA graph and replay identical ones."""
@@ -363,6 +406,107 @@ class Plan:
         if report:
             return h, {f: getattr(rep, f) for f, _ in ContractReport._fields_}
         return h
+
+
+def plan_within_budget(circuit, query, dtype=F16, max_log2_elems=24, trials=4,
+                       workspace_budget=1 << 30, **kw):
+    """Plan with automatic slicing under a width cap, running as many of the
+    slices together (slice_batch_log2) as fit in ``workspace_budget`` bytes:
+    fewer launches where memory allows, plain slicing where it does not."""
+    base = Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
+                trials=trials, torch_allocator=False)
+    s = base.info()["n_slice_edges"]
+    for b in range(min(s, 16), -1, -1):
+        p = Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
+                 trials=trials, slice_batch_log2=b, torch_allocator=False)
+        if p.info()["workspace_bytes"] <= workspace_budget or b == 0:
+            return Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
+                        trials=trials, slice_batch_log2=b, **kw)
+    return base
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def cost_features(records) -> np.ndarray:
+    """Feature rows (n x COST_NFEAT) of autotuner records (dicts)."""
+    n = len(records)
+    arr = (TuneRecord * max(1, n))()
+    for i, r in enumerate(records):
+        for f, _ in TuneRecord._fields_:
+            setattr(arr[i], f, r.get(f, 0))
+    out = np.zeros((n, COST_NFEAT), dtype=np.float32)
+    _check(lib().tn_cost_features(arr, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def cost_targets(records) -> np.ndarray:
+    """Training targets: log2 of each record's time in microseconds."""
+    return np.log2(np.array([max(r["ms"], 1e-6) * 1e3 for r in records], dtype=np.float64)).astype(np.float32)
+
+
+class CostModel:
+    """The learned cost model (tn_cost_model_*): MLP trained on the GPU."""
+
+    def __init__(self, hidden: int = 128, seed: int = 1):
+        h = ctypes.c_void_p()
+        _check(lib().tn_cost_model_create(int(hidden), int(seed), ctypes.byref(h)))
+        self._h = h
+        self.hidden = hidden
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().tn_cost_model_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def params(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        _check(lib().tn_cost_model_params(self._h, None, 0, ctypes.byref(n), 0))
+        out = np.zeros(n.value, dtype=np.float32)
+        _check(lib().tn_cost_model_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          n.value, ctypes.byref(n), 0))
+        return out
+
+    def set_params(self, p):
+        a, ptr = _f32(p)
+        n = ctypes.c_int64(0)
+        _check(lib().tn_cost_model_params(self._h, ptr, a.size, ctypes.byref(n), 1))
+
+    def grad(self, x, t, stream=None):
+        xa, xp = _f32(x)
+        ta, tp = _f32(t)
+        g = np.zeros(self.params().size, dtype=np.float32)
+        loss = ctypes.c_double(0)
+        _check(lib().tn_cost_model_grad(self._h, xp, tp, int(ta.size),
+                                        g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value, g
+
+    def train(self, x, t, epochs=20, batch=256, lr=1e-3, seed=1, stream=None) -> float:
+        xa, xp = _f32(x)
+        ta, tp = _f32(t)
+        loss = ctypes.c_double(0)
+        _check(lib().tn_cost_model_train(self._h, xp, tp, int(ta.size), int(epochs), int(batch),
+                                         float(lr), int(seed), ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def predict(self, x, stream=None) -> np.ndarray:
+        xa, xp = _f32(x)
+        y = np.zeros(xa.shape[0], dtype=np.float32)
+        _check(lib().tn_cost_model_predict(self._h, xp, xa.shape[0],
+                                           y.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           _stream_ptr(stream)))
+        return y
 
 
 def contract_batch(plans, outs, stream=None):

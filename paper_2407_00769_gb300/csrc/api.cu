@@ -59,10 +59,18 @@ int ensure_device(tn_plan_s *P) {
     P->d_ws = (char *)plan_dev_alloc(P, (size_t)S.ws_bytes);
     P->d_store = (double2 *)plan_dev_alloc(P, std::max<size_t>(16, P->leaf_store.size() * 16));
     P->d_jobs = (LeafJob *)plan_dev_alloc(P, std::max<size_t>(64, S.leaf_jobs.size() * sizeof(LeafJob)));
-    P->d_tmax = (float *)plan_dev_alloc(P, std::max<size_t>(64, (size_t)S.n_meta * 4));
-    P->d_texp = (int32_t *)plan_dev_alloc(P, std::max<size_t>(64, (size_t)S.n_meta * 4));
+    P->d_tmax = (float *)plan_dev_alloc(P, std::max<size_t>(64, (size_t)(S.n_meta + S.n_meta_extra) * 4));
+    P->d_texp = (int32_t *)plan_dev_alloc(P, std::max<size_t>(64, (size_t)(S.n_meta + S.n_meta_extra) * 4));
     P->d_err = (int32_t *)plan_dev_alloc(P, 64);
-    if (!P->d_ws || !P->d_store || !P->d_jobs || !P->d_tmax || !P->d_texp || !P->d_err) {
+    P->d_stepcorr = (double2 *)plan_dev_alloc(P, std::max<size_t>(64, S.steps.size() * sizeof(double2)));
+    size_t split_bytes = 64;
+    for (const Op &op : S.ops)
+        if (op.kind == OP_GEMM && op.gemm.kernel == GK_LP_TC)
+            split_bytes = std::max(split_bytes, tc_split_bytes(op.gemm.lm, op.gemm.ln, op.gemm.lk,
+                                                               (int64_t)1 << op.gemm.lb));
+    P->d_splitk = (float *)plan_dev_alloc(P, split_bytes);
+    if (!P->d_ws || !P->d_store || !P->d_jobs || !P->d_tmax || !P->d_texp || !P->d_err || !P->d_stepcorr ||
+        !P->d_splitk) {
         plan_dev_free_all(P);
         return fail(TN_ENOMEM, "device allocation of the plan workspace (" +
                                    std::to_string(S.ws_bytes) + " bytes) failed");
@@ -78,6 +86,12 @@ int ensure_device(tn_plan_s *P) {
         TN_CUDA(cudaMemcpy(P->d_jobs, S.leaf_jobs.data(), S.leaf_jobs.size() * sizeof(LeafJob),
                            cudaMemcpyHostToDevice),
                 "upload leaf jobs");
+    {
+        // per-step rounding compensation: 1 until a step measures its own
+        std::vector<double2> ones(std::max<size_t>(1, S.steps.size()), make_double2(1.0, 0.0));
+        TN_CUDA(cudaMemcpy(P->d_stepcorr, ones.data(), ones.size() * sizeof(double2), cudaMemcpyHostToDevice),
+                "init step corrections");
+    }
     TN_CUDA(tc_prepare(), "tensor-core kernel attributes");
     tc_num_sms();
     P->dev_ready = true;
@@ -98,7 +112,7 @@ int op_class(const tn_plan_s *P, const Op &op, double &flops, double &bytes) {
             }
             return TN_KC_LEAF;
         }
-        case OP_PERM: bytes = 2 * std::ldexp(esz, op.perm.rank); return TN_KC_PERMUTE;
+        case OP_PERM: bytes = 2 * std::ldexp((double)op.perm.esz, op.perm.rank); return TN_KC_PERMUTE;
         case OP_BPREP: {
             const double b = std::ldexp(1.0, op.bprep.lb);
             bytes = b * (std::ldexp(esz, op.bprep.lk + op.bprep.ln) + (double)op.bprep.np * std::ldexp(4.0, op.bprep.lk));
@@ -107,10 +121,12 @@ int op_class(const tn_plan_s *P, const Op &op, double &flops, double &bytes) {
         case OP_GEMM: {
             const GemmOp &g = op.gemm;
             flops = 8.0 * std::ldexp(1.0, g.lm + g.ln + g.lk + g.lb);
+            const double ea = dtype == TN_C64 ? 8 : (g.ta ? 4 : 8), eb = dtype == TN_C64 ? 8 : (g.tb ? 4 : 8),
+                         ec = dtype == TN_C64 ? 8 : (g.tc ? 4 : 8);
             const double bsz = g.kernel == GK_LP_TC
                                    ? std::max(16.0, std::ldexp(2.0, g.ln)) * std::ldexp(4.0, g.lk)
-                                   : std::ldexp(esz, g.lk + g.ln);
-            bytes = std::ldexp(1.0, g.lb) * (std::ldexp(esz, g.lm + g.lk) + bsz + std::ldexp(esz, g.lm + g.ln));
+                                   : std::ldexp(eb, g.lk + g.ln);
+            bytes = std::ldexp(1.0, g.lb) * (std::ldexp(ea, g.lm + g.lk) + bsz + std::ldexp(ec, g.lm + g.ln));
             if (g.kernel == GK_LP_TC) return TN_KC_GEMM_TC;
             if (g.kernel == GK_LP_ROWS) return TN_KC_GEMM_LP;
             return TN_KC_GEMM_C64;
@@ -163,13 +179,15 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             break;
         case OP_PERM: {
             const PermParams pp = make_perm_params(op.perm.rank, op.perm.perm);
-            e = launch_permute(ws + op.perm.src, ws + op.perm.dst, pp, esz, s);
+            e = launch_permute(ws + op.perm.src, ws + op.perm.dst, pp, op.perm.esz, s);
             ++launches;
             break;
         }
         case OP_BPREP:
             e = launch_bprep_perm(ws + op.bprep.src, ws + op.bprep.dst, op.bprep.rank, op.bprep.perm,
-                                  op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, s);
+                                  op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, op.bprep.tb, dtype,
+                                  P->d_stepcorr + op.bprep.step, P->d_tmax, P->d_texp, op.bprep.meta_src,
+                                  op.bprep.meta_dst, s);
             ++launches;
             break;
         case OP_GEMM: {
@@ -184,6 +202,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             sr.meta_b = g.meta_b;
             sr.meta_c = g.meta_c;
             sr.out_max = P->d_tmax + g.meta_c;
+            sr.headroom = g.headroom;
+            sr.err = P->d_err;
             switch (g.kernel) {
                 case GK_C64_ROWS:
                     e = launch_gemm_rows_c64((const float2 *)(ws + g.a), (const float2 *)(ws + g.b),
@@ -195,8 +215,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                                               sc, g.tile, s);
                     break;
                 case GK_LP_ROWS:
-                    e = launch_gemm_rows_lp(dtype, ws + g.a, ws + g.b, ws + g.c, g.lm, g.ln, g.lk,
-                                            batch, sa, sb, sc, sr, s);
+                    e = launch_gemm_rows_mixed(dtype, g.ta, g.tb, g.tc, ws + g.a, ws + g.b, ws + g.c, g.lm,
+                                               g.ln, g.lk, batch, sa, sb, sc, sr, s);
                     break;
                 case GK_LP_TC: {
                     TcGemmDesc d;
@@ -211,6 +231,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.np = std::max(16, 2 << g.ln);
                     d.bn = tc_tile_bn(g.tile);
                     d.gm = tc_tile_gm(g.tile);
+                    d.out_c64 = g.tc == 0;
+                    d.partial = P->d_splitk;
                     e = launch_gemm_tc(d, sr, P->d_err, s);
                     break;
                 }
@@ -222,7 +244,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
         }
         case OP_SUM:
             e = launch_slice_sum(ws + op.sum.src, dtype, op.sum, amps, P->net.n_open, t_lo, t_hi,
-                                 overwrite, P->d_texp, s);
+                                 overwrite, P->d_texp, P->d_stepcorr, (int)P->sched.steps.size(), s);
             ++launches;
             break;
         default:
@@ -254,8 +276,10 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
                 if (kTcGm[code] <= 2 * n_mt) gm_codes.push_back(code);
         }
         if (gm_codes.empty()) gm_codes.push_back(0);
+        c.push_back({GK_LP_TC, 0});   // the fixed heuristic's own choice
         for (int b : bn_codes)
-            for (int m : gm_codes) c.push_back({GK_LP_TC, b | (m << 4)});
+            for (int m : gm_codes)
+                if ((b | (m << 4)) != 0) c.push_back({GK_LP_TC, b | (m << 4)});
     }
     return c;
 }
@@ -289,6 +313,47 @@ int time_op(tn_plan_s *P, const Op &op, int64_t slice_base, cudaStream_t s, doub
     return TN_OK;
 }
 
+// Power-of-two scale calibration (complex-half plans).  Each GEMM's output
+// exponent comes from a bound, 2 K max|A| max|B|, that assumes the K terms add
+// coherently; random-phase sums grow like sqrt(K), so large-K outputs land far
+// below the top of the FP16 range and their small entries lose precision.
+// Run slice 0's pass once: after each GEMM read the stored maximum and, if it
+// is below 2^12, raise that step's exponent (headroom) so the maximum lands in
+// [2^12, 2^13) (16x below the FP16 limit), re-run it, and go on.  The
+// headrooms are then fixed, so later calls stay deterministic.
+int calibrate_plan(tn_plan_s *P, cudaStream_t s) {
+    Schedule &S = P->sched;
+    TN_CUDA(cudaMemsetAsync(P->d_err, 0, 4, s), "memset");
+    TN_CUDA(cudaMemsetAsync(P->d_tmax, 0, (size_t)S.n_meta * 4, s), "memset");
+    TN_CUDA(cudaMemsetAsync(P->d_texp, 0, (size_t)S.n_meta * 4, s), "memset");
+    for (int phase = 0; phase < 2; ++phase)
+        for (Op &op : S.ops) {
+            if (op.phase != phase || op.kind == OP_SUM) continue;
+            int launches = 0;
+            int rc = run_op_raw(P, op, 0, nullptr, 0, 0, 0, s, launches);
+            if (rc != TN_OK) return rc;
+            if (op.kind != OP_GEMM || op.gemm.tc == 0) continue;   // complex64 outputs keep e = 0
+            float mx = 0.0f;
+            TN_CUDA(cudaMemcpyAsync(&mx, P->d_tmax + op.gemm.meta_c, 4, cudaMemcpyDeviceToHost, s), "read max");
+            TN_CUDA(cudaStreamSynchronize(s), "sync");
+            if (!(mx > 0.0f) || !std::isfinite(mx) || mx >= 4096.0f) continue;
+            const int hr = std::min(100, (int)std::floor(std::log2(4096.0 / (double)mx)));
+            if (hr <= 0) continue;
+            op.gemm.headroom = hr;
+            rc = run_op_raw(P, op, 0, nullptr, 0, 0, 0, s, launches);
+            if (rc != TN_OK) return rc;
+        }
+    P->calibrated = true;
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    int32_t herr = 0;
+    TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
+    if (herr & 1) return fail(TN_ETIMEOUT, "a bounded device wait gave up while calibrating");
+    return TN_OK;
+}
+
 int tune_plan(tn_plan_s *P, cudaStream_t s) {
     Schedule &S = P->sched;
     const int dtype = P->opts.dtype;
@@ -314,7 +379,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
                     if (rc != TN_OK) return rc;
                     ms = std::min(ms, ms2);
                     P->tune_recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, dtype, cand.first,
-                                                          cand.second, ms});
+                                                          cand.second, g.step, 0, ms});
                     if (ms < best) { best = ms; pick = cand; }
                 }
                 g.kernel = pick.first;
@@ -329,7 +394,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
                 if (rc != TN_OK) return rc;
                 if (op.kind == OP_PERM)
                     P->tune_recs.push_back(tn_tune_record{1, op.perm.rank, 0, 0, 0, dtype, -1,
-                                                          perm_stride_class(op.perm), ms});
+                                                          perm_stride_class(op.perm), -1, 0, ms});
             }
         }
     // keep the per-step records (tn_plan_step) in line with the choices
@@ -345,7 +410,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
     }
     int32_t herr = 0;
     TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
-    if (herr) return fail(TN_ETIMEOUT, "a bounded device wait gave up while tuning");
+    if (herr & 1) return fail(TN_ETIMEOUT, "a bounded device wait gave up while tuning");
     return TN_OK;
 }
 
@@ -396,7 +461,8 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         if (op.kind != OP_GEMM) continue;
         const GemmOp &g = op.gemm;
         for (const auto &cand : gemm_candidates(g)) {
-            recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second, 0});
+            recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second,
+                                          g.step, 0, 0});
             who.push_back({i, cand});
         }
     }
@@ -405,13 +471,26 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         const int rc = predict_records(M, recs, ms, s);
         if (rc != TN_OK) return rc;
     }
-    std::vector<float> best(S.ops.size(), 1e30f);
+    // per op: the predicted time of the fixed heuristic's own choice and of
+    // the best candidate; move away from the default only when the model
+    // predicts a clear gain (kLearnedMargin)
+    constexpr float kLearnedMargin = 0.92f;
+    std::vector<float> best(S.ops.size(), 1e30f), dflt(S.ops.size(), -1.0f);
+    std::vector<std::pair<int, int>> pick(S.ops.size());
     for (size_t k = 0; k < recs.size(); ++k) {
         const int i = who[k].first;
+        const GemmOp &g = S.ops[i].gemm;
+        if (who[k].second.first == g.kernel && who[k].second.second == g.tile) dflt[i] = ms[k];
         if (ms[k] < best[i]) {
             best[i] = ms[k];
-            S.ops[i].gemm.kernel = who[k].second.first;
-            S.ops[i].gemm.tile = who[k].second.second;
+            pick[i] = who[k].second;
+        }
+    }
+    for (size_t i = 0; i < S.ops.size(); ++i) {
+        if (S.ops[i].kind != OP_GEMM || best[i] >= 1e29f) continue;
+        if (dflt[i] < 0 || best[i] < kLearnedMargin * dflt[i]) {
+            S.ops[i].gemm.kernel = pick[i].first;
+            S.ops[i].gemm.tile = pick[i].second;
         }
     }
     for (const Op &op : S.ops)
@@ -458,6 +537,7 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
     if (o.max_log2_elems > 40) return fail(TN_EINVAL, "max_log2_elems must be <= 40");
     if (o.slice_batch_log2 < 0 || o.slice_batch_log2 > 16) return fail(TN_EINVAL, "slice_batch_log2 must be in 0..16");
     if (o.tile_policy < 0 || o.tile_policy > 2) return fail(TN_EINVAL, "bad tile_policy");
+    if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
     try {
         tn_plan_s *P = new tn_plan_s();
         P->opts = o;
@@ -479,7 +559,9 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
             return fail(TN_EINVAL, "slice_batch_log2 exceeds the number of sliced edges");
         }
         P->batch_log2 = o.slice_batch_log2;
-        rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype, P->sched, err);
+        rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
+                            o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
+                            P->sched, err);
         if (rc != TN_OK) { delete P; return fail(rc, err); }
         // leaf store
         int64_t offs = 0;
@@ -542,6 +624,10 @@ int tn_plan_step(const tn_plan_t *P, int32_t i, tn_step_info *out) {
     out->log2_m = r.lm; out->log2_n = r.ln; out->log2_k = r.lk; out->log2_batch = r.lb;
     out->permute_a = r.permute_a;
     out->permute_b = r.permute_b;
+    out->storage = r.storage;
+    out->scale_headroom = 0;
+    for (const Op &op : P->sched.ops)
+        if (op.kind == OP_GEMM && op.gemm.step == i) out->scale_headroom = op.gemm.headroom;
     out->slice_invariant = r.invariant;
     out->kernel = r.kernel;
     out->tile = r.tile;
@@ -606,6 +692,38 @@ int tn_plan_tune(tn_plan_t *P, void *stream) {
     return tune_plan(P, (cudaStream_t)stream);
 }
 
+int tn_plan_apply_tuning(tn_plan_t *P, const tn_tune_record *recs, int32_t n) {
+    if (!P || n < 0 || (n > 0 && !recs)) return fail(TN_EINVAL, "bad argument");
+    auto family = [](int k) { return (k == GK_C64_ROWS || k == GK_C64_TILED) ? 0 : (k == GK_LP_ROWS ? 1 : 2); };
+    Schedule &S = P->sched;
+    for (Op &op : S.ops) {
+        if (op.kind != OP_GEMM) continue;
+        GemmOp &g = op.gemm;
+        double best = 1e300;
+        for (int i = 0; i < n; ++i) {
+            const tn_tune_record &r = recs[i];
+            if (r.kind != 0 || r.dtype != P->opts.dtype || r.lm != g.lm || r.ln != g.ln || r.lk != g.lk ||
+                r.lb != g.lb || family(r.kernel) != family(g.kernel))
+                continue;
+            if (r.ms < best) {
+                best = r.ms;
+                g.kernel = r.kernel;
+                g.tile = r.tile;
+            }
+        }
+        if (g.step >= 0 && g.step < (int)S.steps.size()) {
+            S.steps[g.step].kernel = g.kernel;
+            S.steps[g.step].tile = g.tile;
+        }
+    }
+    P->tuned = true;
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    return TN_OK;
+}
+
 int tn_tune_records(const tn_plan_t *P, tn_tune_record *out, int32_t capacity, int32_t *n_total) {
     if (!P) return fail(TN_EINVAL, "NULL plan");
     if (n_total) *n_total = (int32_t)P->tune_recs.size();
@@ -633,10 +751,10 @@ int tn_plan_predict_ms(tn_plan_t *P, tn_cost_model_t *M, double *out_ms, void *s
     for (const Op &op : S.ops) {
         if (op.kind == OP_GEMM)
             recs.push_back(tn_tune_record{0, op.gemm.lm, op.gemm.ln, op.gemm.lk, op.gemm.lb, P->opts.dtype,
-                                          op.gemm.kernel, op.gemm.tile, 0});
+                                          op.gemm.kernel, op.gemm.tile, op.gemm.step, 0, 0});
         else if (op.kind == OP_PERM)
             recs.push_back(tn_tune_record{1, op.perm.rank, 0, 0, 0, P->opts.dtype, -1,
-                                          perm_stride_class(op.perm), 0});
+                                          perm_stride_class(op.perm), -1, 0, 0});
         else
             continue;
         phase.push_back(op.phase);
@@ -673,6 +791,10 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
     int rc = ensure_device(P);
     if (rc != TN_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    if (!P->calibrated && P->opts.dtype != TN_C64 && P->prof_mask == 0) {
+        rc = calibrate_plan(P, s);
+        if (rc != TN_OK) return rc;
+    }
     if (!P->tuned && P->opts.tile_policy == TN_TILE_EXHAUSTIVE && P->prof_mask == 0) {
         rc = tune_plan(P, s);
         if (rc != TN_OK) return rc;
@@ -742,7 +864,9 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
         rep->kernels = launches;
         int32_t herr = 0;
         TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
-        if (herr) return fail(TN_ETIMEOUT, "a bounded device wait gave up");
+        if (herr & 1) return fail(TN_ETIMEOUT, "a bounded device wait gave up");
+        if (herr & 2)
+            return fail(TN_EUNSUPPORTED, "a complex-half value overflowed its power-of-two scale");
     }
     return TN_OK;
 }
@@ -873,7 +997,9 @@ int tn_batch_run(tn_batch_t *B, void *stream, tn_contract_report *rep) {
         for (tn_plan_s *P : B->plans) {
             int32_t herr = 0;
             TN_CUDA(cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost), "read error flag");
-            if (herr) return fail(TN_ETIMEOUT, "a bounded device wait gave up");
+            if (herr & 1) return fail(TN_ETIMEOUT, "a bounded device wait gave up");
+            if (herr & 2)
+                return fail(TN_EUNSUPPORTED, "a complex-half value overflowed its power-of-two scale");
         }
     }
     return TN_OK;
@@ -1052,7 +1178,10 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                 d.batch_a = batch_a ? 1 : 0;
                 d.batch_b = batch_b ? 1 : 0;
                 d.np = np;
-                e = launch_gemm_tc(d, sr, nullptr, s);
+                const size_t pb = tc_split_bytes(lm, ln, lk, batch);
+                if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
+                if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);
+                if (d.partial) cudaFreeAsync(d.partial, s);
             }
             cudaFreeAsync(bp, s);
         } else {

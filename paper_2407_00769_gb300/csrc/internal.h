@@ -79,6 +79,7 @@ struct LeafJob {          // one leaf to prepare (device-side struct)
 
 struct PermOp {
     int64_t src, dst;     // byte offsets
+    int32_t esz;          // element bytes (8: complex64, 4: complex-half)
     int32_t rank;
     int32_t perm[kMaxRank];  // output mode i (outermost first) = input mode perm[i]
 };
@@ -89,6 +90,8 @@ struct GemmOp {
     int32_t a_batched, b_batched;  // operand carries the batch modes (else broadcast)
     int32_t meta_a, meta_b, meta_c, step;
     int32_t kernel, tile;
+    int32_t headroom;     // extra power-of-two scale from calibration (complex-half)
+    int32_t ta, tb, tc;   // storage of A, B, C: 0 complex64, 1 complex-half
 };
 
 struct BprepOp {
@@ -96,6 +99,8 @@ struct BprepOp {
     int32_t lk, ln, lb, step;
     int32_t np;           // padded N' (real columns, >= 16)
     int32_t rank;         // modes of B
+    int32_t tb;           // storage of B: 0 complex64 (scaled and rounded here), 1 complex-half
+    int32_t meta_src, meta_dst;  // tb = 0: scale slots of B and of B' (B' = B 2^s)
     int32_t perm[kMaxRank];  // [batch][N][K] order: output mode i = stored mode perm[i]
 };
 
@@ -106,7 +111,14 @@ struct SumOp {
     int32_t n_batch;      // batched slice bits in the final tensor
     int32_t batch_pos[16];// bit position (from LSB) of batched slice bit j
     int32_t meta;
+    int32_t tf;           // storage of the final tensor: 0 complex64, 1 complex-half
 };
+
+// Storage rule of complex-half plans: tensors of at most 2^kSmallLog2
+// elements (leaves and small intermediates, whose values come from a few
+// gates and are far from random) stay complex64; larger ones are stored in
+// complex-half.
+constexpr int kSmallLog2 = 16;   // default of tn_plan_opts.small_log2
 
 struct Op {
     int32_t kind = 0;
@@ -127,6 +139,7 @@ struct StepRec {
     int a, b, c;
     int lm, ln, lk, lb;
     int permute_a, permute_b;
+    int storage;
     int invariant;
     int kernel, tile;
 };

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -62,7 +63,6 @@ __device__ __forceinline__ float exp2i(int e) {   // exact 2^e, |e| <= 126
 // element in(o) = kept bits placed at keep_pos, fixed legs at the value of
 // their slice-id bit (slice decoding: bit j of the slice id is sliced edge
 // j's value).  Converts complex128 -> the contraction dtype (RN).
-template <int DT>
 __global__ void leaf_prep_kernel(const LeafJob *jobs, const double2 *store, char *ws,
                                  int64_t slice_base, float *tmax, int32_t *texp) {
     const LeafJob j = jobs[blockIdx.x];
@@ -75,17 +75,11 @@ __global__ void leaf_prep_kernel(const LeafJob *jobs, const double2 *store, char
         for (int f = 0; f < j.n_fixed; ++f)
             in |= ((slice_base >> j.fixed_bit[f]) & 1) << j.fixed_pos[f];
         const double2 v = store[j.src + in];
-        if constexpr (DT == TN_C64) {
-            reinterpret_cast<float2 *>(ws + j.dst)[o] = make_float2((float)v.x, (float)v.y);
-        } else {
-            using L = LpT<DT>;
-            const typename L::T2 h = L::from_d2(v.x, v.y);
-            reinterpret_cast<typename L::T2 *>(ws + j.dst)[o] = h;
-            const float2 f = L::to_f2(h);
-            m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
-        }
+        const float2 w = make_float2((float)v.x, (float)v.y);
+        reinterpret_cast<float2 *>(ws + j.dst)[o] = w;
+        m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
     }
-    if constexpr (DT != TN_C64) {
+    if (tmax) {
         m = warp_max(m);
         __shared__ float sm[32];
         if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -103,12 +97,10 @@ cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_
                              int dtype, int64_t slice_base, float *tmax, int32_t *texp,
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (dtype == TN_C64)
-        leaf_prep_kernel<TN_C64><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
-    else if (dtype == TN_F16)
-        leaf_prep_kernel<TN_F16><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
-    else
-        leaf_prep_kernel<TN_BF16><<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base, tmax, texp);
+    // leaves are stored complex64 in every plan; complex-half plans record
+    // each leaf's maximum for the scaling of the steps that consume it
+    leaf_prep_kernel<<<count, 32, 0, s>>>(d_jobs, d_store, ws, slice_base,
+                                          dtype == TN_C64 ? nullptr : tmax, texp);
     return cudaGetLastError();
 }
 
@@ -391,9 +383,111 @@ __global__ void bprep_gather_kernel(const uint32_t *__restrict__ B, uint32_t *__
     }
 }
 
+// Complex64 B (a small tensor) -> B' in complex-half, one block: every
+// element is rounded to the plan's dtype here, and the rounding's component
+// along B, alpha = <B, B~ - B> / <B, B>, is measured (FP64, fixed order) so
+// the final sum can divide the factor (1 + alpha) out exactly (the network is
+// linear in B): corr = 1 / (1 + alpha).
+template <int DT>
+__global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restrict__ B,
+                                                         uint32_t *__restrict__ Bp, int lk, int ln,
+                                                         int lb, int np,
+                                                         const __grid_constant__ PermParams p,
+                                                         int rank, double2 *corr, float *tmax,
+                                                         int32_t *texp, int meta_src, int meta_dst) {
+    using L = LpT<DT>;
+    const int K = 1 << lk, N = 1 << ln;
+    const int64_t total = ((int64_t)np * K) << lb;
+    // exact power-of-two scale bringing max |B| to [2^11, 2^12]
+    int bshift = 0;
+    {
+        const float mb = tmax[meta_src];
+        if (mb > 0.0f && isfinite(mb)) {
+            int x;
+            const float f = frexpf(mb, &x);
+            bshift = 12 - ((f == 0.5f) ? x - 1 : x);
+            bshift = max(-120, min(120, bshift));
+        }
+    }
+    const float scale = __int_as_float((127 + bshift) << 23);
+    float bmax = 0.0f;
+    double nr = 0.0, ni = 0.0, den = 0.0;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = (int)(i % K);
+        const int64_t row = i / K;
+        const int rr = (int)(row % np);
+        const int64_t b = row / np;
+        const int n = rr >> 1, co = rr & 1;
+        uint32_t v = 0;
+        if (n < N) {
+            const int64_t tidx = ((b * N + n) << lk) | k;
+            int64_t src = 0;
+            for (int t = 0; t < rank; ++t)
+                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
+            const float2 x0 = B[src];
+            const float2 x = make_float2(x0.x * scale, x0.y * scale);
+            const typename L::T2 h = L::from_f2(x);
+            const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
+            v = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
+            if (co == 0) {
+                const float2 r = L::to_f2(h);
+                bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+                const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
+                nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
+                ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
+                den += (double)x.x * x.x + (double)x.y * x.y;
+            }
+        }
+        Bp[i] = v;
+    }
+    __shared__ double sh[3][1024];
+    __shared__ float smax[1024];
+    sh[0][threadIdx.x] = nr;
+    sh[1][threadIdx.x] = ni;
+    sh[2][threadIdx.x] = den;
+    smax[threadIdx.x] = bmax;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+            smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tmax[meta_dst] = smax[0];
+        texp[meta_dst] = texp[meta_src] + bshift;
+    }
+    if (threadIdx.x == 0 && corr) {
+        double fr = 1.0, fi = 0.0;
+        if (sh[2][0] > 0.0) {
+            // 1 / (1 + alpha)
+            const double ar = 1.0 + sh[0][0] / sh[2][0], ai = sh[1][0] / sh[2][0];
+            const double d = ar * ar + ai * ai;
+            fr = ar / d;
+            fi = -ai / d;
+        }
+        *corr = make_double2(fr, fi);
+    }
+}
+
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
-                              int lb, int np, cudaStream_t s) {
+                              int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s) {
     const ExpandArgs ex{lk, ln, np};
+    // direct-gather table: outer_in[t] = input bit position of target bit t
+    PermParams g;
+    std::memset(&g, 0, sizeof(g));
+    for (int i = 0; i < rank; ++i) g.outer_in[rank - 1 - i] = (int8_t)(rank - 1 - perm[i]);
+    if (tb == 0) {
+        if (dtype == TN_F16)
+            bprep_c64_kernel<TN_F16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,
+                                                        np, g, rank, corr, tmax, texp, meta_src, meta_dst);
+        else
+            bprep_c64_kernel<TN_BF16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,
+                                                         np, g, rank, corr, tmax, texp, meta_src, meta_dst);
+        return cudaGetLastError();
+    }
     if (rank >= 10 && lk >= 2 && np == 2 << ln) {
         const PermParams pp = make_perm_params(rank, perm);
         if (pp.tile_bits == 10 && pp.lin == 5 && pp.lout == 5 && pp.n_outer <= 32) {
@@ -403,10 +497,6 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
             return cudaGetLastError();
         }
     }
-    // direct gather: outer_in[t] = input bit position of target bit t
-    PermParams g;
-    std::memset(&g, 0, sizeof(g));
-    for (int i = 0; i < rank; ++i) g.outer_in[rank - 1 - i] = (int8_t)(rank - 1 - perm[i]);
     const int64_t total = ((int64_t)np << lk) << lb;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((total + threads - 1) / threads, 8192);
@@ -424,12 +514,22 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 constexpr int kRows = 128;
 constexpr int kKC = 32;
 
-template <typename T, int NC, int DT>
+// operand conversion: complex64 as is, complex-half widened to FP32
+template <typename T, int DT>
+__device__ __forceinline__ float2 widen(T v) {
+    if constexpr (std::is_same<T, float2>::value) return v;
+    else return LpT<DT>::to_f2(v);
+}
+
+// Operand and result storage may differ (complex-half plans keep small
+// tensors in complex64): TA, TB, TC are float2 or the plan's complex-half
+// type, DT the plan's dtype.
+template <typename TA, typename TB, typename TC, int NC, int DT>
 __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
-    const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C, int lm, int ln, int lk,
+    const TA *__restrict__ A, const TB *__restrict__ B, TC *__restrict__ C, int lm, int ln, int lk,
     int64_t sa, int64_t sb, int64_t sc, ScaleRef sr) {
     constexpr int KC = kKC;
-    __shared__ __align__(16) T As[kRows * KC];
+    __shared__ __align__(16) TA As[kRows * KC];
     __shared__ float2 Bs[KC][NC];
     const int64_t M = (int64_t)1 << lm;
     const int N = 1 << ln, K = 1 << lk;
@@ -437,9 +537,9 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const int64_t m0 = (int64_t)blockIdx.x * kRows;
     const int n0 = blockIdx.y * NC;
     const int nc = min(NC, N);
-    const T *Ab = A + b * sa;
-    const T *Bb = B + b * sb;
-    T *Cb = C + b * sc;
+    const TA *Ab = A + b * sa;
+    const TB *Bb = B + b * sb;
+    TC *Cb = C + b * sc;
     const int rows = (int)min((int64_t)kRows, M - m0);
     float2 acc[NC];
 #pragma unroll
@@ -449,7 +549,7 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
         __syncthreads();
         // A tile: rows x kc elements; when kc == K the tile is contiguous
         {
-            const int per16 = 16 / (int)sizeof(T);
+            const int per16 = 16 / (int)sizeof(TA);
             const int total = rows * kc;
             if (kc == K && (total % per16) == 0) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(Ab + m0 * K);
@@ -464,16 +564,12 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
         }
         for (int i = threadIdx.x; i < kc * nc; i += kRows) {
             const int kk = i / nc, j = i % nc;
-            const T v = Bb[(int64_t)(k0 + kk) * N + n0 + j];
-            if constexpr (DT == TN_C64) Bs[kk][j] = v;
-            else Bs[kk][j] = LpT<DT>::to_f2(v);
+            Bs[kk][j] = widen<TB, DT>(Bb[(int64_t)(k0 + kk) * N + n0 + j]);
         }
         __syncthreads();
         if (threadIdx.x < rows) {
             for (int kk = 0; kk < kc; ++kk) {
-                float2 a;
-                if constexpr (DT == TN_C64) a = As[threadIdx.x * kc + kk];
-                else a = LpT<DT>::to_f2(As[threadIdx.x * kc + kk]);
+                const float2 a = widen<TA, DT>(As[threadIdx.x * kc + kk]);
 #pragma unroll
                 for (int j = 0; j < NC; ++j) {
                     if (j < nc) {
@@ -487,15 +583,26 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     }
     if (threadIdx.x >= rows) return;
     const int64_t m = m0 + threadIdx.x;
-    T *crow = Cb + m * N + n0;
-    if constexpr (DT == TN_C64) {
+    TC *crow = Cb + m * N + n0;
+    if constexpr (std::is_same<TC, float2>::value) {
+        // complex64 result: no rounding to complex-half, no scaling (e = 0);
+        // in complex-half plans its exponent and maximum feed later steps
+        float mx = 0.f;
 #pragma unroll
         for (int j = 0; j < NC; ++j)
-            if (j < nc) crow[j] = acc[j];
+            if (j < nc) {
+                crow[j] = acc[j];
+                mx = fmaxf(mx, fmaxf(fabsf(acc[j].x), fabsf(acc[j].y)));
+            }
+        if (sr.tmax) {
+            if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+                sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b];
+            if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+        }
     } else {
         // power-of-two scaling (exact): e from the operands' recorded maxima
         int e;
-        if (sr.tmax) e = scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk);
+        if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
         else e = sr.fixed_exp;
         if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
             sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
@@ -510,22 +617,24 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
                 mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
             }
         if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+        if (DT == TN_F16 && sr.err && !(mx <= 65504.0f)) atomicOr(sr.err, 2);
     }
 }
 
-template <typename T, int DT>
-static cudaError_t rows_dispatch(const T *A, const T *B, T *C, int lm, int ln, int lk,
+template <typename TA, typename TB, typename TC, int DT>
+static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, int ln, int lk,
                                  int64_t batch, int64_t sa, int64_t sb, int64_t sc,
                                  const ScaleRef &sr, cudaStream_t s) {
     const int64_t M = (int64_t)1 << lm;
     const int N = 1 << ln;
     const int64_t gx = (M + kRows - 1) / kRows;
     if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
-#define TN_ROWS_CASE(NCV)                                                                   \
-    {                                                                                        \
-        dim3 g((unsigned)gx, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);              \
-        gemm_rows_kernel<T, NCV, DT><<<g, kRows, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc, sr); \
-        break;                                                                               \
+#define TN_ROWS_CASE(NCV)                                                                        \
+    {                                                                                             \
+        dim3 g((unsigned)gx, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);                   \
+        gemm_rows_kernel<TA, TB, TC, NCV, DT><<<g, kRows, 0, s>>>(                                \
+            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr);                   \
+        break;                                                                                    \
     }
     switch (N >= 16 ? 16 : N) {
         case 1: TN_ROWS_CASE(1)
@@ -542,18 +651,38 @@ cudaError_t launch_gemm_rows_c64(const float2 *A, const float2 *B, float2 *C, in
                                  int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
                                  cudaStream_t s) {
     ScaleRef sr{};
-    return rows_dispatch<float2, TN_C64>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return rows_dispatch<float2, float2, float2, TN_C64>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+}
+
+template <int DT, typename H>
+static cudaError_t rows_mixed(int ta, int tb, int tc, const void *A, const void *B, void *C, int lm,
+                              int ln, int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
+                              const ScaleRef &sr, cudaStream_t s) {
+    // A is the larger operand, so a complex64 A implies a complex64 B
+    const int code = ta * 4 + tb * 2 + tc;
+    switch (code) {
+        case 0: return rows_dispatch<float2, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 1: return rows_dispatch<float2, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 4: return rows_dispatch<H, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 5: return rows_dispatch<H, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 6: return rows_dispatch<H, H, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 7: return rows_dispatch<H, H, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
+                                   void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
+                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s) {
+    if (dtype == TN_F16)
+        return rows_mixed<TN_F16, __half2>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return rows_mixed<TN_BF16, __nv_bfloat162>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
 }
 
 cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C, int lm, int ln,
                                 int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
                                 const ScaleRef &sr, cudaStream_t s) {
-    if (dtype == TN_F16)
-        return rows_dispatch<__half2, TN_F16>((const __half2 *)A, (const __half2 *)B, (__half2 *)C,
-                                              lm, ln, lk, batch, sa, sb, sc, sr, s);
-    return rows_dispatch<__nv_bfloat162, TN_BF16>((const __nv_bfloat162 *)A,
-                                                  (const __nv_bfloat162 *)B, (__nv_bfloat162 *)C,
-                                                  lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return launch_gemm_rows_mixed(dtype, 1, 1, 1, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
 }
 
 // ---------------------------------------------------------- tiled c64 --
@@ -668,33 +797,96 @@ cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------- split-K reduce --
+template <int DT, bool OUT_C64>
+__global__ void splitk_reduce_kernel(const float2 *__restrict__ partial, int split, void *C,
+                                     int64_t n, int lk, ScaleRef sr) {
+    int e = 0;
+    if (!OUT_C64) {
+        if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
+        else e = sr.fixed_exp;
+    }
+    if (sr.texp && blockIdx.x == 0 && threadIdx.x == 0)
+        sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
+    const float sc = exp2i(e);
+    float mx = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int p = 0; p < split; ++p) {
+            const float2 v = partial[(int64_t)p * n + i];
+            re += v.x;
+            im += v.y;
+        }
+        if constexpr (OUT_C64) {
+            const float2 w = make_float2((float)re, (float)im);
+            reinterpret_cast<float2 *>(C)[i] = w;
+            mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
+        } else {
+            const auto h = LpT<DT>::from_f2(make_float2((float)re * sc, (float)im * sc));
+            reinterpret_cast<typename LpT<DT>::T2 *>(C)[i] = h;
+            const float2 f = LpT<DT>::to_f2(h);
+            mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+        }
+    }
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0 && sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+    if (!OUT_C64 && DT == TN_F16 && sr.err && (threadIdx.x & 31) == 0 && !(mx <= 65504.0f))
+        atomicOr(sr.err, 2);
+}
+
+cudaError_t launch_splitk_reduce(const float *partial, int split, void *C, int out_c64, int dtype,
+                                 int64_t batch, int lm, int ln, int lk, const ScaleRef &sr,
+                                 cudaStream_t s) {
+    const int64_t n = batch << (lm + ln);
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)tc_num_sms() * 8);
+    const float2 *p = reinterpret_cast<const float2 *>(partial);
+    if (out_c64) {
+        if (dtype == TN_F16) splitk_reduce_kernel<TN_F16, true><<<blocks, threads, 0, s>>>(p, split, C, n, lk, sr);
+        else splitk_reduce_kernel<TN_BF16, true><<<blocks, threads, 0, s>>>(p, split, C, n, lk, sr);
+    } else {
+        if (dtype == TN_F16) splitk_reduce_kernel<TN_F16, false><<<blocks, threads, 0, s>>>(p, split, C, n, lk, sr);
+        else splitk_reduce_kernel<TN_BF16, false><<<blocks, threads, 0, s>>>(p, split, C, n, lk, sr);
+    }
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- slice sum --
 // amp[j] (+)= sum over batch index t in [t_lo, t_hi), ascending, of
-// F[idx(j, t)] * 2^-E (FP64; one slice added at a time).
-template <typename T, int DT>
-__global__ void slice_sum_kernel(const T *__restrict__ F, const SumOp op, double2 *amps,
+// c * F[idx(j, t)] * 2^-E (FP64; one slice added at a time).  F is stored
+// complex64 or complex-half; c is the product of the per-step rounding
+// compensations of the complex-half plan (1 otherwise).
+template <typename TF, int DT>
+__global__ void slice_sum_kernel(const TF *__restrict__ F, const SumOp op, double2 *amps,
                                  int n_open, int t_lo, int t_hi, int overwrite,
-                                 const int32_t *texp) {
+                                 const int32_t *texp, const double2 *__restrict__ stepcorr,
+                                 int n_steps) {
     const int64_t n = (int64_t)1 << n_open;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int64_t base = 0;
     for (int t = 0; t < n_open; ++t)
         if ((j >> t) & 1) base |= (int64_t)1 << op.open_pos[t];
-    const int E = (DT == TN_C64 || !texp) ? 0 : texp[op.meta];
+    const int E = texp ? texp[op.meta] : 0;
+    double cr = 1.0, ci = 0.0;
+    for (int k = 0; k < n_steps; ++k) {
+        const double2 f = stepcorr[k];
+        const double nr = cr * f.x - ci * f.y;
+        ci = cr * f.y + ci * f.x;
+        cr = nr;
+    }
     double2 a = overwrite ? make_double2(0.0, 0.0) : amps[j];
     for (int t = t_lo; t < t_hi; ++t) {
         int64_t idx = base;
         for (int q = 0; q < op.n_batch; ++q)
             if ((t >> q) & 1) idx |= (int64_t)1 << op.batch_pos[q];
-        double re, im;
-        if constexpr (DT == TN_C64) {
-            const float2 v = F[idx];
-            re = v.x; im = v.y;
-        } else {
-            const float2 v = LpT<DT>::to_f2(F[idx]);
-            re = ldexp((double)v.x, -E);
-            im = ldexp((double)v.y, -E);
+        const float2 v = widen<TF, DT>(F[idx]);
+        double re = ldexp((double)v.x, -E), im = ldexp((double)v.y, -E);
+        if (n_steps > 0) {
+            const double nre = cr * re - ci * im;
+            im = cr * im + ci * re;
+            re = nre;
         }
         a.x += re;
         a.y += im;
@@ -704,19 +896,26 @@ __global__ void slice_sum_kernel(const T *__restrict__ F, const SumOp op, double
 
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
                              int t_lo, int t_hi, int overwrite, const int32_t *texp,
-                             cudaStream_t s) {
+                             const double2 *stepcorr, int n_steps, cudaStream_t s) {
     const int64_t n = (int64_t)1 << n_open;
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     if (dtype == TN_C64)
         slice_sum_kernel<float2, TN_C64><<<blocks, threads, 0, s>>>(
-            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, nullptr, nullptr, 0);
+    else if (op.tf == 0 && dtype == TN_F16)
+        slice_sum_kernel<float2, TN_F16><<<blocks, threads, 0, s>>>(
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
+    else if (op.tf == 0)
+        slice_sum_kernel<float2, TN_BF16><<<blocks, threads, 0, s>>>(
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
     else if (dtype == TN_F16)
         slice_sum_kernel<__half2, TN_F16><<<blocks, threads, 0, s>>>(
-            (const __half2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+            (const __half2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
     else
         slice_sum_kernel<__nv_bfloat162, TN_BF16><<<blocks, threads, 0, s>>>(
-            (const __nv_bfloat162 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp);
+            (const __nv_bfloat162 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr,
+            n_steps);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,8 @@ struct ScaleRef {          // power-of-two scaling state (complex-half)
     int32_t meta_a, meta_b, meta_c;
     int32_t fixed_exp;     // used when tmax == nullptr (tests): e = fixed_exp
     float *out_max;        // where the epilogue records max |C| (atomicMax)
+    int32_t headroom;      // added to the bound-based exponent (calibrated per step)
+    int32_t *err;          // bit 2 set when a stored value overflowed (inf)
 };
 
 cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_store, char *ws,
@@ -54,11 +56,22 @@ cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int
                          cudaStream_t s);
 // B in any mode order -> B' in one pass (perm: output mode i of the
 // [batch][N][K] order = stored mode perm[i]); complex-half only.
+// tb = 0: B is complex64, rounded here to `dtype`, and the rounding's
+// compensation factor 1/(1 + alpha) is written to *corr.
+// and B is first scaled by an exact 2^s that brings its recorded maximum
+// (tmax[meta_src]) near 2^12; B' gets tmax[meta_dst] and texp[meta_dst] =
+// texp[meta_src] + s.
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
-                              int lb, int np, cudaStream_t s);
+                              int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s);
+cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
+                                   void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
+                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s);
+// stepcorr / n_steps: per-step rounding compensation factors of a
+// complex-half plan (n_steps = 0: none).
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
                              int t_lo, int t_hi, int overwrite, const int32_t *texp,
-                             cudaStream_t s);
+                             const double2 *stepcorr, int n_steps, cudaStream_t s);
 cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double *d_out5,
                            double *d_partials, int n_blocks, cudaStream_t s);
 cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,
@@ -78,7 +91,21 @@ struct TcGemmDesc {
     int withhold = 0;      // self-test: the TMA producer issues nothing
     int bn = 0;            // N-tile width in real columns (0: min(np, 256))
     int gm = 0;            // m tiles per raster group (0: from the L2 budget)
+    int out_c64 = 0;       // write C as complex64 (no rounding, exponent e = 0)
+    float *partial = nullptr;  // tc_split_bytes() of FP32 partials when tc_split() > 1
 };
+
+// Split-K: the tensor cores' FP32 accumulation over very long K drifts
+// (error growing with K), so a step with K > 2^kSplitLog2K complex is cut
+// into parts of that length, each accumulated separately in TMEM, and the
+// parts are added here in FP64, in part order (deterministic), then scaled
+// and rounded like the single-part epilogue.
+constexpr int kSplitLog2K = 15;
+int tc_split(int lm, int ln, int lk, int64_t batch);
+size_t tc_split_bytes(int lm, int ln, int lk, int64_t batch);
+cudaError_t launch_splitk_reduce(const float *partial, int split, void *C, int out_c64, int dtype,
+                                 int64_t batch, int lm, int ln, int lk, const ScaleRef &sr,
+                                 cudaStream_t s);
 
 // Tile configuration of a tensor-core step: (bn, gm) packed as
 // bn_code | gm_code << 4 (code 0 = automatic choice).

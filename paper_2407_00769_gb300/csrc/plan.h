@@ -20,16 +20,19 @@ struct Schedule {
     std::vector<StepRec> steps;
     int64_t ws_bytes = 0;               // workspace bytes
     int n_meta = 0, n_meta_inv = 0;     // meta slots; [0, n_meta_inv) invariant
+    int n_meta_extra = 0;               // B' slots after n_meta (always written before read)
     double flops_per_pass = 0, flops_inv = 0;
     double bytes_per_pass = 0;
     int n_permutes = 0;
     int n_steps_inv = 0;
     int final_tensor = -1;
     int kernels_per_pass = 0, kernels_inv = 0;
+    int n_gemm_steps = 0;
 };
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
-                   int batch_log2, int dtype, Schedule &out, std::string &err);
+                   int batch_log2, int dtype, int small_log2, bool allow_tc, Schedule &out,
+                   std::string &err);
 
 }  // namespace tn
 
@@ -51,6 +54,8 @@ struct tn_plan_s {
     float *d_tmax = nullptr;
     int32_t *d_texp = nullptr;
     int32_t *d_err = nullptr;
+    double2 *d_stepcorr = nullptr;      // per step: 1/(1+alpha) of its B' rounding
+    float *d_splitk = nullptr;          // FP32 partials of split-K tensor-core steps
     void *h_store_pinned = nullptr;     // pinned copy of the leaf store
     // per-kernel-class event timing (tn_profile)
     uint32_t prof_mask = 0;
@@ -76,6 +81,7 @@ struct tn_plan_s {
     // autotuner: chosen (kernel, tile) per GEMM op live in sched.ops; every
     // timing taken is kept as a record (the cost model's training data)
     bool tuned = false;
+    bool calibrated = false;
     std::vector<tn_tune_record> tune_recs;
     struct tn_cost_model_s *cost_model = nullptr;
 };

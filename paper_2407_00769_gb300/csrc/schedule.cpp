@@ -18,6 +18,7 @@
 // by the final FP64 kernel.  Steps whose inputs do not depend on the looped
 // slice bits run once per contract call (phase 0).
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <set>
 
@@ -82,7 +83,8 @@ struct BufReq {
 }  // namespace
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
-                   int batch_log2, int dtype, Schedule &S, std::string &err) {
+                   int batch_log2, int dtype, int small_log2, bool allow_tc, Schedule &S,
+                   std::string &err) {
     S = Schedule();
     const int L = (int)net.leaves.size();
     const int NS = (int)path.steps.size();
@@ -98,8 +100,6 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
     for (int j = 0; j < (int)sliced.size(); ++j) sbit[sliced[j]] = j;
     auto looped = [&](int e) { return sbit[e] >= batch_log2; };
     auto batched = [&](int e) { return sbit[e] >= 0 && sbit[e] < batch_log2; };
-    const int esz = dtype == TN_C64 ? 8 : 4;
-
     // ---- leg orders, invariance, sets
     std::vector<std::vector<int>> legs(T), sets(T);
     std::vector<char> inv(T, 1);
@@ -131,6 +131,12 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
     }
     const int final_t = NS > 0 ? T - 1 : 0;
     S.final_tensor = final_t;
+    // storage of each tensor: complex64 for complex64 plans; in complex-half
+    // plans, complex64 for leaves and tensors of <= 2^kSmallLog2 elements
+    std::vector<int> tdt(T, 0);
+    for (int t = 0; t < T; ++t)
+        tdt[t] = (dtype != TN_C64 && t >= L && (int)sets[t].size() > small_log2) ? 1 : 0;
+    auto esz_of = [&](int t) { return tdt[t] ? 4 : 8; };
 
     // role of each step: A = operand with more legs (ties: the first)
     auto a_side = [&](int s) {
@@ -163,9 +169,11 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         if (!inv[t]) meta[t] = nm++;
     S.n_meta = nm;
 
+    int n_extra_meta = 0;   // scale slots of complex64 B operands rounded for tensor cores
+
     // ---- ops with symbolic buffers: buffer id t for tensor t, temps after
     std::vector<BufReq> bufs(T);
-    auto tensor_bytes = [&](int t) { return (int64_t)esz << legs[t].size(); };
+    auto tensor_bytes = [&](int t) { return (int64_t)esz_of(t) << legs[t].size(); };
     std::vector<Op> ph[2];
     auto new_temp = [&](int64_t bytes) {
         BufReq r;
@@ -246,6 +254,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             if (!shared.count(e)) no.push_back(e);
         no = for_consumer(c, no);
 
+        int meta_b_override = -1;
         StepRec rec{};
         rec.a = ia; rec.b = ib; rec.c = c;
         rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = nk; rec.lb = nb;
@@ -253,9 +262,11 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
 
         int64_t abuf = ia, bbuf = ib;
         auto permute_to = [&](int src_t, const std::vector<int> &from, const std::vector<int> &to) {
+            const int esz = esz_of(src_t);
             Op op;
             op.kind = OP_PERM;
             op.phase = phase;
+            op.perm.esz = esz;
             op.perm.rank = (int)to.size();
             for (int i = 0; i < (int)to.size(); ++i)
                 op.perm.perm[i] = (int)(std::find(from.begin(), from.end(), to[i]) - from.begin());
@@ -275,9 +286,11 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             abuf = permute_to(ia, LA, tgt);
             rec.permute_a = 1;
         }
+        const int ta = tdt[ia], tb = tdt[ib], tc = tdt[c];
+        rec.storage = ta | (tb << 1) | (tc << 2);
         int kernel;
         if (dtype == TN_C64) kernel = (rec.lm >= 6 && rec.ln >= 6 && rec.lk >= 4) ? GK_C64_TILED : GK_C64_ROWS;
-        else kernel = (rec.lk >= 3 && rec.lk <= 24 && rec.ln <= 24) ? GK_LP_TC : GK_LP_ROWS;
+        else kernel = (allow_tc && ta == 1 && rec.lk >= 3 && rec.lk <= 24 && rec.ln <= 24) ? GK_LP_TC : GK_LP_ROWS;
         rec.kernel = kernel;
         rec.tile = 0;
         if (kernel == GK_LP_TC) {
@@ -297,13 +310,21 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             op.bprep.np = np;
             op.bprep.step = s;
             op.bprep.rank = (int)tgt.size();
+            op.bprep.tb = tb;
+            op.bprep.meta_src = meta[ib];
+            op.bprep.meta_dst = meta[ib];
+            if (tb == 0) {
+                // complex64 B: B' = B 2^s gets a scale slot of its own
+                op.bprep.meta_dst = S.n_meta + n_extra_meta++;
+                meta_b_override = op.bprep.meta_dst;
+            }
             for (int i = 0; i < (int)tgt.size(); ++i)
                 op.bprep.perm[i] = (int)(std::find(LB.begin(), LB.end(), tgt[i]) - LB.begin());
             const int64_t bpbytes = ((int64_t)np * (2LL << rec.lk) * 2) << rec.lb;
             const int tmp = new_temp(bpbytes);
             op.bprep.dst = tmp;
             ops.push_back(op);
-            if (phase) S.bytes_per_pass += (double)(((int64_t)esz << (rec.lk + rec.ln + rec.lb)) + bpbytes);
+            if (phase) S.bytes_per_pass += (double)(((int64_t)esz_of(ib) << (rec.lk + rec.ln + rec.lb)) + bpbytes);
             bbuf = tmp;
         } else {
             std::vector<int> tgt(bo);
@@ -327,15 +348,21 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.lm = rec.lm; op.gemm.ln = rec.ln; op.gemm.lk = rec.lk; op.gemm.lb = rec.lb;
         op.gemm.a_batched = rec.lb > 0;
         op.gemm.b_batched = rec.lb > 0;
-        op.gemm.meta_a = meta[ia]; op.gemm.meta_b = meta[ib]; op.gemm.meta_c = meta[c];
+        op.gemm.meta_a = meta[ia];
+        op.gemm.meta_b = meta_b_override >= 0 ? meta_b_override : meta[ib];
+        op.gemm.meta_c = meta[c];
         op.gemm.step = s;
         op.gemm.kernel = kernel;
         op.gemm.tile = 0;
+        op.gemm.ta = ta;
+        op.gemm.tb = tb;
+        op.gemm.tc = tc;
         ops.push_back(op);
+        ++S.n_gemm_steps;
         const double fl = 8.0 * std::ldexp(1.0, rec.lm + rec.ln + rec.lk + rec.lb);
-        const double by = (double)(((int64_t)esz << (rec.lm + rec.lk + rec.lb)) +
-                                   ((int64_t)esz << (rec.lk + rec.ln + rec.lb)) +
-                                   ((int64_t)esz << (rec.lm + rec.ln + rec.lb)));
+        const double by = (double)(((int64_t)esz_of(ia) << (rec.lm + rec.lk + rec.lb)) +
+                                   ((int64_t)esz_of(ib) << (rec.lk + rec.ln + rec.lb)) +
+                                   ((int64_t)esz_of(c) << (rec.lm + rec.ln + rec.lb)));
         if (phase) { S.flops_per_pass += fl; S.bytes_per_pass += by; }
         else { S.flops_inv += fl; ++S.n_steps_inv; }
         S.steps.push_back(rec);
@@ -358,8 +385,11 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         }
         if (r != net.n_open + batch_log2) { err = "final tensor misses output modes"; return TN_EINVAL; }
         op.sum.n_batch = batch_log2;
+        op.sum.tf = tdt[final_t];
         ph[1].push_back(op);
     }
+
+    S.n_meta_extra = n_extra_meta;
 
     // ---- lifetimes over the op sequence (phase 0 then phase 1)
     S.ops = ph[0];

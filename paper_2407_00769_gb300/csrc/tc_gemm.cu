@@ -173,6 +173,10 @@ struct TcArgs {
     int batch_a, batch_b;
     int gm;                // m tiles per raster group
     int withhold;          // self-test: issue no loads, so consumers' waits run out
+    int out_c64;           // C stored complex64 (no rounding, e = 0)
+    int split;             // K parts (split-K); tiles of part p cover K chunks [p*nk, (p+1)*nk)
+    float *partial;        // split > 1: FP32 partial sums [part][batch][M][N] complex
+    int64_t tiles_per_part;
     ScaleRef sr;
     int32_t *err;
 };
@@ -184,6 +188,7 @@ struct TcArgs {
 // instead of once per m-tile.
 __device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt,
                                             int &nt) {
+    t %= a.tiles_per_part;          // the K part is t / tiles_per_part
     const int64_t per_batch = a.n_mt * a.n_nt;
     b = t / per_batch;
     const int64_t r = t - b * per_batch;
@@ -263,14 +268,15 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                 int64_t b, mt;
                 int nt;
                 tile_coords(args, t, b, mt, nt);
+                const int kbase = (int)(t / args.tiles_per_part) * args.nk * BK;
                 for (int kc = 0; kc < args.nk; ++kc) {
                     if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
                     uint8_t *sa = smem + stage * S::stage_bytes;
                     uint8_t *sb = sa + S::a_bytes;
                     mbar_expect_tx(&full[stage], S::a_bytes + S::b_bytes);
-                    tma_load_3d(sa, &tmA, &full[stage], kc * BK, (int)(mt * 128),
+                    tma_load_3d(sa, &tmA, &full[stage], kbase + kc * BK, (int)(mt * 128),
                                 args.batch_a ? (int)b : 0);
-                    tma_load_3d(sb, &tmB, &full[stage], kc * BK, nt * BN, args.batch_b ? (int)b : 0);
+                    tma_load_3d(sb, &tmB, &full[stage], kbase + kc * BK, nt * BN, args.batch_b ? (int)b : 0);
                     armed[stage] = (int8_t)phase;
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -331,11 +337,14 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         const int q = warp & 3;                 // TMEM lane quadrant of this warp
         const int row = q * 32 + lane;
         int e;
-        if (args.sr.tmax)
-            e = scale_exp_tc(args.sr.tmax[args.sr.meta_a], args.sr.tmax[args.sr.meta_b], args.lk);
+        if (args.out_c64)
+            e = 0;
+        else if (args.sr.tmax)
+            e = min(120, scale_exp_tc(args.sr.tmax[args.sr.meta_a], args.sr.tmax[args.sr.meta_b], args.lk) +
+                             args.sr.headroom);
         else
             e = args.sr.fixed_exp;
-        if (args.sr.texp && blockIdx.x == 0 && threadIdx.x == 64)
+        if (args.sr.texp && !args.partial && blockIdx.x == 0 && threadIdx.x == 64)
             args.sr.texp[args.sr.meta_c] = args.sr.texp[args.sr.meta_a] + args.sr.texp[args.sr.meta_b] + e;
         const float sc = __int_as_float((127 + e) << 23);
         float mx = 0.f;
@@ -354,7 +363,31 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                 uint32_t r[16];
                 tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 tmem_wait_ld();
-                if (m < args.M) {
+                if (m < args.M && (args.out_c64 || args.partial)) {
+                    // complex64 result (or split-K partial): the FP32 accumulators as they are
+                    const int nreal = min(16, valid_real - c);
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = __uint_as_float(r[j]);
+                        if (j < nreal) mx = fmaxf(mx, fabsf(v[j]));
+                    }
+                    const int64_t part = t / args.tiles_per_part;
+                    float *dst = args.partial
+                                     ? args.partial + (((part * args.batch + b) * args.M + m) * (int64_t)args.N +
+                                                       (col0 + c) / 2) * 2
+                                     : reinterpret_cast<float *>(args.C) +
+                                           ((b * args.M + m) * (int64_t)args.N + (col0 + c) / 2) * 2;
+                    if (nreal >= 4) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (4 * q < nreal)
+                                reinterpret_cast<float4 *>(dst)[q] =
+                                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    } else {
+                        reinterpret_cast<float2 *>(dst)[0] = make_float2(v[0], v[1]);
+                    }
+                } else if (m < args.M) {
                     const int nreal = min(16, valid_real - c);   // 2, 4, 8 or 16
                     uint32_t packed[8];
 #pragma unroll
@@ -396,13 +429,16 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-        if (lane == 0 && args.sr.out_max)
+        if (lane == 0 && args.sr.out_max && !args.partial)
             atomicMax(reinterpret_cast<int *>(args.sr.out_max), __float_as_int(mx));
+        if (lane == 0 && args.sr.err && args.dtype == TN_F16 && !args.out_c64 && !args.partial &&
+            !(mx <= 65504.0f))
+            atomicOr(args.sr.err, 2);
     }
 
     tc_fence_before();
     __syncthreads();
-    if (abort_flag && threadIdx.x == 0 && args.err) atomicExch(args.err, 1);
+    if (abort_flag && threadIdx.x == 0 && args.err) atomicOr(args.err, 1);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -526,6 +562,31 @@ cudaError_t tc_prepare() {
 
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
 
+// K parts of one tensor-core GEMM.  Each part accumulates at most
+// 2^kSplitLog2K complex terms in TMEM (the tensor cores' FP32 accumulation
+// drifts with K: 2.6e-4 relative at K = 2^16, 2e-2 at 2^23 against 2e-4 for
+// the output rounding alone); a step with few output tiles is cut further so
+// that its parts fill the GPU, down to 512 complex terms per part and within
+// 256 MB of FP32 partials.  Depends on the shape only, so a plan sizes its
+// partial buffer once.
+int tc_split(int lm, int ln, int lk, int64_t batch) {
+    if (lk < 9) return 1;
+    int split = lk > kSplitLog2K ? 1 << (lk - kSplitLog2K) : 1;
+    const int np = std::max(16, 2 << ln);
+    const int64_t tiles = (((int64_t)1 << lm) + 127) / 128 * (np / std::min(np, 256)) * batch;
+    const int64_t part_bytes = (batch << (lm + ln)) * 8;
+    const int max_split = 1 << (lk - 9);                 // parts of >= 512 complex terms
+    while (split < max_split && tiles * split < tc_num_sms() &&
+           part_bytes * split * 2 <= ((int64_t)256 << 20))
+        split *= 2;
+    return split;
+}
+
+size_t tc_split_bytes(int lm, int ln, int lk, int64_t batch) {
+    const int split = tc_split(lm, ln, lk, batch);
+    return split > 1 ? (size_t)split * (size_t)(batch << (lm + ln)) * 8 : 0;
+}
+
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
     if (!tc_gemm_supported(d.lk, d.ln)) return cudaErrorInvalidValue;
     {
@@ -557,10 +618,19 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.N = 1 << d.ln;
     a.lk = d.lk;
     a.nk = kreal / bk;
+    a.split = d.withhold ? 1 : tc_split(d.lm, d.ln, d.lk, d.batch);
+    a.partial = a.split > 1 ? d.partial : nullptr;
+    if (a.split > 1) {
+        if (!d.partial || a.nk % a.split != 0) return cudaErrorInvalidValue;
+        a.nk /= a.split;
+    }
+    a.tiles_per_part = a.tiles;
+    a.tiles *= a.split;
     a.dtype = d.dtype;
     a.batch_a = d.batch_a;
     a.batch_b = d.batch_b;
     a.withhold = d.withhold;
+    a.out_c64 = d.out_c64;
     if (d.gm > 0) {
         a.gm = d.gm;
     } else {
@@ -570,11 +640,15 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     }
     a.sr = sr;
     a.err = d_err;
+    cudaError_t e;
     switch (bk) {
-        case 16: return run_tc_bn<16>(bn, ma, mb, a, s);
-        case 32: return run_tc_bn<32>(bn, ma, mb, a, s);
-        default: return run_tc_bn<64>(bn, ma, mb, a, s);
+        case 16: e = run_tc_bn<16>(bn, ma, mb, a, s); break;
+        case 32: e = run_tc_bn<32>(bn, ma, mb, a, s); break;
+        default: e = run_tc_bn<64>(bn, ma, mb, a, s); break;
     }
+    if (e == cudaSuccess && a.split > 1)
+        e = launch_splitk_reduce(a.partial, a.split, d.C, d.out_c64, d.dtype, d.batch, d.lm, d.ln, d.lk, sr, s);
+    return e;
 }
 
 }  // namespace tn

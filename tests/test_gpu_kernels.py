@@ -214,3 +214,23 @@ def test_bounded_wait_times_out_and_context_survives():
     assert rc == tn.TN_ETIMEOUT, L.tn_last_error()
     # the context is still usable: a normal tensor-core GEMM is correct
     _lp_case(tn.F16, 256, 16, 32, 1, 3)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 32, 1 << 22), (1024, 32, 1 << 18), (128, 256, 1 << 16),
+                                   (65536, 16, 1 << 12)])
+def test_gemm_f16_tensor_cores_long_k(M, N, K):
+    # Long contractions (the last steps of a sliced network reach K = 2^23):
+    # the relative L2 error must stay at the level of the FP16 output rounding
+    # (about 2e-4 for Gaussian data) whatever K is.  Reference: complex128
+    # product of the same FP16-rounded operands, on the device.
+    g = torch.Generator(device="cuda").manual_seed(K + M + N)
+    a = torch.randn(1, M, K, 2, generator=g, device="cuda").half()
+    b = (torch.randn(1, K, N, 2, generator=g, device="cuda") / K ** 0.5).half()
+    c = torch.zeros(1, M, N, 2, dtype=torch.float16, device="cuda")
+    tn.gemm(tn.F16, a, b, c, M, N, K, scale_exp=0, kernel=3)
+    ar = torch.view_as_complex(a.double())
+    br = torch.view_as_complex(b.double())
+    want = torch.matmul(ar[0], br[0])
+    got = torch.view_as_complex(c.double())[0]
+    rel = (torch.linalg.norm(got - want) / torch.linalg.norm(want)).item()
+    assert rel < 3e-4, rel

@@ -1,0 +1,147 @@
+"""Autotuner and learned cost model on the GPU.
+
+* the cost-model MLP's gradients (FP32, own kernels) against the FP64
+  reference MLP (oracle/mlp.py) at the same parameters;
+* training reduces the loss;
+* tuning keeps results bit-identical (the tile configuration does not
+  change the accumulation order) and records every timing;
+* the learned policy, trained on other plans' records, picks tile
+  configurations whose measured time is compared with the fixed heuristic
+  and with exhaustive timing on a held-out plan."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import rqcgen  # noqa: E402
+from oracle import mlp  # noqa: E402
+import paper_2407_00769_gb300 as tn  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def test_cost_model_gradient_matches_fp64_reference():
+    m = tn.CostModel(hidden=64, seed=3)
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(96, tn.COST_NFEAT)).astype(np.float32)
+    t = rng.normal(size=96).astype(np.float32)
+    p = m.params()
+    loss, g = m.grad(x, t)
+    ref_loss, ref_g = mlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), 64)
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
+    err = np.abs(g - ref_g)
+    assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+    assert np.all(err <= 1e-3 * np.abs(ref_g).max())
+
+
+def test_training_reduces_loss():
+    m = tn.CostModel(hidden=128, seed=5)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(size=(4096, tn.COST_NFEAT)).astype(np.float32)
+    t = (3 * x[:, 0] + 2 * x[:, 1] * x[:, 2] - x[:, 5] + 1).astype(np.float32)
+    l0, _ = m.grad(x[:512], t[:512])
+    m.train(x, t, epochs=40, batch=256, lr=2e-3, seed=7)
+    l1, _ = m.grad(x[:512], t[:512])
+    assert l1 < 0.05 * l0, (l0, l1)
+    y = m.predict(x[:512])
+    assert np.mean((y - t[:512]) ** 2) == pytest.approx(l1, rel=1e-4)
+
+
+def _plan(c, q, **kw):
+    return tn.Plan(c, q, dtype=tn.F16, **kw)
+
+
+def test_tuning_keeps_results_and_records_timings():
+    c, q = rqcgen.small_grid(4, 5, 12, seed=8, n_open=6)
+    p = _plan(c, q, n_slice_edges=4, slice_batch_log2=2)
+    before = p.contract().cpu().numpy()
+    p.tune()
+    recs = p.tune_records()
+    gemm_steps = [s for s in p.steps()]
+    assert len([r for r in recs if r["kind"] == 0]) >= len(gemm_steps)
+    assert all(r["ms"] > 0 for r in recs)
+    after = p.contract().cpu().numpy()
+    assert np.array_equal(before, after)
+    # exhaustive policy tunes itself on the first contract
+    p2 = _plan(c, q, n_slice_edges=4, slice_batch_log2=2, tile_policy=tn.TILE_EXHAUSTIVE)
+    assert np.array_equal(p2.contract().cpu().numpy(), before)
+    assert len(p2.tune_records()) > 0
+
+
+def _oversample(recs):
+    # the plan's total time is dominated by its largest steps; repeat each
+    # record in proportion to its time (1..16x) so training sees them
+    ms = np.array([r["ms"] for r in recs])
+    med = np.median(ms)
+    out = []
+    for r, m in zip(recs, ms):
+        out += [r] * int(np.clip(round(m / med), 1, 16))
+    return out
+
+
+def _records_of(rows, cols, cyc, seed, sl, b):
+    c, q = rqcgen.small_grid(rows, cols, cyc, seed=seed, n_open=6)
+    p = _plan(c, q, n_slice_edges=sl, slice_batch_log2=b)
+    p.tune()
+    return p.tune_records()
+
+
+def test_learned_policy_against_fixed_and_exhaustive():
+    import time
+    train = []
+    for args in [(4, 5, 12, 1, 4, 2), (5, 5, 12, 2, 6, 3), (4, 6, 14, 3, 6, 4), (5, 6, 10, 4, 6, 6),
+                 (3, 6, 12, 5, 3, 1), (5, 5, 14, 6, 6, 5), (4, 6, 12, 7, 5, 5)]:
+        train += _records_of(*args)
+    model = tn.CostModel(hidden=128, seed=11)
+    tr = _oversample(train)
+    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=150, batch=128, lr=1e-3, seed=3)
+    # held-out plan, timed exhaustively: every candidate of every step
+    c, q = rqcgen.small_grid(5, 6, 12, seed=9, n_open=6)
+    held = _plan(c, q, n_slice_edges=6, slice_batch_log2=6)
+    t0 = time.perf_counter()
+    held.tune()
+    t_exhaustive = time.perf_counter() - t0
+    recs = [r for r in held.tune_records() if r["kind"] == 0]
+    by_step = {}
+    for r in recs:
+        by_step.setdefault(r["step"], {})[(r["kernel"], r["tile"])] = r["ms"]
+    # the same plan with the learned policy: its choices come from the model
+    lp = _plan(c, q, n_slice_edges=6, slice_batch_log2=6, tile_policy=tn.TILE_LEARNED)
+    lp.set_cost_model(model)
+    t0 = time.perf_counter()
+    lp.contract()
+    torch.cuda.synchronize()
+    t_learned_call = time.perf_counter() - t0
+    ranks = []
+    pred = dict(zip([(r["step"], r["kernel"], r["tile"]) for r in recs],
+                    model.predict(tn.cost_features(recs))))
+    for i in range(len(lp.steps())):
+        cand = by_step.get(i)
+        if cand and len(cand) >= 3:
+            keys = list(cand)
+            m = np.argsort(np.argsort([cand[k] for k in keys]))
+            p_ = np.argsort(np.argsort([pred[(i,) + k] for k in keys]))
+            ranks.append(np.corrcoef(m, p_)[0, 1])
+    rank_corr = float(np.nanmean(ranks)) if ranks else float("nan")
+    # whole-plan device time of the three choices, median of 15 calls each
+    fx = _plan(c, q, n_slice_edges=6, slice_batch_log2=6, tile_policy=tn.TILE_FIXED)
+    fixed, learned, best = (_median_ms(p) for p in (fx, lp, held))
+    print(f"held-out plan: fixed {fixed:.3f} ms, learned {learned:.3f} ms, exhaustive {best:.3f} ms; "
+          f"selection: exhaustive tuning {t_exhaustive:.2f} s, learned first call {t_learned_call:.2f} s; "
+          f"mean within-step rank correlation {rank_corr:.2f}")
+    assert rank_corr > 0.2
+    assert learned <= 1.08 * fixed
+    assert learned <= 1.15 * best
+    assert t_learned_call < t_exhaustive
+
+
+def _median_ms(plan, n=15):
+    plan.contract()
+    times = []
+    for _ in range(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.contract()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))

@@ -1,0 +1,98 @@
+"""The large-slice 53-qubit workload and the batch of 256 uneven circuits.
+
+53 qubits has no state-vector oracle (2^53 amplitudes).  Its slices are
+checked by invariants that hold at any size: the sum of single-slice calls
+equals the range call (bit-identical for looped slices), a plan that runs
+the slices batched gives the same sum, and the complex64 and FP16 paths
+agree on the same slices (a consistency check, not an oracle).  The 30-qubit
+workload (same planner and kernels) is checked against the state vector in
+test_gpu_contract.py.
+
+The uneven batch is checked circuit by circuit against the FP64 state vector
+(live for the smaller circuits, stored oracle values for the others when
+tests/golden/make_golden.py has written them)."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle  # noqa: E402
+import rqcgen  # noqa: E402
+import paper_2407_00769_gb300 as tn  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "batch")
+
+
+def _grid53(dtype, batch=0):
+    c, q = rqcgen.grid_53q()
+    return tn.Plan(c, q, dtype=dtype, n_slice_edges=-1, max_log2_elems=30, trials=1,
+                   slice_batch_log2=batch)
+
+
+def test_grid53_slice_invariants():
+    p16 = _grid53(tn.F16)
+    info = p16.info()
+    assert info["max_log2_elems"] <= 30 and info["n_open"] == 12
+    whole = p16.contract(0, 4).cpu().numpy()
+    acc = p16.contract(0, 1)
+    for s in range(1, 4):
+        p16.contract(s, 1, out=acc, accumulate=True)
+    assert np.array_equal(acc.cpu().numpy(), whole)
+    one16 = [p16.contract(s, 1).cpu().numpy() for s in range(2)]
+    del p16
+    torch.cuda.empty_cache()
+    # batched slices: same sum, rounded differently (shared scale per pass)
+    pb = _grid53(tn.F16, batch=2)
+    assert oracle.rel_l2(pb.contract(0, 4).cpu().numpy(), whole) <= 5e-3
+    del pb
+    torch.cuda.empty_cache()
+    # complex64 path on the same two slices
+    p64 = _grid53(tn.C64)
+    for s in range(2):
+        c64 = p64.contract(s, 1).cpu().numpy()
+        assert np.linalg.norm(c64) > 0
+        assert oracle.rel_l2(one16[s], c64) <= 5e-3
+        assert oracle.fidelity(c64, one16[s]) >= 0.999
+    del p64
+    torch.cuda.empty_cache()
+
+
+def _golden(i):
+    path = os.path.join(GOLD, f"circuit{i:03d}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        _, a, b = line.split()
+        vals.append(complex(float(a), float(b)))
+    return np.array(vals)
+
+
+def test_uneven_batch_against_state_vector():
+    items = rqcgen.uneven_batch()
+    # the first 48 circuits: live oracle when small, stored values otherwise
+    idx, want = [], []
+    for i in range(48):
+        c, q = items[i]
+        w = _golden(i)
+        if w is None and c.n_qubits <= 22:
+            w = oracle.amplitudes(c, q)
+        if w is not None:
+            idx.append(i)
+            want.append(w)
+    assert len(idx) >= 16
+    plans = [tn.plan_within_budget(*items[i], dtype=tn.F16) for i in idx]
+    outs = [torch.zeros(64, dtype=torch.complex128, device="cuda") for _ in idx]
+    b = tn.Batch(plans, outs, n_streams=16)
+    b.run(stream=torch.cuda.Stream(), report=True)
+    errs = []
+    for o, w in zip(outs, want):
+        got = o.cpu().numpy()
+        errs.append(oracle.rel_l2(got, w))
+        assert oracle.fidelity(w, got) >= 0.999
+    print(f"uneven batch: {len(idx)} circuits, max rel-L2 {max(errs):.2e}")
+    assert max(errs) <= 5e-3
