@@ -258,7 +258,7 @@ def _timed(fn, stream, flush, reps=1):
     return statistics.mean(ts)
 
 
-def leg_grid53(tn, torch, dev, flush, stream, peaks):
+def leg_grid53(tn, torch, dev, flush, stream, peaks, want_records=False):
     """Large-slice workload: 53-qubit 6x9-minus-one grid, 12 cycles, each
     slice's largest intermediate <= 2^30 elements; slices 0..63 in one call
     (8 slices per pass, batched), FP16 tensor cores."""
@@ -286,9 +286,13 @@ def leg_grid53(tn, torch, dev, flush, stream, peaks):
            "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12,
            "gemm_tc_share": g["ms"] / ms, "max_log2_elems": info["max_log2_elems"],
            "peak_tflops": peak}
+    recs = []
+    if want_records:
+        plan.tune()
+        recs = plan.tune_records()
     del plan, amps
     torch.cuda.empty_cache()
-    return out
+    return out, recs
 
 
 def leg_batch256(tn, torch, dev, flush, stream):
@@ -320,6 +324,107 @@ def leg_batch256(tn, torch, dev, flush, stream):
            "kernels_in_graph": rep["kernels"], "plan_s": t_plan, "graph_capture_s": t_capture,
            "tuned_plans": len(plans[::32])}
     del b, plans, outs
+    torch.cuda.empty_cache()
+    return out, recs
+
+
+def _oversample(recs):
+    # a plan's time is dominated by its largest steps: repeat each record in
+    # proportion to its time (1..16x) so that training sees them
+    import numpy as np
+    ms = np.array([r["ms"] for r in recs])
+    med = float(np.median(ms))
+    out = []
+    for r, m in zip(recs, ms):
+        out += [r] * int(np.clip(round(m / med), 1, 16))
+    return out
+
+
+# path seeds of the 40-qubit grid whose plans (32 randomized greedy trials,
+# 10 sliced edges) cost 1.1e14-2.4e14 flops per slice: close enough that
+# their ranking is not settled by the flop count alone
+GRID40_SEEDS = (2, 8, 13, 15, 20, 21, 22)
+
+
+def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
+    """Learned cost model on the 40-qubit 5x8 grid (14 cycles, 10 sliced
+    edges = 1024 slices, greedy paths of 32 randomized trials per seed).  The
+    MLP, trained on the autotuner timings of the other workloads, ranks
+    candidate slicing plans (path seeds) by predicted time and picks every
+    step's tile configuration; both choices are compared with measurement:
+    plan regret = measured time of the predicted-best plan / best measured;
+    tile regret = learned-policy time / exhaustively tuned time of that plan."""
+    import time as _t
+    import numpy as np
+    import rqcgen
+    c, q = rqcgen.grid_40q()
+    model = tn.CostModel(hidden=128, seed=11)
+    tr = _oversample(train_recs)
+    t0 = _t.perf_counter()
+    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=100, batch=128, lr=1e-3, seed=3)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    amps = torch.zeros(1 << 10, dtype=torch.complex128, device=dev)
+
+    def mk(seed, policy):
+        return tn.Plan(c, q, dtype=tn.F16, n_slice_edges=10, trials=32, seed=seed,
+                       slice_batch_log2=1, tile_policy=policy)
+
+    cands = []
+    for s in GRID40_SEEDS:
+        p = mk(s, tn.TILE_LEARNED)
+        p.set_cost_model(model)
+        pred_ms = p.predict_ms(model)
+        t0 = _t.perf_counter()
+        p.contract(0, 2, out=amps)           # first call: learned tile selection
+        torch.cuda.synchronize()
+        t_sel = _t.perf_counter() - t0
+        ms = _timed(lambda: p.contract(0, n_meas, out=amps), stream, flush)
+        inf = p.info()
+        cands.append({"seed": s, "pred_job_s": pred_ms * 1e-3,
+                      "meas_job_s": ms * 1e-3 * inf["n_slices"] / n_meas,
+                      "flops_per_slice": inf["flops_per_slice"], "max_log2_elems": inf["max_log2_elems"],
+                      "first_call_s": t_sel, "ms_timed_slices": ms})
+        del p
+        torch.cuda.empty_cache()
+    pred = np.array([x["pred_job_s"] for x in cands])
+    meas = np.array([x["meas_job_s"] for x in cands])
+    best_pred = int(np.argmin(pred))
+    rank_corr = float(np.corrcoef(np.argsort(np.argsort(pred)), np.argsort(np.argsort(meas)))[0, 1])
+    seed = cands[best_pred]["seed"]
+    # the chosen plan, tuned exhaustively instead
+    pe = mk(seed, tn.TILE_EXHAUSTIVE)
+    t0 = _t.perf_counter()
+    pe.contract(0, 2, out=amps)
+    torch.cuda.synchronize()
+    t_tune = _t.perf_counter() - t0
+    ms_exh = _timed(lambda: pe.contract(0, n_meas, out=amps), stream, flush)
+    recs = [r for r in pe.tune_records() if r["kind"] == 0]
+    # per-step regret of the model's own pick among the timed candidates,
+    # weighted by each step's best time
+    by = {}
+    for r, y in zip(recs, model.predict(tn.cost_features(recs))):
+        by.setdefault(r["step"], []).append((y, r["ms"], r["kernel"] == 3 and r["tile"] == 0))
+    num = den = dfl = 0.0
+    for v in by.values():
+        pick = min(v)[1]
+        best = min(m for _, m, _ in v)
+        d = [m for _, m, is_d in v if is_d]
+        num += pick
+        den += best
+        dfl += d[0] if d else pick
+    ms_learned = cands[best_pred]["ms_timed_slices"]
+    out = {"workload": "grid5x8-14c: 40 qubits, 14 cycles, 10 sliced edges (1024 slices), "
+                       "10 open qubits; slices 0-7 timed per candidate, 2 per pass",
+           "train_records": len(train_recs), "train_s": t_train, "candidates": cands,
+           "plan_regret": float(meas[best_pred] / meas.min()), "plan_rank_corr": rank_corr,
+           "chosen_seed": seed, "tile_regret": ms_learned / ms_exh,
+           "step_regret_weighted": num / den, "default_tile_regret_weighted": dfl / den,
+           "selection_s": {"learned_first_call": cands[best_pred]["first_call_s"],
+                           "exhaustive_first_call": t_tune},
+           "slices_per_s": {"learned": n_meas / (ms_learned * 1e-3),
+                            "exhaustive": n_meas / (ms_exh * 1e-3)}}
+    del pe, amps
     torch.cuda.empty_cache()
     return out
 
@@ -538,13 +643,22 @@ def main():
                        "ms_per_step": e2e_s * 1e3}
 
     legs = [x for x in args.legs.split(",") if x and x != "none"] if world == 1 else []
+    train = []
+    if "grid40" in legs:
+        if not plan.tune_records():
+            plan.tune()
+        train += plan.tune_records()
     del plan
     torch.cuda.empty_cache()
     side = torch.cuda.Stream()
     if "grid53" in legs:
-        line["grid53"] = leg_grid53(tn, torch, dev, flush, stream, peaks)
+        line["grid53"], r = leg_grid53(tn, torch, dev, flush, stream, peaks, want_records="grid40" in legs)
+        train += r
     if "batch256" in legs:
-        line["batch256"] = leg_batch256(tn, torch, dev, flush, side)
+        line["batch256"], r = leg_batch256(tn, torch, dev, flush, side)
+        train += r
+    if "grid40" in legs:
+        line["grid40"] = leg_grid40(tn, torch, dev, flush, stream, train)
 
     if not args.no_cpu_baseline and world == 1:
         full, sample, threads = oracle_sample()

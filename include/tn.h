@@ -172,8 +172,17 @@ int tn_plan_info(const tn_plan_t *plan, tn_plan_stats *out);
 int tn_plan_sliced_edges(const tn_plan_t *plan, int32_t *qubit, int32_t *after_gate,
                          int32_t capacity);
 
-/* Step i of the per-slice schedule (0 <= i < n_steps). */
+/* Step i of the per-slice schedule (0 <= i < n_steps).  Tensor ids a, b, c:
+ * ids below n_leaves are leaves (tn_plan_leaf_source), step s creates id
+ * n_leaves + s; the steps in order are the contraction path. */
 int tn_plan_step(const tn_plan_t *plan, int32_t i, tn_step_info *out);
+
+/* Where leaf i (0 <= i < n_leaves) comes from: *gate = index in the circuit
+ * of its two-qubit gate (the single-qubit gates, initial states and output
+ * bits around it absorbed, Sec. 2 circuit-to-network), or -1 for a qubit
+ * that no two-qubit gate touches, whose index is then written to *qubit
+ * (else -1).  Errors: TN_EINVAL (NULL plan, i out of range). */
+int tn_plan_leaf_source(const tn_plan_t *plan, int32_t i, int32_t *gate, int32_t *qubit);
 
 /*
  * tn_contract: contract slices [slice_begin, slice_begin + slice_count) and

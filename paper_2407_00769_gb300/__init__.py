@@ -30,6 +30,7 @@ TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 
 EXPORTED = [
     "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
+    "tn_plan_leaf_source",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
     "tn_profile", "tn_profile_read", "tn_sample_noalloc", "tn_selftest_wait_timeout",
@@ -146,6 +147,7 @@ def lib():
         L.tn_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
         L.tn_plan_sliced_edges.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
         L.tn_plan_step.argtypes = [vp, i32, ctypes.POINTER(StepInfo)]
+        L.tn_plan_leaf_source.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.tn_contract.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, ctypes.POINTER(ContractReport)]
         L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp, ctypes.POINTER(ContractReport)]
         L.tn_contract_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
@@ -314,6 +316,16 @@ class Plan:
         g = (ctypes.c_int32 * max(1, n))()
         _check(lib().tn_plan_sliced_edges(self._h, q, g, n))
         return [(int(q[j]), int(g[j])) for j in range(n)]
+
+    def leaf_sources(self):
+        """(gate, qubit) of every leaf: the circuit index of its two-qubit gate,
+        or (-1, q) for a qubit no two-qubit gate touches."""
+        out = []
+        g, q = ctypes.c_int32(), ctypes.c_int32()
+        for i in range(self.info()["n_leaves"]):
+            _check(lib().tn_plan_leaf_source(self._h, i, ctypes.byref(g), ctypes.byref(q)))
+            out.append((g.value, q.value))
+        return out
 
     def steps(self):
         out = []

@@ -472,9 +472,12 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         if (rc != TN_OK) return rc;
     }
     // per op: the predicted time of the fixed heuristic's own choice and of
-    // the best candidate; move away from the default only when the model
-    // predicts a clear gain (kLearnedMargin)
+    // the best candidate.  Steps predicted to take under kSmallStepMs are
+    // launch-latency bound, where the timings the model learned from are
+    // mostly noise: there it moves away from the default only for a clear
+    // predicted gain (kLearnedMargin); larger steps take the model's best.
     constexpr float kLearnedMargin = 0.92f;
+    constexpr float kSmallStepMs = 0.05f;
     std::vector<float> best(S.ops.size(), 1e30f), dflt(S.ops.size(), -1.0f);
     std::vector<std::pair<int, int>> pick(S.ops.size());
     for (size_t k = 0; k < recs.size(); ++k) {
@@ -488,7 +491,8 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
     }
     for (size_t i = 0; i < S.ops.size(); ++i) {
         if (S.ops[i].kind != OP_GEMM || best[i] >= 1e29f) continue;
-        if (dflt[i] < 0 || best[i] < kLearnedMargin * dflt[i]) {
+        const float margin = dflt[i] < kSmallStepMs ? kLearnedMargin : 1.0f;
+        if (dflt[i] < 0 || best[i] < margin * dflt[i]) {
             S.ops[i].gemm.kernel = pick[i].first;
             S.ops[i].gemm.tile = pick[i].second;
         }
@@ -613,6 +617,14 @@ int tn_plan_sliced_edges(const tn_plan_t *P, int32_t *qubit, int32_t *after_gate
         if (qubit) qubit[j] = e.qubit;
         if (after_gate) after_gate[j] = e.after_gate;
     }
+    return TN_OK;
+}
+
+int tn_plan_leaf_source(const tn_plan_t *P, int32_t i, int32_t *gate, int32_t *qubit) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    if (i < 0 || i >= (int)P->net.leaves.size()) return fail(TN_EINVAL, "leaf index out of range");
+    if (gate) *gate = P->net.leaves[i].gate;
+    if (qubit) *qubit = P->net.leaves[i].qubit;
     return TN_OK;
 }
 

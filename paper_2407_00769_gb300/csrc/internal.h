@@ -31,6 +31,7 @@ struct Leaf {
     std::vector<int> legs;
     std::vector<cd> data;
     int gate = -1;        // circuit gate index it came from (-1: isolated qubit)
+    int qubit = -1;       // the isolated qubit (gate == -1)
 };
 
 struct Network {

@@ -152,6 +152,7 @@ int build_network(const tn_circuit *c, const tn_query *q, Network &net, std::str
         const int x = t < 0 ? (q->fixed_bits[qq] ? 1 : 0) : 0;
         if (last_edge[qq] < 0) {
             Leaf L;
+            L.qubit = qq;
             const cd v0 = pend[qq][0], v1 = pend[qq][2];  // P|0>
             if (t >= 0) {
                 const int e = (int)net.edges.size();

@@ -634,9 +634,15 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     if (d.gm > 0) {
         a.gm = d.gm;
     } else {
-        // keep a group's A rows (gm x 128 x 2K halves) within ~48 MB of L2
-        const int64_t per_mtile = (int64_t)128 * kreal * 2;
-        a.gm = (int)std::max<int64_t>(1, std::min<int64_t>(16, (48ll << 20) / per_mtile));
+        // A wave of one tile per SM covers gm m-tiles x (SMs / gm) n-tiles, and
+        // its CTAs walk K roughly in step, so L2 only has to hold the current
+        // K chunk of the wave's operands while DRAM delivers each of its
+        // gm A tiles (128 rows) and SMs/gm B' tiles (BN rows) once: fewest
+        // bytes at gm^2 = SMs * BN / 128 (power of two at or below).
+        const int target = tc_num_sms() * bn / 128;
+        int g = 1;
+        while (4 * g * g <= target && g < 64) g *= 2;
+        a.gm = g;
     }
     a.sr = sr;
     a.err = d_err;

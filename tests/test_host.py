@@ -8,6 +8,7 @@ import re
 import numpy as np
 import pytest
 
+import oracle
 import rqcgen
 import paper_2407_00769_gb300 as tn
 
@@ -135,3 +136,22 @@ def test_workload_plans():
     c, q = rqcgen.grid_53q()
     i = _plan(c, q, n_slice_edges=-1, max_log2_elems=30, trials=2).info()
     assert i["max_log2_elems"] <= 30 and i["n_open"] == 12
+
+
+def test_plan_path_replayed_by_tn_oracle():
+    # the planner's path and slicing, handed to the FP64 network oracle as
+    # data, give the projector state vector's slices: the leaf sources and
+    # step ids mean what the header says
+    from oracle import tn as otn
+    c, q = rqcgen.small_grid(3, 4, 8, seed=3, n_open=4)
+    p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=2, torch_allocator=False)
+    keys = [("g", g) if g >= 0 else ("q", qq) for g, qq in p.leaf_sources()]
+    assert sorted(keys) == sorted(otn.leaf_keys(c))
+    st = p.steps()
+    assert [s["c"] for s in st] == list(range(len(keys), len(keys) + len(st)))
+    steps = [(s["a"], s["b"]) for s in st]
+    edges = p.sliced_edges()
+    for sid in range(4):
+        got = otn.contract(c, q, keys, steps, fixed=otn.slice_fixed(edges, sid))
+        want = oracle.sliced_amplitudes(c, q, edges, [sid])
+        assert np.max(np.abs(got - want)) <= 1e-13
