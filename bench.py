@@ -49,10 +49,11 @@ def parse():
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--legs", default="grid53,batch256",
+    ap.add_argument("--legs", default="grid53,batch256,fp8",
                     help="extra workloads timed after the main line (comma list, or 'none')")
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute"],
                     help="time one kernel on one shape instead (profiling aid)")
+    ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
     ap.add_argument("--lm", type=int, default=14)
     ap.add_argument("--ln", type=int, default=14)
     ap.add_argument("--lk", type=int, default=12)
@@ -74,8 +75,14 @@ def kernel_case(args):
         A = (torch.randn(b, M, K, 2, device="cuda", generator=g) * 0.5).half()
         B = (torch.randn(b, K, N, 2, device="cuda", generator=g) / (K ** 0.5)).half()
         C = torch.empty(b, M, N, 2, dtype=torch.float16, device="cuda")
-        run = lambda: tn.gemm(tn.F16, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
-                              scale_exp=0, kernel=3)
+        dt = tn.F16
+        if args.fp8:
+            # E4M3 operands (kind::f8f6f4), same shape
+            A = (A.float() * 64).to(torch.float8_e4m3fn)
+            B = (B.float() * 64 * (K ** 0.5)).to(torch.float8_e4m3fn)
+            dt = tn.FP8
+        run = lambda: tn.gemm(dt, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
+                              scale_exp=-12 if args.fp8 else 0, kernel=3)
         work, unit = 8.0 * M * N * K * b, "TFLOP/s"
     else:
         r = args.rank
@@ -337,6 +344,41 @@ def _oversample(recs):
     out = []
     for r, m in zip(recs, ms):
         out += [r] * int(np.clip(round(m / med), 1, 16))
+    return out
+
+
+def leg_fp8(tn, torch, dev, flush, stream, gold, min_log2_flops=40):
+    """The main workload with E4M3 operands on its largest tensor-core steps
+    (>= 2^40 flops per pass): throughput and error against FP64.  E4M3's 3
+    mantissa bits put each such step's error at a few percent, so this is
+    measured, not used for the headline."""
+    import rqcgen
+    c, q = rqcgen.grid_30q()
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                   slice_batch_log2=8, fp8_min_log2_flops=min_log2_flops)
+    info = plan.info()
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        plan.contract(out=amps)
+    torch.cuda.synchronize()
+    plan.profile(["gemm_tc", "quant"])
+    ms = _timed(lambda: plan.contract(out=amps), stream, flush, reps=3)
+    prof = plan.profile_read()
+    plan.profile(None)
+    flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
+    g = prof.get("gemm_tc", {"flops": 0, "ms": 1})
+    out = {"workload": "grid5x6-14c, all 256 slices, E4M3 operands on tensor-core steps of "
+                       f">= 2^{min_log2_flops} flops per pass",
+           "fp8_steps": sum(1 for s in plan.steps() if s["storage"] & 8),
+           "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+           "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3 / 3) / 1e12 if g["ms"] else None,
+           "quant_ms": prof.get("quant", {"ms": 0})["ms"] / 3}
+    if gold is not None:
+        m = tn.metrics(amps, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
+        out.update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"],
+                    "within_5e-3_budget": m["rel_l2"] <= 5e-3})
+    del plan, amps
+    torch.cuda.empty_cache()
     return out
 
 
@@ -659,6 +701,8 @@ def main():
         train += r
     if "grid40" in legs:
         line["grid40"] = leg_grid40(tn, torch, dev, flush, stream, train)
+    if "fp8" in legs:
+        line["fp8"] = leg_fp8(tn, torch, dev, flush, stream, gold)
 
     if not args.no_cpu_baseline and world == 1:
         full, sample, threads = oracle_sample()

@@ -57,6 +57,8 @@ extern "C" {
 #define TN_C64 0    /* complex64: FP32 re/im, FP32 SIMT arithmetic           */
 #define TN_F16 1    /* complex-half: FP16 re/im, tensor-core FP32 accumulate */
 #define TN_BF16 2   /* BF16 re/im, tensor-core FP32 accumulate               */
+#define TN_FP8 3    /* tn_gemm only: E4M3 re/im operands, FP16 result; in a
+                       plan, see tn_plan_opts.fp8_min_log2_flops          */
 
 /* ---- tile policies (which GEMM tile each step uses) ---- */
 #define TN_TILE_FIXED 0       /* built-in heuristic                              */
@@ -97,6 +99,11 @@ typedef struct {
                                  (0: default 16; > 40: every tensor)            */
     int32_t no_tensor_cores;  /* 1: complex-half steps on CUDA cores only
                                  (validation of the tensor-core path)           */
+    int32_t fp8_min_log2_flops; /* complex-half plans: tensor-core steps of at
+                                 least 2^this real flops per pass (and K >= 64)
+                                 take E4M3 operands (A and B' quantized with a
+                                 power-of-two scale, FP32 accumulate, result in
+                                 the plan's dtype); 0: never                    */
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *ctx);
@@ -145,7 +152,8 @@ typedef struct {
     int32_t permute_b;            /* 1 if B is permuted before the GEMM          */
     int32_t scale_headroom;       /* calibrated extra 2^e of the step's output   */
     int32_t storage;              /* bit 0: A, bit 1: B, bit 2: C stored
-                                     complex-half (else complex64)               */
+                                     complex-half (else complex64); bit 3: the
+                                     GEMM takes E4M3 copies of A and B'          */
 } tn_step_info;
 
 /*
@@ -359,7 +367,8 @@ int tn_plan_predict_ms(tn_plan_t *plan, tn_cost_model_t *model, double *ms, void
 #define TN_KC_GEMM_LP 4     /* complex-half GEMM on CUDA cores              */
 #define TN_KC_GEMM_C64 5    /* complex64 GEMMs on CUDA cores                */
 #define TN_KC_SUM 6         /* FP64 cross-slice sum                          */
-#define TN_KC_COUNT 7
+#define TN_KC_QUANT 7       /* E4M3 operand quantization (FP8 steps)         */
+#define TN_KC_COUNT 8
 
 typedef struct {
     int64_t launches;

@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build_mod
 
-C64, F16, BF16 = 0, 1, 2
+C64, F16, BF16, FP8 = 0, 1, 2, 3
 TILE_FIXED, TILE_EXHAUSTIVE, TILE_LEARNED = 0, 1, 2
 DTYPE_NAMES = {C64: "c64", F16: "f16", BF16: "bf16"}
 KERNEL_NAMES = {0: "c64_rows", 1: "c64_tiled", 2: "lp_rows", 3: "lp_tc"}
@@ -41,7 +41,7 @@ EXPORTED = [
     "tn_plan_predict_ms", "tn_plan_apply_tuning",
 ]
 COST_NFEAT = 26
-KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum"]
+KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum", "quant"]
 
 
 class TnError(RuntimeError):
@@ -75,6 +75,7 @@ class PlanOpts(ctypes.Structure):
                 ("path_trials", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
                 ("tile_policy", ctypes.c_int32), ("small_log2", ctypes.c_int32),
                 ("no_tensor_cores", ctypes.c_int32),
+                ("fp8_min_log2_flops", ctypes.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -263,7 +264,7 @@ class Plan:
                  n_slice_edges: int = 0, seed: int = 1, trials: int = 1,
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
-                 no_tensor_cores: bool = False):
+                 no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
@@ -278,6 +279,7 @@ class Plan:
         opts.tile_policy = int(tile_policy)
         opts.small_log2 = int(small_log2)
         opts.no_tensor_cores = 1 if no_tensor_cores else 0
+        opts.fp8_min_log2_flops = int(fp8_min_log2_flops)
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()

@@ -121,10 +121,10 @@ int op_class(const tn_plan_s *P, const Op &op, double &flops, double &bytes) {
         case OP_GEMM: {
             const GemmOp &g = op.gemm;
             flops = 8.0 * std::ldexp(1.0, g.lm + g.ln + g.lk + g.lb);
-            const double ea = dtype == TN_C64 ? 8 : (g.ta ? 4 : 8), eb = dtype == TN_C64 ? 8 : (g.tb ? 4 : 8),
-                         ec = dtype == TN_C64 ? 8 : (g.tc ? 4 : 8);
+            const double ea = dtype == TN_C64 ? 8 : g.fp8 ? 2 : (g.ta ? 4 : 8),
+                         eb = dtype == TN_C64 ? 8 : (g.tb ? 4 : 8), ec = dtype == TN_C64 ? 8 : (g.tc ? 4 : 8);
             const double bsz = g.kernel == GK_LP_TC
-                                   ? std::max(16.0, std::ldexp(2.0, g.ln)) * std::ldexp(4.0, g.lk)
+                                   ? std::max(16.0, std::ldexp(2.0, g.ln)) * std::ldexp(g.fp8 ? 2.0 : 4.0, g.lk)
                                    : std::ldexp(eb, g.lk + g.ln);
             bytes = std::ldexp(1.0, g.lb) * (std::ldexp(ea, g.lm + g.lk) + bsz + std::ldexp(ec, g.lm + g.ln));
             if (g.kernel == GK_LP_TC) return TN_KC_GEMM_TC;
@@ -132,6 +132,7 @@ int op_class(const tn_plan_s *P, const Op &op, double &flops, double &bytes) {
             return TN_KC_GEMM_C64;
         }
         case OP_SUM: bytes = std::ldexp(esz, op.sum.rank); return TN_KC_SUM;
+        case OP_QUANT: bytes = 6.0 * (double)op.quant.n_pairs; return TN_KC_QUANT;
     }
     return -1;
 }
@@ -233,6 +234,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.gm = tc_tile_gm(g.tile);
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
+                    d.fp8 = g.fp8;
                     e = launch_gemm_tc(d, sr, P->d_err, s);
                     break;
                 }
@@ -242,6 +244,14 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             ++launches;
             break;
         }
+        case OP_QUANT:
+            // the destination's max is an atomic max over the quantized values
+            e = cudaMemsetAsync(P->d_tmax + op.quant.meta_dst, 0, 4, s);
+            if (e == cudaSuccess)
+                e = launch_quant_e4m3(ws + op.quant.src, ws + op.quant.dst, op.quant.n_pairs, dtype, P->d_tmax,
+                                  P->d_texp, op.quant.meta_src, op.quant.meta_dst, s);
+            ++launches;
+            break;
         case OP_SUM:
             e = launch_slice_sum(ws + op.sum.src, dtype, op.sum, amps, P->net.n_open, t_lo, t_hi,
                                  overwrite, P->d_texp, P->d_stepcorr, (int)P->sched.steps.size(), s);
@@ -565,7 +575,7 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
         P->batch_log2 = o.slice_batch_log2;
         rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
                             o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
-                            P->sched, err);
+                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err);
         if (rc != TN_OK) { delete P; return fail(rc, err); }
         // leaf store
         int64_t offs = 0;
@@ -1166,6 +1176,34 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                                      batch, sa, sb, sc, s);
         else
             return fail(TN_EINVAL, "kernel variant not valid for TN_C64");
+    } else if (dtype == TN_FP8) {
+        // E4M3 A [batch][M][K] and B [batch][K][N] complex, FP16 result
+        if (kernel >= 0 && kernel != GK_LP_TC) return fail(TN_EINVAL, "TN_FP8 runs on the tensor cores only");
+        if (!tc_gemm_supported_fp8(lk, ln)) return fail(TN_EUNSUPPORTED, "FP8 tensor-core path needs K >= 64");
+        ScaleRef sr{};
+        sr.fixed_exp = scale_exp;
+        sr.out_max = out_max;
+        const int np = std::max(16, (int)(2 * N));
+        const int64_t bbatch = batch_b ? batch : 1;
+        void *bp = nullptr;
+        TN_CUDA(cudaMallocAsync(&bp, (size_t)np * 2 * K * bbatch, s), "cudaMallocAsync");
+        e = launch_bprep_e4m3(B, bp, lk, ln, bbatch, np, s);
+        if (e == cudaSuccess) {
+            TcGemmDesc d;
+            d.dtype = TN_F16;
+            d.A = A; d.Bp = bp; d.C = C;
+            d.lm = lm; d.ln = ln; d.lk = lk;
+            d.batch = batch;
+            d.batch_a = batch_a ? 1 : 0;
+            d.batch_b = batch_b ? 1 : 0;
+            d.np = np;
+            d.fp8 = 1;
+            const size_t pb = tc_split_bytes(lm, ln, lk, batch);
+            if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
+            if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);
+            if (d.partial) cudaFreeAsync(d.partial, s);
+        }
+        cudaFreeAsync(bp, s);
     } else if (dtype == TN_F16 || dtype == TN_BF16) {
         ScaleRef sr{};
         sr.fixed_exp = scale_exp;

@@ -56,6 +56,7 @@ enum OpKind : int32_t {
     OP_BPREP = 3,   // B [batch][K][N] complex-half -> B' real [batch][N'][K'] + colsum
     OP_GEMM = 4,    // one contraction step
     OP_SUM = 5,     // final tensor -> FP64 amplitudes
+    OP_QUANT = 6,   // complex-half -> E4M3 operand of an FP8 tensor-core step
 };
 
 enum GemmKernel : int32_t {
@@ -93,6 +94,13 @@ struct GemmOp {
     int32_t kernel, tile;
     int32_t headroom;     // extra power-of-two scale from calibration (complex-half)
     int32_t ta, tb, tc;   // storage of A, B, C: 0 complex64, 1 complex-half
+    int32_t fp8;          // tensor-core step on E4M3 copies of A and B'
+};
+
+struct QuantOp {
+    int64_t src, dst;     // byte offsets: complex-half (or B' real) -> E4M3
+    int64_t n_pairs;      // 16-bit value pairs
+    int32_t meta_src, meta_dst;
 };
 
 struct BprepOp {
@@ -129,6 +137,7 @@ struct Op {
     GemmOp gemm{};
     BprepOp bprep{};
     SumOp sum{};
+    QuantOp quant{};
 };
 
 // Record `msg` as the calling thread's last error (tn_last_error) and

@@ -3,6 +3,7 @@
 // cross-slice sum, FP64 reductions and top-k post-selection.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -794,6 +795,87 @@ cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int
     else
         bprep_kernel<__nv_bfloat16><<<g, threads, 0, s>>>((const __nv_bfloat16 *)B,
                                                           (__nv_bfloat16 *)Bp, lk, ln, np);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- E4M3 operands --
+template <int DT>
+__global__ void quant_e4m3_kernel(const typename LpT<DT>::T2 *__restrict__ src,
+                                  __nv_fp8x2_storage_t *__restrict__ dst, int64_t n, float *tmax,
+                                  int32_t *texp, int meta_src, int meta_dst) {
+    int sh = 0;
+    {
+        const float m = tmax[meta_src];
+        if (m > 0.0f && isfinite(m)) {
+            int x;
+            frexpf(448.0f / m, &x);           // 2^(x-1) <= 448 / m < 2^x
+            sh = max(-120, min(120, x - 1));
+        }
+    }
+    const float sc = exp2i(sh);
+    float mx = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = LpT<DT>::to_f2(src[i]);
+        v.x *= sc;
+        v.y *= sc;
+        const __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+        dst[i] = q;
+        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+        const float2 back = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+        mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
+    }
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&tmax[meta_dst], mx);
+    if (blockIdx.x == 0 && threadIdx.x == 0) texp[meta_dst] = texp[meta_src] + sh;
+}
+
+cudaError_t launch_quant_e4m3(const void *src, void *dst, int64_t n_pairs, int dtype, float *tmax,
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n_pairs + threads - 1) / threads,
+                                                                   (int64_t)tc_num_sms() * 8));
+    auto *d = reinterpret_cast<__nv_fp8x2_storage_t *>(dst);
+    if (dtype == TN_BF16)
+        quant_e4m3_kernel<TN_BF16><<<blocks, threads, 0, s>>>(
+            reinterpret_cast<const typename LpT<TN_BF16>::T2 *>(src), d, n_pairs, tmax, texp, meta_src,
+            meta_dst);
+    else
+        quant_e4m3_kernel<TN_F16><<<blocks, threads, 0, s>>>(
+            reinterpret_cast<const typename LpT<TN_F16>::T2 *>(src), d, n_pairs, tmax, texp, meta_src,
+            meta_dst);
+    return cudaGetLastError();
+}
+
+// B [batch][K][N] complex E4M3 (re, im bytes) -> B' [batch][np][2K]:
+// row (n, 0) = (Re, -Im) per k, row (n, 1) = (Im, Re); E4M3 negation is the
+// sign bit.  One uint16 (a k pair) per thread.
+__global__ void bprep_e4m3_kernel(const uint16_t *__restrict__ B, uint16_t *__restrict__ Bp, int lk,
+                                  int ln, int np) {
+    const int K = 1 << lk, N = 1 << ln;
+    const int64_t per = (int64_t)np * K;
+    const int64_t b = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(i / K), k = (int)(i % K);
+        const int n = row >> 1, co = row & 1;
+        uint16_t v = 0;
+        if (n < N) {
+            const uint16_t x = B[(b * K + k) * (int64_t)N + n];
+            v = co == 0 ? (uint16_t)(x ^ 0x8000u) : (uint16_t)((x >> 8) | (x << 8));
+        }
+        Bp[b * per + i] = v;
+    }
+}
+
+cudaError_t launch_bprep_e4m3(const void *B, void *Bp, int lk, int ln, int64_t batch, int np,
+                              cudaStream_t s) {
+    const int64_t per = (int64_t)np << lk;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((per + threads - 1) / threads, 4096);
+    if (batch > 65535) return cudaErrorInvalidValue;
+    dim3 g(blocks, (unsigned)batch);
+    bprep_e4m3_kernel<<<g, threads, 0, s>>>((const uint16_t *)B, (uint16_t *)Bp, lk, ln, np);
     return cudaGetLastError();
 }
 

@@ -93,7 +93,21 @@ struct TcGemmDesc {
     int gm = 0;            // m tiles per raster group (0: from the L2 budget)
     int out_c64 = 0;       // write C as complex64 (no rounding, exponent e = 0)
     float *partial = nullptr;  // tc_split_bytes() of FP32 partials when tc_split() > 1
+    int fp8 = 0;           // A and B' are E4M3 bytes (kind::f8f6f4), K >= 64
 };
+
+// E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs
+// (a complex-half tensor, or B' read as pairs of reals) -> E4M3 pairs scaled
+// by 2^s, s chosen on the device from tmax[meta_src] so that the largest
+// magnitude lands in (224, 448] (E4M3's largest finite value is 448); writes
+// tmax[meta_dst] (atomic max, slot zeroed beforehand) and texp[meta_dst] =
+// texp[meta_src] + s.  Round to nearest even, saturating.
+cudaError_t launch_quant_e4m3(const void *src, void *dst, int64_t n_pairs, int dtype, float *tmax,
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s);
+// B [batch][K][N] complex E4M3 -> B' [batch][np][2K] E4M3 (Eq. 6 padding)
+cudaError_t launch_bprep_e4m3(const void *B, void *Bp, int lk, int ln, int64_t batch, int np,
+                              cudaStream_t s);
+bool tc_gemm_supported_fp8(int lk, int ln);
 
 // Split-K: the tensor cores' FP32 accumulation over very long K drifts
 // (error growing with K), so a step with K > 2^kSplitLog2K complex is cut

@@ -83,8 +83,8 @@ struct BufReq {
 }  // namespace
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
-                   int batch_log2, int dtype, int small_log2, bool allow_tc, Schedule &S,
-                   std::string &err) {
+                   int batch_log2, int dtype, int small_log2, bool allow_tc, int fp8_min_log2_flops,
+                   Schedule &S, std::string &err) {
     S = Schedule();
     const int L = (int)net.leaves.size();
     const int NS = (int)path.steps.size();
@@ -254,7 +254,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             if (!shared.count(e)) no.push_back(e);
         no = for_consumer(c, no);
 
-        int meta_b_override = -1;
+        int meta_b_override = -1, meta_a_override = -1, fp8 = 0;
         StepRec rec{};
         rec.a = ia; rec.b = ib; rec.c = c;
         rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = nk; rec.lb = nb;
@@ -326,6 +326,32 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             ops.push_back(op);
             if (phase) S.bytes_per_pass += (double)(((int64_t)esz_of(ib) << (rec.lk + rec.ln + rec.lb)) + bpbytes);
             bbuf = tmp;
+            // FP8 step: E4M3 copies of B' and A, each with its own scale slot
+            if (fp8_min_log2_flops > 0 && rec.lk >= 6 &&
+                rec.lm + rec.ln + rec.lk + rec.lb + 3 >= fp8_min_log2_flops) {
+                auto quant = [&](int64_t src, int64_t pairs, int meta_src) {
+                    Op q;
+                    q.kind = OP_QUANT;
+                    q.phase = phase;
+                    q.quant.src = src;
+                    q.quant.n_pairs = pairs;
+                    q.quant.meta_src = meta_src;
+                    q.quant.meta_dst = S.n_meta + n_extra_meta++;
+                    const int t = new_temp(2 * pairs);
+                    q.quant.dst = t;
+                    ops.push_back(q);
+                    if (phase) S.bytes_per_pass += 6.0 * (double)pairs;
+                    return std::make_pair(t, q.quant.meta_dst);
+                };
+                const auto qb = quant(bbuf, bpbytes / 4, op.bprep.meta_dst);
+                bbuf = qb.first;
+                meta_b_override = qb.second;
+                const auto qa = quant(abuf, (int64_t)1 << (rec.lm + rec.lk + rec.lb), meta[ia]);
+                abuf = qa.first;
+                meta_a_override = qa.second;
+                fp8 = 1;
+                rec.storage |= 8;
+            }
         } else {
             std::vector<int> tgt(bo);
             tgt.insert(tgt.end(), ko.begin(), ko.end());
@@ -348,7 +374,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.lm = rec.lm; op.gemm.ln = rec.ln; op.gemm.lk = rec.lk; op.gemm.lb = rec.lb;
         op.gemm.a_batched = rec.lb > 0;
         op.gemm.b_batched = rec.lb > 0;
-        op.gemm.meta_a = meta[ia];
+        op.gemm.meta_a = meta_a_override >= 0 ? meta_a_override : meta[ia];
         op.gemm.meta_b = meta_b_override >= 0 ? meta_b_override : meta[ib];
         op.gemm.meta_c = meta[c];
         op.gemm.step = s;
@@ -357,6 +383,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.ta = ta;
         op.gemm.tb = tb;
         op.gemm.tc = tc;
+        op.gemm.fp8 = fp8;
         ops.push_back(op);
         ++S.n_gemm_steps;
         const double fl = 8.0 * std::ldexp(1.0, rec.lm + rec.ln + rec.lk + rec.lb);
@@ -411,6 +438,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
                 break;
             case OP_PERM: touch_read(op.perm.src, i); touch_create(op.perm.dst, i); break;
             case OP_BPREP: touch_read(op.bprep.src, i); touch_create(op.bprep.dst, i); break;
+            case OP_QUANT: touch_read(op.quant.src, i); touch_create(op.quant.dst, i); break;
             case OP_GEMM:
                 touch_read(op.gemm.a, i); touch_read(op.gemm.b, i); touch_create(op.gemm.c, i);
                 break;
@@ -435,6 +463,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         switch (op.kind) {
             case OP_PERM: op.perm.src = off(op.perm.src); op.perm.dst = off(op.perm.dst); break;
             case OP_BPREP: op.bprep.src = off(op.bprep.src); op.bprep.dst = off(op.bprep.dst); break;
+            case OP_QUANT: op.quant.src = off(op.quant.src); op.quant.dst = off(op.quant.dst); break;
             case OP_GEMM:
                 op.gemm.a = off(op.gemm.a); op.gemm.b = off(op.gemm.b); op.gemm.c = off(op.gemm.c);
                 break;

@@ -14,7 +14,8 @@
 //   * warp 1      : allocates TMEM and issues tcgen05.mma kind::f16
 //                   (M=128, N=BN, K=16 per instruction, FP32 accumulate in
 //                   TMEM), double-buffered accumulators, tcgen05.commit frees
-//                   ring stages and publishes finished tiles;
+//                   ring stages and publishes finished tiles; the FP8
+//                   variant issues kind::f8f6f4 with E4M3 operands (K=32);
 //   * warps 2..5  : epilogue -- tcgen05.ld rows out of TMEM, exact 2^e scale,
 //                   round to FP16/BF16, record max |C| for the next step's
 //                   exponent, store interleaved complex-half rows.
@@ -24,6 +25,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cstdio>
 #include <mutex>
@@ -108,23 +110,31 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
+template <bool F8>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                        uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (F8)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
 
 // K-major shared-memory matrix descriptor (tcgen05): start address, leading
 // byte offset (unused for swizzled K-major), stride byte offset = 8 rows,
-// descriptor version 1, swizzle mode.
-template <int BK>
+// descriptor version 1, swizzle mode.  BKB: bytes of one K chunk row.
+template <int BKB>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    constexpr uint32_t row_bytes = BK * 2;             // one swizzle row
+    constexpr uint32_t row_bytes = BKB;                // one swizzle row
     constexpr uint32_t sbo = 8 * row_bytes;            // 8-row core-matrix group
-    constexpr uint64_t layout = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // 128B / 64B / 32B
+    constexpr uint64_t layout = BKB == 128 ? 2 : (BKB == 64 ? 4 : 6);  // 128B / 64B / 32B
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                            // LBO (16 B, ignored)
@@ -200,21 +210,23 @@ __device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t 
     nt = (int)(in / gm);
 }
 
-template <int BN, int BK, int STAGES>
+template <int BN, int BKB, int STAGES>
 struct TcSmem {
-    static constexpr int a_bytes = 128 * BK * 2;
-    static constexpr int b_bytes = BN * BK * 2;
+    static constexpr int a_bytes = 128 * BKB;
+    static constexpr int b_bytes = BN * BKB;
     static constexpr int stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
     static constexpr int ring = STAGES * stage_bytes;
     static constexpr int bars = (2 * STAGES + 4) * 8;
     static constexpr int total = 1024 + ring + bars + 16;   // + alignment slack
 };
 
-template <int BN, int BK, int STAGES>
+// BKB: bytes of a K chunk per row (32, 64 or 128); F8: E4M3 operands.
+template <int BN, int BKB, int STAGES, bool F8>
 __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const TcArgs args) {
-    using S = TcSmem<BN, BK, STAGES>;
+    using S = TcSmem<BN, BKB, STAGES>;
+    constexpr int BK = F8 ? BKB : BKB / 2;             // K chunk in operand elements
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + S::ring);
@@ -298,7 +310,8 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         if (lane == 0) {
             uint32_t idesc = 0;
             idesc |= 1u << 4;                                  // D = F32
-            const uint32_t fmt = args.dtype == TN_BF16 ? 1u : 0u;
+            // kind::f16: 0 F16, 1 BF16; kind::f8f6f4: 0 E4M3
+            const uint32_t fmt = (!F8 && args.dtype == TN_BF16) ? 1u : 0u;
             idesc |= fmt << 7;                                 // A format
             idesc |= fmt << 10;                                // B format
             idesc |= (uint32_t)(BN >> 3) << 17;                // N
@@ -318,10 +331,10 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                     const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
                     const uint32_t b_addr = a_addr + S::a_bytes;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t ad = smem_desc<BK>(a_addr + kk * 32);
-                        const uint64_t bd = smem_desc<BK>(b_addr + kk * 32);
-                        tc_mma(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < BKB / 32; ++kk) {     // 32 bytes of K per MMA
+                        const uint64_t ad = smem_desc<BKB>(a_addr + kk * 32);
+                        const uint64_t bd = smem_desc<BKB>(b_addr + kk * 32);
+                        tc_mma<F8>(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                     }
                     tc_commit(&empty[stage]);
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -467,68 +480,71 @@ EncodeFn get_encode() {
     return fn;
 }
 
-bool encode_3d(CUtensorMap *m, int dtype, const void *base, uint64_t inner, uint64_t rows,
+// esz 2: FP16/BF16 elements (dtype), esz 1: E4M3 bytes
+bool encode_3d(CUtensorMap *m, int dtype, int esz, const void *base, uint64_t inner, uint64_t rows,
                uint64_t depth, uint32_t box_inner, uint32_t box_rows) {
     EncodeFn enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[3] = {inner, rows, depth};
-    const cuuint64_t strides[2] = {inner * 2, inner * rows * 2};
+    const cuuint64_t strides[2] = {inner * esz, inner * rows * esz};
     const cuuint32_t box[3] = {box_inner, box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapSwizzle sw = box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                  : box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+    const uint32_t row_bytes = box_inner * esz;
+    const CUtensorMapSwizzle sw = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                     : CU_TENSOR_MAP_SWIZZLE_32B;
-    const CUtensorMapDataType dt =
-        dtype == TN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const CUtensorMapDataType dt = esz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : dtype == TN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int BK>
+template <int BN, int BKB>
 struct TcCfg {
-    static constexpr int stage_bytes = (128 * BK * 2 + BN * BK * 2 + 1023) / 1024 * 1024;
+    static constexpr int stage_bytes = (128 * BKB + BN * BKB + 1023) / 1024 * 1024;
     static constexpr int stages0 = (196 * 1024) / stage_bytes;
     static constexpr int STAGES = stages0 > 12 ? 12 : (stages0 < 2 ? 2 : stages0);
 };
 
-template <int BN, int BK>
+template <int BN, int BKB, bool F8>
 cudaError_t set_attr() {
-    constexpr int ST = TcCfg<BN, BK>::STAGES;
-    using S = TcSmem<BN, BK, ST>;
-    return cudaFuncSetAttribute(gemm_tc_kernel<BN, BK, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                S::total);
+    constexpr int ST = TcCfg<BN, BKB>::STAGES;
+    using S = TcSmem<BN, BKB, ST>;
+    return cudaFuncSetAttribute(gemm_tc_kernel<BN, BKB, ST, F8>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, S::total);
 }
 
-template <int BK>
+template <int BKB, bool F8>
 cudaError_t set_attr_bn() {
-    cudaError_t e = set_attr<16, BK>();
-    if (e == cudaSuccess) e = set_attr<32, BK>();
-    if (e == cudaSuccess) e = set_attr<64, BK>();
-    if (e == cudaSuccess) e = set_attr<128, BK>();
-    if (e == cudaSuccess) e = set_attr<256, BK>();
+    cudaError_t e = set_attr<16, BKB, F8>();
+    if (e == cudaSuccess) e = set_attr<32, BKB, F8>();
+    if (e == cudaSuccess) e = set_attr<64, BKB, F8>();
+    if (e == cudaSuccess) e = set_attr<128, BKB, F8>();
+    if (e == cudaSuccess) e = set_attr<256, BKB, F8>();
     return e;
 }
 
-template <int BN, int BK>
+template <int BN, int BKB, bool F8>
 cudaError_t run_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, cudaStream_t s) {
-    constexpr int ST = TcCfg<BN, BK>::STAGES;
-    using S = TcSmem<BN, BK, ST>;
-    auto kern = gemm_tc_kernel<BN, BK, ST>;
+    constexpr int ST = TcCfg<BN, BKB>::STAGES;
+    using S = TcSmem<BN, BKB, ST>;
+    auto kern = gemm_tc_kernel<BN, BKB, ST, F8>;
     const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
     kern<<<(unsigned)grid, 192, S::total, s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
-template <int BK>
+template <int BKB, bool F8>
 cudaError_t run_tc_bn(int bn, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
                       cudaStream_t s) {
     switch (bn) {
-        case 16: return run_tc<16, BK>(ma, mb, a, s);
-        case 32: return run_tc<32, BK>(ma, mb, a, s);
-        case 64: return run_tc<64, BK>(ma, mb, a, s);
-        case 128: return run_tc<128, BK>(ma, mb, a, s);
-        case 256: return run_tc<256, BK>(ma, mb, a, s);
+        case 16: return run_tc<16, BKB, F8>(ma, mb, a, s);
+        case 32: return run_tc<32, BKB, F8>(ma, mb, a, s);
+        case 64: return run_tc<64, BKB, F8>(ma, mb, a, s);
+        case 128: return run_tc<128, BKB, F8>(ma, mb, a, s);
+        case 256: return run_tc<256, BKB, F8>(ma, mb, a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -553,14 +569,16 @@ cudaError_t tc_prepare() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 31 && ((done_mask >> dev) & 1)) return cudaSuccess;
-    cudaError_t e = set_attr_bn<16>();
-    if (e == cudaSuccess) e = set_attr_bn<32>();
-    if (e == cudaSuccess) e = set_attr_bn<64>();
+    cudaError_t e = set_attr_bn<32, false>();
+    if (e == cudaSuccess) e = set_attr_bn<64, false>();
+    if (e == cudaSuccess) e = set_attr_bn<128, false>();
+    if (e == cudaSuccess) e = set_attr_bn<128, true>();
     if (e == cudaSuccess && dev < 31) done_mask |= 1 << dev;
     return e;
 }
 
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
+bool tc_gemm_supported_fp8(int lk, int ln) { return lk >= 6 && lk <= 24 && ln <= 24; }
 
 // K parts of one tensor-core GEMM.  Each part accumulates at most
 // 2^kSplitLog2K complex terms in TMEM (the tensor cores' FP32 accumulation
@@ -588,13 +606,16 @@ size_t tc_split_bytes(int lm, int ln, int lk, int64_t batch) {
 }
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
-    if (!tc_gemm_supported(d.lk, d.ln)) return cudaErrorInvalidValue;
+    if (d.fp8 ? !tc_gemm_supported_fp8(d.lk, d.ln) : !tc_gemm_supported(d.lk, d.ln))
+        return cudaErrorInvalidValue;
     {
         const cudaError_t e = tc_prepare();
         if (e != cudaSuccess) return e;
     }
-    const int kreal = 2 << d.lk;                 // 2K
-    const int bk = kreal >= 64 ? 64 : kreal;     // 16, 32 or 64
+    const int esz = d.fp8 ? 1 : 2;
+    const int kreal = 2 << d.lk;                 // 2K elements
+    // K chunk: 128-byte rows where K allows (FP8: always, K >= 64)
+    const int bk = d.fp8 ? 128 : (kreal >= 64 ? 64 : kreal);
     int bn = d.np >= 256 ? 256 : d.np;           // 16 .. 256
     if (d.bn > 0) {
         if ((d.bn & (d.bn - 1)) != 0 || d.bn < 16 || d.bn > 256) return cudaErrorInvalidValue;
@@ -602,10 +623,10 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     }
     const int64_t M = (int64_t)1 << d.lm;
     CUtensorMap ma, mb;
-    if (!encode_3d(&ma, d.dtype, d.A, (uint64_t)kreal, (uint64_t)M,
+    if (!encode_3d(&ma, d.dtype, esz, d.A, (uint64_t)kreal, (uint64_t)M,
                    (uint64_t)(d.batch_a ? d.batch : 1), bk, 128))
         return cudaErrorInvalidValue;
-    if (!encode_3d(&mb, d.dtype, d.Bp, (uint64_t)kreal, (uint64_t)d.np,
+    if (!encode_3d(&mb, d.dtype, esz, d.Bp, (uint64_t)kreal, (uint64_t)d.np,
                    (uint64_t)(d.batch_b ? d.batch : 1), bk, bn))
         return cudaErrorInvalidValue;
     TcArgs a;
@@ -647,10 +668,14 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.sr = sr;
     a.err = d_err;
     cudaError_t e;
-    switch (bk) {
-        case 16: e = run_tc_bn<16>(bn, ma, mb, a, s); break;
-        case 32: e = run_tc_bn<32>(bn, ma, mb, a, s); break;
-        default: e = run_tc_bn<64>(bn, ma, mb, a, s); break;
+    if (d.fp8) {
+        e = run_tc_bn<128, true>(bn, ma, mb, a, s);
+    } else {
+        switch (bk) {
+            case 16: e = run_tc_bn<32, false>(bn, ma, mb, a, s); break;
+            case 32: e = run_tc_bn<64, false>(bn, ma, mb, a, s); break;
+            default: e = run_tc_bn<128, false>(bn, ma, mb, a, s); break;
+        }
     }
     if (e == cudaSuccess && a.split > 1)
         e = launch_splitk_reduce(a.partial, a.split, d.C, d.out_c64, d.dtype, d.batch, d.lm, d.ln, d.lk, sr, s);

@@ -215,3 +215,24 @@ def test_batch_of_uneven_circuits(dtype):
     tn.contract_batch(plans, outs2)
     for o, o2 in zip(outs, outs2):
         assert np.array_equal(o.cpu().numpy(), o2.cpu().numpy())
+
+
+@pytest.mark.parametrize("min_log2_flops", [44, 40, 1])
+def test_grid_30q_fp8_steps_measured(min_log2_flops):
+    # E4M3 operands on the tensor-core steps of at least 2^min_log2_flops
+    # flops per pass: the error against the FP64 state vector is measured and
+    # reported; E4M3 keeps 3 mantissa bits (relative rounding up to 2^-4), so
+    # each such step costs a few percent and the 5e-3 budget of the
+    # complex-half path does not hold.  Bounds here only catch a broken path.
+    want = _golden("grid5x6_14c_amps.txt")
+    c, q = rqcgen.grid_30q()
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=8, trials=4, slice_batch_log2=8,
+                fp8_min_log2_flops=min_log2_flops)
+    n8 = sum(1 for s in p.steps() if s["storage"] & 8)
+    assert n8 > 0
+    got = p.contract().cpu().numpy()
+    e = oracle.rel_l2(got, want)
+    f = oracle.fidelity(want, got)
+    print(f"grid30 f16 + e4m3 on {n8} steps (>= 2^{min_log2_flops} flops): rel_l2={e:.3e} fidelity={f:.6f}")
+    assert np.isfinite(e) and e < 0.5
+    assert f > 0.8

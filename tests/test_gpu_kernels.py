@@ -234,3 +234,37 @@ def test_gemm_f16_tensor_cores_long_k(M, N, K):
     got = torch.view_as_complex(c.double())[0]
     rel = (torch.linalg.norm(got - want) / torch.linalg.norm(want)).item()
     assert rel < 3e-4, rel
+
+
+@pytest.mark.parametrize("M,N,K,batch", [(128, 8, 64, 1), (256, 16, 128, 2), (1024, 128, 512, 1),
+                                         (512, 256, 1024, 1), (384, 4, 256, 1), (128, 32, 1 << 17, 1)])
+def test_gemm_fp8_tensor_cores(M, N, K, batch):
+    # E4M3 operands (kind::f8f6f4), FP32 accumulation, FP16 result; the
+    # reference is the FP64 product of the same E4M3 values
+    M = 1 << int(np.ceil(np.log2(M)))
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    a = (torch.randn(batch, M, K, 2, generator=g, device="cuda") * 16).to(torch.float8_e4m3fn)
+    b = (torch.randn(batch, K, N, 2, generator=g, device="cuda") * 16).to(torch.float8_e4m3fn)
+    c = torch.zeros(batch, M, N, 2, dtype=torch.float16, device="cuda")
+    mx = torch.zeros(1, dtype=torch.float32, device="cuda")
+    e = -int(np.ceil(np.log2(256 * np.sqrt(K)))) - 1
+    tn.gemm(tn.FP8, a, b, c, M, N, K, batch=batch, batch_a=True, batch_b=True, scale_exp=e,
+            kernel=3, out_max=mx)
+    ar = torch.view_as_complex(a.double())
+    br = torch.view_as_complex(b.double())
+    want = torch.matmul(ar, br) * 2.0 ** e
+    got = torch.view_as_complex(c.double())
+    mag = torch.matmul(ar.abs(), br.abs()) * 2.0 ** e
+    err = (got - want).abs()
+    tol = 2 * 2.0 ** -11 * want.abs() + 1e-6 * mag + 2.0 ** -24
+    assert bool((err <= tol).all()), float((err / (want.abs() + 1e-9)).max())
+    gmax = max(got.real.abs().max().item(), got.imag.abs().max().item())
+    assert abs(mx.item() - gmax) <= 1e-6 * gmax
+
+
+def test_gemm_fp8_rejects_short_k():
+    a = torch.zeros(128, 32, 2, dtype=torch.uint8, device="cuda")
+    b = torch.zeros(32, 8, 2, dtype=torch.uint8, device="cuda")
+    c = torch.zeros(128, 8, 2, dtype=torch.float16, device="cuda")
+    with pytest.raises(tn.TnError):
+        tn.gemm(tn.FP8, a, b, c, 128, 8, 32, kernel=3)

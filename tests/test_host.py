@@ -155,3 +155,27 @@ def test_plan_path_replayed_by_tn_oracle():
         got = otn.contract(c, q, keys, steps, fixed=otn.slice_fixed(edges, sid))
         want = oracle.sliced_amplitudes(c, q, edges, [sid])
         assert np.max(np.abs(got - want)) <= 1e-13
+
+
+def test_fp8_steps_are_marked_and_quantized():
+    c, q = rqcgen.grid_30q()
+    base = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=8, trials=4, torch_allocator=False)
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=8, trials=4, torch_allocator=False,
+                fp8_min_log2_flops=36)
+    s0, s1 = base.steps(), p.steps()
+    marked = [i for i, s in enumerate(s1) if s["storage"] & 8]
+    assert marked
+    for i in marked:
+        s = s1[i]
+        # only tensor-core steps with K >= 64 at or above the threshold
+        assert s["kernel"] == 3 and s["log2_k"] >= 6
+        assert s["log2_m"] + s["log2_n"] + s["log2_k"] + s["log2_batch"] + 3 >= 36
+    for i, s in enumerate(s1):
+        if i not in marked and s["kernel"] == 3 and s["log2_k"] >= 6:
+            assert s["log2_m"] + s["log2_n"] + s["log2_k"] + s["log2_batch"] + 3 < 36
+        assert (s["storage"] & 7) == s0[i]["storage"]
+    # the E4M3 copies are extra traffic, the flops are unchanged
+    assert p.info()["flops_per_slice"] == base.info()["flops_per_slice"]
+    assert p.info()["bytes_per_slice"] > base.info()["bytes_per_slice"]
+    c64 = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=8, trials=4, torch_allocator=False, fp8_min_log2_flops=1)
+    assert not any(s["storage"] & 8 for s in c64.steps())
