@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--legs", default="grid53,batch256,fp8",
+    ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute"],
                     help="time one kernel on one shape instead (profiling aid)")
@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--rank", type=int, default=28)
     return ap.parse_args()
+
+
+def _plain(o):
+    """JSON fallback for numpy scalars."""
+    return o.item() if hasattr(o, "item") else str(o)
 
 
 def kernel_case(args):
@@ -206,8 +211,16 @@ def oracle_sample(seconds_target=15.0, max_gates=None):
     t = run(g)
     per_gate = (t - t_init) / g
     full = t_init + per_gate * c.n_gates
+    # one core: two gates of the same circuit, scaled the same way
+    oracle.set_threads(1)
+    try:
+        t1_init = run(0)
+        t1 = run(2)
+        full_1 = t1_init + (t1 - t1_init) / 2 * c.n_gates
+    finally:
+        oracle.set_threads(threads)
     return full, (f"FP64 state vector of the 30-qubit circuit (2^30 amplitudes, 16 GiB), first "
-                  f"{g} of {c.n_gates} gates timed ({t:.1f} s), scaled to all gates"), threads
+                  f"{g} of {c.n_gates} gates timed ({t:.1f} s), scaled to all gates"), threads, full_1
 
 
 def reference_arm(args):
@@ -245,7 +258,7 @@ def reference_arm(args):
                              "kind": "oracle", "sample": sub_t},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_plain), flush=True)
 
 
 # ------------------------------------------------------------ extra legs
@@ -263,6 +276,34 @@ def _timed(fn, stream, flush, reps=1):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     return statistics.mean(ts)
+
+
+def leg_grid12(tn, torch, dev, stream):
+    """The small exact case: 12-qubit 3x4 grid, 8 cycles, no slicing, all
+    4096 amplitudes in complex64 -- a latency figure (median of 20 calls,
+    inputs resident) with its error against the FP64 state vector."""
+    import oracle
+    import rqcgen
+    c, q = rqcgen.grid_12q()
+    plan = tn.Plan(c, q, dtype=tn.C64)
+    amps = torch.zeros(1 << 12, dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        plan.contract(out=amps)
+    ts = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.contract(out=amps)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    want = oracle.amplitudes(c, q)
+    got = amps.cpu().numpy()
+    info = plan.info()
+    return {"workload": "grid3x4-8c: 12 qubits, 8 cycles, unsliced, 4096 amplitudes, complex64",
+            "ms_median": statistics.median(ts), "steps": info["n_steps"],
+            "rel_l2": float(oracle.rel_l2(got, want))}
 
 
 def leg_grid53(tn, torch, dev, flush, stream, peaks, want_records=False):
@@ -347,6 +388,48 @@ def _oversample(recs):
     return out
 
 
+def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
+    """Paths refined by simulated annealing (tree rotations under the memory
+    cap, sliced edges given back where the refined path allows): the 30-qubit
+    job (8 sliced edges, all 256 slices) and the 53-qubit circuit at cap 2^30
+    (slices 0-63 timed, the time of all slices extrapolated).  Reported as
+    time to solution against the greedy plans of the main line and grid53."""
+    import rqcgen
+    out = {}
+    c, q = rqcgen.grid_30q()
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                   slice_batch_log2=8, anneal_iters=iters, tile_policy=tn.TILE_EXHAUSTIVE)
+    info = plan.info()
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    for _ in range(3):
+        plan.contract(out=amps)
+    ms = _timed(lambda: plan.contract(out=amps), stream, flush, reps=3)
+    flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
+    out["grid30"] = {"job_flops": flops, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "slices_per_s": info["n_slices"] / (ms * 1e-3), "max_log2_elems": info["max_log2_elems"]}
+    if gold is not None:
+        m = tn.metrics(amps, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
+        out["grid30"].update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]})
+    del plan, amps
+    torch.cuda.empty_cache()
+    c, q = rqcgen.grid_53q()
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=1,
+                   slice_batch_log2=3, anneal_iters=iters)
+    info = plan.info()
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    n = min(64, info["n_slices"])
+    plan.contract(0, n, out=amps)
+    ms = _timed(lambda: plan.contract(0, n, out=amps), stream, flush)
+    flops = info["flops_per_slice"] * n + info["flops_invariant"]
+    out["grid53"] = {"n_slices": info["n_slices"], "timed_slices": n, "ms": ms,
+                     "tflops": flops / (ms * 1e-3) / 1e12,
+                     "job_flops": info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"],
+                     "est_job_s": ms * 1e-3 * info["n_slices"] / n, "max_log2_elems": info["max_log2_elems"]}
+    del plan, amps
+    torch.cuda.empty_cache()
+    return out
+
+
 def leg_fp8(tn, torch, dev, flush, stream, gold, min_log2_flops=40):
     """The main workload with E4M3 operands on its largest tensor-core steps
     (>= 2^40 flops per pass): throughput and error against FP64.  E4M3's 3
@@ -376,7 +459,7 @@ def leg_fp8(tn, torch, dev, flush, stream, gold, min_log2_flops=40):
     if gold is not None:
         m = tn.metrics(amps, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
         out.update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"],
-                    "within_5e-3_budget": m["rel_l2"] <= 5e-3})
+                    "within_5e-3_budget": bool(m["rel_l2"] <= 5e-3)})
     del plan, amps
     torch.cuda.empty_cache()
     return out
@@ -610,6 +693,12 @@ def main():
                                   "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9,
                                   "gbs": v["bytes"] / max(v["ms"], 1e-9) / 1e6}
                               for k, v in prof.items()}}
+    # the HBM-bound kernels against the measured copy bandwidth
+    hbm = peaks.get("hbm_gbs")
+    for k in ("permute", "bprep", "quant"):
+        v = roofline["per_class"].get(k)
+        if v and v["launches"] and hbm:
+            v["frac_of_hbm"] = v["gbs"] / hbm
     # DRAM traffic per launch from the committed ncu capture, only while the
     # kernel source is the one that was captured
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
@@ -693,6 +782,8 @@ def main():
     del plan
     torch.cuda.empty_cache()
     side = torch.cuda.Stream()
+    if "grid12" in legs:
+        line["grid12"] = leg_grid12(tn, torch, dev, stream)
     if "grid53" in legs:
         line["grid53"], r = leg_grid53(tn, torch, dev, flush, stream, peaks, want_records="grid40" in legs)
         train += r
@@ -703,13 +794,18 @@ def main():
         line["grid40"] = leg_grid40(tn, torch, dev, flush, stream, train)
     if "fp8" in legs:
         line["fp8"] = leg_fp8(tn, torch, dev, flush, stream, gold)
+    if "anneal" in legs:
+        line["anneal"] = leg_anneal(tn, torch, dev, flush, stream, gold)
 
     if not args.no_cpu_baseline and world == 1:
-        full, sample, threads = oracle_sample()
+        full, sample, threads, full_1 = oracle_sample()
         line["cpu_baseline"] = {"value": job_flops / full / 1e12, "unit": "TFLOP/s",
                                 "cores": threads, "kind": "oracle", "sample": sample,
-                                "est_seconds_per_step": full}
-    print(json.dumps(line), flush=True)
+                                "est_seconds_per_step": full,
+                                "one_core": {"value": job_flops / full_1 / 1e12,
+                                             "est_seconds_per_step": full_1,
+                                             "sample": "first 2 gates on 1 thread, scaled"}}
+    print(json.dumps(line, default=_plain), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -72,7 +72,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class PlanOpts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("max_log2_elems", ctypes.c_int32),
                 ("n_slice_edges", ctypes.c_int32), ("path_seed", ctypes.c_uint64),
-                ("path_trials", ctypes.c_int32), ("slice_batch_log2", ctypes.c_int32),
+                ("path_trials", ctypes.c_int32), ("path_anneal_iters", ctypes.c_int32),
+                ("slice_batch_log2", ctypes.c_int32),
                 ("tile_policy", ctypes.c_int32), ("small_log2", ctypes.c_int32),
                 ("no_tensor_cores", ctypes.c_int32),
                 ("fp8_min_log2_flops", ctypes.c_int32),
@@ -264,7 +265,7 @@ class Plan:
                  n_slice_edges: int = 0, seed: int = 1, trials: int = 1,
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
-                 no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0):
+                 no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
@@ -275,6 +276,7 @@ class Plan:
         opts.n_slice_edges = int(n_slice_edges)
         opts.path_seed = int(seed)
         opts.path_trials = int(trials)
+        opts.path_anneal_iters = int(anneal_iters)
         opts.slice_batch_log2 = int(slice_batch_log2)
         opts.tile_policy = int(tile_policy)
         opts.small_log2 = int(small_log2)

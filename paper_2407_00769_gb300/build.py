@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtn.so")
 
-SOURCES = ["network.cpp", "path.cpp", "schedule.cpp", "kernels.cu", "tc_gemm.cu", "api.cu",
+SOURCES = ["network.cpp", "path.cpp", "anneal.cpp", "schedule.cpp", "kernels.cu", "tc_gemm.cu", "api.cu",
            "sample_noalloc.cu", "mlp.cu"]
 HEADERS = ["internal.h", "plan.h", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -552,6 +552,7 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
     if (o.slice_batch_log2 < 0 || o.slice_batch_log2 > 16) return fail(TN_EINVAL, "slice_batch_log2 must be in 0..16");
     if (o.tile_policy < 0 || o.tile_policy > 2) return fail(TN_EINVAL, "bad tile_policy");
     if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
+    if (o.path_anneal_iters < 0) return fail(TN_EINVAL, "path_anneal_iters must be >= 0");
     try {
         tn_plan_s *P = new tn_plan_s();
         P->opts = o;
@@ -563,6 +564,12 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
         if (n_target < 0 && cap <= 0) { delete P; return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0"); }
         rc = choose_slices(P->net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
         if (rc != TN_OK) { delete P; return fail(rc, err); }
+        if (o.path_anneal_iters > 0)
+            // kappa: flops one element of HBM traffic is worth at the ridge
+            // (complex-half 4 B x ~250 flop/B on the tensor cores; complex64
+            // 8 B x ~12 flop/B on the CUDA cores)
+            refine_plan(P->net, n_target, cap, o.path_seed, o.path_anneal_iters,
+                        o.dtype == TN_C64 ? 100.0 : 1000.0, P->path, P->sliced);
         if (cap > 0 && P->path.max_log2 > cap) {
             delete P;
             return fail(TN_EINVAL, "the slicing does not reach the cap (largest intermediate 2^" +

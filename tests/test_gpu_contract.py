@@ -236,3 +236,18 @@ def test_grid_30q_fp8_steps_measured(min_log2_flops):
     print(f"grid30 f16 + e4m3 on {n8} steps (>= 2^{min_log2_flops} flops): rel_l2={e:.3e} fidelity={f:.6f}")
     assert np.isfinite(e) and e < 0.5
     assert f > 0.8
+
+
+@pytest.mark.parametrize("dtype,batch", [(tn.C64, 0), (tn.F16, 8)])
+def test_grid_30q_annealed_path_full_size(dtype, batch):
+    # the same 256 slices on a path refined by simulated annealing (about 20x
+    # fewer flops than the greedy path), against the FP64 state vector
+    want = _golden("grid5x6_14c_amps.txt")
+    c, q = rqcgen.grid_30q()
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=8, trials=4, slice_batch_log2=batch,
+                anneal_iters=200000)
+    got = p.contract()
+    e, f = check(got, want, dtype)
+    i = p.info()
+    print(f"grid30 annealed {tn.DTYPE_NAMES[dtype]}: {i['flops_per_slice'] * i['n_slices'] + i['flops_invariant']:.3e} "
+          f"flops, rel_l2={e:.3e} fidelity={f:.6f}")

@@ -179,3 +179,32 @@ def test_fp8_steps_are_marked_and_quantized():
     assert p.info()["bytes_per_slice"] > base.info()["bytes_per_slice"]
     c64 = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=8, trials=4, torch_allocator=False, fp8_min_log2_flops=1)
     assert not any(s["storage"] & 8 for s in c64.steps())
+
+
+@pytest.mark.parametrize("n_slice,cap", [(2, 0), (-1, 7)])
+def test_annealed_path_is_valid_and_cheaper(n_slice, cap):
+    # simulated annealing over tree rotations (Sec. 3 path search): the
+    # refined path and its slices still give the projector state vector's
+    # slices (FP64 network oracle, path as data), within the same width,
+    # for no more flops than the greedy path
+    from oracle import tn as otn
+    c, q = rqcgen.small_grid(3, 4, 8, seed=3, n_open=4)
+    kw = dict(dtype=tn.C64, n_slice_edges=n_slice, max_log2_elems=cap, torch_allocator=False)
+    g = tn.Plan(c, q, **kw)
+    a = tn.Plan(c, q, anneal_iters=20000, **kw)
+    gi, ai = g.info(), a.info()
+    total = lambda i: i["flops_per_slice"] * i["n_slices"] + i["flops_invariant"]
+    assert total(ai) <= total(gi)
+    if cap:
+        assert ai["max_log2_elems"] <= cap
+    else:
+        assert ai["max_log2_elems"] <= gi["max_log2_elems"]
+    keys = [("g", gg) if gg >= 0 else ("q", qq) for gg, qq in a.leaf_sources()]
+    steps = [(s["a"], s["b"]) for s in a.steps()]
+    edges = a.sliced_edges()
+    full = 0
+    for sid in range(ai["n_slices"]):
+        got = otn.contract(c, q, keys, steps, fixed=otn.slice_fixed(edges, sid))
+        assert np.max(np.abs(got - oracle.sliced_amplitudes(c, q, edges, [sid]))) <= 1e-13
+        full = full + got
+    assert np.max(np.abs(full - oracle.amplitudes(c, q))) <= 1e-13
