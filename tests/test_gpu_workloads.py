@@ -88,7 +88,7 @@ def test_grid53_slice0_against_network_oracle(dtype, batch, tol):
     # the stored values are for these sliced wires; the path only ordered
     # the oracle's work
     assert p.sliced_edges() == edges
-    assert [(s["a"], s["b"]) for s in p.steps()] == steps
+    assert [tuple(sorted((s["a"], s["b"]))) for s in p.steps()] == [tuple(sorted(x)) for x in steps]
     got = p.contract(0, 1).cpu().numpy()
     del p
     torch.cuda.empty_cache()
