@@ -514,6 +514,7 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 // K is walked in chunks of KC.
 constexpr int kRows = 128;
 constexpr int kKC = 32;
+constexpr int kFlushK = 256;   // FP32 terms per partial sum before the FP64 add
 
 // operand conversion: complex64 as is, complex-half widened to FP32
 template <typename T, int DT>
@@ -542,9 +543,15 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const TB *Bb = B + b * sb;
     TC *Cb = C + b * sc;
     const int rows = (int)min((int64_t)kRows, M - m0);
+    // FP32 partial sums over at most kFlushK terms, added into FP64: a long
+    // FP32 running sum would lose ~sqrt(K) ulps (2^23-term steps occur)
     float2 acc[NC];
+    double2 tot[NC];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < NC; ++j) {
+        acc[j] = make_float2(0.f, 0.f);
+        tot[j] = make_double2(0.0, 0.0);
+    }
     for (int k0 = 0; k0 < K; k0 += KC) {
         const int kc = min(KC, K - k0);
         __syncthreads();
@@ -581,7 +588,17 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
                 }
             }
         }
+        if (((k0 + KC) % kFlushK) == 0 || k0 + KC >= K) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                tot[j].x += acc[j].x;
+                tot[j].y += acc[j].y;
+                acc[j] = make_float2(0.f, 0.f);
+            }
+        }
     }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = make_float2((float)tot[j].x, (float)tot[j].y);
     if (threadIdx.x >= rows) return;
     const int64_t m = m0 + threadIdx.x;
     TC *crow = Cb + m * N + n0;
@@ -689,7 +706,10 @@ cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C
 // ---------------------------------------------------------- tiled c64 --
 // 64x64 output tile per block of 256 threads, 4x4 complex outputs per
 // thread, K in chunks of 16 staged through shared memory.  Needs M, N >= 64.
-template <int BM, int BN, int BK>
+// LONGK: FP32 partial sums over kFlushK terms added into FP64 (for K >
+// 2^12, where one FP32 running sum would lose ~sqrt(K) ulps); the short-K
+// instance keeps the FP32 sum and half the registers.
+template <int BM, int BN, int BK, bool LONGK>
 __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
     const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C, int lm,
     int ln, int lk, int64_t sa, int64_t sb, int64_t sc) {
@@ -704,10 +724,14 @@ __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
     const float2 *Bb = B + b * sb + n0;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float2 acc[TM][TN];
+    double2 tot[LONGK ? TM : 1][LONGK ? TN : 1];   // FP64 sum of the FP32 partials
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < TN; ++j) {
+            acc[i][j] = make_float2(0.f, 0.f);
+            if constexpr (LONGK) tot[i][j] = make_double2(0.0, 0.0);
+        }
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int i = threadIdx.x; i < BM * BK; i += 256) {
             const int r = i / BK, kk = i % BK;
@@ -734,12 +758,28 @@ __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
                 }
         }
         __syncthreads();
+        if constexpr (LONGK) {
+            if (((k0 + BK) % kFlushK) == 0 || k0 + BK >= K) {
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        tot[i][j].x += acc[i][j].x;
+                        tot[i][j].y += acc[i][j].y;
+                        acc[i][j] = make_float2(0.f, 0.f);
+                    }
+            }
+        }
     }
     float2 *Cb = C + b * sc + m0 * N + n0;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) Cb[(int64_t)(ty * TM + i) * N + tx + 16 * j] = acc[i][j];
+        for (int j = 0; j < TN; ++j) {
+            float2 v = acc[i][j];
+            if constexpr (LONGK) v = make_float2((float)tot[i][j].x, (float)tot[i][j].y);
+            Cb[(int64_t)(ty * TM + i) * N + tx + 16 * j] = v;
+        }
 }
 
 cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
@@ -750,7 +790,10 @@ cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, i
     const int64_t gx = ((int64_t)1 << lm) / 64;
     if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
     dim3 g((unsigned)gx, (unsigned)((1 << ln) / 64), (unsigned)batch);
-    gemm_tiled_c64_kernel<64, 64, 16><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
+    if (lk > 12)
+        gemm_tiled_c64_kernel<64, 64, 16, true><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
+    else
+        gemm_tiled_c64_kernel<64, 64, 16, false><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
     return cudaGetLastError();
 }
 
