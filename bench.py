@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
-    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute"],
+    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather"],
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
+    ap.add_argument("--padded", action="store_true", help="--case gather with the padded 2-D index")
     ap.add_argument("--lm", type=int, default=14)
     ap.add_argument("--ln", type=int, default=14)
     ap.add_argument("--lk", type=int, default=12)
@@ -89,6 +90,22 @@ def kernel_case(args):
         run = lambda: tn.gemm(dt, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
                               scale_exp=-12 if args.fp8 else 0, kernel=3)
         work, unit = 8.0 * M * N * K * b, "TFLOP/s"
+    elif args.case == "gather":
+        # sparse-state contraction of many tensor pairs: 2048 A chunks of
+        # 256 x 1024 complex, 64 B chunks of 1024 x 16, 16384 pairs (sorted
+        # A indices, about 8 per A chunk), both index schemes timed
+        import numpy as np
+        m_a, m_b, m_n, M, K, N = 2048, 64, 16384, 256, 1024, 16
+        g = torch.Generator(device="cuda").manual_seed(2)
+        A = torch.randn(m_a, M, K, 2, device="cuda", generator=g).half()
+        B = (torch.randn(m_b, K, N, 2, device="cuda", generator=g) / K ** 0.5).half()
+        C = torch.empty(m_n, M, N, 2, dtype=torch.float16, device="cuda")
+        rng = np.random.default_rng(3)
+        ia = np.sort(rng.integers(0, m_a, size=m_n))
+        ib = rng.integers(0, m_b, size=m_n)
+        scheme = tn.GATHER_PADDED if args.padded else tn.GATHER_DIRECT
+        run = lambda: tn.gemm_gather(tn.F16, A, B, C, ia, ib, scheme=scheme)
+        work, unit = 8.0 * M * N * K * m_n, "TFLOP/s"
     else:
         r = args.rank
         x = torch.empty(1 << r, dtype=torch.int32, device="cuda").random_()

@@ -416,6 +416,38 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
             int32_t kernel, float *out_max, void *stream);
 
 /*
+ * tn_gemm_gather: contraction of many tensor pairs in the sparse state (paper
+ * Sec. 3.4.2).  A holds m_a chunks [m_a][M][K], B holds m_b chunks
+ * [m_b][K][N], C receives m_n chunks [m_n][M][N], all complex-half (dtype
+ * TN_F16 or TN_BF16, interleaved re/im, device memory, caller-owned):
+ *
+ *     C[n] = 2^scale_exp A[index_a[n]] B[index_b[n]]      (0 <= n < m_n)
+ *
+ * index_a, index_b: HOST int32 arrays of m_n entries in [0, m_a) and
+ * [0, m_b); m_a, m_n <= 2^30, m_b <= 65535.  The tensor-core GEMM reads the operand chunks where they are
+ * (TMA coordinates from the indices, no gathered copy).  scheme:
+ *   TN_GATHER_DIRECT  one output chunk per n;
+ *   TN_GATHER_PADDED  index_a non-decreasing: the paper's padded 2-D index,
+ *                     P[i][r] = the B chunk of the r-th n paired with A chunk
+ *                     i, -1 past its count (m_r columns, m_r = the largest
+ *                     repeat count, written to *out_m_r if non-NULL); tiles
+ *                     walk (i, r) so one A chunk serves all its r in turn,
+ *                     the -1 places are computed and not stored, and C is
+ *                     written straight at the valid places (the extraction).
+ * M, N, K powers of two, N <= 2^24, 8 <= K <= 2^15.  out_max (device,
+ * nullable) receives max |C| (atomic max on a zeroed float).  Enqueued on
+ * `stream`; device scratch is allocated stream-ordered and freed after.
+ * Errors: TN_EINVAL (NULL pointers, sizes, index out of range, unsorted
+ * index_a for TN_GATHER_PADDED), TN_EUNSUPPORTED (K outside the range).
+ */
+#define TN_GATHER_DIRECT 0
+#define TN_GATHER_PADDED 1
+int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int64_t m_b, void *C,
+                   int64_t m_n, int64_t M, int64_t N, int64_t K, const int32_t *index_a,
+                   const int32_t *index_b, int32_t scheme, int32_t scale_exp, float *out_max,
+                   int32_t *out_m_r, void *stream);
+
+/*
  * tn_selftest_wait_timeout: failure-detection self-test.  Launches one small
  * tensor-core GEMM whose TMA producer is told to issue nothing, so the MMA
  * warp's bounded mbarrier wait runs out (about 2 s); the kernel then records

@@ -38,7 +38,7 @@ EXPORTED = [
     "tn_plan_tune", "tn_tune_records",
     "tn_cost_model_create", "tn_cost_model_destroy", "tn_cost_model_params", "tn_cost_model_grad",
     "tn_cost_model_train", "tn_cost_model_predict", "tn_cost_features", "tn_plan_set_cost_model",
-    "tn_plan_predict_ms", "tn_plan_apply_tuning",
+    "tn_plan_predict_ms", "tn_plan_apply_tuning", "tn_gemm_gather",
 ]
 COST_NFEAT = 26
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum", "quant"]
@@ -182,6 +182,9 @@ def lib():
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
         L.tn_gemm.argtypes = [i32, vp, vp, vp, i64, i64, i64, i64, i32, i32, i32, i32, vp, vp]
+        L.tn_gemm_gather.argtypes = [i32, vp, i64, vp, i64, vp, i64, i64, i64, i64,
+                                     ctypes.POINTER(i32), ctypes.POINTER(i32), i32, i32, vp,
+                                     ctypes.POINTER(i32), vp]
         L.tn_profile.argtypes = [vp, ctypes.c_uint32]
         L.tn_profile_read.argtypes = [vp, ctypes.POINTER(KernelStats)]
         L.tn_strerror.argtypes = [ctypes.c_int]
@@ -612,6 +615,29 @@ def permute(x, perm, out=None, elem_bytes=None, stream=None):
     _check(lib().tn_permute(x.data_ptr(), out.data_ptr(), r, p, int(elem_bytes),
                             _stream_ptr(stream)))
     return out
+
+
+GATHER_DIRECT, GATHER_PADDED = 0, 1
+
+
+def gemm_gather(dtype, A, B, C, index_a, index_b, scheme=GATHER_DIRECT, scale_exp=0, out_max=None,
+                stream=None):
+    """Sparse-state contraction of many tensor pairs (tn_gemm_gather):
+    C[n] = 2^scale_exp A[index_a[n]] B[index_b[n]]; A [m_a][M][K][2],
+    B [m_b][K][N][2], C [m_n][M][N][2] complex-half CUDA tensors; the index
+    arrays are host sequences.  Returns m_r (the padded index's columns)."""
+    ia = np.ascontiguousarray(index_a, dtype=np.int32)
+    ib = np.ascontiguousarray(index_b, dtype=np.int32)
+    m_a, M, K = int(A.shape[0]), int(A.shape[1]), int(A.shape[2])
+    m_b, N = int(B.shape[0]), int(B.shape[2])
+    m_r = ctypes.c_int32(0)
+    _check(lib().tn_gemm_gather(int(dtype), A.data_ptr(), m_a, B.data_ptr(), m_b, C.data_ptr(),
+                                int(ia.shape[0]), M, N, K,
+                                ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                ib.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(scheme),
+                                int(scale_exp), out_max.data_ptr() if out_max is not None else None,
+                                ctypes.byref(m_r), _stream_ptr(stream)))
+    return m_r.value
 
 
 def gemm(dtype, A, B, C, M, N, K, batch=1, batch_a=False, batch_b=False, scale_exp=0,

@@ -1251,6 +1251,107 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
     return TN_OK;
 }
 
+int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int64_t m_b, void *C,
+                   int64_t m_n, int64_t M, int64_t N, int64_t K, const int32_t *index_a,
+                   const int32_t *index_b, int32_t scheme, int32_t scale_exp, float *out_max,
+                   int32_t *out_m_r, void *stream) {
+    if (!A || !B || !C || !index_a || !index_b) return fail(TN_EINVAL, "NULL argument");
+    if (dtype != TN_F16 && dtype != TN_BF16) return fail(TN_EINVAL, "tn_gemm_gather: dtype must be TN_F16 or TN_BF16");
+    if (scheme != TN_GATHER_DIRECT && scheme != TN_GATHER_PADDED) return fail(TN_EINVAL, "bad scheme");
+    auto lg = [](int64_t v) {
+        int l = 0;
+        while (l < 62 && ((int64_t)1 << l) < v) ++l;
+        return (((int64_t)1 << l) == v) ? l : -1;
+    };
+    const int lm = lg(M), ln = lg(N), lk = lg(K);
+    if (lm < 0 || ln < 0 || lk < 0 || lm > 30 || ln > 24) return fail(TN_EINVAL, "M, N, K must be powers of two");
+    if (lk < 3 || lk > kSplitLog2K) return fail(TN_EUNSUPPORTED, "tn_gemm_gather needs 8 <= K <= 2^15");
+    if (m_a < 1 || m_b < 1 || m_n < 1 || m_a > (1 << 30) || m_b > 65535 || m_n > (1 << 30))
+        return fail(TN_EINVAL, "chunk counts: m_a, m_n in 1..2^30, m_b in 1..65535");
+    for (int64_t n = 0; n < m_n; ++n) {
+        if (index_a[n] < 0 || index_a[n] >= m_a || index_b[n] < 0 || index_b[n] >= m_b)
+            return fail(TN_EINVAL, "index out of range at n = " + std::to_string(n));
+        if (scheme == TN_GATHER_PADDED && n > 0 && index_a[n] < index_a[n - 1])
+            return fail(TN_EINVAL, "TN_GATHER_PADDED needs a non-decreasing index_a");
+    }
+    // per tile-batch entry: A chunk, B' chunk, output chunk
+    std::vector<int32_t> z;
+    int64_t T = 0;
+    int32_t m_r = 0;
+    if (scheme == TN_GATHER_DIRECT) {
+        T = m_n;
+        z.resize(3 * T);
+        for (int64_t n = 0; n < m_n; ++n) {
+            z[n] = index_a[n];
+            z[T + n] = index_b[n];
+            z[2 * T + n] = (int32_t)n;
+        }
+    } else {
+        std::vector<int32_t> count(m_a, 0);
+        for (int64_t n = 0; n < m_n; ++n) m_r = std::max(m_r, ++count[index_a[n]]);
+        T = m_a * (int64_t)m_r;
+        if (T > (1LL << 31) - 1) return fail(TN_EINVAL, "padded index too large");
+        z.assign(3 * T, 0);
+        std::vector<int32_t> fill(m_a, 0);
+        for (int64_t i = 0; i < m_a; ++i)
+            for (int r = 0; r < m_r; ++r) {
+                z[i * m_r + r] = (int32_t)i;
+                z[2 * T + i * m_r + r] = -1;          // padded place: not stored
+            }
+        for (int64_t n = 0; n < m_n; ++n) {
+            const int64_t i = index_a[n];
+            const int64_t t = i * m_r + fill[i]++;
+            z[T + t] = index_b[n];
+            z[2 * T + t] = (int32_t)n;
+        }
+    }
+    if (out_m_r) *out_m_r = m_r;
+    if (T > 65535 * 65535LL) return fail(TN_EINVAL, "too many chunk pairs");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = std::max(16, (int)(2 * N));
+    int32_t *dz = nullptr;
+    void *bp = nullptr;
+    TN_CUDA(cudaMallocAsync((void **)&dz, z.size() * 4, s), "cudaMallocAsync");
+    cudaError_t e = cudaMemcpyAsync(dz, z.data(), z.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);        // z is host memory of this call
+    if (e == cudaSuccess) e = cudaMallocAsync(&bp, (size_t)np * 2 * K * 2 * m_b, s);
+    if (e == cudaSuccess) e = launch_bprep(dtype, B, bp, lk, ln, m_b, np, s);
+    if (e == cudaSuccess) {
+        TcGemmDesc d;
+        d.dtype = dtype;
+        d.A = A; d.Bp = bp; d.C = C;
+        d.lm = lm; d.ln = ln; d.lk = lk;
+        d.batch = T;
+        d.batch_a = 1;
+        d.batch_b = 1;
+        d.np = np;
+        d.za = dz;
+        d.zb = dz + T;
+        d.zc = dz + 2 * T;
+        d.depth_a = m_a;
+        d.depth_b = m_b;
+        if (scheme == TN_GATHER_PADDED && np <= 256) {
+            // C_P = A x B_P: each N tile holds R whole B' chunks side by side,
+            // so an A tile is loaded once for R places of its padded row
+            int R = 1;
+            while (R * 2 * np <= 256 && R < m_r) R *= 2;
+            d.batch = m_a;
+            d.za = nullptr;
+            d.gather_r = R;
+            d.m_r = m_r;
+            d.bn = R * np;
+        }
+        ScaleRef sr{};
+        sr.fixed_exp = scale_exp;
+        sr.out_max = out_max;
+        e = launch_gemm_tc(d, sr, nullptr, s);
+    }
+    if (bp) cudaFreeAsync(bp, s);
+    cudaFreeAsync(dz, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tn_gemm_gather");
+    return TN_OK;
+}
+
 int tn_selftest_wait_timeout(void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const int lm = 7, ln = 3, lk = 3, np = 16;

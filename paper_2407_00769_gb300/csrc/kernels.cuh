@@ -94,6 +94,14 @@ struct TcGemmDesc {
     int out_c64 = 0;       // write C as complex64 (no rounding, exponent e = 0)
     float *partial = nullptr;  // tc_split_bytes() of FP32 partials when tc_split() > 1
     int fp8 = 0;           // A and B' are E4M3 bytes (kind::f8f6f4), K >= 64
+    // sparse-state gathers: per batch entry the A chunk, B' chunk and output
+    // chunk (device int32[batch], < 0 output: not stored); depth_a/depth_b:
+    // chunks held by A and B' (0: from batch_a / batch_b).  K <= 2^15.
+    const int32_t *za = nullptr, *zb = nullptr, *zc = nullptr;
+    int64_t depth_a = 0, depth_b = 0;
+    // padded 2-D index: gather_r B' chunks side by side per N tile (bn =
+    // gather_r * np), zb/zc indexed [batch][m_r]; 0: one chunk per entry
+    int gather_r = 0, m_r = 0;
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs

@@ -187,6 +187,12 @@ struct TcArgs {
     int split;             // K parts (split-K); tiles of part p cover K chunks [p*nk, (p+1)*nk)
     float *partial;        // split > 1: FP32 partial sums [part][batch][M][N] complex
     int64_t tiles_per_part;
+    // sparse-state gathers (Sec. 3.4.2): per batch entry b the A chunk za[b],
+    // the B' chunk zb[b] and the output chunk zc[b] (< 0: not stored); NULL:
+    // the batch entry itself
+    const int32_t *za, *zb, *zc;
+    int gather_r;          // > 0: B' tile = gather_r chunks (padded 2-D index), zb/zc [batch][m_r]
+    int m_r, np_chunk;
     ScaleRef sr;
     int32_t *err;
 };
@@ -286,9 +292,20 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                     uint8_t *sa = smem + stage * S::stage_bytes;
                     uint8_t *sb = sa + S::a_bytes;
                     mbar_expect_tx(&full[stage], S::a_bytes + S::b_bytes);
-                    tma_load_3d(sa, &tmA, &full[stage], kbase + kc * BK, (int)(mt * 128),
-                                args.batch_a ? (int)b : 0);
-                    tma_load_3d(sb, &tmB, &full[stage], kbase + kc * BK, nt * BN, args.batch_b ? (int)b : 0);
+                    const int zA = args.za ? args.za[b] : (args.batch_a ? (int)b : 0);
+                    tma_load_3d(sa, &tmA, &full[stage], kbase + kc * BK, (int)(mt * 128), zA);
+                    if (args.gather_r) {
+                        // B_P: one whole B' chunk (np_chunk rows) per r of this tile
+                        for (int rr = 0; rr < args.gather_r; ++rr) {
+                            const int r = nt * args.gather_r + rr;
+                            const int zB = r < args.m_r ? max(0, args.zb[b * args.m_r + r]) : 0;
+                            tma_load_3d(sb + rr * args.np_chunk * BKB, &tmB, &full[stage], kbase + kc * BK,
+                                        0, zB);
+                        }
+                    } else {
+                        const int zB = args.zb ? max(0, args.zb[b]) : (args.batch_b ? (int)b : 0);
+                        tma_load_3d(sb, &tmB, &full[stage], kbase + kc * BK, nt * BN, zB);
+                    }
                     armed[stage] = (int8_t)phase;
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
@@ -371,14 +388,27 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             tc_fence_after();
             const int64_t m = mt * 128 + row;
             const int col0 = nt * BN;                          // real column of this tile
-            const int valid_real = min(BN, 2 * args.N - col0);  // warp-uniform
-            for (int c = 0; c < valid_real; c += 16) {
+            const int64_t cb = args.zc ? (int64_t)args.zc[b] : b;   // output chunk (< 0: skip)
+            // gather_r: the tile's columns are gather_r chunks of np_chunk real
+            // columns, chunk r of row b going to output chunk zc[b m_r + r]
+            const int col_end = args.gather_r ? BN : min(BN, 2 * args.N - col0);   // warp-uniform
+            for (int c = 0; c < col_end; c += 16) {
                 uint32_t r[16];
                 tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 tmem_wait_ld();
-                if (m < args.M && (args.out_c64 || args.partial)) {
+                int64_t cbk = cb;              // output chunk of these 16 columns
+                int colr = col0 + c;           // their first real column in that chunk
+                int nreal = min(16, col_end - c);
+                if (args.gather_r) {
+                    const int gcol = col0 + c, rr = gcol / args.np_chunk;
+                    colr = gcol - rr * args.np_chunk;
+                    cbk = rr < args.m_r ? (int64_t)args.zc[b * args.m_r + rr] : -1;
+                    nreal = min(16, 2 * args.N - colr);
+                }
+                if (cbk < 0 || nreal <= 0) {
+                    // padded place of the 2-D index (or padding of B'): computed, not stored
+                } else if (m < args.M && (args.out_c64 || args.partial)) {
                     // complex64 result (or split-K partial): the FP32 accumulators as they are
-                    const int nreal = min(16, valid_real - c);
                     float v[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -388,9 +418,9 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                     const int64_t part = t / args.tiles_per_part;
                     float *dst = args.partial
                                      ? args.partial + (((part * args.batch + b) * args.M + m) * (int64_t)args.N +
-                                                       (col0 + c) / 2) * 2
+                                                       colr / 2) * 2
                                      : reinterpret_cast<float *>(args.C) +
-                                           ((b * args.M + m) * (int64_t)args.N + (col0 + c) / 2) * 2;
+                                           ((cbk * args.M + m) * (int64_t)args.N + colr / 2) * 2;
                     if (nreal >= 4) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
@@ -401,7 +431,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         reinterpret_cast<float2 *>(dst)[0] = make_float2(v[0], v[1]);
                     }
                 } else if (m < args.M) {
-                    const int nreal = min(16, valid_real - c);   // 2, 4, 8 or 16
+                    // nreal: 2, 4, 8 or 16
                     uint32_t packed[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -420,7 +450,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         if (2 * j < nreal) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
                     }
                     uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) +
-                                    (b * args.M + m) * (int64_t)args.N + (col0 + c) / 2;
+                                    (cbk * args.M + m) * (int64_t)args.N + colr / 2;
                     if (nreal == 16) {
                         reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                         reinterpret_cast<uint4 *>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
@@ -619,27 +649,31 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     int bn = d.np >= 256 ? 256 : d.np;           // 16 .. 256
     if (d.bn > 0) {
         if ((d.bn & (d.bn - 1)) != 0 || d.bn < 16 || d.bn > 256) return cudaErrorInvalidValue;
-        bn = d.bn < bn ? d.bn : bn;
+        bn = (d.bn < bn || d.gather_r > 0) ? d.bn : bn;   // B_P tiles span several chunks
     }
     const int64_t M = (int64_t)1 << d.lm;
     CUtensorMap ma, mb;
-    if (!encode_3d(&ma, d.dtype, esz, d.A, (uint64_t)kreal, (uint64_t)M,
-                   (uint64_t)(d.batch_a ? d.batch : 1), bk, 128))
+    const int64_t depth_a = d.depth_a > 0 ? d.depth_a : (d.batch_a ? d.batch : 1);
+    const int64_t depth_b = d.depth_b > 0 ? d.depth_b : (d.batch_b ? d.batch : 1);
+    if (!encode_3d(&ma, d.dtype, esz, d.A, (uint64_t)kreal, (uint64_t)M, (uint64_t)depth_a, bk, 128))
         return cudaErrorInvalidValue;
-    if (!encode_3d(&mb, d.dtype, esz, d.Bp, (uint64_t)kreal, (uint64_t)d.np,
-                   (uint64_t)(d.batch_b ? d.batch : 1), bk, bn))
+    if (d.gather_r > 0 && (bn % d.np != 0 || bn / d.np != d.gather_r)) return cudaErrorInvalidValue;
+    if (!encode_3d(&mb, d.dtype, esz, d.Bp, (uint64_t)kreal, (uint64_t)d.np, (uint64_t)depth_b, bk,
+                   d.gather_r > 0 ? d.np : bn))
         return cudaErrorInvalidValue;
     TcArgs a;
     a.C = d.C;
     a.M = M;
     a.n_mt = (M + 127) / 128;
-    a.n_nt = d.np / bn;
+    a.n_nt = d.gather_r > 0 ? ((int64_t)d.m_r * d.np + bn - 1) / bn : d.np / bn;
     a.batch = d.batch;
     a.tiles = a.n_mt * a.n_nt * d.batch;
     a.N = 1 << d.ln;
     a.lk = d.lk;
     a.nk = kreal / bk;
-    a.split = d.withhold ? 1 : tc_split(d.lm, d.ln, d.lk, d.batch);
+    const bool gathered = d.za || d.zb || d.zc;
+    if (gathered && d.lk > kSplitLog2K) return cudaErrorInvalidValue;   // one K part only
+    a.split = (d.withhold || gathered) ? 1 : tc_split(d.lm, d.ln, d.lk, d.batch);
     a.partial = a.split > 1 ? d.partial : nullptr;
     if (a.split > 1) {
         if (!d.partial || a.nk % a.split != 0) return cudaErrorInvalidValue;
@@ -651,6 +685,12 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.batch_a = d.batch_a;
     a.batch_b = d.batch_b;
     a.withhold = d.withhold;
+    a.za = d.za;
+    a.zb = d.zb;
+    a.zc = d.zc;
+    a.gather_r = d.gather_r;
+    a.m_r = d.m_r;
+    a.np_chunk = d.np;
     a.out_c64 = d.out_c64;
     if (d.gm > 0) {
         a.gm = d.gm;

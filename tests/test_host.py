@@ -208,3 +208,20 @@ def test_annealed_path_is_valid_and_cheaper(n_slice, cap):
         assert np.max(np.abs(got - oracle.sliced_amplitudes(c, q, edges, [sid]))) <= 1e-13
         full = full + got
     assert np.max(np.abs(full - oracle.amplitudes(c, q))) <= 1e-13
+
+
+def test_gather_rejects_bad_indices_before_touching_the_device():
+    L = tn.lib()
+    fake = ctypes.c_void_p(256)
+    ia = (ctypes.c_int32 * 3)(0, 5, 1)
+    ib = (ctypes.c_int32 * 3)(0, 0, 0)
+    rc = L.tn_gemm_gather(tn.F16, fake, 4, fake, 2, fake, 3, 128, 8, 64, ia, ib, tn.GATHER_DIRECT, 0,
+                          None, None, None)
+    assert rc == tn.TN_EINVAL and "out of range" in L.tn_last_error().decode()
+    ia2 = (ctypes.c_int32 * 3)(2, 1, 3)
+    rc = L.tn_gemm_gather(tn.F16, fake, 4, fake, 2, fake, 3, 128, 8, 64, ia2, ib, tn.GATHER_PADDED, 0,
+                          None, None, None)
+    assert rc == tn.TN_EINVAL and "non-decreasing" in L.tn_last_error().decode()
+    rc = L.tn_gemm_gather(tn.F16, fake, 4, fake, 2, fake, 3, 128, 8, 1 << 16, ia2, ib, tn.GATHER_DIRECT, 0,
+                          None, None, None)
+    assert rc == tn.TN_EUNSUPPORTED
