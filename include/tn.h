@@ -435,8 +435,10 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
  *                     the -1 places are computed and not stored, and C is
  *                     written straight at the valid places (the extraction).
  * M, N, K powers of two, N <= 2^24, 8 <= K <= 2^15.  out_max (device,
- * nullable) receives max |C| (atomic max on a zeroed float).  Enqueued on
- * `stream`; device scratch is allocated stream-ordered and freed after.
+ * nullable) receives max |C| (atomic max on a zeroed float).  The per-call
+ * index table is uploaded from host memory, so the call synchronizes
+ * `stream` once, before the B' build and the GEMM are enqueued; device
+ * scratch is allocated stream-ordered and freed after.
  * Errors: TN_EINVAL (NULL pointers, sizes, index out of range, unsorted
  * index_a for TN_GATHER_PADDED), TN_EUNSUPPORTED (K outside the range).
  */
