@@ -491,7 +491,9 @@ GRID40_SEEDS = (2, 8, 13, 15, 20, 21, 22)
 def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
     """Learned cost model on the 40-qubit 5x8 grid (14 cycles, 10 sliced
     edges = 1024 slices, greedy paths of 32 randomized trials per seed).  The
-    MLP, trained on the autotuner timings of the other workloads, ranks
+    MLP, trained on the autotuner timings of the 12-, 30- and 53-qubit workloads
+    (the bundled set collected by paper_2407_00769_gb300.data.collect_timings
+    plus this run's tuning), ranks
     candidate slicing plans (path seeds) by predicted time and picks every
     step's tile configuration; both choices are compared with measurement:
     plan regret = measured time of the predicted-best plan / best measured;
@@ -501,9 +503,11 @@ def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
     import rqcgen
     c, q = rqcgen.grid_40q()
     model = tn.CostModel(hidden=128, seed=11)
-    tr = _oversample(train_recs)
+    bundled = tn.load_timings()
+    tr = _oversample(bundled + train_recs)
     t0 = _t.perf_counter()
-    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=100, batch=128, lr=1e-3, seed=3)
+    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=20 if bundled else 100, batch=128,
+                lr=1e-3, seed=3)
     torch.cuda.synchronize()
     t_train = _t.perf_counter() - t0
     amps = torch.zeros(1 << 10, dtype=torch.complex128, device=dev)
@@ -558,7 +562,8 @@ def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
     ms_learned = cands[best_pred]["ms_timed_slices"]
     out = {"workload": "grid5x8-14c: 40 qubits, 14 cycles, 10 sliced edges (1024 slices), "
                        "10 open qubits; slices 0-7 timed per candidate, 2 per pass",
-           "train_records": len(train_recs), "train_s": t_train, "candidates": cands,
+           "train_records": len(bundled) + len(train_recs), "train_records_bundled": len(bundled),
+           "train_s": t_train, "candidates": cands,
            "plan_regret": float(meas[best_pred] / meas.min()), "plan_rank_corr": rank_corr,
            "chosen_seed": seed, "tile_regret": ms_learned / ms_exh,
            "step_regret_weighted": num / den, "default_tile_regret_weighted": dfl / den,

@@ -461,6 +461,23 @@ def cost_features(records) -> np.ndarray:
     return out
 
 
+def load_timings(path=None):
+    """Autotuner timings saved by paper_2407_00769_gb300.data.collect_timings
+    (default: the bundled GB300 set), as record dicts for cost_features /
+    cost_targets.  Returns [] when the file is absent."""
+    import os
+    if path is None:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "timings_gb300.npz")
+    if not os.path.exists(path):
+        return []
+    z = np.load(path)
+    n = int(z["ms"].shape[0])
+    keys = ("kind", "lm", "ln", "lk", "lb", "dtype", "kernel", "tile")
+    cols = {k: z[k].tolist() for k in keys}
+    ms = z["ms"].tolist()
+    return [dict({k: cols[k][i] for k in keys}, step=-1, pad_=0, ms=ms[i]) for i in range(n)]
+
+
 def cost_targets(records) -> np.ndarray:
     """Training targets: log2 of each record's time in microseconds."""
     return np.log2(np.array([max(r["ms"], 1e-6) * 1e3 for r in records], dtype=np.float64)).astype(np.float32)

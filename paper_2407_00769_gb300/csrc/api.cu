@@ -287,9 +287,15 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
         }
         if (gm_codes.empty()) gm_codes.push_back(0);
         c.push_back({GK_LP_TC, 0});   // the fixed heuristic's own choice
+        std::vector<int> seen = {tc_effective_tile(0, g.ln)};
         for (int b : bn_codes)
-            for (int m : gm_codes)
-                if ((b | (m << 4)) != 0) c.push_back({GK_LP_TC, b | (m << 4)});
+            for (int m : gm_codes) {
+                const int code = b | (m << 4);
+                const int eff = tc_effective_tile(code, g.ln);
+                if (code == 0 || std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
+                seen.push_back(eff);
+                c.push_back({GK_LP_TC, code});
+            }
     }
     return c;
 }
@@ -439,7 +445,10 @@ void cost_features(const tn_tune_record &r, float *f) {
         f[5] = (float)(std::log2(bytes) / 40.0);
         if (r.kernel >= 0 && r.kernel <= 3) f[10 + r.kernel] = 1.0f;
         if (r.kernel == GK_LP_TC) {
-            const int bc = r.tile & 15, gc = (r.tile >> 4) & 15;
+            // the configuration the launch really uses (tile 0 = the fixed
+            // heuristic's choice for this shape)
+            const int eff = tc_effective_tile(r.tile, r.ln);
+            const int bc = eff & 15, gc = (eff >> 4) & 15;
             if (bc < 5) f[14 + bc] = 1.0f;
             if (gc < 5) f[19 + gc] = 1.0f;
         }
@@ -482,11 +491,12 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         if (rc != TN_OK) return rc;
     }
     // per op: the predicted time of the fixed heuristic's own choice and of
-    // the best candidate.  Steps predicted to take under kSmallStepMs are
-    // launch-latency bound, where the timings the model learned from are
-    // mostly noise: there it moves away from the default only for a clear
-    // predicted gain (kLearnedMargin); larger steps take the model's best.
-    constexpr float kLearnedMargin = 0.92f;
+    // the best candidate.  The model moves away from the default only for a
+    // predicted gain beyond its own error: 8% on steps predicted under
+    // kSmallStepMs (launch-latency bound, where the timings it learned from
+    // are mostly noise), 10% on larger ones (held-out steps of 0.2 s were
+    // mispredicted by that much in relative terms).
+    constexpr float kLearnedMargin = 0.92f, kLargeStepMargin = 0.90f;
     constexpr float kSmallStepMs = 0.05f;
     std::vector<float> best(S.ops.size(), 1e30f), dflt(S.ops.size(), -1.0f);
     std::vector<std::pair<int, int>> pick(S.ops.size());
@@ -501,7 +511,7 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
     }
     for (size_t i = 0; i < S.ops.size(); ++i) {
         if (S.ops[i].kind != OP_GEMM || best[i] >= 1e29f) continue;
-        const float margin = dflt[i] < kSmallStepMs ? kLearnedMargin : 1.0f;
+        const float margin = dflt[i] < kSmallStepMs ? kLearnedMargin : kLargeStepMargin;
         if (dflt[i] < 0 || best[i] < margin * dflt[i]) {
             S.ops[i].gemm.kernel = pick[i].first;
             S.ops[i].gemm.tile = pick[i].second;

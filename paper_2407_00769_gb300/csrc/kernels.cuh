@@ -135,6 +135,9 @@ constexpr int kTcBn[5] = {0, 256, 128, 64, 32};
 constexpr int kTcGm[6] = {0, 4, 8, 16, 32, 64};
 inline int tc_tile_bn(int tile) { return kTcBn[(tile & 15) < 5 ? (tile & 15) : 0]; }
 inline int tc_tile_gm(int tile) { return kTcGm[((tile >> 4) & 15) < 6 ? ((tile >> 4) & 15) : 0]; }
+// The (BN, raster group) codes a tensor-core launch with tile code `tile`
+// really uses for N = 2^ln (tile 0 and explicit codes may coincide).
+int tc_effective_tile(int tile, int ln);
 bool tc_gemm_supported(int lk, int ln);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);

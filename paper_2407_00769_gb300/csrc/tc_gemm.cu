@@ -584,12 +584,38 @@ cudaError_t run_tc_bn(int bn, const CUtensorMap &ma, const CUtensorMap &mb, cons
 int tc_num_sms() {
     static int n = 0;
     if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;     // no device (host-side planning and features): GB300's count
     }
     return n;
+}
+
+// Raster group the launcher picks when none is given (see launch_gemm_tc).
+static int default_gm(int bn) {
+    const int target = tc_num_sms() * bn / 128;
+    int g = 1;
+    while (4 * g * g <= target && g < 64) g *= 2;
+    return g;
+}
+
+int tc_effective_tile(int tile, int ln) {
+    const int np = std::max(16, 2 << ln);
+    const int bn_max = np >= 256 ? 256 : np;
+    int bn = bn_max;
+    const int bq = tc_tile_bn(tile);
+    if (bq > 0 && bq < bn) bn = bq;
+    const int gq = tc_tile_gm(tile);
+    const int gm = gq > 0 ? gq : default_gm(bn);
+    int bc = 0, gc = 0;
+    for (int c = 1; c < 5; ++c)
+        if (kTcBn[c] == bn) bc = c;
+    for (int c = 1; c < 6; ++c)
+        if (kTcGm[c] == gm) gc = c;
+    return bc | (gc << 4);
 }
 
 // Set the dynamic shared-memory limit of every tensor-core GEMM variant on
@@ -700,10 +726,7 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         // K chunk of the wave's operands while DRAM delivers each of its
         // gm A tiles (128 rows) and SMs/gm B' tiles (BN rows) once: fewest
         // bytes at gm^2 = SMs * BN / 128 (power of two at or below).
-        const int target = tc_num_sms() * bn / 128;
-        int g = 1;
-        while (4 * g * g <= target && g < 64) g *= 2;
-        a.gm = g;
+        a.gm = default_gm(bn);
     }
     a.sr = sr;
     a.err = d_err;

@@ -87,13 +87,18 @@ def _records_of(rows, cols, cyc, seed, sl, b):
 
 def test_learned_policy_against_fixed_and_exhaustive():
     import time
-    train = []
-    for args in [(4, 5, 12, 1, 4, 2), (5, 5, 12, 2, 6, 3), (4, 6, 14, 3, 6, 4), (5, 6, 10, 4, 6, 6),
-                 (3, 6, 12, 5, 3, 1), (5, 5, 14, 6, 6, 5), (4, 6, 12, 7, 5, 5)]:
-        train += _records_of(*args)
+    # training set: the bundled GB300 timings of the 12-, 30- and 53-qubit
+    # workloads (~45k), or, without them, timings taken here on other plans
+    train = tn.load_timings()
+    epochs = 20
+    if not train:
+        epochs = 150
+        for args in [(4, 5, 12, 1, 4, 2), (5, 5, 12, 2, 6, 3), (4, 6, 14, 3, 6, 4), (5, 6, 10, 4, 6, 6),
+                     (3, 6, 12, 5, 3, 1), (5, 5, 14, 6, 6, 5), (4, 6, 12, 7, 5, 5)]:
+            train += _records_of(*args)
     model = tn.CostModel(hidden=128, seed=11)
     tr = _oversample(train)
-    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=150, batch=128, lr=1e-3, seed=3)
+    model.train(tn.cost_features(tr), tn.cost_targets(tr), epochs=epochs, batch=128, lr=1e-3, seed=3)
     # held-out plan, timed exhaustively: every candidate of every step
     c, q = rqcgen.small_grid(5, 6, 12, seed=9, n_open=6)
     held = _plan(c, q, n_slice_edges=6, slice_batch_log2=6)

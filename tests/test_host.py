@@ -225,3 +225,15 @@ def test_gather_rejects_bad_indices_before_touching_the_device():
     rc = L.tn_gemm_gather(tn.F16, fake, 4, fake, 2, fake, 3, 128, 8, 1 << 16, ia2, ib, tn.GATHER_DIRECT, 0,
                           None, None, None)
     assert rc == tn.TN_EUNSUPPORTED
+
+
+def test_bundled_timings_for_the_cost_model():
+    recs = tn.load_timings()
+    if not recs:
+        pytest.skip("no bundled timings")
+    assert len(recs) >= 40000
+    kinds = {r["kind"] for r in recs}
+    assert kinds == {0, 1}
+    assert all(r["ms"] > 0 for r in recs)
+    x = tn.cost_features(recs[:1000])
+    assert x.shape == (1000, tn.COST_NFEAT) and np.isfinite(x).all()
