@@ -599,7 +599,13 @@ def main():
     dtype = {"f16": tn.F16, "bf16": tn.BF16, "c64": tn.C64}[args.dtype]
 
     c, q = rqcgen.grid_30q()
-    sb = args.slice_batch if world == 1 else 0
+    # each rank's contiguous share of the 256 slices runs batched too: 2^b
+    # slices per pass with 2^b <= the share (shares are aligned to 2^b when
+    # the number of ranks is a power of two)
+    per_rank = (1 << N_SLICE_EDGES) // world
+    sb = args.slice_batch
+    while sb > 0 and ((1 << sb) > per_rank or per_rank % (1 << sb)):
+        sb -= 1
     policy = tn.TILE_EXHAUSTIVE if args.tile_policy == "exhaustive" else tn.TILE_FIXED
     plan = tn.Plan(c, q, dtype=dtype, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
                    slice_batch_log2=sb, tile_policy=policy)

@@ -51,7 +51,7 @@ extern "C" {
 #define TN_ENOMEM 2        /* host or device allocation failed                 */
 #define TN_ECUDA 3         /* a CUDA runtime/driver call failed                */
 #define TN_ETIMEOUT 4      /* a bounded device wait gave up (kernel returned)  */
-#define TN_EUNSUPPORTED 5  /* valid request this build cannot serve            */
+#define TN_EUNSUPPORTED 5  /* valid request outside the supported range        */
 
 /* ---- element types of the contraction ---- */
 #define TN_C64 0    /* complex64: FP32 re/im, FP32 SIMT arithmetic           */

@@ -10,7 +10,7 @@ pairs that the cycle's coupler pattern selects, then a half cycle of
 single-qubit gates before all qubits are measured.  Gate set (same section):
 sqrt(X), sqrt(Y), sqrt(W) and fSim(theta, phi).
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
   * 1q gate draw: one splitmix64 stream per circuit seeded with ``seed``;
     first layer uniform over {sqrt(X), sqrt(Y), sqrt(W)}: ``(u >> 11) % 3``;
     later layers uniform over the two gates that differ from the previous one
