@@ -235,6 +235,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
                     d.fp8 = g.fp8;
+                    d.out_rank = g.out_rank;
+                    for (int i = 0; i < g.out_rank && i < 40; ++i) d.out_dpos[i] = g.out_dpos[i];
                     e = launch_gemm_tc(d, sr, P->d_err, s);
                     break;
                 }

@@ -95,6 +95,11 @@ struct GemmOp {
     int32_t headroom;     // extra power-of-two scale from calibration (complex-half)
     int32_t ta, tb, tc;   // storage of A, B, C: 0 complex64, 1 complex-half
     int32_t fp8;          // tensor-core step on E4M3 copies of A and B'
+    // > 0: C is written straight in a permuted mode order (a permutation of
+    // its out_rank modes fused into the epilogue): source bit i of the
+    // element index goes to bit out_dpos[i]; the lowest 3 bits stay
+    int32_t out_rank;
+    int8_t out_dpos[kMaxRank];
 };
 
 struct QuantOp {

@@ -102,6 +102,10 @@ struct TcGemmDesc {
     // padded 2-D index: gather_r B' chunks side by side per N tile (bn =
     // gather_r * np), zb/zc indexed [batch][m_r]; 0: one chunk per entry
     int gather_r = 0, m_r = 0;
+    // > 0: write C in a permuted mode order (bit i of the natural element
+    // index -> bit out_dpos[i]; bits 0..2 unchanged, N >= 8, K <= 2^15)
+    int out_rank = 0;
+    int8_t out_dpos[40] = {};
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs

@@ -11,6 +11,11 @@
 
 namespace tn {
 
+// Tensor-core split-K rule (tc_gemm.cu): K parts of one step; steps with
+// K above 2^kSplitLog2KHost are always split.
+int tc_split(int lm, int ln, int lk, int64_t batch);
+constexpr int kSplitLog2KHost = 15;
+
 // Refine `path` (on the network with `sliced` removed) by simulated
 // annealing over tree rotations; intermediates stay within
 // max(width_cap, current width).  Keeps the input when nothing improves.

@@ -418,6 +418,51 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
 
     S.n_meta_extra = n_extra_meta;
 
+    // ---- a permutation of a tensor-core GEMM's result (its only reader) is
+    // written by that GEMM's epilogue instead: each thread stores
+    // 8 consecutive complex values of C, so the innermost 3 modes must stay
+    // in place (whole 32-byte pieces move) and C must hold >= 8 columns
+    for (auto &ops_p : ph) {
+        std::vector<int> readers;
+        auto count_reads = [&](int64_t id) {
+            int n = 0;
+            for (const auto &pv : ph)
+                for (const Op &o : pv) {
+                    if (o.kind == OP_PERM && o.perm.src == id) ++n;
+                    if (o.kind == OP_BPREP && o.bprep.src == id) ++n;
+                    if (o.kind == OP_QUANT && o.quant.src == id) ++n;
+                    if (o.kind == OP_SUM && o.sum.src == id) ++n;
+                    if (o.kind == OP_GEMM && (o.gemm.a == id || o.gemm.b == id)) ++n;
+                }
+            return n;
+        };
+        for (size_t i = 1; i < ops_p.size(); ++i) {
+            Op &pm = ops_p[i];
+            if (pm.kind != OP_PERM) continue;
+            size_t gi = i;                       // the op that made the permuted tensor
+            while (gi > 0 && !(ops_p[gi - 1].kind == OP_GEMM && ops_p[gi - 1].gemm.c == pm.perm.src)) --gi;
+            if (gi == 0) continue;
+            Op &g = ops_p[gi - 1];
+            if (g.gemm.kernel != GK_LP_TC || g.gemm.ln < 3) continue;
+            const int r = pm.perm.rank;
+            if (r != g.gemm.lb + g.gemm.lm + g.gemm.ln || r < 3) continue;
+            bool low_kept = true;
+            for (int k = r - 3; k < r; ++k) low_kept = low_kept && pm.perm.perm[k] == k;
+            if (!low_kept) continue;
+            if (g.gemm.lk > kSplitLog2KHost ||
+                tc_split(g.gemm.lm, g.gemm.ln, g.gemm.lk, (int64_t)1 << g.gemm.lb) != 1)
+                continue;
+            if (count_reads(g.gemm.c) != 1) continue;
+            g.gemm.out_rank = r;
+            for (int k = 0; k < r; ++k) g.gemm.out_dpos[r - 1 - pm.perm.perm[k]] = (int8_t)(r - 1 - k);
+            g.gemm.c = pm.perm.dst;
+            --S.n_permutes;
+            if (pm.phase) S.bytes_per_pass -= 2.0 * (double)((int64_t)pm.perm.esz << r);
+            ops_p.erase(ops_p.begin() + (long)i);
+            --i;
+        }
+    }
+
     // ---- lifetimes over the op sequence (phase 0 then phase 1)
     S.ops = ph[0];
     S.ops.insert(S.ops.end(), ph[1].begin(), ph[1].end());

@@ -193,6 +193,10 @@ struct TcArgs {
     const int32_t *za, *zb, *zc;
     int gather_r;          // > 0: B' tile = gather_r chunks (padded 2-D index), zb/zc [batch][m_r]
     int m_r, np_chunk;
+    // > 0: C stored in a permuted mode order: bit i of the natural element
+    // index goes to bit out_dpos[i] (bits 0..2 stay)
+    int out_rank;
+    int8_t out_dpos[40];
     ScaleRef sr;
     int32_t *err;
 };
@@ -202,6 +206,13 @@ struct TcArgs {
 // cover about gm m-tiles x (SMs / gm) n-tiles, whose A rows and B' columns
 // fit in L2 together; A and B' are then read from DRAM about once per group
 // instead of once per m-tile.
+// C element index in the consumer's mode order (the fused permutation)
+__device__ __forceinline__ int64_t permuted_index(const TcArgs &a, int64_t e) {
+    int64_t d = e & 7;
+    for (int i = 3; i < a.out_rank; ++i) d |= ((e >> i) & 1) << a.out_dpos[i];
+    return d;
+}
+
 __device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt,
                                             int &nt) {
     t %= a.tiles_per_part;          // the K part is t / tiles_per_part
@@ -416,11 +427,12 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         if (j < nreal) mx = fmaxf(mx, fabsf(v[j]));
                     }
                     const int64_t part = t / args.tiles_per_part;
+                    int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
+                    if (args.out_rank) ei = permuted_index(args, ei);
                     float *dst = args.partial
                                      ? args.partial + (((part * args.batch + b) * args.M + m) * (int64_t)args.N +
                                                        colr / 2) * 2
-                                     : reinterpret_cast<float *>(args.C) +
-                                           ((cbk * args.M + m) * (int64_t)args.N + colr / 2) * 2;
+                                     : reinterpret_cast<float *>(args.C) + ei * 2;
                     if (nreal >= 4) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
@@ -449,8 +461,9 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         }
                         if (2 * j < nreal) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
                     }
-                    uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) +
-                                    (cbk * args.M + m) * (int64_t)args.N + colr / 2;
+                    int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
+                    if (args.out_rank) ei = permuted_index(args, ei);
+                    uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) + ei;
                     if (nreal == 16) {
                         reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                         reinterpret_cast<uint4 *>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
@@ -699,7 +712,9 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.nk = kreal / bk;
     const bool gathered = d.za || d.zb || d.zc;
     if (gathered && d.lk > kSplitLog2K) return cudaErrorInvalidValue;   // one K part only
-    a.split = (d.withhold || gathered) ? 1 : tc_split(d.lm, d.ln, d.lk, d.batch);
+    if (d.out_rank > 0 && d.lk > kSplitLog2K) return cudaErrorInvalidValue;
+    // a permuted C is written by this kernel's epilogue, so no K parts
+    a.split = (d.withhold || gathered || d.out_rank > 0) ? 1 : tc_split(d.lm, d.ln, d.lk, d.batch);
     a.partial = a.split > 1 ? d.partial : nullptr;
     if (a.split > 1) {
         if (!d.partial || a.nk % a.split != 0) return cudaErrorInvalidValue;
@@ -717,6 +732,9 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.gather_r = d.gather_r;
     a.m_r = d.m_r;
     a.np_chunk = d.np;
+    a.out_rank = d.out_rank;
+    for (int i = 0; i < 40; ++i) a.out_dpos[i] = i < d.out_rank ? d.out_dpos[i] : 0;
+    if (a.out_rank > 0 && (a.N < 8 || a.out_rank > 40)) return cudaErrorInvalidValue;
     a.out_c64 = d.out_c64;
     if (d.gm > 0) {
         a.gm = d.gm;
