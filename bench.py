@@ -471,7 +471,7 @@ def leg_fp8(tn, torch, dev, flush, stream, gold, min_log2_flops=40):
                        f">= 2^{min_log2_flops} flops per pass",
            "fp8_steps": sum(1 for s in plan.steps() if s["storage"] & 8),
            "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-           "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3 / 3) / 1e12 if g["ms"] else None,
+           "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] else None,
            "quant_ms": prof.get("quant", {"ms": 0})["ms"] / 3}
     if gold is not None:
         m = tn.metrics(amps, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
