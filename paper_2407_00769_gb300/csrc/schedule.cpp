@@ -419,9 +419,9 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
     S.n_meta_extra = n_extra_meta;
 
     // ---- a permutation of a tensor-core GEMM's result (its only reader) is
-    // written by that GEMM's epilogue instead: each thread stores
-    // 8 consecutive complex values of C, so the innermost 3 modes must stay
-    // in place (whole 32-byte pieces move) and C must hold >= 8 columns
+    // written by that GEMM's epilogue instead: each thread holds 8
+    // consecutive complex values of one row of C (C must hold >= 8 columns)
+    // and a warp 32 consecutive rows
     for (auto &ops_p : ph) {
         std::vector<int> readers;
         auto count_reads = [&](int64_t id) {
@@ -446,9 +446,17 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             if (g.gemm.kernel != GK_LP_TC || g.gemm.ln < 3) continue;
             const int r = pm.perm.rank;
             if (r != g.gemm.lb + g.gemm.lm + g.gemm.ln || r < 3) continue;
-            bool low_kept = true;
-            for (int k = r - 3; k < r; ++k) low_kept = low_kept && pm.perm.perm[k] == k;
-            if (!low_kept) continue;
+            // the destination's lowest 3 bits must come from the 8 columns a
+            // thread holds or from the 32 rows of a warp, so that a warp's
+            // stores still fill whole 32-byte sectors
+            bool coalesced = true;
+            for (int k = r - 3; k < r; ++k) {
+                const int src = r - 1 - pm.perm.perm[k];      // source bit of destination bit r-1-k
+                const bool thread_col = src < 3;
+                const bool warp_row = src >= g.gemm.ln && src < g.gemm.ln + std::min(5, g.gemm.lm);
+                coalesced = coalesced && (thread_col || warp_row);
+            }
+            if (!coalesced) continue;
             if (g.gemm.lk > kSplitLog2KHost ||
                 tc_split(g.gemm.lm, g.gemm.ln, g.gemm.lk, (int64_t)1 << g.gemm.lb) != 1)
                 continue;

@@ -197,6 +197,7 @@ struct TcArgs {
     // index goes to bit out_dpos[i] (bits 0..2 stay)
     int out_rank;
     int8_t out_dpos[40];
+    int ln;                // log2 N (bit position of the row part of an element index)
     ScaleRef sr;
     int32_t *err;
 };
@@ -206,10 +207,11 @@ struct TcArgs {
 // cover about gm m-tiles x (SMs / gm) n-tiles, whose A rows and B' columns
 // fit in L2 together; A and B' are then read from DRAM about once per group
 // instead of once per m-tile.
-// C element index in the consumer's mode order (the fused permutation)
-__device__ __forceinline__ int64_t permuted_index(const TcArgs &a, int64_t e) {
-    int64_t d = e & 7;
-    for (int i = 3; i < a.out_rank; ++i) d |= ((e >> i) & 1) << a.out_dpos[i];
+// Bits lo..hi-1 of a C element index moved to the consumer's mode order
+// (the fused permutation is a bit permutation, so the parts OR together).
+__device__ __forceinline__ int64_t permute_bits(const TcArgs &a, int64_t e, int lo, int hi) {
+    int64_t d = 0;
+    for (int i = lo; i < hi; ++i) d |= ((e >> i) & 1) << a.out_dpos[i];
     return d;
 }
 
@@ -388,6 +390,14 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         if (args.sr.texp && !args.partial && blockIdx.x == 0 && threadIdx.x == 64)
             args.sr.texp[args.sr.meta_c] = args.sr.texp[args.sr.meta_a] + args.sr.texp[args.sr.meta_b] + e;
         const float sc = __int_as_float((127 + e) << 23);
+        // fused permutation: where the 8 values of one chunk go (low 3 bits)
+        int64_t lowtab[8];
+        bool low_kept = true;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            lowtab[j] = args.out_rank ? permute_bits(args, j, 0, 3) : j;
+            low_kept = low_kept && lowtab[j] == j;
+        }
         float mx = 0.f;
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -400,6 +410,9 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             const int64_t m = mt * 128 + row;
             const int col0 = nt * BN;                          // real column of this tile
             const int64_t cb = args.zc ? (int64_t)args.zc[b] : b;   // output chunk (< 0: skip)
+            // fused permutation: destination = row part | column part | low 3 bits
+            int64_t prow = 0;
+            if (args.out_rank) prow = permute_bits(args, (cb * args.M + m) * (int64_t)args.N, args.ln, args.out_rank);
             // gather_r: the tile's columns are gather_r chunks of np_chunk real
             // columns, chunk r of row b going to output chunk zc[b m_r + r]
             const int col_end = args.gather_r ? BN : min(BN, 2 * args.N - col0);   // warp-uniform
@@ -427,13 +440,18 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         if (j < nreal) mx = fmaxf(mx, fabsf(v[j]));
                     }
                     const int64_t part = t / args.tiles_per_part;
-                    int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
-                    if (args.out_rank) ei = permuted_index(args, ei);
+                    const int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
                     float *dst = args.partial
                                      ? args.partial + (((part * args.batch + b) * args.M + m) * (int64_t)args.N +
                                                        colr / 2) * 2
                                      : reinterpret_cast<float *>(args.C) + ei * 2;
-                    if (nreal >= 4) {
+                    if (args.out_rank) {
+                        // 8 complex values, each to its permuted place
+                        const int64_t base = prow | permute_bits(args, colr / 2, 3, args.ln);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            reinterpret_cast<float2 *>(args.C)[base | lowtab[j]] = make_float2(v[2 * j], v[2 * j + 1]);
+                    } else if (nreal >= 4) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             if (4 * q < nreal)
@@ -461,10 +479,20 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                         }
                         if (2 * j < nreal) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
                     }
-                    int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
-                    if (args.out_rank) ei = permuted_index(args, ei);
+                    const int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
                     uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) + ei;
-                    if (nreal == 16) {
+                    if (args.out_rank) {
+                        const int64_t base = prow | permute_bits(args, colr / 2, 3, args.ln);
+                        if (low_kept) {
+                            uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(args.C) + base);
+                            d4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            d4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                reinterpret_cast<uint32_t *>(args.C)[base | lowtab[j]] = packed[j];
+                        }
+                    } else if (nreal == 16) {
                         reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                         reinterpret_cast<uint4 *>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                     } else if (nreal == 8) {
@@ -733,6 +761,7 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     a.m_r = d.m_r;
     a.np_chunk = d.np;
     a.out_rank = d.out_rank;
+    a.ln = d.ln;
     for (int i = 0; i < 40; ++i) a.out_dpos[i] = i < d.out_rank ? d.out_dpos[i] : 0;
     if (a.out_rank > 0 && (a.N < 8 || a.out_rank > 40)) return cudaErrorInvalidValue;
     a.out_c64 = d.out_c64;
