@@ -201,7 +201,7 @@ def read_golden():
 
 
 # ------------------------------------------------------------- oracle leg
-def oracle_sample(seconds_target=15.0, max_gates=None):
+def oracle_sample(seconds_target=15.0, max_gates=None, one_core=True):
     """Time the FP64 state-vector oracle on a bounded prefix of the 30-qubit
     circuit; return (estimated seconds for the whole circuit, sample text,
     threads)."""
@@ -229,13 +229,15 @@ def oracle_sample(seconds_target=15.0, max_gates=None):
     per_gate = (t - t_init) / g
     full = t_init + per_gate * c.n_gates
     # one core: two gates of the same circuit, scaled the same way
-    oracle.set_threads(1)
-    try:
-        t1_init = run(0)
-        t1 = run(2)
-        full_1 = t1_init + (t1 - t1_init) / 2 * c.n_gates
-    finally:
-        oracle.set_threads(threads)
+    full_1 = None
+    if one_core:
+        oracle.set_threads(1)
+        try:
+            t1_init = run(0)
+            t1 = run(2)
+            full_1 = t1_init + (t1 - t1_init) / 2 * c.n_gates
+        finally:
+            oracle.set_threads(threads)
     return full, (f"FP64 state vector of the 30-qubit circuit (2^30 amplitudes, 16 GiB), first "
                   f"{g} of {c.n_gates} gates timed ({t:.1f} s), scaled to all gates"), threads, full_1
 
@@ -258,7 +260,8 @@ def reference_arm(args):
     gates_per_step = None
     sub_t = None
     for i in range(args.warmup + args.steps):
-        full, sample, threads = oracle_sample(seconds_target=8.0, max_gates=gates_per_step)
+        full, sample, threads, _ = oracle_sample(seconds_target=8.0, max_gates=gates_per_step,
+                                                 one_core=False)
         if i >= args.warmup:
             per_step.append(full)
         sub_t = sample
