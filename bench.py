@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
-    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather"],
+    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec"],
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
     ap.add_argument("--padded", action="store_true", help="--case gather with the padded 2-D index")
@@ -106,6 +106,18 @@ def kernel_case(args):
         scheme = tn.GATHER_PADDED if args.padded else tn.GATHER_DIRECT
         run = lambda: tn.gemm_gather(tn.F16, A, B, C, ia, ib, scheme=scheme)
         work, unit = 8.0 * M * N * K * m_n, "TFLOP/s"
+    elif args.case == "codec":
+        # Eq. 1 int4 codec, groups of 128, on 2^28 reals (a 1 GiB complex64
+        # tensor): algorithmic bytes = 4 read + 0.5 written per value + 8 per group
+        n, group = 1 << 28, 128
+        x = torch.randn(n, device="cuda")
+        codes = torch.empty(n // 2, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(n // group, device="cuda")
+        ze = torch.empty(n // group, device="cuda")
+        L = tn.lib()
+        run = lambda: L.tn_encode(tn.CODEC_INT4, x.data_ptr(), n, group, codes.data_ptr(), sc.data_ptr(),
+                                  ze.data_ptr(), None)
+        work, unit = n * 4.5 + (n // group) * 8.0, "GB/s"
     else:
         r = args.rank
         x = torch.empty(1 << r, dtype=torch.int32, device="cuda").random_()

@@ -442,6 +442,36 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
  * Errors: TN_EINVAL (NULL pointers, sizes, index out of range, unsorted
  * index_a for TN_GATHER_PADDED), TN_EUNSUPPORTED (K outside the range).
  */
+/*
+ * Low-precision codec for tensors that cross a link (paper Sec. 3.2, Eq. 1,
+ * Table 1).  Per group i of a real FP32 tensor x[n] (a complex64 tensor as
+ * its 2n interleaved reals):
+ *     Q([x]_i) = [x]_i^exp * scale + zero,
+ *     scale = (q_max - q_min) / (max - min),
+ *     zero  = (q_min max - q_max min) / (max - min),
+ * max / min over the group's transformed values, x^exp = sign(x)|x|^exp.
+ *   TN_CODEC_HALF  q in +-65504, exp 1, one group (group = 0), not rounded;
+ *                  codes: FP16[n]
+ *   TN_CODEC_INT8  q in -128..127, exp 0.2, one group (group = 0), rounded to
+ *                  nearest even; codes: int8[n]
+ *   TN_CODEC_INT4  q in 0..15, exp 1, groups of `group` values (a power of
+ *                  two in 128..65536 dividing n), rounded; codes: uint8[n/2],
+ *                  two per byte, even index in the low nibble
+ * scale, zero: device FP32[n / group] (one entry for the whole-tensor kinds).
+ * A group of equal values gets scale 1 and zero q_min - value.  tn_decode
+ * inverts Eq. 1 into x[n] (FP32).  All pointers are device memory,
+ * caller-owned; enqueued on `stream` (tn_encode of the whole-tensor kinds
+ * allocates a small stream-ordered scratch).  Errors: TN_EINVAL (NULL, bad
+ * kind, group or n), TN_ECUDA.
+ */
+#define TN_CODEC_HALF 0
+#define TN_CODEC_INT8 1
+#define TN_CODEC_INT4 2
+int tn_encode(int32_t kind, const float *x, int64_t n, int32_t group, void *codes, float *scale,
+              float *zero, void *stream);
+int tn_decode(int32_t kind, const void *codes, const float *scale, const float *zero, int64_t n,
+              int32_t group, float *x, void *stream);
+
 #define TN_GATHER_DIRECT 0
 #define TN_GATHER_PADDED 1
 int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int64_t m_b, void *C,

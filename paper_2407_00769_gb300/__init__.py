@@ -38,7 +38,7 @@ EXPORTED = [
     "tn_plan_tune", "tn_tune_records",
     "tn_cost_model_create", "tn_cost_model_destroy", "tn_cost_model_params", "tn_cost_model_grad",
     "tn_cost_model_train", "tn_cost_model_predict", "tn_cost_features", "tn_plan_set_cost_model",
-    "tn_plan_predict_ms", "tn_plan_apply_tuning", "tn_gemm_gather",
+    "tn_plan_predict_ms", "tn_plan_apply_tuning", "tn_gemm_gather", "tn_encode", "tn_decode",
 ]
 COST_NFEAT = 26
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum", "quant"]
@@ -182,6 +182,8 @@ def lib():
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
         L.tn_gemm.argtypes = [i32, vp, vp, vp, i64, i64, i64, i64, i32, i32, i32, i32, vp, vp]
+        L.tn_encode.argtypes = [i32, vp, i64, i32, vp, vp, vp, vp]
+        L.tn_decode.argtypes = [i32, vp, vp, vp, i64, i32, vp, vp]
         L.tn_gemm_gather.argtypes = [i32, vp, i64, vp, i64, vp, i64, i64, i64, i64,
                                      ctypes.POINTER(i32), ctypes.POINTER(i32), i32, i32, vp,
                                      ctypes.POINTER(i32), vp]
@@ -632,6 +634,38 @@ def permute(x, perm, out=None, elem_bytes=None, stream=None):
     _check(lib().tn_permute(x.data_ptr(), out.data_ptr(), r, p, int(elem_bytes),
                             _stream_ptr(stream)))
     return out
+
+
+CODEC_HALF, CODEC_INT8, CODEC_INT4 = 0, 1, 2
+
+
+def encode(kind, x, group=0, stream=None):
+    """Eq. 1 codec (tn_encode) of a float32 CUDA tensor (complex64: its
+    reals).  Returns (codes, scale, zero) CUDA tensors."""
+    torch = _torch()
+    xf = x.contiguous().view(torch.float32).reshape(-1)
+    n = xf.numel()
+    ng = 1 if kind != CODEC_INT4 else n // group
+    if kind == CODEC_HALF:
+        codes = torch.empty(n, dtype=torch.float16, device=xf.device)
+    elif kind == CODEC_INT8:
+        codes = torch.empty(n, dtype=torch.int8, device=xf.device)
+    else:
+        codes = torch.empty(n // 2, dtype=torch.uint8, device=xf.device)
+    scale = torch.empty(ng, dtype=torch.float32, device=xf.device)
+    zero = torch.empty(ng, dtype=torch.float32, device=xf.device)
+    _check(lib().tn_encode(int(kind), xf.data_ptr(), n, int(group), codes.data_ptr(), scale.data_ptr(),
+                           zero.data_ptr(), _stream_ptr(stream)))
+    return codes, scale, zero
+
+
+def decode(kind, codes, scale, zero, n, group=0, stream=None):
+    """Inverse of encode (tn_decode): float32 CUDA tensor of n values."""
+    torch = _torch()
+    x = torch.empty(n, dtype=torch.float32, device=codes.device)
+    _check(lib().tn_decode(int(kind), codes.data_ptr(), scale.data_ptr(), zero.data_ptr(), int(n), int(group),
+                           x.data_ptr(), _stream_ptr(stream)))
+    return x
 
 
 GATHER_DIRECT, GATHER_PADDED = 0, 1
