@@ -445,7 +445,7 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
     del plan, amps
     torch.cuda.empty_cache()
     c, q = rqcgen.grid_53q()
-    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=1,
+    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=4,
                    slice_batch_log2=3, anneal_iters=iters)
     info = plan.info()
     amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)

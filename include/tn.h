@@ -91,10 +91,11 @@ typedef struct {
                                  -1: as many as the cap needs                    */
     uint64_t path_seed;       /* seed of the randomized greedy path search       */
     int32_t path_trials;      /* greedy restarts (>= 1); trial 0 is noiseless    */
-    int32_t path_anneal_iters;/* > 0: refine the chosen path by this many
-                                 simulated-annealing tree rotations per round
-                                 (3 rounds), and with a cap give back sliced
-                                 edges the refined path no longer needs      */
+    int32_t path_anneal_iters;/* > 0: refine the chosen path by simulated
+                                 annealing: path_trials independent chains of
+                                 3 rounds of this many tree rotations, the
+                                 cheapest kept; with a cap, sliced edges the
+                                 refined path no longer needs are given back */
     int32_t slice_batch_log2; /* run 2^this consecutive slices in one pass, the
                                  batch carried as an extra tensor mode (>= 0)    */
     int32_t tile_policy;      /* TN_TILE_*                                       */

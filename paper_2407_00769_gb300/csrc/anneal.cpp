@@ -191,8 +191,9 @@ static void measure(const Network &net, const std::vector<int> &sliced, const Pa
     }
 }
 
-int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
-                Path &path, std::vector<int> &sliced) {
+// One annealing chain of 3 rounds from (path, sliced); returns its job cost.
+static double refine_chain(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
+                           Path &path, std::vector<int> &sliced) {
     int mx;
     double fl, co;
     measure(net, sliced, path, kappa, mx, fl, co);
@@ -220,6 +221,29 @@ int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int it
     }
     path.max_log2 = mx;
     path.flops = fl;
+    return std::ldexp(co, (int)sliced.size());
+}
+
+int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
+                int chains, Path &path, std::vector<int> &sliced) {
+    // independent chains from the same start; the cheapest job wins (the
+    // lowest time complexity found under the cap)
+    Path best_path;
+    std::vector<int> best_sliced;
+    double best = 0;
+    for (int c = 0; c < std::max(1, chains); ++c) {
+        Path p = path;
+        std::vector<int> s = sliced;
+        const double cost = refine_chain(net, n_target, cap, seed + 0x9E3779B97F4A7C15ull * (uint64_t)c, iters,
+                                         kappa, p, s);
+        if (c == 0 || cost < best) {
+            best = cost;
+            best_path = std::move(p);
+            best_sliced = std::move(s);
+        }
+    }
+    path = std::move(best_path);
+    sliced = std::move(best_sliced);
     return TN_OK;
 }
 

@@ -581,7 +581,7 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
             // (complex-half 4 B x ~250 flop/B on the tensor cores; complex64
             // 8 B x ~12 flop/B on the CUDA cores)
             refine_plan(P->net, n_target, cap, o.path_seed, o.path_anneal_iters,
-                        o.dtype == TN_C64 ? 100.0 : 1000.0, P->path, P->sliced);
+                        o.dtype == TN_C64 ? 100.0 : 1000.0, o.path_trials, P->path, P->sliced);
         if (cap > 0 && P->path.max_log2 > cap) {
             delete P;
             return fail(TN_EINVAL, "the slicing does not reach the cap (largest intermediate 2^" +

@@ -21,11 +21,12 @@ constexpr int kSplitLog2KHost = 15;
 // max(width_cap, current width).  Keeps the input when nothing improves.
 int anneal_path(const Network &net, const std::vector<int> &sliced, int width_cap, uint64_t seed,
                 int iters, double kappa, Path &path);
-// Annealing rounds on the chosen path and slices; with a cap (n_target < 0)
-// a sliced edge is given back whenever the refined path stays within the cap
-// and the job's flops (2^S x per-slice) drop.
+// `chains` independent annealing chains (3 rounds each) on the chosen path
+// and slices, the cheapest job kept; with a cap (n_target < 0) a sliced edge
+// is given back whenever the refined path stays within the cap and the
+// job's cost (2^S x per-slice) drops.
 int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
-                Path &path, std::vector<int> &sliced);
+                int chains, Path &path, std::vector<int> &sliced);
 int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, int cap, Path &path,
                   std::vector<int> &sliced, std::string &err);
 
