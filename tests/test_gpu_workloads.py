@@ -137,3 +137,20 @@ def test_uneven_batch_against_state_vector():
         assert oracle.fidelity(w, got) >= 0.999
     print(f"uneven batch: {len(idx)} circuits, max rel-L2 {max(errs):.2e}, median {np.median(errs):.2e}")
     assert max(errs) <= 5e-3
+
+
+def test_grid53_full_job_porter_thomas():
+    # every slice of the 53-qubit circuit on an annealed path (512 slices at
+    # cap 2^30): the 4096 probabilities of a deep random circuit follow the
+    # Porter-Thomas law, 2^n p ~ Exp(1): mean 1 (+-0.05 at 3 sigma for 4096
+    # values) and second moment 2 -- a property of the whole sum of slices
+    c, q = rqcgen.grid_53q()
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=4, slice_batch_log2=3,
+                anneal_iters=200000)
+    amps = p.contract().cpu().numpy()
+    del p
+    torch.cuda.empty_cache()
+    x = (2.0 ** 53) * np.abs(amps) ** 2
+    print(f"53-qubit full job: mean 2^n p = {x.mean():.4f}, second moment {np.mean(x ** 2):.4f}")
+    assert 0.93 <= x.mean() <= 1.07
+    assert 1.6 <= np.mean(x ** 2) <= 2.4
