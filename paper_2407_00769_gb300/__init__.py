@@ -29,7 +29,8 @@ KERNEL_NAMES = {0: "c64_rows", 1: "c64_tiled", 2: "lp_rows", 3: "lp_tc"}
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 
 EXPORTED = [
-    "tn_plan", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges", "tn_plan_step",
+    "tn_plan", "tn_plan_samples", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges",
+    "tn_plan_step",
     "tn_plan_leaf_source",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
@@ -145,6 +146,8 @@ def lib():
         L.tn_plan.argtypes = [ctypes.POINTER(CircuitC), ctypes.POINTER(QueryC),
                               ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
         L.tn_plan_opts_default.argtypes = [ctypes.POINTER(PlanOpts)]
+        L.tn_plan_samples.argtypes = [ctypes.POINTER(CircuitC), ctypes.POINTER(ctypes.c_uint8), i32,
+                                      ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
         L.tn_plan_opts_default.restype = None
         L.tn_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
         L.tn_plan_sliced_edges.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
@@ -270,10 +273,12 @@ class Plan:
                  n_slice_edges: int = 0, seed: int = 1, trials: int = 1,
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
-                 no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0):
+                 no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
+                 _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
-        self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
+        if _samples is None:
+            self._q, self._qkeep = query_struct(query, int(circuit.n_qubits))
         opts = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(opts))
         opts.dtype = int(dtype)
@@ -294,12 +299,29 @@ class Plan:
             opts.dev_free = self._alloc.free
         self._opts = opts
         h = ctypes.c_void_p()
-        _check(L.tn_plan(ctypes.byref(self._c), ctypes.byref(self._q), ctypes.byref(opts),
-                         ctypes.byref(h)))
-        self._h = h
-        self.n_open = int(query.n_open) if hasattr(query, "n_open") else len(query.open_qubits)
+        if _samples is None:
+            _check(L.tn_plan(ctypes.byref(self._c), ctypes.byref(self._q), ctypes.byref(opts),
+                             ctypes.byref(h)))
+            self._h = h
+            self.n_open = int(query.n_open) if hasattr(query, "n_open") else len(query.open_qubits)
+        else:
+            sm = np.ascontiguousarray(_samples, dtype=np.uint8)
+            if sm.ndim != 2 or sm.shape[1] != int(circuit.n_qubits):
+                raise ValueError("samples must be (n_samples, n_qubits) bits")
+            _check(L.tn_plan_samples(ctypes.byref(self._c), sm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                     int(sm.shape[0]), ctypes.byref(opts), ctypes.byref(h)))
+            self._h = h
+            self.n_open = int(self.info()["n_open"])
+            self.n_samples = int(sm.shape[0])
         self.n_qubits = int(circuit.n_qubits)
         self.dtype = int(dtype)
+
+    @classmethod
+    def from_samples(cls, circuit, samples, **kw):
+        """A plan for the amplitudes of arbitrary bitstrings (tn_plan_samples):
+        samples is (n_samples, n_qubits) of 0/1; contract() returns 2^k
+        amplitudes, entry s for bitstring s (k = ceil(log2 n_samples))."""
+        return cls(circuit, None, _samples=samples, **kw)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -550,13 +550,11 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->tile_policy = TN_TILE_FIXED;
 }
 
-int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts *opts,
-            tn_plan_t **out) {
-    if (!out) return fail(TN_EINVAL, "out is NULL");
-    *out = nullptr;
-    tn_plan_opts o;
-    if (opts) o = *opts;
-    else tn_plan_opts_default(&o);
+}  // extern "C"
+
+namespace {
+
+int check_opts(const tn_plan_opts &o) {
     if (o.dtype != TN_C64 && o.dtype != TN_F16 && o.dtype != TN_BF16) return fail(TN_EINVAL, "bad dtype");
     if (o.path_trials < 1 || o.path_trials > 4096) return fail(TN_EINVAL, "path_trials must be in 1..4096");
     if (o.n_slice_edges < -1 || o.n_slice_edges > 40) return fail(TN_EINVAL, "n_slice_edges must be in -1..40");
@@ -565,45 +563,129 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
     if (o.tile_policy < 0 || o.tile_policy > 2) return fail(TN_EINVAL, "bad tile_policy");
     if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
     if (o.path_anneal_iters < 0) return fail(TN_EINVAL, "path_anneal_iters must be >= 0");
+    if (o.n_slice_edges < 0 && o.max_log2_elems <= 0)
+        return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0");
+    return TN_OK;
+}
+
+// Path and slices on `plan_net` (the network the planner sees), refined by
+// annealing when asked; checks the cap and the slice batch.
+int plan_path(tn_plan_s *P, const Network &plan_net, std::string &err) {
+    const tn_plan_opts &o = P->opts;
+    const int n_target = o.n_slice_edges >= 0 ? o.n_slice_edges : -1;
+    const int cap = o.max_log2_elems;
+    int rc = choose_slices(plan_net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
+    if (rc != TN_OK) return rc;
+    if (o.path_anneal_iters > 0)
+        // kappa: flops one element of HBM traffic is worth at the ridge
+        // (complex-half 4 B x ~250 flop/B on the tensor cores; complex64
+        // 8 B x ~12 flop/B on the CUDA cores)
+        refine_plan(plan_net, n_target, cap, o.path_seed, o.path_anneal_iters,
+                    o.dtype == TN_C64 ? 100.0 : 1000.0, o.path_trials, P->path, P->sliced);
+    if (cap > 0 && P->path.max_log2 > cap) {
+        err = "the slicing does not reach the cap (largest intermediate 2^" + std::to_string(P->path.max_log2) + ")";
+        return TN_EINVAL;
+    }
+    if (o.slice_batch_log2 > (int)P->sliced.size()) {
+        err = "slice_batch_log2 exceeds the number of sliced edges";
+        return TN_EINVAL;
+    }
+    P->batch_log2 = o.slice_batch_log2;
+    return TN_OK;
+}
+
+// Schedule and leaf store of a planned network.
+int finish_plan(tn_plan_s *P, const std::vector<int> *sample_edges, std::string &err) {
+    const tn_plan_opts &o = P->opts;
+    int rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
+                            o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
+                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err, sample_edges);
+    if (rc != TN_OK) return rc;
+    int64_t offs = 0;
+    for (const Leaf &L : P->net.leaves) {
+        P->leaf_offset.push_back(offs);
+        P->leaf_store.insert(P->leaf_store.end(), L.data.begin(), L.data.end());
+        offs += (int64_t)L.data.size();
+    }
+    for (LeafJob &j : P->sched.leaf_jobs) j.src = P->leaf_offset[j.src];
+    return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts *opts,
+            tn_plan_t **out) {
+    if (!out) return fail(TN_EINVAL, "out is NULL");
+    *out = nullptr;
+    tn_plan_opts o;
+    if (opts) o = *opts;
+    else tn_plan_opts_default(&o);
+    int rc = check_opts(o);
+    if (rc != TN_OK) return rc;
     try {
         tn_plan_s *P = new tn_plan_s();
         P->opts = o;
         std::string err;
-        int rc = build_network(circuit, query, P->net, err);
+        rc = build_network(circuit, query, P->net, err);
+        if (rc == TN_OK) rc = plan_path(P, P->net, err);
+        if (rc == TN_OK) rc = finish_plan(P, nullptr, err);
         if (rc != TN_OK) { delete P; return fail(rc, err); }
-        const int n_target = o.n_slice_edges >= 0 ? o.n_slice_edges : -1;
-        const int cap = o.max_log2_elems;
-        if (n_target < 0 && cap <= 0) { delete P; return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0"); }
-        rc = choose_slices(P->net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
+        *out = P;
+        return TN_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(TN_ENOMEM, "host allocation failed");
+    } catch (const std::exception &ex) {
+        return fail(TN_EINVAL, ex.what());
+    }
+}
+
+int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n_samples,
+                    const tn_plan_opts *opts, tn_plan_t **out) {
+    if (!out || !circuit || !samples) return fail(TN_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_samples < 1 || n_samples > (1 << 20)) return fail(TN_EINVAL, "n_samples must be in 1..2^20");
+    tn_plan_opts o;
+    if (opts) o = *opts;
+    else tn_plan_opts_default(&o);
+    int rc = check_opts(o);
+    if (rc != TN_OK) return rc;
+    const int n = circuit->n_qubits;
+    if (n < 1 || n > 64) return fail(TN_EINVAL, "n_qubits must be in 1..64");
+    int k = 0;
+    while ((1 << k) < n_samples) ++k;
+    if (k + o.slice_batch_log2 > 24) return fail(TN_EINVAL, "too many batch modes (samples and slice batch)");
+    try {
+        std::vector<uint64_t> bits((size_t)1 << k);
+        for (int64_t s = 0; s < ((int64_t)1 << k); ++s) {
+            const int64_t src = s < n_samples ? s : n_samples - 1;     // padding repeats the last
+            uint64_t b = 0;
+            for (int q = 0; q < n; ++q) {
+                const uint8_t v = samples[src * n + q];
+                if (v > 1) return fail(TN_EINVAL, "sample bits must be 0 or 1");
+                b |= (uint64_t)v << q;
+            }
+            bits[(size_t)s] = b;
+        }
+        std::vector<int32_t> all(n);
+        for (int q = 0; q < n; ++q) all[q] = q;
+        std::vector<uint8_t> zeros(n, 0);
+        tn_query query{n, all.data(), zeros.data()};
+        tn_plan_s *P = new tn_plan_s();
+        P->opts = o;
+        std::string err;
+        rc = build_network_open(circuit, &query, 64, P->net, err);
+        Network plan_net;
+        if (rc == TN_OK) {
+            plan_net = P->net;
+            rc = fix_open_legs(plan_net);
+        }
+        if (rc == TN_OK) rc = plan_path(P, plan_net, err);
+        std::vector<int> sample_edges;
+        if (rc == TN_OK) rc = expand_samples(P->net, bits, k, sample_edges, err);
+        if (rc == TN_OK) rc = finish_plan(P, &sample_edges, err);
         if (rc != TN_OK) { delete P; return fail(rc, err); }
-        if (o.path_anneal_iters > 0)
-            // kappa: flops one element of HBM traffic is worth at the ridge
-            // (complex-half 4 B x ~250 flop/B on the tensor cores; complex64
-            // 8 B x ~12 flop/B on the CUDA cores)
-            refine_plan(P->net, n_target, cap, o.path_seed, o.path_anneal_iters,
-                        o.dtype == TN_C64 ? 100.0 : 1000.0, o.path_trials, P->path, P->sliced);
-        if (cap > 0 && P->path.max_log2 > cap) {
-            delete P;
-            return fail(TN_EINVAL, "the slicing does not reach the cap (largest intermediate 2^" +
-                                       std::to_string(P->path.max_log2) + ")");
-        }
-        if (o.slice_batch_log2 > (int)P->sliced.size()) {
-            delete P;
-            return fail(TN_EINVAL, "slice_batch_log2 exceeds the number of sliced edges");
-        }
-        P->batch_log2 = o.slice_batch_log2;
-        rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
-                            o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
-                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err);
-        if (rc != TN_OK) { delete P; return fail(rc, err); }
-        // leaf store
-        int64_t offs = 0;
-        for (const Leaf &L : P->net.leaves) {
-            P->leaf_offset.push_back(offs);
-            P->leaf_store.insert(P->leaf_store.end(), L.data.begin(), L.data.end());
-            offs += (int64_t)L.data.size();
-        }
-        for (LeafJob &j : P->sched.leaf_jobs) j.src = P->leaf_offset[j.src];
         *out = P;
         return TN_OK;
     } catch (const std::bad_alloc &) {

@@ -41,6 +41,16 @@ struct Network {
 };
 
 int build_network(const tn_circuit *c, const tn_query *q, Network &out, std::string &err);
+// build_network allowing up to max_open open qubits (sample networks: all)
+int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Network &out, std::string &err);
+// Uncorrelated bitstrings: every open output leg is replaced by k sample
+// edges (batch hyperedges, output bit j = bit j of the sample index) shared
+// by all output leaves; leaf data per sample has its outputs fixed to that
+// sample's bits (samples[s] bit q = qubit q).  fix_open_legs: the planning
+// copy, outputs at 0.
+int expand_samples(Network &net, const std::vector<uint64_t> &samples, int k, std::vector<int> &sample_edges,
+                   std::string &err);
+int fix_open_legs(Network &net);
 
 // ------------------------------------------------------------------- path --
 struct Path {
@@ -74,7 +84,7 @@ struct LeafJob {          // one leaf to prepare (device-side struct)
     int32_t n_fixed;      // legs fixed by looped slice bits
     int32_t fixed_pos[4]; // bit position (from LSB) of each fixed leg in the input
     int32_t fixed_bit[4]; // slice-id bit that fixes it
-    int32_t keep_pos[4];  // bit position (from LSB) in the input of output bit i
+    int32_t keep_pos[32]; // bit position (from LSB) in the input of output bit i
     int32_t meta;         // tensor meta slot (complex-half)
     int32_t pad_;
 };

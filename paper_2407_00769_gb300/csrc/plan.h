@@ -48,7 +48,7 @@ struct Schedule {
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
                    int batch_log2, int dtype, int small_log2, bool allow_tc, int fp8_min_log2_flops,
-                   Schedule &out, std::string &err);
+                   Schedule &out, std::string &err, const std::vector<int> *sample_edges = nullptr);
 
 }  // namespace tn
 

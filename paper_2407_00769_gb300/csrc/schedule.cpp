@@ -84,7 +84,7 @@ struct BufReq {
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
                    int batch_log2, int dtype, int small_log2, bool allow_tc, int fp8_min_log2_flops,
-                   Schedule &S, std::string &err) {
+                   Schedule &S, std::string &err, const std::vector<int> *sample_edges) {
     S = Schedule();
     const int L = (int)net.leaves.size();
     const int NS = (int)path.steps.size();
@@ -98,8 +98,13 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
     }
     std::vector<int> sbit(E, -1);
     for (int j = 0; j < (int)sliced.size(); ++j) sbit[sliced[j]] = j;
+    // sample edges (uncorrelated bitstrings): batch hyperedges carried to the
+    // end like batched slice bits, then read out as output bits
+    std::vector<char> is_sample(E, 0);
+    if (sample_edges)
+        for (int e : *sample_edges) is_sample[e] = 1;
     auto looped = [&](int e) { return sbit[e] >= batch_log2; };
-    auto batched = [&](int e) { return sbit[e] >= 0 && sbit[e] < batch_log2; };
+    auto batched = [&](int e) { return (sbit[e] >= 0 && sbit[e] < batch_log2) || is_sample[e]; };
     // ---- leg orders, invariance, sets
     std::vector<std::vector<int>> legs(T), sets(T);
     std::vector<char> inv(T, 1);
@@ -192,6 +197,10 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             const Leaf &lf = net.leaves[l];
             LeafJob j{};
             const int rin = (int)lf.legs.size();
+            if ((int)legs[l].size() > 31 || rin > 40) {
+                err = "a leaf has too many legs";
+                return TN_EINVAL;
+            }
             j.rank_in = rin;
             j.rank_out = (int)legs[l].size();
             int nf = 0;

@@ -237,3 +237,13 @@ def test_bundled_timings_for_the_cost_model():
     assert all(r["ms"] > 0 for r in recs)
     x = tn.cost_features(recs[:1000])
     assert x.shape == (1000, tn.COST_NFEAT) and np.isfinite(x).all()
+
+
+def test_sample_plan_builds_on_the_host():
+    c, _ = rqcgen.small_grid(3, 4, 8, seed=3, n_open=4)
+    rng = np.random.default_rng(0)
+    s = rng.integers(0, 2, size=(10, 12))
+    p = tn.Plan.from_samples(c, s, dtype=tn.C64, n_slice_edges=2, torch_allocator=False)
+    assert p.info()["n_open"] == 4 and p.n_samples == 10
+    with pytest.raises(tn.TnError):
+        tn.Plan.from_samples(c, np.full((3, 12), 2), dtype=tn.C64, torch_allocator=False)
