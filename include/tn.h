@@ -177,16 +177,18 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
 /*
  * tn_plan_samples: a plan for the amplitudes of n_samples arbitrary
  * (uncorrelated) bitstrings of `circuit`: samples[s * n_qubits + q] is bit q
- * (0 or 1) of bitstring s.  Every qubit's output leg is replaced by
- * k = ceil(log2 n_samples) sample modes shared by all output tensors (batch
- * hyperedges carried through the contraction, like batched slice bits), each
- * output tensor holding its values for every sample; the path is planned on
- * the network with its outputs fixed.  tn_contract then fills 2^k
+ * (0 or 1) of bitstring s.  The network keeps every qubit's output leg; a
+ * tensor holds its output legs densely while it has at most
+ * k = ceil(log2 n_samples) of them, and the step that would give it more (or
+ * that meets a tensor already indexed by sample, or the last step) switches
+ * to one row per sample: each operand still holding dense outputs is read at
+ * the row the sample's bits select, through index arrays built here (the
+ * sparse state of paper Sec. 3.4.2, on the gathering GEMMs).  The path is
+ * planned on the network with its outputs fixed.  tn_contract fills 2^k
  * amplitudes, entry s for bitstring s (entries past n_samples repeat the
- * last bitstring); slicing, batching and dtypes as for tn_plan.  Tensors
- * that carry sample modes are 2^k times larger than in a tn_plan of one
- * bitstring.  Errors: TN_EINVAL (NULL, n_samples outside 1..2^20, a bit
- * other than 0/1, k + slice_batch_log2 > 24), as tn_plan otherwise.
+ * last bitstring); slicing and dtypes as for tn_plan, slice_batch_log2 = 0.
+ * Errors: TN_EINVAL (NULL, n_samples outside 1..2^20, a bit other than 0/1,
+ * slice_batch_log2 != 0), as tn_plan otherwise.
  */
 int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n_samples,
                     const tn_plan_opts *opts, tn_plan_t **out);

@@ -69,8 +69,9 @@ int ensure_device(tn_plan_s *P) {
             split_bytes = std::max(split_bytes, tc_split_bytes(op.gemm.lm, op.gemm.ln, op.gemm.lk,
                                                                (int64_t)1 << op.gemm.lb));
     P->d_splitk = (float *)plan_dev_alloc(P, split_bytes);
+    P->d_gidx = (int32_t *)plan_dev_alloc(P, std::max<size_t>(64, S.gidx.size() * 4));
     if (!P->d_ws || !P->d_store || !P->d_jobs || !P->d_tmax || !P->d_texp || !P->d_err || !P->d_stepcorr ||
-        !P->d_splitk) {
+        !P->d_splitk || !P->d_gidx) {
         plan_dev_free_all(P);
         return fail(TN_ENOMEM, "device allocation of the plan workspace (" +
                                    std::to_string(S.ws_bytes) + " bytes) failed");
@@ -86,6 +87,9 @@ int ensure_device(tn_plan_s *P) {
         TN_CUDA(cudaMemcpy(P->d_jobs, S.leaf_jobs.data(), S.leaf_jobs.size() * sizeof(LeafJob),
                            cudaMemcpyHostToDevice),
                 "upload leaf jobs");
+    if (!S.gidx.empty())
+        TN_CUDA(cudaMemcpy(P->d_gidx, S.gidx.data(), S.gidx.size() * 4, cudaMemcpyHostToDevice),
+                "upload gather indices");
     {
         // per-step rounding compensation: 1 until a step measures its own
         std::vector<double2> ones(std::max<size_t>(1, S.steps.size()), make_double2(1.0, 0.0));
@@ -194,8 +198,11 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
         case OP_GEMM: {
             const GemmOp &g = op.gemm;
             const int64_t batch = (int64_t)1 << g.lb;
-            const int64_t sa = (int64_t)1 << (g.lm + g.lk), sb = (int64_t)1 << (g.lk + g.ln),
-                          sc = (int64_t)1 << (g.lm + g.ln);
+            const int64_t sa = g.bcast_a ? 0 : (int64_t)1 << (g.lm + g.lk),
+                          sb = g.bcast_b ? 0 : (int64_t)1 << (g.lk + g.ln), sc = (int64_t)1 << (g.lm + g.ln);
+            // sparse-state gathers: the operand chunk of each batch entry
+            const int32_t *za = g.idx_a >= 0 ? P->d_gidx + g.idx_a : nullptr;
+            const int32_t *zb = g.idx_b >= 0 ? P->d_gidx + g.idx_b : nullptr;
             ScaleRef sr{};
             sr.tmax = P->d_tmax;
             sr.texp = P->d_texp;
@@ -208,16 +215,17 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             switch (g.kernel) {
                 case GK_C64_ROWS:
                     e = launch_gemm_rows_c64((const float2 *)(ws + g.a), (const float2 *)(ws + g.b),
-                                             (float2 *)(ws + g.c), g.lm, g.ln, g.lk, batch, sa, sb, sc, s);
+                                             (float2 *)(ws + g.c), g.lm, g.ln, g.lk, batch, sa, sb, sc, s, za,
+                                             zb);
                     break;
                 case GK_C64_TILED:
                     e = launch_gemm_tiled_c64((const float2 *)(ws + g.a), (const float2 *)(ws + g.b),
                                               (float2 *)(ws + g.c), g.lm, g.ln, g.lk, batch, sa, sb,
-                                              sc, g.tile, s);
+                                              sc, g.tile, s, za, zb);
                     break;
                 case GK_LP_ROWS:
                     e = launch_gemm_rows_mixed(dtype, g.ta, g.tb, g.tc, ws + g.a, ws + g.b, ws + g.c, g.lm,
-                                               g.ln, g.lk, batch, sa, sb, sc, sr, s);
+                                               g.ln, g.lk, batch, sa, sb, sc, sr, s, za, zb);
                     break;
                 case GK_LP_TC: {
                     TcGemmDesc d;
@@ -227,8 +235,12 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.C = ws + g.c;
                     d.lm = g.lm; d.ln = g.ln; d.lk = g.lk;
                     d.batch = batch;
-                    d.batch_a = g.lb > 0;
-                    d.batch_b = g.lb > 0;
+                    d.batch_a = g.lb > 0 && !g.bcast_a;
+                    d.batch_b = g.lb > 0 && !g.bcast_b;
+                    d.za = za;
+                    d.zb = zb;
+                    if (za) d.depth_a = (int64_t)1 << g.gather_a_log2;
+                    if (zb) d.depth_b = (int64_t)1 << g.gather_b_log2;
                     d.np = std::max(16, 2 << g.ln);
                     d.bn = tc_tile_bn(g.tile);
                     d.gm = tc_tile_gm(g.tile);
@@ -595,11 +607,11 @@ int plan_path(tn_plan_s *P, const Network &plan_net, std::string &err) {
 }
 
 // Schedule and leaf store of a planned network.
-int finish_plan(tn_plan_s *P, const std::vector<int> *sample_edges, std::string &err) {
+int finish_plan(tn_plan_s *P, const SampleSpec *spec, std::string &err) {
     const tn_plan_opts &o = P->opts;
     int rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
                             o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
-                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err, sample_edges);
+                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err, spec);
     if (rc != TN_OK) return rc;
     int64_t offs = 0;
     for (const Leaf &L : P->net.leaves) {
@@ -630,7 +642,7 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
         std::string err;
         rc = build_network(circuit, query, P->net, err);
         if (rc == TN_OK) rc = plan_path(P, P->net, err);
-        if (rc == TN_OK) rc = finish_plan(P, nullptr, err);
+        if (rc == TN_OK) rc = finish_plan(P, nullptr, err);  // correlated query
         if (rc != TN_OK) { delete P; return fail(rc, err); }
         *out = P;
         return TN_OK;
@@ -655,7 +667,8 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
     if (n < 1 || n > 64) return fail(TN_EINVAL, "n_qubits must be in 1..64");
     int k = 0;
     while ((1 << k) < n_samples) ++k;
-    if (k + o.slice_batch_log2 > 24) return fail(TN_EINVAL, "too many batch modes (samples and slice batch)");
+    if (k > 24) return fail(TN_EINVAL, "too many samples");
+    if (o.slice_batch_log2 != 0) return fail(TN_EINVAL, "sample plans run their slices one at a time (slice_batch_log2 = 0)");
     try {
         std::vector<uint64_t> bits((size_t)1 << k);
         for (int64_t s = 0; s < ((int64_t)1 << k); ++s) {
@@ -676,15 +689,24 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
         P->opts = o;
         std::string err;
         rc = build_network_open(circuit, &query, 64, P->net, err);
+        // the planner sees the output legs as legs (dense), so it merges the
+        // tensors that carry them late, where few rows per sample remain
         Network plan_net;
-        if (rc == TN_OK) {
-            plan_net = P->net;
-            rc = fix_open_legs(plan_net);
-        }
+        if (rc == TN_OK) plan_net = P->net;
         if (rc == TN_OK) rc = plan_path(P, plan_net, err);
-        std::vector<int> sample_edges;
-        if (rc == TN_OK) rc = expand_samples(P->net, bits, k, sample_edges, err);
-        if (rc == TN_OK) rc = finish_plan(P, &sample_edges, err);
+        SampleSpec spec;
+        spec.k = k;
+        spec.bits = bits;
+        if (rc == TN_OK) {
+            for (int j = 0; j < k; ++j) {
+                spec.sample_edges.push_back((int)P->net.edges.size());
+                P->net.edges.push_back(Edge{-1, -1, -1, -1, j});   // output bit j = sample index bit j
+            }
+            for (Edge &e : P->net.edges)
+                if (e.qubit >= 0) e.open_t = e.open_t >= 0 ? n + e.open_t : -1;   // dense outputs: not amplitude bits
+            P->net.n_open = k;
+            rc = finish_plan(P, &spec, err);
+        }
         if (rc != TN_OK) { delete P; return fail(rc, err); }
         *out = P;
         return TN_OK;

@@ -43,14 +43,8 @@ struct Network {
 int build_network(const tn_circuit *c, const tn_query *q, Network &out, std::string &err);
 // build_network allowing up to max_open open qubits (sample networks: all)
 int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Network &out, std::string &err);
-// Uncorrelated bitstrings: every open output leg is replaced by k sample
-// edges (batch hyperedges, output bit j = bit j of the sample index) shared
-// by all output leaves; leaf data per sample has its outputs fixed to that
-// sample's bits (samples[s] bit q = qubit q).  fix_open_legs: the planning
-// copy, outputs at 0.
-int expand_samples(Network &net, const std::vector<uint64_t> &samples, int k, std::vector<int> &sample_edges,
-                   std::string &err);
-int fix_open_legs(Network &net);
+// Every open output leg fixed at 0: the copy of an uncorrelated-bitstring
+// network the path planner sees.
 
 // ------------------------------------------------------------------- path --
 struct Path {
@@ -110,6 +104,13 @@ struct GemmOp {
     // element index goes to bit out_dpos[i]; the lowest 3 bits stay
     int32_t out_rank;
     int8_t out_dpos[kMaxRank];
+    // sparse-state gather step (uncorrelated bitstrings): per operand, the
+    // batch entry s reads chunk idx[s] (offset of an int32 array in the plan's
+    // index table, -1: chunk s) out of 2^gather_log2 chunks; bcast: one chunk
+    // for every entry
+    int64_t idx_a = -1, idx_b = -1;
+    int32_t gather_a_log2 = 0, gather_b_log2 = 0;
+    int32_t bcast_a = 0, bcast_b = 0;
 };
 
 struct QuantOp {

@@ -529,7 +529,7 @@ __device__ __forceinline__ float2 widen(T v) {
 template <typename TA, typename TB, typename TC, int NC, int DT>
 __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const TA *__restrict__ A, const TB *__restrict__ B, TC *__restrict__ C, int lm, int ln, int lk,
-    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr) {
+    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb) {
     constexpr int KC = kKC;
     __shared__ __align__(16) TA As[kRows * KC];
     __shared__ float2 Bs[KC][NC];
@@ -539,8 +539,9 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const int64_t m0 = (int64_t)blockIdx.x * kRows;
     const int n0 = blockIdx.y * NC;
     const int nc = min(NC, N);
-    const TA *Ab = A + b * sa;
-    const TB *Bb = B + b * sb;
+    // sparse-state gathers: operand chunks by index instead of by batch entry
+    const TA *Ab = A + (za ? (int64_t)za[b] : b) * sa;
+    const TB *Bb = B + (zb ? (int64_t)zb[b] : b) * sb;
     TC *Cb = C + b * sc;
     const int rows = (int)min((int64_t)kRows, M - m0);
     // FP32 partial sums over at most kFlushK terms, added into FP64: a long
@@ -642,7 +643,8 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
 template <typename TA, typename TB, typename TC, int DT>
 static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, int ln, int lk,
                                  int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                                 const ScaleRef &sr, cudaStream_t s) {
+                                 const ScaleRef &sr, cudaStream_t s, const int32_t *za = nullptr,
+                                 const int32_t *zb = nullptr) {
     const int64_t M = (int64_t)1 << lm;
     const int N = 1 << ln;
     const int64_t gx = (M + kRows - 1) / kRows;
@@ -651,7 +653,7 @@ static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, 
     {                                                                                             \
         dim3 g((unsigned)gx, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);                   \
         gemm_rows_kernel<TA, TB, TC, NCV, DT><<<g, kRows, 0, s>>>(                                \
-            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr);                   \
+            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr, za, zb);           \
         break;                                                                                    \
     }
     switch (N >= 16 ? 16 : N) {
@@ -667,40 +669,42 @@ static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, 
 
 cudaError_t launch_gemm_rows_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
                                  int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const int32_t *za, const int32_t *zb) {
     ScaleRef sr{};
-    return rows_dispatch<float2, float2, float2, TN_C64>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return rows_dispatch<float2, float2, float2, TN_C64>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
 }
 
 template <int DT, typename H>
 static cudaError_t rows_mixed(int ta, int tb, int tc, const void *A, const void *B, void *C, int lm,
                               int ln, int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                              const ScaleRef &sr, cudaStream_t s) {
+                              const ScaleRef &sr, cudaStream_t s, const int32_t *za, const int32_t *zb) {
     // A is the larger operand, so a complex64 A implies a complex64 B
     const int code = ta * 4 + tb * 2 + tc;
     switch (code) {
-        case 0: return rows_dispatch<float2, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-        case 1: return rows_dispatch<float2, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-        case 4: return rows_dispatch<H, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-        case 5: return rows_dispatch<H, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-        case 6: return rows_dispatch<H, H, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-        case 7: return rows_dispatch<H, H, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        case 0: return rows_dispatch<float2, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+        case 1: return rows_dispatch<float2, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+        case 4: return rows_dispatch<H, float2, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+        case 5: return rows_dispatch<H, float2, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+        case 6: return rows_dispatch<H, H, float2, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+        case 7: return rows_dispatch<H, H, H, DT>(A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
                                    void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
-                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s) {
+                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,
+                                   const int32_t *za, const int32_t *zb) {
     if (dtype == TN_F16)
-        return rows_mixed<TN_F16, __half2>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
-    return rows_mixed<TN_BF16, __nv_bfloat162>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+        return rows_mixed<TN_F16, __half2>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za, zb);
+    return rows_mixed<TN_BF16, __nv_bfloat162>(ta, tb, tc, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, za,
+                                               zb);
 }
 
 cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C, int lm, int ln,
                                 int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
                                 const ScaleRef &sr, cudaStream_t s) {
-    return launch_gemm_rows_mixed(dtype, 1, 1, 1, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
+    return launch_gemm_rows_mixed(dtype, 1, 1, 1, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------- tiled c64 --
@@ -712,7 +716,7 @@ cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C
 template <int BM, int BN, int BK, bool LONGK>
 __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
     const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C, int lm,
-    int ln, int lk, int64_t sa, int64_t sb, int64_t sc) {
+    int ln, int lk, int64_t sa, int64_t sb, int64_t sc, const int32_t *za, const int32_t *zb) {
     constexpr int TM = BM / 16, TN = BN / 16;
     __shared__ float2 As[BK][BM + 1];
     __shared__ float2 Bs[BK][BN];
@@ -720,8 +724,8 @@ __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
     const int64_t b = blockIdx.z;
     const int64_t m0 = (int64_t)blockIdx.x * BM;
     const int n0 = blockIdx.y * BN;
-    const float2 *Ab = A + b * sa + m0 * K;
-    const float2 *Bb = B + b * sb + n0;
+    const float2 *Ab = A + (za ? (int64_t)za[b] : b) * sa + m0 * K;
+    const float2 *Bb = B + (zb ? (int64_t)zb[b] : b) * sb + n0;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float2 acc[TM][TN];
     double2 tot[LONGK ? TM : 1][LONGK ? TN : 1];   // FP64 sum of the FP32 partials
@@ -784,16 +788,16 @@ __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
 
 cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
                                   int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                                  int tile, cudaStream_t s) {
+                                  int tile, cudaStream_t s, const int32_t *za, const int32_t *zb) {
     (void)tile;
     if (lm < 6 || ln < 6 || lk < 4) return cudaErrorInvalidValue;
     const int64_t gx = ((int64_t)1 << lm) / 64;
     if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
     dim3 g((unsigned)gx, (unsigned)((1 << ln) / 64), (unsigned)batch);
     if (lk > 12)
-        gemm_tiled_c64_kernel<64, 64, 16, true><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
+        gemm_tiled_c64_kernel<64, 64, 16, true><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc, za, zb);
     else
-        gemm_tiled_c64_kernel<64, 64, 16, false><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc);
+        gemm_tiled_c64_kernel<64, 64, 16, false><<<g, 256, 0, s>>>(A, B, C, lm, ln, lk, sa, sb, sc, za, zb);
     return cudaGetLastError();
 }
 

@@ -43,12 +43,15 @@ cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_
                              cudaStream_t s);
 cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int elem_bytes,
                            cudaStream_t s);
+// za / zb (device int32[batch], nullable): the A / B chunk of each batch
+// entry (sparse-state gathers); NULL: the entry itself (times sa / sb).
 cudaError_t launch_gemm_rows_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
                                  int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const int32_t *za = nullptr, const int32_t *zb = nullptr);
 cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
                                   int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
-                                  int tile, cudaStream_t s);
+                                  int tile, cudaStream_t s, const int32_t *za = nullptr,
+                                  const int32_t *zb = nullptr);
 cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C, int lm, int ln,
                                 int lk, int64_t batch, int64_t sa, int64_t sb, int64_t sc,
                                 const ScaleRef &sr, cudaStream_t s);
@@ -66,7 +69,8 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
                               int32_t *texp, int meta_src, int meta_dst, cudaStream_t s);
 cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
                                    void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
-                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s);
+                                   int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,
+                                   const int32_t *za = nullptr, const int32_t *zb = nullptr);
 // stepcorr / n_steps: per-step rounding compensation factors of a
 // complex-half plan (n_steps = 0: none).
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,

@@ -199,55 +199,4 @@ int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Net
     return TN_OK;
 }
 
-int fix_open_legs(Network &net) {
-    // every open output leg at value 0: the planning copy of a sample network
-    for (Leaf &L : net.leaves)
-        for (int i = (int)L.legs.size() - 1; i >= 0; --i)
-            if (L.legs[i] >= 0 && net.edges[L.legs[i]].open_t >= 0) select_leg(L, i, 0);
-    return TN_OK;
-}
-
-int expand_samples(Network &net, const std::vector<uint64_t> &samples, int k, std::vector<int> &sample_edges,
-                   std::string &err) {
-    if ((int64_t)samples.size() != ((int64_t)1 << k)) { err = "sample count must be 2^k"; return TN_EINVAL; }
-    sample_edges.clear();
-    for (int j = 0; j < k; ++j) {
-        sample_edges.push_back((int)net.edges.size());
-        net.edges.push_back(Edge{-1, -1, -1, -1, j});   // output bit j = sample index bit j
-    }
-    for (Leaf &L : net.leaves) {
-        std::vector<int> open_pos, keep_pos;
-        const int r = (int)L.legs.size();
-        for (int i = 0; i < r; ++i) {
-            if (L.legs[i] >= 0 && net.edges[L.legs[i]].open_t >= 0) open_pos.push_back(i);
-            else keep_pos.push_back(i);
-        }
-        if (open_pos.empty()) continue;
-        const int rk = (int)keep_pos.size();
-        std::vector<cd> data((size_t)samples.size() << rk);
-        for (size_t s = 0; s < samples.size(); ++s)
-            for (int64_t o = 0; o < ((int64_t)1 << rk); ++o) {
-                // legs are row-major, the first leg outermost: bit (r-1-i) of the index
-                int64_t in = 0;
-                for (int t = 0; t < rk; ++t)
-                    if ((o >> (rk - 1 - t)) & 1) in |= (int64_t)1 << (r - 1 - keep_pos[t]);
-                for (int p : open_pos) {
-                    const int qubit = net.edges[L.legs[p]].qubit;
-                    if ((samples[s] >> qubit) & 1) in |= (int64_t)1 << (r - 1 - p);
-                }
-                data[(s << rk) | (size_t)o] = L.data[(size_t)in];
-            }
-        std::vector<int> legs;
-        for (int j = k - 1; j >= 0; --j) legs.push_back(sample_edges[j]);   // sample bit k-1 outermost
-        for (int p : keep_pos) legs.push_back(L.legs[p]);
-        L.legs.swap(legs);
-        L.data.swap(data);
-    }
-    // the open edges are replaced by the sample edges
-    for (Edge &e : net.edges)
-        if (e.open_t >= 0 && e.qubit >= 0) e.open_t = -1;
-    net.n_open = k;
-    return TN_OK;
-}
-
 }  // namespace tn

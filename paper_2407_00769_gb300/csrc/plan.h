@@ -44,11 +44,24 @@ struct Schedule {
     int final_tensor = -1;
     int kernels_per_pass = 0, kernels_inv = 0;
     int n_gemm_steps = 0;
+    std::vector<int32_t> gidx;          // index table of sparse-state gather steps
+};
+
+// Uncorrelated bitstrings: k sample edges (output bit j of the amplitude
+// index = bit j of the sample index) and the 2^k bitstrings (bit q = qubit q).
+// Tensors keep their output legs dense while they hold at most k of them; the
+// step that would hold more (or that meets a tensor already indexed by
+// sample) switches to one row per sample, gathering each operand's row by the
+// sample's bits on that operand's output legs (the paper's sparse state).
+struct SampleSpec {
+    int k = 0;
+    std::vector<int> sample_edges;       // [j] = edge of sample bit j
+    std::vector<uint64_t> bits;          // 2^k bitstrings
 };
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
                    int batch_log2, int dtype, int small_log2, bool allow_tc, int fp8_min_log2_flops,
-                   Schedule &out, std::string &err, const std::vector<int> *sample_edges = nullptr);
+                   Schedule &out, std::string &err, const SampleSpec *spec = nullptr);
 
 }  // namespace tn
 
@@ -72,6 +85,7 @@ struct tn_plan_s {
     int32_t *d_err = nullptr;
     double2 *d_stepcorr = nullptr;      // per step: 1/(1+alpha) of its B' rounding
     float *d_splitk = nullptr;          // FP32 partials of split-K tensor-core steps
+    int32_t *d_gidx = nullptr;          // index table of sparse-state gather steps
     void *h_store_pinned = nullptr;     // pinned copy of the leaf store
     // per-kernel-class event timing (tn_profile)
     uint32_t prof_mask = 0;

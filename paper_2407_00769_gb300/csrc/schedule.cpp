@@ -84,7 +84,7 @@ struct BufReq {
 
 int build_schedule(const Network &net, const Path &path, const std::vector<int> &sliced,
                    int batch_log2, int dtype, int small_log2, bool allow_tc, int fp8_min_log2_flops,
-                   Schedule &S, std::string &err, const std::vector<int> *sample_edges) {
+                   Schedule &S, std::string &err, const SampleSpec *spec) {
     S = Schedule();
     const int L = (int)net.leaves.size();
     const int NS = (int)path.steps.size();
@@ -98,11 +98,19 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
     }
     std::vector<int> sbit(E, -1);
     for (int j = 0; j < (int)sliced.size(); ++j) sbit[sliced[j]] = j;
-    // sample edges (uncorrelated bitstrings): batch hyperedges carried to the
-    // end like batched slice bits, then read out as output bits
+    // sample edges (uncorrelated bitstrings): batch modes of the tensors that
+    // hold one row per sample, read out at the end as the amplitude index
     std::vector<char> is_sample(E, 0);
-    if (sample_edges)
-        for (int e : *sample_edges) is_sample[e] = 1;
+    if (spec)
+        for (int e : spec->sample_edges) is_sample[e] = 1;
+    // dense output legs (sample mode: a qubit's output leg before its tensor
+    // switches to rows per sample)
+    auto is_open = [&](int e) { return net.edges[e].open_t >= 0 && !is_sample[e]; };
+    auto n_open_in = [&](const std::vector<int> &v) {
+        int n = 0;
+        for (int e : v) n += is_open(e);
+        return n;
+    };
     auto looped = [&](int e) { return sbit[e] >= batch_log2; };
     auto batched = [&](int e) { return (sbit[e] >= 0 && sbit[e] < batch_log2) || is_sample[e]; };
     // ---- leg orders, invariance, sets
@@ -116,6 +124,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         sets[l] = sorted_copy(legs[l]);
     }
     std::vector<int> consumer(T, -1);
+    std::vector<char> samp(T, 0);   // sample mode: the tensor holds one row per sample
     for (int s = 0; s < NS; ++s) {
         const int a = path.steps[s].first, b = path.steps[s].second;
         if (a < 0 || b < 0 || a >= L + s || b >= L + s || a == b || consumer[a] >= 0 || consumer[b] >= 0) {
@@ -129,8 +138,18 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         std::vector<int> un;
         std::set_union(sets[a].begin(), sets[a].end(), sets[b].begin(), sets[b].end(),
                        std::back_inserter(un));
+        bool to_rows = false;
+        if (spec) {
+            const int oa = n_open_in(sets[a]), ob = n_open_in(sets[b]);
+            to_rows = samp[a] || samp[b] || oa + ob > spec->k || (s == NS - 1 && oa + ob > 0);
+        }
+        samp[L + s] = to_rows;
         for (int e : un)
-            if (!(std::binary_search(sh.begin(), sh.end(), e) && !batched(e))) out.push_back(e);
+            if (!(std::binary_search(sh.begin(), sh.end(), e) && !batched(e)) && !(to_rows && is_open(e)))
+                out.push_back(e);
+        if (to_rows)
+            for (int e : spec->sample_edges)
+                if (!std::binary_search(out.begin(), out.end(), e)) out.insert(std::lower_bound(out.begin(), out.end(), e), e);
         sets[L + s] = out;
         inv[L + s] = inv[a] && inv[b];
     }
@@ -263,10 +282,57 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             if (!shared.count(e)) no.push_back(e);
         no = for_consumer(c, no);
 
+        // sparse-state gather step: C switches to (or stays in) one row per
+        // sample while an operand still holds dense output legs.  Operand
+        // roles: rows per sample (its batch dims: the sample edges), dense
+        // outputs (batch dims: those legs, gathered by each sample's bits),
+        // or neither (broadcast).
+        enum { R_NONE = 0, R_ROWS = 1, R_GATHER = 2 };
+        auto role = [&](int x) {
+            if (samp[x]) return (int)R_ROWS;
+            return (samp[c] && n_open_in(legs[x]) > 0) ? (int)R_GATHER : (int)R_NONE;
+        };
+        const bool gstep = spec && samp[c] && (role(ia) == R_GATHER || role(ib) == R_GATHER);
+        std::vector<int> abat, bbat;
+        int role_a = R_NONE, role_b = R_NONE;
+        if (gstep) {
+            role_a = role(ia);
+            role_b = role(ib);
+            std::vector<int> sord;                       // sample bit k-1 outermost
+            for (int j = spec->k - 1; j >= 0; --j) sord.push_back(spec->sample_edges[j]);
+            auto bat_of = [&](int x, int r) {
+                std::vector<int> v;
+                if (r == R_ROWS) return sord;
+                if (r == R_GATHER) {
+                    for (int e : legs[x])
+                        if (is_open(e)) v.push_back(e);
+                    std::sort(v.begin(), v.end(), [&](int p, int q) { return net.edges[p].qubit < net.edges[q].qubit; });
+                }
+                return v;
+            };
+            abat = bat_of(ia, role_a);
+            bbat = bat_of(ib, role_b);
+            bo = sord;
+            ko.clear();
+            mo.clear();
+            no.clear();
+            for (int e : LA)
+                if (!contains(abat, e) && shared.count(e) && !batched(e)) ko.push_back(e);
+            for (int e : LA)
+                if (!contains(abat, e) && !contains(ko, e)) mo.push_back(e);
+            for (int e : LB)
+                if (!contains(bbat, e) && !contains(ko, e)) no.push_back(e);
+            std::vector<int> want(abat);
+            want.insert(want.end(), mo.begin(), mo.end());
+            want.insert(want.end(), ko.begin(), ko.end());
+            okA = want == LA;
+        }
+
         int meta_b_override = -1, meta_a_override = -1, fp8 = 0;
         StepRec rec{};
         rec.a = ia; rec.b = ib; rec.c = c;
-        rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = nk; rec.lb = nb;
+        rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = gstep ? (int)ko.size() : nk;
+        rec.lb = gstep ? spec->k : nb;
         rec.invariant = inv[c];
 
         int64_t abuf = ia, bbuf = ib;
@@ -289,7 +355,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             return tmp;
         };
         if (!okA) {
-            std::vector<int> tgt(bo);
+            std::vector<int> tgt(gstep ? abat : bo);
             tgt.insert(tgt.end(), mo.begin(), mo.end());
             tgt.insert(tgt.end(), ko.begin(), ko.end());
             abuf = permute_to(ia, LA, tgt);
@@ -305,9 +371,10 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         if (kernel == GK_LP_TC) {
             // B goes straight from its stored order to the padded B' of
             // Eq. 6 ([batch][N][K] complex expanded to real rows) in one pass
-            std::vector<int> tgt(bo);
+            std::vector<int> tgt(gstep ? bbat : bo);
             tgt.insert(tgt.end(), no.begin(), no.end());
             tgt.insert(tgt.end(), ko.begin(), ko.end());
+            const int blb = gstep ? (int)bbat.size() : rec.lb;    // B' chunks: 2^blb
             Op op;
             op.kind = OP_BPREP;
             op.phase = phase;
@@ -315,7 +382,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             op.bprep.src = bbuf;
             op.bprep.lk = rec.lk;
             op.bprep.ln = rec.ln;
-            op.bprep.lb = rec.lb;
+            op.bprep.lb = blb;
             op.bprep.np = np;
             op.bprep.step = s;
             op.bprep.rank = (int)tgt.size();
@@ -329,14 +396,14 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             }
             for (int i = 0; i < (int)tgt.size(); ++i)
                 op.bprep.perm[i] = (int)(std::find(LB.begin(), LB.end(), tgt[i]) - LB.begin());
-            const int64_t bpbytes = ((int64_t)np * (2LL << rec.lk) * 2) << rec.lb;
+            const int64_t bpbytes = ((int64_t)np * (2LL << rec.lk) * 2) << blb;
             const int tmp = new_temp(bpbytes);
             op.bprep.dst = tmp;
             ops.push_back(op);
             if (phase) S.bytes_per_pass += (double)(((int64_t)esz_of(ib) << (rec.lk + rec.ln + rec.lb)) + bpbytes);
             bbuf = tmp;
             // FP8 step: E4M3 copies of B' and A, each with its own scale slot
-            if (fp8_min_log2_flops > 0 && rec.lk >= 6 &&
+            if (!gstep && fp8_min_log2_flops > 0 && rec.lk >= 6 &&
                 rec.lm + rec.ln + rec.lk + rec.lb + 3 >= fp8_min_log2_flops) {
                 auto quant = [&](int64_t src, int64_t pairs, int meta_src) {
                     Op q;
@@ -362,7 +429,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
                 rec.storage |= 8;
             }
         } else {
-            std::vector<int> tgt(bo);
+            std::vector<int> tgt(gstep ? bbat : bo);
             tgt.insert(tgt.end(), ko.begin(), ko.end());
             tgt.insert(tgt.end(), no.begin(), no.end());
             if (tgt != LB) {
@@ -393,6 +460,34 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.tb = tb;
         op.gemm.tc = tc;
         op.gemm.fp8 = fp8;
+        if (gstep) {
+            // per operand: rows per sample (chunk s), gathered (chunk =
+            // the sample's bits on its output legs, outermost first), or
+            // broadcast
+            auto gather_table = [&](const std::vector<int> &bat) {
+                const int64_t off = (int64_t)S.gidx.size();
+                const int m = (int)bat.size();
+                for (uint64_t bits : spec->bits) {
+                    int32_t z = 0;
+                    for (int i = 0; i < m; ++i)
+                        z |= (int32_t)((bits >> net.edges[bat[i]].qubit) & 1) << (m - 1 - i);
+                    S.gidx.push_back(z);
+                }
+                return off;
+            };
+            op.gemm.a_batched = role_a != R_NONE;
+            op.gemm.b_batched = role_b != R_NONE;
+            op.gemm.bcast_a = role_a == R_NONE;
+            op.gemm.bcast_b = role_b == R_NONE;
+            if (role_a == R_GATHER) {
+                op.gemm.idx_a = gather_table(abat);
+                op.gemm.gather_a_log2 = (int)abat.size();
+            }
+            if (role_b == R_GATHER) {
+                op.gemm.idx_b = gather_table(bbat);
+                op.gemm.gather_b_log2 = (int)bbat.size();
+            }
+        }
         ops.push_back(op);
         ++S.n_gemm_steps;
         const double fl = 8.0 * std::ldexp(1.0, rec.lm + rec.ln + rec.lk + rec.lb);

@@ -247,3 +247,19 @@ def test_sample_plan_builds_on_the_host():
     assert p.info()["n_open"] == 4 and p.n_samples == 10
     with pytest.raises(tn.TnError):
         tn.Plan.from_samples(c, np.full((3, 12), 2), dtype=tn.C64, torch_allocator=False)
+
+
+def test_sample_plan_cost_grows_slowly_with_the_sample_count():
+    # tensors keep the output legs dense while they carry at most
+    # log2(n_samples) of them, so 1024 bitstrings cost a few times one
+    # bitstring, not 1024 times
+    c, _ = rqcgen.grid_30q()
+    rng = np.random.default_rng(1)
+    flops = []
+    for ns in (1, 1024):
+        s = rng.integers(0, 2, size=(ns, 30))
+        i = tn.Plan.from_samples(c, s, dtype=tn.F16, n_slice_edges=8, trials=4, torch_allocator=False).info()
+        flops.append(i["flops_per_slice"] * i["n_slices"] + i["flops_invariant"])
+    assert flops[1] < 8 * flops[0]
+    with pytest.raises(tn.TnError):
+        tn.Plan.from_samples(c, np.zeros((4, 30)), dtype=tn.F16, slice_batch_log2=2, torch_allocator=False)
