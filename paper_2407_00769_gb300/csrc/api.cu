@@ -685,29 +685,64 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
         for (int q = 0; q < n; ++q) all[q] = q;
         std::vector<uint8_t> zeros(n, 0);
         tn_query query{n, all.data(), zeros.data()};
-        tn_plan_s *P = new tn_plan_s();
-        P->opts = o;
-        std::string err;
-        rc = build_network_open(circuit, &query, 64, P->net, err);
-        // the planner sees the output legs as legs (dense), so it merges the
-        // tensors that carry them late, where few rows per sample remain
-        Network plan_net;
-        if (rc == TN_OK) plan_net = P->net;
-        if (rc == TN_OK) rc = plan_path(P, plan_net, err);
-        SampleSpec spec;
-        spec.k = k;
-        spec.bits = bits;
-        if (rc == TN_OK) {
-            for (int j = 0; j < k; ++j) {
-                spec.sample_edges.push_back((int)P->net.edges.size());
-                P->net.edges.push_back(Edge{-1, -1, -1, -1, j});   // output bit j = sample index bit j
+        // Two planning views, the cheaper schedule kept: output legs visible
+        // as legs (the planner merges the tensors that carry them late, where
+        // few rows per sample remain; best for many samples), or fixed (the
+        // path of one closed network; best for few samples).  A view whose
+        // hybrid schedule holds a tensor above the cap is dropped.
+        tn_plan_s *P = nullptr;
+        double best = 0;
+        std::string err, first_err;
+        rc = TN_OK;
+        int first_rc = TN_OK;
+        for (int view = 0; view < 2; ++view) {
+            tn_plan_s *Q = new tn_plan_s();
+            Q->opts = o;
+            std::string e;
+            int r = build_network_open(circuit, &query, 64, Q->net, e);
+            Network plan_net;
+            if (r == TN_OK) {
+                plan_net = Q->net;
+                if (view == 1) fix_open_legs(plan_net);
+                r = plan_path(Q, plan_net, e);
             }
-            for (Edge &e : P->net.edges)
-                if (e.qubit >= 0) e.open_t = e.open_t >= 0 ? n + e.open_t : -1;   // dense outputs: not amplitude bits
-            P->net.n_open = k;
-            rc = finish_plan(P, &spec, err);
+            if (r == TN_OK) {
+                SampleSpec spec;
+                spec.k = k;
+                spec.bits = bits;
+                for (int j = 0; j < k; ++j) {
+                    spec.sample_edges.push_back((int)Q->net.edges.size());
+                    Q->net.edges.push_back(Edge{-1, -1, -1, -1, j});   // output bit j = sample index bit j
+                }
+                for (Edge &ed : Q->net.edges)
+                    if (ed.qubit >= 0) ed.open_t = ed.open_t >= 0 ? n + ed.open_t : -1;   // dense outputs: not amplitude bits
+                Q->net.n_open = k;
+                r = finish_plan(Q, &spec, e);
+            }
+            if (r == TN_OK) {
+                int real_max = 0;
+                for (const StepRec &st : Q->sched.steps) real_max = std::max(real_max, st.lm + st.ln + st.lb);
+                Q->path.max_log2 = real_max;
+                if (view > 0 && o.max_log2_elems > 0 && real_max > o.max_log2_elems) {
+                    r = TN_EINVAL;
+                    e = "hybrid schedule above the cap";
+                }
+            }
+            if (r != TN_OK) {
+                if (first_rc == TN_OK) { first_rc = r; first_err = e; }
+                delete Q;
+                continue;
+            }
+            const double flops = Q->sched.flops_per_pass * (double)((int64_t)1 << Q->sliced.size()) + Q->sched.flops_inv;
+            if (!P || flops < best) {
+                delete P;
+                P = Q;
+                best = flops;
+            } else {
+                delete Q;
+            }
         }
-        if (rc != TN_OK) { delete P; return fail(rc, err); }
+        if (!P) return fail(first_rc, first_err);
         *out = P;
         return TN_OK;
     } catch (const std::bad_alloc &) {

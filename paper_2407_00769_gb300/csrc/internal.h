@@ -43,8 +43,9 @@ struct Network {
 int build_network(const tn_circuit *c, const tn_query *q, Network &out, std::string &err);
 // build_network allowing up to max_open open qubits (sample networks: all)
 int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Network &out, std::string &err);
-// Every open output leg fixed at 0: the copy of an uncorrelated-bitstring
-// network the path planner sees.
+// Every open output leg fixed at 0: one planning view of an
+// uncorrelated-bitstring network.
+int fix_open_legs(Network &net);
 
 // ------------------------------------------------------------------- path --
 struct Path {

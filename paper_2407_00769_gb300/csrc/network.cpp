@@ -199,4 +199,12 @@ int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Net
     return TN_OK;
 }
 
+int fix_open_legs(Network &net) {
+    // every open output leg at value 0: a planning view of a sample network
+    for (Leaf &L : net.leaves)
+        for (int i = (int)L.legs.size() - 1; i >= 0; --i)
+            if (L.legs[i] >= 0 && net.edges[L.legs[i]].open_t >= 0) select_leg(L, i, 0);
+    return TN_OK;
+}
+
 }  // namespace tn
