@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,grid40",
+    ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,samples,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec"],
                     help="time one kernel on one shape instead (profiling aid)")
@@ -198,8 +198,8 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def read_golden():
-    path = os.path.join(ROOT, "tests", "golden", "grid5x6_14c_amps.txt")
+def read_golden(name="grid5x6_14c_amps.txt"):
+    path = os.path.join(ROOT, "tests", "golden", name)
     if not os.path.exists(path):
         return None
     import numpy as np
@@ -313,8 +313,8 @@ def _timed(fn, stream, flush, reps=1):
 def leg_grid12(tn, torch, dev, stream):
     """The small exact case: 12-qubit 3x4 grid, 8 cycles, no slicing, all
     4096 amplitudes in complex64 -- a latency figure (median of 20 calls,
-    inputs resident) with its error against the FP64 state vector."""
-    import oracle
+    inputs resident) with its error against the stored FP64 state-vector
+    amplitudes."""
     import rqcgen
     c, q = rqcgen.grid_12q()
     plan = tn.Plan(c, q, dtype=tn.C64)
@@ -330,12 +330,13 @@ def leg_grid12(tn, torch, dev, stream):
         e1.record(stream)
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-    want = oracle.amplitudes(c, q)
-    got = amps.cpu().numpy()
+    want = read_golden("grid3x4_8c_amps.txt")
     info = plan.info()
-    return {"workload": "grid3x4-8c: 12 qubits, 8 cycles, unsliced, 4096 amplitudes, complex64",
-            "ms_median": statistics.median(ts), "steps": info["n_steps"],
-            "rel_l2": float(oracle.rel_l2(got, want))}
+    out = {"workload": "grid3x4-8c: 12 qubits, 8 cycles, unsliced, 4096 amplitudes, complex64",
+           "ms_median": statistics.median(ts), "steps": info["n_steps"]}
+    if want is not None:
+        out["rel_l2"] = tn.metrics(amps, torch.from_numpy(want).to(dev))["rel_l2"]
+    return out
 
 
 def leg_grid53(tn, torch, dev, flush, stream, peaks, want_records=False):
@@ -457,6 +458,40 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
                      "tflops": flops / (ms * 1e-3) / 1e12,
                      "job_flops": info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"],
                      "est_job_s": ms * 1e-3 * info["n_slices"] / n, "max_log2_elems": info["max_log2_elems"]}
+    del plan, amps
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
+    """Uncorrelated bitstrings (Sec. 3.4.2): the 30-qubit circuit at n
+    arbitrary bitstrings in one sample plan (tensors keep output legs dense
+    up to log2 n of them, rows per sample beyond).  The first 1024 bitstrings
+    are the workload's correlated subspace, checked against its stored FP64
+    amplitudes; the rest are uniform random.  Reported per bitstring."""
+    import numpy as np
+    import rqcgen
+    c, q = rqcgen.grid_30q()
+    rng = np.random.default_rng(2407)
+    samples = rng.integers(0, 2, size=(n, c.n_qubits)).astype(np.uint8)
+    j = np.arange(1024)
+    samples[:1024, :] = np.asarray(q.fixed_bits, dtype=np.uint8)[None, :]
+    for t, qq in enumerate(q.open_qubits):
+        samples[:1024, qq] = (j >> t) & 1
+    t0 = time.time()
+    plan = tn.Plan.from_samples(c, samples, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS)
+    plan_s = time.time() - t0
+    info = plan.info()
+    amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+    for _ in range(2):
+        plan.contract(out=amps)
+    ms = _timed(lambda: plan.contract(out=amps), stream, flush, reps=3)
+    flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
+    out = {"n_bitstrings": n, "plan_s": plan_s, "job_flops": flops, "ms": ms,
+           "tflops": flops / (ms * 1e-3) / 1e12, "us_per_bitstring": ms * 1e3 / n,
+           "max_log2_elems": info["max_log2_elems"], "workspace_gib": info["workspace_bytes"] / 2**30}
+    if gold is not None:
+        out["rel_l2_first_1024"] = tn.metrics(amps[:1024], torch.from_numpy(gold).to(dev))["rel_l2"]
     del plan, amps
     torch.cuda.empty_cache()
     return out
@@ -839,6 +874,8 @@ def main():
         line["fp8"] = leg_fp8(tn, torch, dev, flush, stream, gold)
     if "anneal" in legs:
         line["anneal"] = leg_anneal(tn, torch, dev, flush, stream, gold)
+    if "samples" in legs:
+        line["samples"] = leg_samples(tn, torch, dev, flush, stream, gold)
 
     if not args.no_cpu_baseline and world == 1:
         full, sample, threads, full_1 = oracle_sample()

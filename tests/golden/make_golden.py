@@ -5,6 +5,7 @@ GPU library.  The 53-qubit slices read which wires are sliced, and the order
 to contract in, from ``grid53_plan.txt`` (data written by dump_plan.py).
 
     python tests/golden/make_golden.py grid30      # 2^30 state, ~16 GiB RAM
+    python tests/golden/make_golden.py grid12      # 3x4 grid, all 4096 amplitudes
     python tests/golden/make_golden.py batch [i0 i1]
     python tests/golden/make_golden.py grid53 [slice ...]   # ~30 min per slice
 
@@ -52,6 +53,13 @@ def grid30():
     write(os.path.join(HERE, "grid5x6_14c_amps.txt"), c.label, amps, time.time() - t)
 
 
+def grid12():
+    c, q = rqcgen.grid_12q()
+    t = time.time()
+    amps = oracle.amplitudes(c, q)
+    write(os.path.join(HERE, "grid3x4_8c_amps.txt"), c.label, amps, time.time() - t)
+
+
 def batch(i0=0, i1=256):
     items = rqcgen.uneven_batch()
     for i in range(i0, i1):
@@ -84,6 +92,8 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "grid30"
     if what == "grid30":
         grid30()
+    elif what == "grid12":
+        grid12()
     elif what == "batch":
         a = [int(x) for x in sys.argv[2:4]] or [0, 256]
         batch(*a)

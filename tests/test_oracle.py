@@ -219,3 +219,13 @@ def test_projector_acts_right_after_its_gate():
 
 def test_slice_bits_lsb_first():
     assert oracle.slice_projectors([(0, 5), (1, 6), (4, 9)], 6) == [(0, 5, 0), (1, 6, 1), (4, 9, 1)]
+
+
+def test_stored_grid12_amplitudes_are_the_oracles():
+    # the stored 12-qubit amplitudes (read by the benchmark's latency leg)
+    # are the oracle's, and form a whole normalised state
+    rows = [l.split() for l in open(os.path.join(GOLD, "grid3x4_8c_amps.txt")) if not l.startswith("#")]
+    stored = np.array([complex(float(r[1]), float(r[2])) for r in rows])
+    c, q = rqcgen.grid_12q()
+    assert np.allclose(stored, oracle.amplitudes(c, q), rtol=0, atol=1e-15)
+    assert abs(np.vdot(stored, stored).real - 1.0) < 1e-12
