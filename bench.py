@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec"],
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
+    ap.add_argument("--pair", action="store_true", help="--case gemm_tc on CTA pairs (256-row tiles)")
     ap.add_argument("--padded", action="store_true", help="--case gather with the padded 2-D index")
     ap.add_argument("--lm", type=int, default=14)
     ap.add_argument("--ln", type=int, default=14)
@@ -88,7 +89,8 @@ def kernel_case(args):
             B = (B.float() * 64 * (K ** 0.5)).to(torch.float8_e4m3fn)
             dt = tn.FP8
         run = lambda: tn.gemm(dt, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
-                              scale_exp=-12 if args.fp8 else 0, kernel=3)
+                              scale_exp=-12 if args.fp8 else 0,
+                              kernel=tn.GEMM_TC_PAIR if args.pair else 3)
         work, unit = 8.0 * M * N * K * b, "TFLOP/s"
     elif args.case == "gather":
         # sparse-state contraction of many tensor pairs: 2048 A chunks of

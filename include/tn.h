@@ -428,7 +428,10 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  *   dtype TN_F16/TN_BF16: A, B, C complex-half (B is padded on the device to
  *   the real 2K x 2N form of Eq. 6 for the tensor-core variant); FP32
  *   accumulation; C is multiplied by 2^scale_exp before rounding.
- * kernel: -1 = automatic; otherwise a variant index (tests).
+ * kernel: -1 = automatic; otherwise a variant index (tests): 0 complex64
+ *   rows, 1 complex64 tiled, 2 complex-half rows, 3 complex-half tensor
+ *   cores, 4 complex-half tensor cores on CTA pairs (clusters of 2 SMs,
+ *   256-row tiles; shapes with M >= 256, N >= 128, K >= 32, else as 3).
  * out_max: optional device float, receives max |component| of the stored C.
  */
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,

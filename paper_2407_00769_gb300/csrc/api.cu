@@ -1367,6 +1367,8 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
         sr.fixed_exp = scale_exp;
         sr.out_max = out_max;
         int kk = kernel;
+        const bool pair = kk == 4;            // tensor cores on CTA pairs
+        if (pair) kk = GK_LP_TC;
         if (kk < 0) kk = tc_gemm_supported(lk, ln) ? GK_LP_TC : GK_LP_ROWS;
         if (kk == GK_LP_ROWS) {
             e = launch_gemm_rows_lp(dtype, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
@@ -1386,6 +1388,7 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                 d.batch_a = batch_a ? 1 : 0;
                 d.batch_b = batch_b ? 1 : 0;
                 d.np = np;
+                d.pair = pair ? 1 : 0;
                 const size_t pb = tc_split_bytes(lm, ln, lk, batch);
                 if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
                 if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);

@@ -110,6 +110,8 @@ struct TcGemmDesc {
     // index -> bit out_dpos[i]; bits 0..2 unchanged, N >= 8, K <= 2^15)
     int out_rank = 0;
     int8_t out_dpos[40] = {};
+    // 1: run on CTA pairs (256-row tiles, cluster of 2) where the shape allows
+    int pair = 0;
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs
@@ -147,6 +149,7 @@ inline int tc_tile_gm(int tile) { return kTcGm[((tile >> 4) & 15) < 6 ? ((tile >
 // really uses for N = 2^ln (tile 0 and explicit codes may coincide).
 int tc_effective_tile(int tile, int ln);
 bool tc_gemm_supported(int lk, int ln);
+bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);
 int tc_num_sms();

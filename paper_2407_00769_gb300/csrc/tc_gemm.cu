@@ -62,30 +62,65 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// CL: cluster-scope acquire (barriers that CTA-pair peers arrive on)
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
+    if constexpr (CL)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
     return ok != 0;
 }
 
 // bounded wait: returns false (and raises the CTA abort flag) on timeout or
 // when another role already aborted
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait<CL>(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait<CL>(bar, parity)) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitLimitNs) {
             *abort_flag = 1;
             return false;
         }
     }
+}
+
+// ---- CTA pairs (cluster of 2): one tcgen05.mma with M = 256 spans both SMs
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the same shared variable in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
@@ -97,6 +132,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// CTA pair: the tile lands in this CTA's shared memory, its byte count on the
+// leader CTA's barrier (bar_cluster: a shared::cluster address)
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cluster,
+                                                 int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -104,19 +150,48 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// completion of this thread's earlier tcgen05 ops arrives on `bar`; a CTA
+// pair arrives on the barrier at the same offset in both CTAs
+template <bool PAIR = false>
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+    if constexpr (PAIR)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+            " [%0], %1;" ::"r"(smem_u32(bar)),
+            "h"((uint16_t)3)
+            : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+}
+
+// the same, on this CTA's barrier only
+__device__ __forceinline__ void tc_commit_pair_local(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
 }
 
-template <bool F8>
+template <bool F8, bool PAIR>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                        uint32_t idesc, uint32_t accumulate) {
-    if constexpr (F8)
+    if constexpr (F8 && PAIR)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else if constexpr (F8)
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else if constexpr (PAIR)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     else
@@ -229,45 +304,61 @@ __device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t 
     nt = (int)(in / gm);
 }
 
-template <int BN, int BKB, int STAGES>
+// BROWS: rows of the B' tile this CTA holds (BN, or BN / 2 in a CTA pair)
+template <int BROWS, int BKB, int STAGES>
 struct TcSmem {
     static constexpr int a_bytes = 128 * BKB;
-    static constexpr int b_bytes = BN * BKB;
+    static constexpr int b_bytes = BROWS * BKB;
     static constexpr int stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
     static constexpr int ring = STAGES * stage_bytes;
-    static constexpr int bars = (2 * STAGES + 4) * 8;
+    static constexpr int bars = (2 * STAGES + 5) * 8;
     static constexpr int total = 1024 + ring + bars + 16;   // + alignment slack
 };
 
 // BKB: bytes of a K chunk per row (32, 64 or 128); F8: E4M3 operands.
-template <int BN, int BKB, int STAGES, bool F8>
+// PAIR: the kernel runs as clusters of 2 CTAs on 2 SMs; a pair computes a
+// 256 x BN tile with one tcgen05.mma (M = 256, cta_group::2) issued by the
+// leader (rank 0): each CTA loads its 128 rows of A and its BN/2 rows of B'
+// and holds its 128 rows of the accumulator in its own TMEM, so each SM
+// streams half the B' bytes of a 1-CTA tile through shared memory.
+template <int BN, int BKB, int STAGES, bool F8, bool PAIR>
 __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const TcArgs args) {
-    using S = TcSmem<BN, BKB, STAGES>;
+    using S = TcSmem<PAIR ? BN / 2 : BN, BKB, STAGES>;
     constexpr int BK = F8 ? BKB : BKB / 2;             // K chunk in operand elements
+    constexpr int TM = PAIR ? 256 : 128;               // rows of a tile
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + S::ring);
     uint64_t *empty = full + STAGES;
     uint64_t *accf = empty + STAGES;
     uint64_t *acce = accf + 2;
-    volatile uint32_t *tmem_slot = (volatile uint32_t *)(acce + 2);
+    uint64_t *drain = acce + 2;
+    volatile uint32_t *tmem_slot = (volatile uint32_t *)(drain + 1);
     __shared__ int abort_flag;
+    __shared__ int peer_abort;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     constexpr uint32_t tmem_cols = (2 * BN < 32) ? 32 : 2 * BN;
+    const uint32_t rank = PAIR ? cluster_rank() : 0;
+    const bool leader = rank == 0;
+    // tile walker: the CTA, or the CTA pair
+    const int64_t walker = PAIR ? blockIdx.x >> 1 : blockIdx.x;
+    const int64_t walkers = PAIR ? gridDim.x >> 1 : gridDim.x;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
+        peer_abort = 0;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
-            mbar_init(&acce[i], 128);
+            mbar_init(&acce[i], PAIR ? 256 : 128);   // pair: both CTAs' epilogue threads
         }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -276,14 +367,23 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32((const void *)tmem_slot)),
-                     "r"(tmem_cols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32((const void *)tmem_slot)),
+                         "r"(tmem_cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32((const void *)tmem_slot)),
+                         "r"(tmem_cols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();     // the peer's barriers exist before any arrive on them
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -295,17 +395,29 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             bool ok = true;
             int8_t armed[STAGES];   // phase parity of the last load issued per stage
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
-            for (int64_t t = blockIdx.x; t < args.tiles && ok; t += gridDim.x) {
+            const uint32_t full_leader = PAIR ? mapa_rank(&full[0], 0) : 0;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
                 int64_t b, mt;
                 int nt;
                 tile_coords(args, t, b, mt, nt);
                 const int kbase = (int)(t / args.tiles_per_part) * args.nk * BK;
                 for (int kc = 0; kc < args.nk; ++kc) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
+                    if (!mbar_wait<PAIR>(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
                     uint8_t *sa = smem + stage * S::stage_bytes;
                     uint8_t *sb = sa + S::a_bytes;
-                    mbar_expect_tx(&full[stage], S::a_bytes + S::b_bytes);
                     const int zA = args.za ? args.za[b] : (args.batch_a ? (int)b : 0);
+                    if constexpr (PAIR) {
+                        // the leader's barrier counts both CTAs' bytes
+                        if (leader) mbar_expect_tx(&full[stage], 2 * (S::a_bytes + S::b_bytes));
+                        const int zB = args.batch_b ? (int)b : 0;
+                        const uint32_t fb = full_leader + (uint32_t)(stage * 8);
+                        tma_load_3d_pair(sa, &tmA, fb, kbase + kc * BK, (int)(mt * 256 + rank * 128), zA);
+                        tma_load_3d_pair(sb, &tmB, fb, kbase + kc * BK, nt * BN + (int)rank * (BN / 2), zB);
+                        armed[stage] = (int8_t)phase;
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                        continue;
+                    }
+                    mbar_expect_tx(&full[stage], S::a_bytes + S::b_bytes);
                     tma_load_3d(sa, &tmA, &full[stage], kbase + kc * BK, (int)(mt * 128), zA);
                     if (args.gather_r) {
                         // B_P: one whole B' chunk (np_chunk rows) per r of this tile
@@ -323,9 +435,11 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
-            if (!ok) {
+            if (!ok && (!PAIR || leader)) {
                 // drain: only the last STAGES loads can still be in flight;
                 // wait (bounded) until each has landed before shared memory goes
+                // (a pair's peer sees its loads land on the leader's barriers
+                // only: it waits out the teardown delay instead)
                 for (int s = 0; s < STAGES; ++s) {
                     if (armed[s] < 0) continue;
                     const uint64_t t0 = globaltimer();
@@ -337,7 +451,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         }
     } else if (warp == 1) {
         // --------------------------------------------------- MMA issue --
-        if (lane == 0) {
+        if (lane == 0 && (!PAIR || leader)) {
             uint32_t idesc = 0;
             idesc |= 1u << 4;                                  // D = F32
             // kind::f16: 0 F16, 1 BF16; kind::f8f6f4: 0 E4M3
@@ -345,18 +459,19 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             idesc |= fmt << 7;                                 // A format
             idesc |= fmt << 10;                                // B format
             idesc |= (uint32_t)(BN >> 3) << 17;                // N
-            idesc |= (uint32_t)(128 >> 4) << 24;               // M
+            idesc |= (uint32_t)(TM >> 4) << 24;                // M
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < args.tiles && ok; t += gridDim.x) {
-                if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
+            bool issued = false;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
+                if (!mbar_wait<PAIR>(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
                 for (int kc = 0; kc < args.nk; ++kc) {
-                    if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                    if (!mbar_wait<PAIR>(&full[stage], phase, &abort_flag)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
                     const uint32_t b_addr = a_addr + S::a_bytes;
@@ -364,14 +479,24 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                     for (int kk = 0; kk < BKB / 32; ++kk) {     // 32 bytes of K per MMA
                         const uint64_t ad = smem_desc<BKB>(a_addr + kk * 32);
                         const uint64_t bd = smem_desc<BKB>(b_addr + kk * 32);
-                        tc_mma<F8>(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        tc_mma<F8, PAIR>(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                     }
-                    tc_commit(&empty[stage]);
+                    issued = true;
+                    tc_commit<PAIR>(&empty[stage]);
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
-                tc_commit(&accf[acc]);
+                tc_commit<PAIR>(&accf[acc]);
                 if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+            if (!ok && issued) {
+                // aborted: MMAs issued may still run; let them finish
+                // (bounded) before TMEM and shared memory are released
+                if constexpr (PAIR) tc_commit_pair_local(drain);
+                else tc_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                }
             }
         }
         __syncwarp();
@@ -401,13 +526,14 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         float mx = 0.f;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t t = blockIdx.x; t < args.tiles; t += gridDim.x) {
+        const uint32_t acce_leader = PAIR ? mapa_rank(&acce[0], 0) : 0;
+        for (int64_t t = walker; t < args.tiles; t += walkers) {
             int64_t b, mt;
             int nt;
             tile_coords(args, t, b, mt, nt);
-            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
+            if (!mbar_wait<PAIR>(&accf[acc], acc_phase, &abort_flag)) break;
             tc_fence_after();
-            const int64_t m = mt * 128 + row;
+            const int64_t m = mt * TM + rank * 128 + row;
             const int col0 = nt * BN;                          // real column of this tile
             const int64_t cb = args.zc ? (int64_t)args.zc[b] : b;   // output chunk (< 0: skip)
             // fused permutation: destination = row part | column part | low 3 bits
@@ -505,7 +631,8 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
                 }
             }
             tc_fence_before();
-            mbar_arrive(&acce[acc]);
+            if constexpr (PAIR) mbar_arrive_cluster(acce_leader + (uint32_t)(acc * 8));
+            else mbar_arrive(&acce[acc]);
             if (++acc == 2) { acc = 0; acc_phase ^= 1; }
         }
         mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
@@ -522,12 +649,33 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
 
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) {
+        // Neither CTA leaves while the other may still use its shared memory
+        // or TMEM.  After an abort, loads the peer issued may still be landing
+        // here (their completion counts on the leader's barriers only): wait
+        // a bounded 2 ms before either CTA releases anything.
+        if (threadIdx.x == 0 && abort_flag)
+            asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(mapa_rank(&peer_abort, rank ^ 1)), "r"(1)
+                         : "memory");
+        cluster_sync();
+        if (abort_flag || peer_abort) {
+            const uint64_t t0 = globaltimer();
+            while (globaltimer() - t0 < 2000000ull) {
+            }
+        }
+        cluster_sync();
+    }
     if (abort_flag && threadIdx.x == 0 && args.err) atomicOr(args.err, 1);
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(tmem_cols)
-                     : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(tmem_cols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(tmem_cols)
+                         : "memory");
     }
 }
 
@@ -572,19 +720,58 @@ bool encode_3d(CUtensorMap *m, int dtype, int esz, const void *base, uint64_t in
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int BKB>
+template <int BN, int BKB, bool PAIR = false>
 struct TcCfg {
-    static constexpr int stage_bytes = (128 * BKB + BN * BKB + 1023) / 1024 * 1024;
+    static constexpr int brows = PAIR ? BN / 2 : BN;
+    static constexpr int stage_bytes = (128 * BKB + brows * BKB + 1023) / 1024 * 1024;
     static constexpr int stages0 = (196 * 1024) / stage_bytes;
     static constexpr int STAGES = stages0 > 12 ? 12 : (stages0 < 2 ? 2 : stages0);
 };
 
-template <int BN, int BKB, bool F8>
+template <int BN, int BKB, bool F8, bool PAIR = false>
 cudaError_t set_attr() {
-    constexpr int ST = TcCfg<BN, BKB>::STAGES;
-    using S = TcSmem<BN, BKB, ST>;
-    return cudaFuncSetAttribute(gemm_tc_kernel<BN, BKB, ST, F8>,
+    constexpr int ST = TcCfg<BN, BKB, PAIR>::STAGES;
+    using S = TcSmem<TcCfg<BN, BKB, PAIR>::brows, BKB, ST>;
+    return cudaFuncSetAttribute(gemm_tc_kernel<BN, BKB, ST, F8, PAIR>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, S::total);
+}
+
+// CTA-pair kernel (BN = 256, 128-byte K chunks): launch configuration with a
+// cluster of 2, and how many pairs the GPU holds at once
+template <bool F8>
+cudaLaunchConfig_t pair_config(int64_t grid, cudaStream_t s, cudaLaunchAttribute *attr) {
+    constexpr int ST = TcCfg<256, 128, true>::STAGES;
+    using S = TcSmem<128, 128, ST>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = S::total;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int g_pair_clusters[2] = {0, 0};   // [F8]: resident CTA pairs (0: not known yet)
+
+template <bool F8>
+cudaError_t prepare_pair() {
+    constexpr int ST = TcCfg<256, 128, true>::STAGES;
+    cudaError_t e = set_attr<256, 128, F8, true>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config<F8>(2 * 76, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_tc_kernel<256, 128, ST, F8, true>, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = tc_num_sms() / 2;
+    }
+    g_pair_clusters[F8 ? 1 : 0] = n;
+    return cudaSuccess;
 }
 
 template <int BKB, bool F8>
@@ -601,10 +788,20 @@ template <int BN, int BKB, bool F8>
 cudaError_t run_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, cudaStream_t s) {
     constexpr int ST = TcCfg<BN, BKB>::STAGES;
     using S = TcSmem<BN, BKB, ST>;
-    auto kern = gemm_tc_kernel<BN, BKB, ST, F8>;
+    auto kern = gemm_tc_kernel<BN, BKB, ST, F8, false>;
     const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
     kern<<<(unsigned)grid, 192, S::total, s>>>(ma, mb, a);
     return cudaGetLastError();
+}
+
+template <bool F8>
+cudaError_t run_tc_pair(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, cudaStream_t s) {
+    constexpr int ST = TcCfg<256, 128, true>::STAGES;
+    const int pairs = g_pair_clusters[F8 ? 1 : 0] > 0 ? g_pair_clusters[F8 ? 1 : 0] : tc_num_sms() / 2;
+    const int64_t grid = 2 * std::min<int64_t>(a.tiles, pairs);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config<F8>(grid, s, attr);
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<256, 128, ST, F8, true>, ma, mb, a);
 }
 
 template <int BKB, bool F8>
@@ -670,11 +867,19 @@ cudaError_t tc_prepare() {
     if (e == cudaSuccess) e = set_attr_bn<64, false>();
     if (e == cudaSuccess) e = set_attr_bn<128, false>();
     if (e == cudaSuccess) e = set_attr_bn<128, true>();
+    if (e == cudaSuccess) e = prepare_pair<false>();
     if (e == cudaSuccess && dev < 31) done_mask |= 1 << dev;
     return e;
 }
 
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
+
+// A step runs on CTA pairs when asked and when its tiles are the pair
+// kernel's: FP16/BF16, N tile 256 real columns, 128-byte K chunks (K >= 32
+// complex), M a multiple of 256.
+bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn) {
+    return want && !fp8 && bn == 256 && (2 << ln) >= 256 && lk >= 5 && lm >= 8;
+}
 bool tc_gemm_supported_fp8(int lk, int ln) { return lk >= 6 && lk <= 24 && ln <= 24; }
 
 // K parts of one tensor-core GEMM.  Each part accumulates at most
@@ -719,6 +924,9 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         bn = (d.bn < bn || d.gather_r > 0) ? d.bn : bn;   // B_P tiles span several chunks
     }
     const int64_t M = (int64_t)1 << d.lm;
+    const bool gathered = d.za || d.zb || d.zc;
+    // CTA pairs: 256 x 256 tiles of FP16/BF16 with 128-byte K chunks
+    const bool pair = tc_pair_eligible(d.pair, d.fp8, d.lm, d.ln, d.lk, bn) && !gathered && d.gather_r == 0;
     CUtensorMap ma, mb;
     const int64_t depth_a = d.depth_a > 0 ? d.depth_a : (d.batch_a ? d.batch : 1);
     const int64_t depth_b = d.depth_b > 0 ? d.depth_b : (d.batch_b ? d.batch : 1);
@@ -726,19 +934,18 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         return cudaErrorInvalidValue;
     if (d.gather_r > 0 && (bn % d.np != 0 || bn / d.np != d.gather_r)) return cudaErrorInvalidValue;
     if (!encode_3d(&mb, d.dtype, esz, d.Bp, (uint64_t)kreal, (uint64_t)d.np, (uint64_t)depth_b, bk,
-                   d.gather_r > 0 ? d.np : bn))
+                   d.gather_r > 0 ? d.np : (pair ? bn / 2 : bn)))
         return cudaErrorInvalidValue;
     TcArgs a;
     a.C = d.C;
     a.M = M;
-    a.n_mt = (M + 127) / 128;
+    a.n_mt = pair ? M / 256 : (M + 127) / 128;
     a.n_nt = d.gather_r > 0 ? ((int64_t)d.m_r * d.np + bn - 1) / bn : d.np / bn;
     a.batch = d.batch;
     a.tiles = a.n_mt * a.n_nt * d.batch;
     a.N = 1 << d.ln;
     a.lk = d.lk;
     a.nk = kreal / bk;
-    const bool gathered = d.za || d.zb || d.zc;
     if (gathered && d.lk > kSplitLog2K) return cudaErrorInvalidValue;   // one K part only
     if (d.out_rank > 0 && d.lk > kSplitLog2K) return cudaErrorInvalidValue;
     // a permuted C is written by this kernel's epilogue, so no K parts
@@ -775,10 +982,13 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         // bytes at gm^2 = SMs * BN / 128 (power of two at or below).
         a.gm = default_gm(bn);
     }
+    if (pair) a.gm = std::max(1, a.gm / 2);   // gm counts 128-row m tiles
     a.sr = sr;
     a.err = d_err;
     cudaError_t e;
-    if (d.fp8) {
+    if (pair) {
+        e = run_tc_pair<false>(ma, mb, a, s);
+    } else if (d.fp8) {
         e = run_tc_bn<128, true>(bn, ma, mb, a, s);
     } else {
         switch (bk) {

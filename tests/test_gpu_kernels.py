@@ -180,6 +180,39 @@ def test_gemm_f16_rows(M, N, K):
     _lp_case(tn.F16, M, N, K, 2, 2)
 
 
+# CTA pairs (cluster of 2, one M = 256 tcgen05.mma over both SMs): one tile,
+# several m and n tiles, more pair tiles than the GPU holds pairs (each pair
+# walks several tiles through both accumulator buffers), K rings that wrap,
+# and shapes the pair kernel does not take (run by the 1-CTA kernel)
+PAIR_SHAPES = [(256, 128, 32), (512, 256, 512), (1024, 128, 64), (32768, 128, 64), (4096, 256, 2048),
+               (128, 128, 64), (256, 64, 64), (256, 128, 16)]
+
+
+@pytest.mark.parametrize("M,N,K", PAIR_SHAPES)
+def test_gemm_f16_tensor_cores_cta_pairs(M, N, K):
+    _lp_case(tn.F16, M, N, K, 1, tn.GEMM_TC_PAIR)
+
+
+@pytest.mark.parametrize("ba,bb", [(True, True), (True, False), (False, True)])
+def test_gemm_tensor_cores_cta_pairs_batched(ba, bb):
+    _lp_case(tn.F16, 512, 128, 64, 3, tn.GEMM_TC_PAIR, ba, bb)
+    _lp_case(tn.BF16, 256, 256, 128, 2, tn.GEMM_TC_PAIR, ba, bb)
+
+
+def test_gemm_tensor_cores_cta_pairs_long_k():
+    # K = 2^16 complex: split into K parts (FP32 partials, FP64 reduction)
+    M, N, K = 256, 128, 1 << 16
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a = torch.randn(1, M, K, 2, generator=g, device="cuda").half()
+    b = (torch.randn(1, K, N, 2, generator=g, device="cuda") / K ** 0.5).half()
+    c = torch.zeros(1, M, N, 2, dtype=torch.float16, device="cuda")
+    tn.gemm(tn.F16, a, b, c, M, N, K, scale_exp=0, kernel=tn.GEMM_TC_PAIR)
+    want = torch.matmul(torch.view_as_complex(a.double())[0], torch.view_as_complex(b.double())[0])
+    got = torch.view_as_complex(c.double())[0]
+    rel = (torch.linalg.norm(got - want) / torch.linalg.norm(want)).item()
+    assert rel < 3e-4, rel
+
+
 def _read_example():
     vals = {}
     for line in open(os.path.join(GOLD, "complex_half_example.txt")):
