@@ -244,6 +244,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.np = std::max(16, 2 << g.ln);
                     d.bn = tc_tile_bn(g.tile);
                     d.gm = tc_tile_gm(g.tile);
+                    d.pair = (g.tile & kTcPairTile) ? 1 : 0;
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
                     d.fp8 = g.fp8;
@@ -279,7 +280,11 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
 }
 
 // Legal (kernel, tile) configurations of a GEMM op.
-std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
+// Kernel and tile candidates of a GEMM step.  pair_variants: CTA-pair tiles
+// as candidates of their own (timed by the exhaustive tuner); otherwise the
+// step's own choice (its tile's pair bit) carries over to every candidate
+// with a 256-column N tile (the cost model does not tell the two apart).
+std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g, bool pair_variants) {
     std::vector<std::pair<int, int>> c;
     if (g.kernel == GK_C64_ROWS || g.kernel == GK_C64_TILED) {
         c.push_back({GK_C64_ROWS, 0});
@@ -300,7 +305,7 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
                 if (kTcGm[code] <= 2 * n_mt) gm_codes.push_back(code);
         }
         if (gm_codes.empty()) gm_codes.push_back(0);
-        c.push_back({GK_LP_TC, 0});   // the fixed heuristic's own choice
+        std::vector<int> codes = {0};   // 0: the fixed heuristic's N tile and raster group
         std::vector<int> seen = {tc_effective_tile(0, g.ln)};
         for (int b : bn_codes)
             for (int m : gm_codes) {
@@ -308,8 +313,22 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
                 const int eff = tc_effective_tile(code, g.ln);
                 if (code == 0 || std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
                 seen.push_back(eff);
-                c.push_back({GK_LP_TC, code});
+                codes.push_back(code);
             }
+        const bool gathered = g.idx_a >= 0 || g.idx_b >= 0;
+        auto pair_ok = [&](int code) {
+            const int bn = tc_tile_bn(tc_effective_tile(code, g.ln));
+            return !gathered && tc_pair_eligible(1, g.fp8, g.lm, g.ln, g.lk, bn);
+        };
+        const bool own_pair = (g.tile & kTcPairTile) != 0;
+        for (int code : codes) {
+            if (pair_variants) {
+                c.push_back({GK_LP_TC, code});
+                if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
+            } else {
+                c.push_back({GK_LP_TC, own_pair && pair_ok(code) ? code | kTcPairTile : code});
+            }
+        }
     }
     return c;
 }
@@ -399,7 +418,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
                 GemmOp &g = op.gemm;
                 double best = 1e30;
                 std::pair<int, int> pick{g.kernel, g.tile};
-                for (const auto &cand : gemm_candidates(g)) {
+                for (const auto &cand : gemm_candidates(g, true)) {
                     Op trial = op;
                     trial.gemm.kernel = cand.first;
                     trial.gemm.tile = cand.second;
@@ -493,7 +512,7 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         const Op &op = S.ops[i];
         if (op.kind != OP_GEMM) continue;
         const GemmOp &g = op.gemm;
-        for (const auto &cand : gemm_candidates(g)) {
+        for (const auto &cand : gemm_candidates(g, false)) {
             recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second,
                                           g.step, 0, 0});
             who.push_back({i, cand});

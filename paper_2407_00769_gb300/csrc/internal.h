@@ -71,6 +71,13 @@ enum GemmKernel : int32_t {
     GK_LP_TC = 3,      // complex-half as real, tcgen05 + TMA, FP32 in TMEM
 };
 
+// Tensor-core tile code: bits 0-3 N-tile width code, bits 4-7 raster-group
+// code, bit 8 CTA pairs (256-row tiles on a cluster of 2 SMs).
+constexpr int kTcPairTile = 0x100;
+// whether a step of this shape runs on CTA pairs when asked (bn: the N tile
+// in real columns the launch uses)
+bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);
+
 struct LeafJob {          // one leaf to prepare (device-side struct)
     int64_t src;          // element offset into the leaf store (complex128)
     int64_t dst;          // byte offset into the workspace

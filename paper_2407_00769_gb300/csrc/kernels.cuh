@@ -149,7 +149,6 @@ inline int tc_tile_gm(int tile) { return kTcGm[((tile >> 4) & 15) < 6 ? ((tile >
 // really uses for N = 2^ln (tile 0 and explicit codes may coincide).
 int tc_effective_tile(int tile, int ln);
 bool tc_gemm_supported(int lk, int ln);
-bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);
 int tc_num_sms();

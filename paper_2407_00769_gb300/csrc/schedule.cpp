@@ -455,6 +455,8 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.meta_c = meta[c];
         op.gemm.step = s;
         op.gemm.kernel = kernel;
+        // the fixed heuristic's tile (1-CTA); CTA pairs are an autotuner
+        // candidate: they lose on some long-K steps
         op.gemm.tile = 0;
         op.gemm.ta = ta;
         op.gemm.tb = tb;
