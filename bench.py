@@ -468,7 +468,7 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
 def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
     """Uncorrelated bitstrings (Sec. 3.4.2): the 30-qubit circuit at n
     arbitrary bitstrings in one sample plan (tensors keep output legs dense
-    up to log2 n of them, rows per sample beyond).  The first 1024 bitstrings
+    up to log2 n of them, rows per sample beyond; 64 slices per pass).  The first 1024 bitstrings
     are the workload's correlated subspace, checked against its stored FP64
     amplitudes; the rest are uniform random.  Reported per bitstring."""
     import numpy as np
@@ -481,7 +481,8 @@ def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
     for t, qq in enumerate(q.open_qubits):
         samples[:1024, qq] = (j >> t) & 1
     t0 = time.time()
-    plan = tn.Plan.from_samples(c, samples, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS)
+    plan = tn.Plan.from_samples(c, samples, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                                slice_batch_log2=6)
     plan_s = time.time() - t0
     info = plan.info()
     amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
@@ -489,7 +490,7 @@ def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
         plan.contract(out=amps)
     ms = _timed(lambda: plan.contract(out=amps), stream, flush, reps=3)
     flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
-    out = {"n_bitstrings": n, "plan_s": plan_s, "job_flops": flops, "ms": ms,
+    out = {"n_bitstrings": n, "slice_batch_log2": 6, "plan_s": plan_s, "job_flops": flops, "ms": ms,
            "tflops": flops / (ms * 1e-3) / 1e12, "us_per_bitstring": ms * 1e3 / n,
            "max_log2_elems": info["max_log2_elems"], "workspace_gib": info["workspace_bytes"] / 2**30}
     if gold is not None:

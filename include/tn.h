@@ -184,11 +184,13 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
  * to one row per sample: each operand still holding dense outputs is read at
  * the row the sample's bits select, through index arrays built here (the
  * sparse state of paper Sec. 3.4.2, on the gathering GEMMs).  The path is
- * planned on the network with its outputs fixed.  tn_contract fills 2^k
+ * planned twice, on the network with its output legs as legs and with them
+ * fixed, and the cheaper resulting schedule is kept.  tn_contract fills 2^k
  * amplitudes, entry s for bitstring s (entries past n_samples repeat the
- * last bitstring); slicing and dtypes as for tn_plan, slice_batch_log2 = 0.
- * Errors: TN_EINVAL (NULL, n_samples outside 1..2^20, a bit other than 0/1,
- * slice_batch_log2 != 0), as tn_plan otherwise.
+ * last bitstring); slicing, slice batching and dtypes as for tn_plan
+ * (slices run together x 2^k must stay within 2^24 rows).
+ * Errors: TN_EINVAL (NULL, n_samples outside 1..2^20, k > 24, a bit other
+ * than 0/1), as tn_plan otherwise.
  */
 int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n_samples,
                     const tn_plan_opts *opts, tn_plan_t **out);
@@ -512,6 +514,10 @@ int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int
  * Synchronizes `stream`; allocates a few KiB of device memory.
  */
 int tn_selftest_wait_timeout(void *stream);
+/* The same on the CTA-pair kernel (one 256 x 256 tile on a cluster of 2):
+ * both CTAs' waits run out, the pair meets at its teardown barrier and
+ * frees its tensor memory.  Same return codes. */
+int tn_selftest_wait_timeout_pair(void *stream);
 
 const char *tn_strerror(int code);
 const char *tn_last_error(void);

@@ -36,6 +36,7 @@ EXPORTED = [
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
     "tn_profile", "tn_profile_read", "tn_sample_noalloc", "tn_selftest_wait_timeout",
+    "tn_selftest_wait_timeout_pair",
     "tn_plan_set_graph", "tn_batch_create", "tn_batch_run", "tn_batch_destroy",
     "tn_plan_tune", "tn_tune_records",
     "tn_cost_model_create", "tn_cost_model_destroy", "tn_cost_model_params", "tn_cost_model_grad",
@@ -161,6 +162,7 @@ def lib():
         L.tn_metrics.argtypes = [vp, vp, i64, i32, vp, vp]
         L.tn_sample_noalloc.argtypes = [vp, i32, i32, vp, vp, vp]
         L.tn_selftest_wait_timeout.argtypes = [vp]
+        L.tn_selftest_wait_timeout_pair.argtypes = [vp]
         L.tn_plan_set_graph.argtypes = [vp, ctypes.c_int]
         L.tn_plan_tune.argtypes = [vp, vp]
         L.tn_plan_apply_tuning.argtypes = [vp, ctypes.POINTER(TuneRecord), i32]

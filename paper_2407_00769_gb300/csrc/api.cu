@@ -687,7 +687,6 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
     int k = 0;
     while ((1 << k) < n_samples) ++k;
     if (k > 24) return fail(TN_EINVAL, "too many samples");
-    if (o.slice_batch_log2 != 0) return fail(TN_EINVAL, "sample plans run their slices one at a time (slice_batch_log2 = 0)");
     try {
         std::vector<uint64_t> bits((size_t)1 << k);
         for (int64_t s = 0; s < ((int64_t)1 << k); ++s) {
@@ -1525,9 +1524,10 @@ int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int
     return TN_OK;
 }
 
-int tn_selftest_wait_timeout(void *stream) {
+static int selftest_wait_timeout(void *stream, bool pair) {
     cudaStream_t s = (cudaStream_t)stream;
-    const int lm = 7, ln = 3, lk = 3, np = 16;
+    // one 128-row tile; pair: one 256 x 256 tile with 128-byte K chunks
+    const int lm = pair ? 8 : 7, ln = pair ? 7 : 3, lk = pair ? 5 : 3, np = pair ? 256 : 16;
     void *A = nullptr, *Bp = nullptr, *C = nullptr;
     int32_t *err = nullptr;
     cudaError_t e = cudaMalloc(&A, (size_t)(4 << (lm + lk)));
@@ -1544,6 +1544,7 @@ int tn_selftest_wait_timeout(void *stream) {
         d.batch = 1; d.batch_a = 0; d.batch_b = 0;
         d.np = np;
         d.withhold = 1;
+        d.pair = pair ? 1 : 0;
         ScaleRef sr{};
         e = launch_gemm_tc(d, sr, err, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1557,6 +1558,9 @@ int tn_selftest_wait_timeout(void *stream) {
     if (herr) return fail(TN_ETIMEOUT, "bounded wait gave up as intended; the kernel returned");
     return fail(TN_OK, "no timeout was reported");
 }
+
+int tn_selftest_wait_timeout(void *stream) { return selftest_wait_timeout(stream, false); }
+int tn_selftest_wait_timeout_pair(void *stream) { return selftest_wait_timeout(stream, true); }
 
 const char *tn_strerror(int code) {
     switch (code) {

@@ -295,6 +295,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         const bool gstep = spec && samp[c] && (role(ia) == R_GATHER || role(ib) == R_GATHER);
         std::vector<int> abat, bbat;
         int role_a = R_NONE, role_b = R_NONE;
+        int nsb = 0;     // slices run together: shared batch modes outside the sample index
         if (gstep) {
             role_a = role(ia);
             role_b = role(ib);
@@ -310,9 +311,22 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
                 }
                 return v;
             };
-            abat = bat_of(ia, role_a);
-            bbat = bat_of(ib, role_b);
-            bo = sord;
+            // slice-batch modes both operands hold stay batch modes, outermost
+            std::vector<int> sbs;
+            for (int e : LA)
+                if (shared.count(e) && batched(e) && !is_sample[e]) sbs.push_back(e);
+            nsb = (int)sbs.size();
+            abat = sbs;
+            bbat = sbs;
+            const std::vector<int> ga = bat_of(ia, role_a), gb = bat_of(ib, role_b);
+            abat.insert(abat.end(), ga.begin(), ga.end());
+            bbat.insert(bbat.end(), gb.begin(), gb.end());
+            if (nsb + spec->k > 24) {
+                err = "slices run together x samples exceed 2^24 rows";
+                return TN_EINVAL;
+            }
+            bo = sbs;
+            bo.insert(bo.end(), sord.begin(), sord.end());
             ko.clear();
             mo.clear();
             no.clear();
@@ -332,7 +346,7 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         StepRec rec{};
         rec.a = ia; rec.b = ib; rec.c = c;
         rec.lm = (int)mo.size(); rec.ln = (int)no.size(); rec.lk = gstep ? (int)ko.size() : nk;
-        rec.lb = gstep ? spec->k : nb;
+        rec.lb = gstep ? nsb + spec->k : nb;
         rec.invariant = inv[c];
 
         int64_t abuf = ia, bbuf = ib;
@@ -463,32 +477,38 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
         op.gemm.tc = tc;
         op.gemm.fp8 = fp8;
         if (gstep) {
-            // per operand: rows per sample (chunk s), gathered (chunk =
-            // the sample's bits on its output legs, outermost first), or
-            // broadcast
-            auto gather_table = [&](const std::vector<int> &bat) {
+            // per operand: rows per sample (chunk z), gathered (chunk = the
+            // slice-batch index, then the sample's bits on its output legs,
+            // outermost first), or broadcast over the samples (chunk = the
+            // slice-batch index; no table without one).  Output batch entry
+            // z = slice-batch index x 2^k + sample.
+            auto gather_table = [&](const std::vector<int> &gat) {
                 const int64_t off = (int64_t)S.gidx.size();
-                const int m = (int)bat.size();
-                for (uint64_t bits : spec->bits) {
-                    int32_t z = 0;
-                    for (int i = 0; i < m; ++i)
-                        z |= (int32_t)((bits >> net.edges[bat[i]].qubit) & 1) << (m - 1 - i);
-                    S.gidx.push_back(z);
-                }
+                const int m = (int)gat.size();
+                for (int64_t zs = 0; zs < ((int64_t)1 << nsb); ++zs)
+                    for (uint64_t bits : spec->bits) {
+                        int64_t z = zs << m;
+                        for (int i = 0; i < m; ++i)
+                            z |= (int64_t)((bits >> net.edges[gat[i]].qubit) & 1) << (m - 1 - i);
+                        S.gidx.push_back((int32_t)z);
+                    }
                 return off;
             };
-            op.gemm.a_batched = role_a != R_NONE;
-            op.gemm.b_batched = role_b != R_NONE;
-            op.gemm.bcast_a = role_a == R_NONE;
-            op.gemm.bcast_b = role_b == R_NONE;
-            if (role_a == R_GATHER) {
-                op.gemm.idx_a = gather_table(abat);
-                op.gemm.gather_a_log2 = (int)abat.size();
-            }
-            if (role_b == R_GATHER) {
-                op.gemm.idx_b = gather_table(bbat);
-                op.gemm.gather_b_log2 = (int)bbat.size();
-            }
+            auto setup = [&](int r, const std::vector<int> &bat, int64_t &idx, int32_t &glog2,
+                             int32_t &is_batched, int32_t &bcast) {
+                is_batched = 1;
+                bcast = 0;
+                if (r == R_ROWS) return;
+                if (r == R_NONE && nsb == 0) {
+                    is_batched = 0;
+                    bcast = 1;
+                    return;
+                }
+                idx = gather_table(std::vector<int>(bat.begin() + nsb, bat.end()));
+                glog2 = (int)bat.size();
+            };
+            setup(role_a, abat, op.gemm.idx_a, op.gemm.gather_a_log2, op.gemm.a_batched, op.gemm.bcast_a);
+            setup(role_b, bbat, op.gemm.idx_b, op.gemm.gather_b_log2, op.gemm.b_batched, op.gemm.bcast_b);
         }
         ops.push_back(op);
         ++S.n_gemm_steps;

@@ -249,6 +249,15 @@ def test_bounded_wait_times_out_and_context_survives():
     _lp_case(tn.F16, 256, 16, 32, 1, 3)
 
 
+def test_bounded_wait_times_out_on_cta_pairs_and_context_survives():
+    # the same on the CTA-pair kernel: both CTAs give up, meet at the
+    # teardown barrier, free TMEM and return; then pairs compute correctly
+    L = tn.lib()
+    rc = L.tn_selftest_wait_timeout_pair(torch.cuda.current_stream().cuda_stream)
+    assert rc == tn.TN_ETIMEOUT, L.tn_last_error()
+    _lp_case(tn.F16, 512, 128, 64, 1, tn.GEMM_TC_PAIR)
+
+
 @pytest.mark.parametrize("M,N,K", [(128, 32, 1 << 22), (1024, 32, 1 << 18), (128, 256, 1 << 16),
                                    (65536, 16, 1 << 12)])
 def test_gemm_f16_tensor_cores_long_k(M, N, K):

@@ -25,12 +25,12 @@ def _sv_at(c, samples):
 
 
 @pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
-@pytest.mark.parametrize("n_samples,slices", [(10, 2), (64, 3), (1, 0), (1000, 2), (257, 4)])
-def test_sample_amplitudes_against_state_vector(dtype, n_samples, slices):
+@pytest.mark.parametrize("n_samples,slices,batch", [(10, 2, 0), (64, 3, 2), (1, 0, 0), (1000, 2, 1), (257, 4, 4), (33, 3, 3)])
+def test_sample_amplitudes_against_state_vector(dtype, n_samples, slices, batch):
     c, _ = rqcgen.small_grid(3, 4, 8, seed=3, n_open=4)
     rng = np.random.default_rng(n_samples + slices)
     samples = rng.integers(0, 2, size=(n_samples, c.n_qubits))
-    p = tn.Plan.from_samples(c, samples, dtype=dtype, n_slice_edges=slices)
+    p = tn.Plan.from_samples(c, samples, dtype=dtype, n_slice_edges=slices, slice_batch_log2=batch)
     got = p.contract().cpu().numpy()
     assert got.shape[0] == 1 << p.n_open and p.n_open == int(np.ceil(np.log2(max(n_samples, 1))))
     got = got[:n_samples]
@@ -50,7 +50,7 @@ def test_sample_amplitudes_30_qubits_full_size():
     samples[:, :] = np.asarray(q.fixed_bits, dtype=np.uint8)[None, :]
     for t, qq in enumerate(q.open_qubits):
         samples[:, qq] = (j >> t) & 1
-    p = tn.Plan.from_samples(c, samples, dtype=tn.F16, n_slice_edges=8, trials=4)
+    p = tn.Plan.from_samples(c, samples, dtype=tn.F16, n_slice_edges=8, trials=4, slice_batch_log2=4)
     got = p.contract().cpu().numpy()[:64]
     e = oracle.rel_l2(got, gold[j])
     print(f"30-qubit, 64 bitstrings, FP16: rel-L2 {e:.2e}")
