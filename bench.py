@@ -468,9 +468,10 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
 def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
     """Uncorrelated bitstrings (Sec. 3.4.2): the 30-qubit circuit at n
     arbitrary bitstrings in one sample plan (tensors keep output legs dense
-    up to log2 n of them, rows per sample beyond; 64 slices per pass).  The first 1024 bitstrings
-    are the workload's correlated subspace, checked against its stored FP64
-    amplitudes; the rest are uniform random.  Reported per bitstring."""
+    up to log2 n of them, rows per sample beyond; 64 slices per pass).  The
+    first 1024 bitstrings are the workload's correlated subspace, checked
+    against its stored FP64 amplitudes; the rest are uniform random.
+    Reported per bitstring."""
     import numpy as np
     import rqcgen
     c, q = rqcgen.grid_30q()
