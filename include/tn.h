@@ -109,6 +109,15 @@ typedef struct {
                                  take E4M3 operands (A and B' quantized with a
                                  power-of-two scale, FP32 accumulate, result in
                                  the plan's dtype); 0: never                    */
+    int32_t recompute_log2;   /* recomputation (Sec. 3.4.1): split this many
+                                 open output legs into sequential passes, each
+                                 computing its part of the amplitude vector
+                                 (concatenated, not summed); the planner picks
+                                 the legs that shrink the largest intermediate
+                                 most.  They become the highest slice-id bits:
+                                 the slices of one part are contiguous.  The
+                                 steps before the legs meet the path run once
+                                 per call.  0: off; correlated plans only     */
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *ctx);
@@ -136,6 +145,8 @@ typedef struct {
     int32_t n_permutes;           /* explicit permutations per slice             */
     int32_t dtype;
     int64_t leaf_bytes;           /* host->device bytes of the leaf tensors      */
+    int32_t n_recompute_edges;    /* open legs split by recomputation; they are
+                                     the last n of the n_slice_edges           */
 } tn_plan_stats;
 
 typedef struct {

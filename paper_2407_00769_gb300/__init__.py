@@ -80,6 +80,7 @@ class PlanOpts(ctypes.Structure):
                 ("tile_policy", ctypes.c_int32), ("small_log2", ctypes.c_int32),
                 ("no_tensor_cores", ctypes.c_int32),
                 ("fp8_min_log2_flops", ctypes.c_int32),
+                ("recompute_log2", ctypes.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -93,7 +94,7 @@ class PlanStats(ctypes.Structure):
                 ("flops_per_slice", ctypes.c_double), ("flops_invariant", ctypes.c_double),
                 ("bytes_per_slice", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
                 ("n_permutes", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("leaf_bytes", ctypes.c_int64)]
+                ("leaf_bytes", ctypes.c_int64), ("n_recompute_edges", ctypes.c_int32)]
 
 
 class ContractReport(ctypes.Structure):
@@ -277,7 +278,7 @@ class Plan:
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
                  no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
-                 _samples=None):
+                 recompute_log2: int = 0, _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         if _samples is None:
@@ -295,6 +296,7 @@ class Plan:
         opts.small_log2 = int(small_log2)
         opts.no_tensor_cores = 1 if no_tensor_cores else 0
         opts.fp8_min_log2_flops = int(fp8_min_log2_flops)
+        opts.recompute_log2 = int(recompute_log2)
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()

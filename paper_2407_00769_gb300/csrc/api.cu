@@ -267,11 +267,17 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                                   P->d_texp, op.quant.meta_src, op.quant.meta_dst, s);
             ++launches;
             break;
-        case OP_SUM:
+        case OP_SUM: {
+            // recomputation: this pass fills the part of the output its
+            // split legs' values (slice-id bits) select
+            uint64_t split_val = 0;
+            for (int i = 0; i < op.sum.n_split; ++i)
+                if ((slice_base >> op.sum.split_bit[i]) & 1) split_val |= 1ull << op.sum.split_t[i];
             e = launch_slice_sum(ws + op.sum.src, dtype, op.sum, amps, P->net.n_open, t_lo, t_hi,
-                                 overwrite, P->d_texp, P->d_stepcorr, (int)P->sched.steps.size(), s);
+                                 overwrite, P->d_texp, P->d_stepcorr, (int)P->sched.steps.size(), split_val, s);
             ++launches;
             break;
+        }
         default:
             return fail(TN_EINVAL, "unknown op");
     }
@@ -594,6 +600,7 @@ int check_opts(const tn_plan_opts &o) {
     if (o.tile_policy < 0 || o.tile_policy > 2) return fail(TN_EINVAL, "bad tile_policy");
     if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
     if (o.path_anneal_iters < 0) return fail(TN_EINVAL, "path_anneal_iters must be >= 0");
+    if (o.recompute_log2 < 0 || o.recompute_log2 > 8) return fail(TN_EINVAL, "recompute_log2 must be in 0..8");
     if (o.n_slice_edges < 0 && o.max_log2_elems <= 0)
         return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0");
     return TN_OK;
@@ -601,11 +608,28 @@ int check_opts(const tn_plan_opts &o) {
 
 // Path and slices on `plan_net` (the network the planner sees), refined by
 // annealing when asked; checks the cap and the slice batch.
-int plan_path(tn_plan_s *P, const Network &plan_net, std::string &err) {
+int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
     const tn_plan_opts &o = P->opts;
     const int n_target = o.n_slice_edges >= 0 ? o.n_slice_edges : -1;
     const int cap = o.max_log2_elems;
-    int rc = choose_slices(plan_net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
+    int rc;
+    // recomputation first: the open legs that shrink the unsliced path's
+    // largest intermediate most are split off, and the path and the summed
+    // slices are planned without them
+    std::vector<int> split;
+    Network split_net;
+    if (o.recompute_log2 > 0) {
+        Path p0;
+        std::vector<int> none;
+        rc = choose_slices(plan_net_in, o.path_seed, o.path_trials, 0, 0, p0, none, err);
+        if (rc != TN_OK) return rc;
+        rc = choose_recompute(plan_net_in, o.recompute_log2, p0, split, err);
+        if (rc != TN_OK) return rc;
+        split_net = plan_net_in;
+        fix_legs(split_net, split);
+    }
+    const Network &plan_net = o.recompute_log2 > 0 ? split_net : plan_net_in;
+    rc = choose_slices(plan_net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
     if (rc != TN_OK) return rc;
     if (o.path_anneal_iters > 0)
         // kappa: flops one element of HBM traffic is worth at the ridge
@@ -620,6 +644,12 @@ int plan_path(tn_plan_s *P, const Network &plan_net, std::string &err) {
     if (o.slice_batch_log2 > (int)P->sliced.size()) {
         err = "slice_batch_log2 exceeds the number of sliced edges";
         return TN_EINVAL;
+    }
+    if (o.recompute_log2 > 0) {
+        // the split legs after the summed slices: a pass's part of the
+        // output is fixed by its highest slice-id bits
+        P->sliced.insert(P->sliced.end(), split.begin(), split.end());
+        P->n_recompute = o.recompute_log2;
     }
     P->batch_log2 = o.slice_batch_log2;
     return TN_OK;
@@ -687,6 +717,7 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
     int k = 0;
     while ((1 << k) < n_samples) ++k;
     if (k > 24) return fail(TN_EINVAL, "too many samples");
+    if (o.recompute_log2 != 0) return fail(TN_EINVAL, "recompute_log2 applies to correlated plans only");
     try {
         std::vector<uint64_t> bits((size_t)1 << k);
         for (int64_t s = 0; s < ((int64_t)1 << k); ++s) {
@@ -793,6 +824,7 @@ int tn_plan_info(const tn_plan_t *P, tn_plan_stats *s) {
     s->n_permutes = P->sched.n_permutes;
     s->dtype = P->opts.dtype;
     s->leaf_bytes = (int64_t)P->leaf_store.size() * 16;
+    s->n_recompute_edges = P->n_recompute;
     return TN_OK;
 }
 
@@ -855,13 +887,18 @@ int enqueue_contract(tn_plan_s *P, int64_t slice_begin, int64_t slice_count, dou
     const int64_t bsize = (int64_t)1 << P->batch_log2;
     const int64_t first = slice_begin / bsize * bsize;
     const int64_t last = (slice_begin + slice_count - 1) / bsize * bsize;
+    // recomputation: passes fill disjoint parts of the output, so it is
+    // cleared once and every pass adds
+    const bool parts = P->n_recompute > 0;
+    if (parts && !accumulate)
+        TN_CUDA(cudaMemsetAsync(d_amps, 0, ((size_t)16) << P->net.n_open, s), "memset");
     for (int64_t base = first; base <= last; base += bsize) {
         if (lp && S.n_meta > S.n_meta_inv)
             TN_CUDA(cudaMemsetAsync(P->d_tmax + S.n_meta_inv, 0, (size_t)(S.n_meta - S.n_meta_inv) * 4, s),
                     "memset");
         const int t_lo = (int)std::max<int64_t>(0, slice_begin - base);
         const int t_hi = (int)std::min<int64_t>(bsize, slice_begin + slice_count - base);
-        const int overwrite = (!accumulate && base == first) ? 1 : 0;
+        const int overwrite = (!accumulate && !parts && base == first) ? 1 : 0;
         for (const Op &op : S.ops)
             if (op.phase == 1) {
                 rc = run_op(P, op, base, (double2 *)d_amps, t_lo, t_hi, overwrite, s, launches);

@@ -46,6 +46,8 @@ int build_network_open(const tn_circuit *c, const tn_query *q, int max_open, Net
 // Every open output leg fixed at 0: one planning view of an
 // uncorrelated-bitstring network.
 int fix_open_legs(Network &net);
+// The given legs fixed at 0 (a planning view with those legs split off).
+int fix_legs(Network &net, const std::vector<int> &edges);
 
 // ------------------------------------------------------------------- path --
 struct Path {
@@ -145,6 +147,10 @@ struct SumOp {
     int32_t batch_pos[16];// bit position (from LSB) of batched slice bit j
     int32_t meta;
     int32_t tf;           // storage of the final tensor: 0 complex64, 1 complex-half
+    // recomputation: open outputs split into passes (absent from the final
+    // tensor): output bit split_t[i] = slice-id bit split_bit[i]
+    int32_t n_split;
+    int32_t split_t[8], split_bit[8];
 };
 
 // Storage rule of complex-half plans: tensors of at most 2^kSmallLog2

@@ -986,17 +986,26 @@ cudaError_t launch_splitk_reduce(const float *partial, int split, void *C, int o
 // c * F[idx(j, t)] * 2^-E (FP64; one slice added at a time).  F is stored
 // complex64 or complex-half; c is the product of the per-step rounding
 // compensations of the complex-half plan (1 otherwise).
+// Recomputation: the op's split outputs are absent from F; thread j covers
+// the amplitude whose split bits are split_val and whose other bits, in
+// order, are j's bits.
 template <typename TF, int DT>
 __global__ void slice_sum_kernel(const TF *__restrict__ F, const SumOp op, double2 *amps,
                                  int n_open, int t_lo, int t_hi, int overwrite,
                                  const int32_t *texp, const double2 *__restrict__ stepcorr,
-                                 int n_steps) {
-    const int64_t n = (int64_t)1 << n_open;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int64_t base = 0;
-    for (int t = 0; t < n_open; ++t)
-        if ((j >> t) & 1) base |= (int64_t)1 << op.open_pos[t];
+                                 int n_steps, uint64_t split_mask, uint64_t split_val) {
+    const int64_t n = (int64_t)1 << (n_open - op.n_split);
+    const int64_t jf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jf >= n) return;
+    int64_t base = 0, j = (int64_t)split_val;
+    for (int t = 0, u = 0; t < n_open; ++t) {
+        if ((split_mask >> t) & 1) continue;
+        if ((jf >> u) & 1) {
+            base |= (int64_t)1 << op.open_pos[t];
+            j |= (int64_t)1 << t;
+        }
+        ++u;
+    }
     const int E = texp ? texp[op.meta] : 0;
     double cr = 1.0, ci = 0.0;
     for (int k = 0; k < n_steps; ++k) {
@@ -1025,26 +1034,30 @@ __global__ void slice_sum_kernel(const TF *__restrict__ F, const SumOp op, doubl
 
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
                              int t_lo, int t_hi, int overwrite, const int32_t *texp,
-                             const double2 *stepcorr, int n_steps, cudaStream_t s) {
-    const int64_t n = (int64_t)1 << n_open;
+                             const double2 *stepcorr, int n_steps, uint64_t split_val, cudaStream_t s) {
+    if (op.n_split < 0 || op.n_split > 8 || op.n_split > n_open) return cudaErrorInvalidValue;
+    uint64_t split_mask = 0;
+    for (int i = 0; i < op.n_split; ++i) split_mask |= 1ull << op.split_t[i];
+    if ((split_val & ~split_mask) != 0) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)1 << (n_open - op.n_split);
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     if (dtype == TN_C64)
         slice_sum_kernel<float2, TN_C64><<<blocks, threads, 0, s>>>(
-            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, nullptr, nullptr, 0);
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, nullptr, nullptr, 0, split_mask, split_val);
     else if (op.tf == 0 && dtype == TN_F16)
         slice_sum_kernel<float2, TN_F16><<<blocks, threads, 0, s>>>(
-            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps, split_mask, split_val);
     else if (op.tf == 0)
         slice_sum_kernel<float2, TN_BF16><<<blocks, threads, 0, s>>>(
-            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
+            (const float2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps, split_mask, split_val);
     else if (dtype == TN_F16)
         slice_sum_kernel<__half2, TN_F16><<<blocks, threads, 0, s>>>(
-            (const __half2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps);
+            (const __half2 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps, split_mask, split_val);
     else
         slice_sum_kernel<__nv_bfloat162, TN_BF16><<<blocks, threads, 0, s>>>(
             (const __nv_bfloat162 *)F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr,
-            n_steps);
+            n_steps, split_mask, split_val);
     return cudaGetLastError();
 }
 

@@ -72,10 +72,12 @@ cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void
                                    int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,
                                    const int32_t *za = nullptr, const int32_t *zb = nullptr);
 // stepcorr / n_steps: per-step rounding compensation factors of a
-// complex-half plan (n_steps = 0: none).
+// complex-half plan (n_steps = 0: none).  split_val: the values of the
+// op's split outputs (recomputation) for this pass, as amplitude-index bits;
+// only the 2^(n_open - n_split) amplitudes with those bits are written.
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,
                              int t_lo, int t_hi, int overwrite, const int32_t *texp,
-                             const double2 *stepcorr, int n_steps, cudaStream_t s);
+                             const double2 *stepcorr, int n_steps, uint64_t split_val, cudaStream_t s);
 cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double *d_out5,
                            double *d_partials, int n_blocks, cudaStream_t s);
 cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,

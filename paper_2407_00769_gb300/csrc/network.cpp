@@ -207,4 +207,13 @@ int fix_open_legs(Network &net) {
     return TN_OK;
 }
 
+int fix_legs(Network &net, const std::vector<int> &edges) {
+    std::vector<char> fix(net.edges.size(), 0);
+    for (int e : edges) fix[e] = 1;
+    for (Leaf &L : net.leaves)
+        for (int i = (int)L.legs.size() - 1; i >= 0; --i)
+            if (L.legs[i] >= 0 && fix[L.legs[i]]) select_leg(L, i, 0);
+    return TN_OK;
+}
+
 }  // namespace tn

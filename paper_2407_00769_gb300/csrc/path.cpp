@@ -246,4 +246,43 @@ int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, i
     return TN_OK;
 }
 
+int choose_recompute(const Network &net, int r, Path &path, std::vector<int> &sliced, std::string &err) {
+    const int E = (int)net.edges.size();
+    std::vector<char> removed(E, 0);
+    for (int e : sliced) removed[e] = 1;
+    std::vector<std::vector<int>> ll_full;
+    for (const Leaf &L : net.leaves) {
+        std::vector<int> k(L.legs);
+        std::sort(k.begin(), k.end());
+        ll_full.push_back(std::move(k));
+    }
+    for (int i = 0; i < r; ++i) {
+        int best_e = -1, best_mx = 0;
+        double best_fl = 0;
+        for (int e = 0; e < E; ++e) {
+            if (net.edges[e].open_t < 0 || net.edges[e].u < 0 || removed[e]) continue;
+            removed[e] = 1;
+            int m2;
+            double f2;
+            replay(ll_full, path, removed, m2, f2, nullptr);
+            removed[e] = 0;
+            if (best_e < 0 || m2 < best_mx || (m2 == best_mx && f2 < best_fl)) {
+                best_e = e; best_mx = m2; best_fl = f2;
+            }
+        }
+        if (best_e < 0) {
+            err = "recompute_log2 exceeds the number of open output legs";
+            return TN_EINVAL;
+        }
+        removed[best_e] = 1;
+        sliced.push_back(best_e);
+    }
+    int mx;
+    double fl;
+    replay(ll_full, path, removed, mx, fl, nullptr);
+    path.max_log2 = mx;
+    path.flops = fl;
+    return TN_OK;
+}
+
 }  // namespace tn

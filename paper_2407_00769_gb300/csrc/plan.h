@@ -29,6 +29,10 @@ int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int it
                 int chains, Path &path, std::vector<int> &sliced);
 int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, int cap, Path &path,
                   std::vector<int> &sliced, std::string &err);
+// Recomputation (Sec. 3.4.1): append r open output legs to `sliced`, each
+// the one whose removal shrinks the largest intermediate of `path` most
+// (then its flops); updates the path's size and flops.
+int choose_recompute(const Network &net, int r, Path &path, std::vector<int> &sliced, std::string &err);
 
 struct Schedule {
     std::vector<Op> ops;                // phase 0 ops first, then phase 1
@@ -70,6 +74,7 @@ struct tn_plan_s {
     tn_plan_opts opts{};
     std::vector<int> sliced;   // edge ids; slice-id bit j <-> sliced[j]
     int batch_log2 = 0;
+    int n_recompute = 0;       // the last n sliced edges are split open legs
     tn::Path path;
     tn::Schedule sched;
     std::vector<tn::cd> leaf_store;     // all leaves, full legs, complex128

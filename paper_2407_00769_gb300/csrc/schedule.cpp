@@ -536,7 +536,23 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
             else if (batched(F[p])) op.sum.batch_pos[sbit[F[p]]] = r - 1 - p;
             else { err = "final tensor has a non-output mode"; return TN_EINVAL; }
         }
-        if (r != net.n_open + batch_log2) { err = "final tensor misses output modes"; return TN_EINVAL; }
+        // recomputation: open outputs sliced (looped) are fixed per pass
+        op.sum.n_split = 0;
+        for (int j = 0; j < (int)sliced.size(); ++j) {
+            const Edge &ed = net.edges[sliced[j]];
+            if (ed.open_t < 0) continue;
+            if (j < batch_log2 || op.sum.n_split >= 8) {
+                err = "an open leg can be split only outside the slice batch (at most 8)";
+                return TN_EINVAL;
+            }
+            op.sum.split_t[op.sum.n_split] = ed.open_t;
+            op.sum.split_bit[op.sum.n_split] = j;
+            ++op.sum.n_split;
+        }
+        if (r != net.n_open - op.sum.n_split + batch_log2) {
+            err = "final tensor misses output modes";
+            return TN_EINVAL;
+        }
         op.sum.n_batch = batch_log2;
         op.sum.tf = tdt[final_t];
         ph[1].push_back(op);

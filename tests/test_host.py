@@ -265,3 +265,17 @@ def test_sample_plan_cost_grows_slowly_with_the_sample_count():
     i = tn.Plan.from_samples(c, np.zeros((4, 30)), dtype=tn.F16, n_slice_edges=8, slice_batch_log2=2,
                              torch_allocator=False).info()
     assert i["slice_batch_log2"] == 2 and i["n_open"] == 2
+
+
+def test_recompute_plan_splits_open_legs():
+    c, q = rqcgen.grid_30q()
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=8, trials=4, slice_batch_log2=8, recompute_log2=2,
+                torch_allocator=False)
+    i = p.info()
+    assert i["n_recompute_edges"] == 2 and i["n_slice_edges"] == 10 and i["n_slices"] == 1 << 10
+    assert {qq for qq, _ in p.sliced_edges()[-2:]} <= set(q.open_qubits)
+    c2, q2 = rqcgen.small_grid(3, 4, 8, seed=3, n_open=2)
+    with pytest.raises(tn.TnError, match="open output legs"):
+        tn.Plan(c2, q2, dtype=tn.F16, recompute_log2=3, torch_allocator=False)   # 2 open legs
+    with pytest.raises(tn.TnError):
+        tn.Plan.from_samples(c, np.zeros((4, 30)), dtype=tn.F16, recompute_log2=1, torch_allocator=False)
