@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-c64", action="store_true", help="skip the complex64 comparison leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,samples,grid40",
+    ap.add_argument("--legs", default="grid12,grid53,batch256,fp8,anneal,samples,recompute,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
     ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec"],
                     help="time one kernel on one shape instead (profiling aid)")
@@ -501,6 +501,38 @@ def leg_samples(tn, torch, dev, flush, stream, gold, n=16384):
     return out
 
 
+def leg_recompute(tn, torch, dev, flush, stream, iters=200000):
+    """Recomputation (Sec. 3.4.1) on the 53-qubit circuit: 3 of its 12 output
+    legs split into 8 sequential passes, on an annealed path at cap 2^30
+    (8 slices per pass).  The whole job (all slices, all 4096 amplitudes) is
+    timed, against the annealed unsplit plan's size; 2^53 mean p is the
+    Porter-Thomas check (1 for a deep random circuit)."""
+    import rqcgen
+    c, q = rqcgen.grid_53q()
+    out = {}
+    for r in (0, 3):
+        t0 = time.time()
+        plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=4,
+                       slice_batch_log2=3, anneal_iters=iters, recompute_log2=r)
+        plan_s = time.time() - t0
+        info = plan.info()
+        flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
+        row = {"n_slices": info["n_slices"], "job_flops": flops, "plan_s": plan_s,
+               "max_log2_elems": info["max_log2_elems"]}
+        if r > 0:
+            amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
+            plan.contract(out=amps)
+            ms = _timed(lambda: plan.contract(out=amps), stream, flush)
+            x = (2.0 ** 53) * (amps.abs() ** 2)
+            row.update({"job_s": ms * 1e-3, "tflops": flops / (ms * 1e-3) / 1e12,
+                        "mean_2n_p": float(x.mean().item())})
+            del amps
+        out[f"split_{r}"] = row
+        del plan
+        torch.cuda.empty_cache()
+    return out
+
+
 def leg_fp8(tn, torch, dev, flush, stream, gold, min_log2_flops=40):
     """The main workload with E4M3 operands on its largest tensor-core steps
     (>= 2^40 flops per pass): throughput and error against FP64.  E4M3's 3
@@ -880,6 +912,8 @@ def main():
         line["anneal"] = leg_anneal(tn, torch, dev, flush, stream, gold)
     if "samples" in legs:
         line["samples"] = leg_samples(tn, torch, dev, flush, stream, gold)
+    if "recompute" in legs:
+        line["recompute"] = leg_recompute(tn, torch, dev, flush, stream)
 
     if not args.no_cpu_baseline and world == 1:
         full, sample, threads, full_1 = oracle_sample()

@@ -97,7 +97,10 @@ typedef struct {
                                  cheapest kept; with a cap, sliced edges the
                                  refined path no longer needs are given back */
     int32_t slice_batch_log2; /* run 2^this consecutive slices in one pass, the
-                                 batch carried as an extra tensor mode (>= 0)    */
+                                 batch carried as an extra tensor mode (>= 0;
+                                 slicing to a cap: lowered to the number of
+                                 summed sliced edges if the planner keeps
+                                 fewer)                                          */
     int32_t tile_policy;      /* TN_TILE_*                                       */
     int32_t small_log2;       /* complex-half plans: tensors of at most
                                  2^small_log2 elements are stored complex64

@@ -642,8 +642,12 @@ int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
         return TN_EINVAL;
     }
     if (o.slice_batch_log2 > (int)P->sliced.size()) {
-        err = "slice_batch_log2 exceeds the number of sliced edges";
-        return TN_EINVAL;
+        if (n_target >= 0) {
+            err = "slice_batch_log2 exceeds the number of sliced edges";
+            return TN_EINVAL;
+        }
+        // slicing to a cap: the planner decides how many slices there are
+        P->opts.slice_batch_log2 = (int)P->sliced.size();
     }
     if (o.recompute_log2 > 0) {
         // the split legs after the summed slices: a pass's part of the
@@ -651,7 +655,7 @@ int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
         P->sliced.insert(P->sliced.end(), split.begin(), split.end());
         P->n_recompute = o.recompute_log2;
     }
-    P->batch_log2 = o.slice_batch_log2;
+    P->batch_log2 = P->opts.slice_batch_log2;
     return TN_OK;
 }
 

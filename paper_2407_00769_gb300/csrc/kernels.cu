@@ -600,7 +600,10 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) acc[j] = make_float2((float)tot[j].x, (float)tot[j].y);
-    if (threadIdx.x >= rows) return;
+    // every thread stays to the end: the maximum is reduced over the warp and
+    // recorded with one atomic per warp (one per thread serialises on a
+    // single address for steps of 2^30 rows)
+    const bool active = threadIdx.x < rows;
     const int64_t m = m0 + threadIdx.x;
     TC *crow = Cb + m * N + n0;
     if constexpr (std::is_same<TC, float2>::value) {
@@ -609,14 +612,15 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
         float mx = 0.f;
 #pragma unroll
         for (int j = 0; j < NC; ++j)
-            if (j < nc) {
+            if (active && j < nc) {
                 crow[j] = acc[j];
                 mx = fmaxf(mx, fmaxf(fabsf(acc[j].x), fabsf(acc[j].y)));
             }
         if (sr.tmax) {
             if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
                 sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b];
-            if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+            mx = warp_max(mx);
+            if (sr.out_max && (threadIdx.x & 31) == 0) atomic_max_nonneg(sr.out_max, mx);
         }
     } else {
         // power-of-two scaling (exact): e from the operands' recorded maxima
@@ -629,14 +633,17 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
         float mx = 0.f;
 #pragma unroll
         for (int j = 0; j < NC; ++j)
-            if (j < nc) {
+            if (active && j < nc) {
                 const auto h = LpT<DT>::from_f2(make_float2(acc[j].x * s, acc[j].y * s));
                 crow[j] = h;
                 const float2 f = LpT<DT>::to_f2(h);
                 mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
             }
-        if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
-        if (DT == TN_F16 && sr.err && !(mx <= 65504.0f)) atomicOr(sr.err, 2);
+        mx = warp_max(mx);
+        if ((threadIdx.x & 31) == 0) {
+            if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
+            if (DT == TN_F16 && sr.err && !(mx <= 65504.0f)) atomicOr(sr.err, 2);
+        }
     }
 }
 

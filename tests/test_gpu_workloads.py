@@ -154,3 +154,15 @@ def test_grid53_full_job_porter_thomas():
     print(f"53-qubit full job: mean 2^n p = {x.mean():.4f}, second moment {np.mean(x ** 2):.4f}")
     assert 0.93 <= x.mean() <= 1.07
     assert 1.6 <= np.mean(x ** 2) <= 2.4
+    # recomputation (3 output legs split into 8 passes, 32 slices in all) on
+    # its own path and slicing gives the same 4096 amplitudes: two FP16
+    # computations, each within ~1e-3 of the exact values
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=30, trials=4, slice_batch_log2=3,
+                anneal_iters=200000, recompute_log2=3)
+    assert p.info()["n_recompute_edges"] == 3
+    amps_r = p.contract().cpu().numpy()
+    del p
+    torch.cuda.empty_cache()
+    e = oracle.rel_l2(amps_r, amps)
+    print(f"53-qubit full job with recomputation: rel-L2 {e:.2e} against the unsplit job")
+    assert e <= 5e-3
