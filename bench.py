@@ -55,6 +55,9 @@ def parse():
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
     ap.add_argument("--pair", action="store_true", help="--case gemm_tc on CTA pairs (256-row tiles)")
+    ap.add_argument("--sustain", type=float, default=0.0,
+                    help="--case gemm_tc: also time calls back to back for this many seconds "
+                         "(the power-capped rate), and cuBLAS on the same real GEMM")
     ap.add_argument("--padded", action="store_true", help="--case gather with the padded 2-D index")
     ap.add_argument("--lm", type=int, default=14)
     ap.add_argument("--ln", type=int, default=14)
@@ -141,8 +144,34 @@ def kernel_case(args):
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts)
     rate = work / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
-    print(json.dumps({"case": args.case, "ms": ms, "rate": rate, "unit": unit,
-                      "shape": vars(args)}), flush=True)
+    line = {"case": args.case, "ms": ms, "rate": rate, "unit": unit, "shape": vars(args)}
+    if args.case == "gemm_tc" and args.sustain > 0 and not args.fp8:
+        # back to back for a few seconds: the rate under the power cap, for
+        # this kernel and for cuBLAS on the real GEMM of the same shape
+        # (C'[M][2N] = A'[M][2K] B'^T, FP16 in and out)
+        def sustained(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            n, t0 = 0, time.time()
+            e0.record()
+            while time.time() - t0 < args.sustain:
+                for _ in range(10):
+                    fn()
+                n += 10
+                torch.cuda.synchronize()
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / n
+        ms_s = sustained(run)
+        Ar = A.reshape(b * M, 2 * K)[:M]
+        Br = torch.randn(2 * K, 2 * N, device="cuda", generator=g).half()
+        Cr = torch.empty(M, 2 * N, dtype=torch.float16, device="cuda")
+        ms_c = sustained(lambda: torch.matmul(Ar, Br, out=Cr)) * b
+        line["sustained"] = {"seconds": args.sustain, "ms": ms_s, "rate": work / (ms_s * 1e-3) / 1e12,
+                             "cublas_same_real_gemm_rate": work / (ms_c * 1e-3) / 1e12}
+    print(json.dumps(line), flush=True)
 
 
 def load_peaks():
