@@ -245,6 +245,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.bn = tc_tile_bn(g.tile);
                     d.gm = tc_tile_gm(g.tile);
                     d.pair = (g.tile & kTcPairTile) ? 1 : 0;
+                    d.half_k = (g.tile & kTcHalfKTile) ? 1 : 0;
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
                     d.fp8 = g.fp8;
@@ -331,6 +332,8 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g, bool pair_vari
             if (pair_variants) {
                 c.push_back({GK_LP_TC, code});
                 if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
+                // (64-byte K chunks, tile bit 9, lost to 128-byte chunks on
+                // every step of the 30-qubit workload: not a candidate)
             } else {
                 c.push_back({GK_LP_TC, own_pair && pair_ok(code) ? code | kTcPairTile : code});
             }
@@ -1427,7 +1430,8 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
         sr.out_max = out_max;
         int kk = kernel;
         const bool pair = kk == 4;            // tensor cores on CTA pairs
-        if (pair) kk = GK_LP_TC;
+        const bool half_k = kk == 5;          // tensor cores, 64-byte K chunks
+        if (pair || half_k) kk = GK_LP_TC;
         if (kk < 0) kk = tc_gemm_supported(lk, ln) ? GK_LP_TC : GK_LP_ROWS;
         if (kk == GK_LP_ROWS) {
             e = launch_gemm_rows_lp(dtype, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
@@ -1448,6 +1452,7 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                 d.batch_b = batch_b ? 1 : 0;
                 d.np = np;
                 d.pair = pair ? 1 : 0;
+                d.half_k = half_k ? 1 : 0;
                 const size_t pb = tc_split_bytes(lm, ln, lk, batch);
                 if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
                 if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);

@@ -74,8 +74,10 @@ enum GemmKernel : int32_t {
 };
 
 // Tensor-core tile code: bits 0-3 N-tile width code, bits 4-7 raster-group
-// code, bit 8 CTA pairs (256-row tiles on a cluster of 2 SMs).
+// code, bit 8 CTA pairs (256-row tiles on a cluster of 2 SMs), bit 9 64-byte
+// K chunks (twice the ring stages of 128-byte chunks in the same memory).
 constexpr int kTcPairTile = 0x100;
+constexpr int kTcHalfKTile = 0x200;
 // whether a step of this shape runs on CTA pairs when asked (bn: the N tile
 // in real columns the launch uses)
 bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);

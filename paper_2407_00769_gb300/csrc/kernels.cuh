@@ -114,6 +114,8 @@ struct TcGemmDesc {
     int8_t out_dpos[40] = {};
     // 1: run on CTA pairs (256-row tiles, cluster of 2) where the shape allows
     int pair = 0;
+    // 1: 64-byte K chunks (FP16/BF16, 1-CTA tiles): a deeper ring
+    int half_k = 0;
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs

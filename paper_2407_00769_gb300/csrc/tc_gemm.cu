@@ -922,7 +922,7 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     const int esz = d.fp8 ? 1 : 2;
     const int kreal = 2 << d.lk;                 // 2K elements
     // K chunk: 128-byte rows where K allows (FP8: always, K >= 64)
-    const int bk = d.fp8 ? 128 : (kreal >= 64 ? 64 : kreal);
+    int bk = d.fp8 ? 128 : (kreal >= 64 ? 64 : kreal);
     int bn = d.np >= 256 ? 256 : d.np;           // 16 .. 256
     if (d.bn > 0) {
         if ((d.bn & (d.bn - 1)) != 0 || d.bn < 16 || d.bn > 256) return cudaErrorInvalidValue;
@@ -932,6 +932,7 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     const bool gathered = d.za || d.zb || d.zc;
     // CTA pairs: 256 x 256 tiles of FP16/BF16 with 128-byte K chunks
     const bool pair = tc_pair_eligible(d.pair, d.fp8, d.lm, d.ln, d.lk, bn) && !gathered && d.gather_r == 0;
+    if (d.half_k && !pair && !d.fp8 && bk == 64) bk = 32;
     CUtensorMap ma, mb;
     const int64_t depth_a = d.depth_a > 0 ? d.depth_a : (d.batch_a ? d.batch : 1);
     const int64_t depth_b = d.depth_b > 0 ? d.depth_b : (d.batch_b ? d.batch : 1);

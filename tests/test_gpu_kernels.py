@@ -199,6 +199,13 @@ def test_gemm_tensor_cores_cta_pairs_batched(ba, bb):
     _lp_case(tn.BF16, 256, 256, 128, 2, tn.GEMM_TC_PAIR, ba, bb)
 
 
+@pytest.mark.parametrize("M,N,K", [(256, 128, 32), (1024, 256, 512), (128, 64, 64), (4096, 128, 2048)])
+def test_gemm_tensor_cores_half_k_chunks(M, N, K):
+    # 64-byte K chunks (32 FP16 per row, 64-byte swizzle, twice the stages)
+    _lp_case(tn.F16, M, N, K, 1, tn.GEMM_TC_HALF_K)
+    _lp_case(tn.BF16, M, N, K, 2, tn.GEMM_TC_HALF_K)
+
+
 def test_gemm_tensor_cores_cta_pairs_long_k():
     # K = 2^16 complex: split into K parts (FP32 partials, FP64 reduction)
     M, N, K = 256, 128, 1 << 16
