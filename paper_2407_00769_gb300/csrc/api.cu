@@ -286,12 +286,9 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
     return TN_OK;
 }
 
-// Legal (kernel, tile) configurations of a GEMM op.
-// Kernel and tile candidates of a GEMM step.  pair_variants: CTA-pair tiles
-// as candidates of their own (timed by the exhaustive tuner); otherwise the
-// step's own choice (its tile's pair bit) carries over to every candidate
-// with a 256-column N tile (the cost model does not tell the two apart).
-std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g, bool pair_variants) {
+// Legal (kernel, tile) configurations of a GEMM op: N tile x raster group,
+// each also on CTA pairs where the shape allows.
+std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
     std::vector<std::pair<int, int>> c;
     if (g.kernel == GK_C64_ROWS || g.kernel == GK_C64_TILED) {
         c.push_back({GK_C64_ROWS, 0});
@@ -327,16 +324,11 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g, bool pair_vari
             const int bn = tc_tile_bn(tc_effective_tile(code, g.ln));
             return !gathered && tc_pair_eligible(1, g.fp8, g.lm, g.ln, g.lk, bn);
         };
-        const bool own_pair = (g.tile & kTcPairTile) != 0;
         for (int code : codes) {
-            if (pair_variants) {
-                c.push_back({GK_LP_TC, code});
-                if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
-                // (64-byte K chunks, tile bit 9, lost to 128-byte chunks on
-                // every step of the 30-qubit workload: not a candidate)
-            } else {
-                c.push_back({GK_LP_TC, own_pair && pair_ok(code) ? code | kTcPairTile : code});
-            }
+            c.push_back({GK_LP_TC, code});
+            if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
+            // (64-byte K chunks, tile bit 9, lost to 128-byte chunks on
+            // every step of the 30-qubit workload: not a candidate)
         }
     }
     return c;
@@ -427,7 +419,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
                 GemmOp &g = op.gemm;
                 double best = 1e30;
                 std::pair<int, int> pick{g.kernel, g.tile};
-                for (const auto &cand : gemm_candidates(g, true)) {
+                for (const auto &cand : gemm_candidates(g)) {
                     Op trial = op;
                     trial.gemm.kernel = cand.first;
                     trial.gemm.tile = cand.second;
@@ -493,6 +485,8 @@ void cost_features(const tn_tune_record &r, float *f) {
             const int bc = eff & 15, gc = (eff >> 4) & 15;
             if (bc < 5) f[14 + bc] = 1.0f;
             if (gc < 5) f[19 + gc] = 1.0f;
+            // CTA pairs (slot 25 is the permutation size in permute records)
+            if ((r.tile & kTcPairTile) && tc_pair_eligible(1, 0, r.lm, r.ln, r.lk, tc_tile_bn(eff))) f[25] = 1.0f;
         }
     } else {
         f[9] = 1.0f;
@@ -521,7 +515,7 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         const Op &op = S.ops[i];
         if (op.kind != OP_GEMM) continue;
         const GemmOp &g = op.gemm;
-        for (const auto &cand : gemm_candidates(g, false)) {
+        for (const auto &cand : gemm_candidates(g)) {
             recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second,
                                           g.step, 0, 0});
             who.push_back({i, cand});

@@ -251,3 +251,15 @@ def test_grid_30q_annealed_path_full_size(dtype, batch):
     i = p.info()
     print(f"grid30 annealed {tn.DTYPE_NAMES[dtype]}: {i['flops_per_slice'] * i['n_slices'] + i['flops_invariant']:.3e} "
           f"flops, rel_l2={e:.3e} fidelity={f:.6f}")
+
+
+def test_empty_slice_range():
+    # no slices: the sum is empty (zeros), or the accumulator is left as it was
+    c, q = rqcgen.small_grid(3, 3, 6, seed=2, n_open=3)
+    p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=2)
+    out = p.contract()
+    before = out.clone()
+    p.contract(0, 0, out=out, accumulate=True)
+    assert torch.equal(out, before)
+    p.contract(0, 0, out=out)
+    assert not out.abs().max().item()
