@@ -857,6 +857,21 @@ def main():
                 roofline["traffic_source"] = tr.get("source")
         except Exception:
             pass
+    # the autotuner's timings of the dominant step, one per candidate
+    # configuration (tile code in hex: N-tile code, raster-group code << 4,
+    # CTA pairs 0x100), taken in the first warm-up step
+    try:
+        by_step = {}
+        for r in plan.tune_records():
+            if r["kind"] == 0 and r["kernel"] == 3:
+                by_step.setdefault((r["step"], r["lm"], r["ln"], r["lk"], r["lb"]), {})[r["tile"]] = r["ms"]
+        if by_step:
+            key, cands = max(by_step.items(), key=lambda kv: min(kv[1].values()))
+            roofline["dominant_step_tuning"] = {
+                "step": key[0], "log2_mnkb": list(key[1:]),
+                "ms_by_tile": {f"{t:#x}": round(m, 3) for t, m in sorted(cands.items(), key=lambda kv: kv[1])}}
+    except Exception:
+        pass
 
     line = {"metric": METRIC, "value": job_flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
