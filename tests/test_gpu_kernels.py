@@ -92,7 +92,9 @@ def bound(a, b, K):
 
 
 C64_SHAPES = [(1, 1, 1), (3, 2, 4), (128, 4, 4), (1000, 8, 16), (4096, 2, 1), (64, 64, 16),
-              (256, 128, 64), (128, 16, 256), (2, 256, 2)]
+              (256, 128, 64), (128, 16, 256), (2, 256, 2),
+              # 128 x 128 tiles of the tiled kernel (M N >= 2^18)
+              (1024, 256, 64), (512, 512, 16), (2048, 128, 1024)]
 
 
 @pytest.mark.parametrize("M,N,K", C64_SHAPES)
