@@ -743,16 +743,37 @@ __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
             acc[i][j] = make_float2(0.f, 0.f);
             if constexpr (LONGK) tot[i][j] = make_double2(0.0, 0.0);
         }
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int i = threadIdx.x; i < BM * BK; i += 256) {
-            const int r = i / BK, kk = i % BK;
-            As[kk][r] = Ab[(int64_t)r * K + k0 + kk];
+    // the next K slice is loaded into registers while the current one is
+    // multiplied out of shared memory
+    constexpr int EA = BM * BK / 256, EB = BK * BN / 256;
+    static_assert(EA * 256 == BM * BK && EB * 256 == BK * BN, "tile not a multiple of the block");
+    float2 ra[EA], rb[EB];
+    auto load_regs = [&](int k0) {
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+            const int i = threadIdx.x + 256 * e, r = i / BK, kk = i % BK;
+            ra[e] = Ab[(int64_t)r * K + k0 + kk];
         }
-        for (int i = threadIdx.x; i < BK * BN; i += 256) {
-            const int kk = i / BN, c = i % BN;
-            Bs[kk][c] = Bb[(int64_t)(k0 + kk) * N + c];
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            const int i = threadIdx.x + 256 * e, kk = i / BN, c = i % BN;
+            rb[e] = Bb[(int64_t)(k0 + kk) * N + c];
+        }
+    };
+    load_regs(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+            const int i = threadIdx.x + 256 * e;
+            As[i % BK][i / BK] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            const int i = threadIdx.x + 256 * e;
+            Bs[i / BN][i % BN] = rb[e];
         }
         __syncthreads();
+        if (k0 + BK < K) load_regs(k0 + BK);
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
             float2 a[TM], bv[TN];
