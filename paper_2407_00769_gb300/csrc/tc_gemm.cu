@@ -16,7 +16,10 @@
 //                   TMEM), double-buffered accumulators, tcgen05.commit frees
 //                   ring stages and publishes finished tiles; the FP8
 //                   variant issues kind::f8f6f4 with E4M3 operands (K=32);
-//   * warps 2..5  : epilogue -- tcgen05.ld rows out of TMEM, exact 2^e scale,
+//   * warps 2..9  : epilogue, two warps per TMEM lane quadrant taking
+//                   alternate 16-column chunks (one warp per scheduler left
+//                   short-K steps bound by the epilogue's own latency) --
+//                   tcgen05.ld rows out of TMEM, exact 2^e scale,
 //                   round to FP16/BF16, record max |C| for the next step's
 //                   exponent, store interleaved complex-half rows.
 // Persistent: one CTA per SM walks tiles (batch, m-tile, n-tile).
@@ -37,6 +40,8 @@ namespace tn {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kEpiThreads = 256;                  // warps 2..9
+constexpr int kTcThreads = 64 + kEpiThreads;      // producer, MMA, epilogue
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -327,7 +332,7 @@ struct TcSmem {
 // and holds its 128 rows of the accumulator in its own TMEM, so each SM
 // streams half the B' bytes of a 1-CTA tile through shared memory.
 template <int BN, int BKB, int STAGES, bool F8, bool PAIR>
-__global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB,
                                                          const TcArgs args) {
     using S = TcSmem<PAIR ? BN / 2 : BN, BKB, STAGES>;
@@ -361,7 +366,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
-            mbar_init(&acce[i], PAIR ? 256 : 128);   // pair: both CTAs' epilogue threads
+            mbar_init(&acce[i], PAIR ? 2 * kEpiThreads : kEpiThreads);   // pair: both CTAs' epilogues
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -508,6 +513,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
     } else {
         // ---------------------------------------------------- epilogue --
         const int q = warp & 3;                 // TMEM lane quadrant of this warp
+        const int half = (warp - 2) >> 2;       // which alternate 16-column chunks
         const int row = q * 32 + lane;
         int e;
         if (args.out_c64)
@@ -547,7 +553,7 @@ __global__ void __launch_bounds__(192, 1) gemm_tc_kernel(const __grid_constant__
             // gather_r: the tile's columns are gather_r chunks of np_chunk real
             // columns, chunk r of row b going to output chunk zc[b m_r + r]
             const int col_end = args.gather_r ? BN : min(BN, 2 * args.N - col0);   // warp-uniform
-            for (int c = 0; c < col_end; c += 16) {
+            for (int c = 16 * half; c < col_end; c += 32) {
                 uint32_t r[16];
                 tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 tmem_wait_ld();
@@ -749,7 +755,7 @@ cudaLaunchConfig_t pair_config(int64_t grid, cudaStream_t s, cudaLaunchAttribute
     using S = TcSmem<128, 128, ST>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(192, 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
     cfg.dynamicSmemBytes = S::total;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -795,7 +801,7 @@ cudaError_t run_tc(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a
     using S = TcSmem<BN, BKB, ST>;
     auto kern = gemm_tc_kernel<BN, BKB, ST, F8, false>;
     const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
-    kern<<<(unsigned)grid, 192, S::total, s>>>(ma, mb, a);
+    kern<<<(unsigned)grid, kTcThreads, S::total, s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
