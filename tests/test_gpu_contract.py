@@ -162,17 +162,23 @@ def _golden(name):
     return np.array(vals)
 
 
-@pytest.mark.parametrize("dtype,batch", [(tn.C64, 0), (tn.F16, 0), (tn.BF16, 0), (tn.F16, 8),
-                                         (tn.C64, 8)])
-def test_grid_30q_sliced_full_size(dtype, batch):
+@pytest.mark.parametrize("dtype,batch,policy", [(tn.C64, 0, tn.TILE_FIXED), (tn.F16, 0, tn.TILE_FIXED),
+                                                (tn.BF16, 0, tn.TILE_FIXED), (tn.F16, 8, tn.TILE_FIXED),
+                                                (tn.C64, 8, tn.TILE_FIXED),
+                                                # the benchmark's configuration: tiles (1-CTA or
+                                                # CTA pairs) chosen by the autotuner
+                                                (tn.F16, 8, tn.TILE_EXHAUSTIVE)])
+def test_grid_30q_sliced_full_size(dtype, batch, policy):
     # the 30-qubit, 14-cycle workload: 8 sliced edges (256 slices), 1024
     # correlated amplitudes, against the FP64 state vector on 2^30 amplitudes
     want = _golden("grid5x6_14c_amps.txt")
     c, q = rqcgen.grid_30q()
-    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=8, trials=4, slice_batch_log2=batch)
+    p = tn.Plan(c, q, dtype=dtype, n_slice_edges=8, trials=4, slice_batch_log2=batch, tile_policy=policy)
     got = p.contract()
     e, f = check(got, want, dtype)
-    print(f"grid30 {tn.DTYPE_NAMES[dtype]} batch 2^{batch}: rel_l2={e:.3e} fidelity={f:.6f}")
+    got2 = p.contract()   # the tuned configuration, replayed
+    check(got2, want, dtype)
+    print(f"grid30 {tn.DTYPE_NAMES[dtype]} batch 2^{batch} policy {policy}: rel_l2={e:.3e} fidelity={f:.6f}")
 
 
 @pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
