@@ -279,3 +279,15 @@ def test_recompute_plan_splits_open_legs():
         tn.Plan(c2, q2, dtype=tn.F16, recompute_log2=3, torch_allocator=False)   # 2 open legs
     with pytest.raises(tn.TnError):
         tn.Plan.from_samples(c, np.zeros((4, 30)), dtype=tn.F16, recompute_log2=1, torch_allocator=False)
+
+
+def test_cost_features_mark_cta_pair_tiles():
+    # slot 25 of a tensor-core GEMM record flags CTA-pair tiles, only where
+    # the shape runs on pairs (M >= 256, N >= 128 complex, K >= 32)
+    base = dict(kind=0, lm=16, ln=12, lk=10, lb=0, dtype=tn.F16, kernel=3)
+    recs = [dict(base, tile=0), dict(base, tile=0x100), dict(base, lm=7, tile=0x100),
+            dict(base, ln=5, tile=0x100), dict(base, lk=4, tile=0x100), dict(base, tile=0x141)]
+    x = tn.cost_features(recs)
+    assert x[:, 25].tolist() == [0.0, 1.0, 0.0, 0.0, 0.0, 1.0]
+    # the pair bit does not change the other features of the record
+    assert np.array_equal(np.delete(x[0], 25), np.delete(x[1], 25))
