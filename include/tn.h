@@ -267,7 +267,8 @@ int tn_plan_set_graph(tn_plan_t *plan, int enable);
  * slice of plans[i] is contracted into d_amps[i] (device, 2^n_open_i
  * complex128, overwritten).  tn_batch_create sets up each plan's device
  * state, spreads the plans over n_streams side streams (largest work first,
- * to the least loaded stream) and captures all their launches into one CUDA
+ * to the least loaded stream; work = the cost model's predicted time when
+ * every plan has one attached, else flops) and captures all their launches into one CUDA
  * graph; tn_batch_run replays that graph on `stream` (rep: optional timing,
  * synchronizes).  Plans must share dtype, have profiling off, and not be
  * used elsewhere while the batch exists.

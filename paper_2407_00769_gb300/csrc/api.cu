@@ -1151,13 +1151,26 @@ int tn_batch_create(tn_plan_t *const *plans, int32_t n, double *const *d_amps, i
         if (rc != TN_OK) return rc;
         if (plans[i]->prof_mask) return fail(TN_EINVAL, "profiling must be off for a batch");
     }
-    // longest-processing-time assignment of plans to side streams by flops
+    // longest-processing-time assignment of plans to side streams: by the
+    // cost model's predicted time when every plan has a model attached,
+    // else by flops
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    auto work = [&](int i) {
+    bool all_models = true;
+    for (int i = 0; i < n; ++i) all_models = all_models && plans[i]->cost_model != nullptr;
+    std::vector<double> w(n);
+    for (int i = 0; i < n; ++i) {
         const tn_plan_s *P = plans[i];
-        return P->sched.flops_inv + P->sched.flops_per_pass * (double)plan_passes(P, 0, (int64_t)1 << P->sliced.size()) + 1.0;
-    };
+        w[i] = P->sched.flops_inv + P->sched.flops_per_pass * (double)plan_passes(P, 0, (int64_t)1 << P->sliced.size()) + 1.0;
+    }
+    if (all_models)
+        for (int i = 0; i < n; ++i) {
+            double ms = 0;
+            const int rc = tn_plan_predict_ms(plans[i], plans[i]->cost_model, &ms, nullptr);
+            if (rc != TN_OK) return rc;
+            w[i] = ms;
+        }
+    auto work = [&](int i) { return w[i]; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
     std::vector<double> load(n_streams, 0.0);
     std::vector<std::vector<int>> assign(n_streams);

@@ -221,6 +221,16 @@ def test_batch_of_uneven_circuits(dtype):
     tn.contract_batch(plans, outs2)
     for o, o2 in zip(outs, outs2):
         assert np.array_equal(o.cpu().numpy(), o2.cpu().numpy())
+    # with a cost model on every plan the streams are loaded by predicted
+    # time instead of flops; each plan's result is the same
+    model = tn.CostModel(hidden=32, seed=5)
+    for p in plans:
+        p.set_cost_model(model)
+    outs3 = [torch.zeros(64, dtype=torch.complex128, device="cuda") for _ in items]
+    tn.Batch(plans, outs3, n_streams=4).run(stream=s)
+    torch.cuda.synchronize()
+    for o, o3 in zip(outs, outs3):
+        assert np.array_equal(o.cpu().numpy(), o3.cpu().numpy())
 
 
 @pytest.mark.parametrize("min_log2_flops", [44, 40, 1])
