@@ -199,7 +199,8 @@ int tn_plan(const tn_circuit *circuit, const tn_query *query, const tn_plan_opts
  * the row the sample's bits select, through index arrays built here (the
  * sparse state of paper Sec. 3.4.2, on the gathering GEMMs).  The path is
  * planned twice, on the network with its output legs as legs and with them
- * fixed, and the cheaper resulting schedule is kept.  tn_contract fills 2^k
+ * fixed (each with at least 4 randomized greedy restarts), and the cheaper
+ * resulting schedule is kept.  tn_contract fills 2^k
  * amplitudes, entry s for bitstring s (entries past n_samples repeat the
  * last bitstring); slicing, slice batching and dtypes as for tn_plan
  * (slices run together x 2^k must stay within 2^24 rows).

@@ -748,6 +748,10 @@ int tn_plan_samples(const tn_circuit *circuit, const uint8_t *samples, int32_t n
         for (int view = 0; view < 2; ++view) {
             tn_plan_s *Q = new tn_plan_s();
             Q->opts = o;
+            // the all-open network defeats the noiseless greedy pass (30-qubit
+            // circuit, 4096 bitstrings: 1.6e18 flops against 1.6e15 with
+            // randomized restarts): at least 4 restarts per view
+            Q->opts.path_trials = std::max(o.path_trials, 4);
             std::string e;
             int r = build_network_open(circuit, &query, 64, Q->net, e);
             Network plan_net;
