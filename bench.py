@@ -261,6 +261,7 @@ def oracle_sample(seconds_target=15.0, max_gates=None, one_core=True):
         oracle.state_vector(sub)
         return time.perf_counter() - t
 
+    run(0)                               # first touch of the 16 GiB state, not timed
     t_init = run(0)                      # allocation + |0> initialisation
     probe = 8
     t_probe = run(probe) - t_init
@@ -270,6 +271,8 @@ def oracle_sample(seconds_target=15.0, max_gates=None, one_core=True):
         g = min(g, max_gates)
     t = run(g)
     per_gate = (t - t_init) / g
+    if per_gate <= 0:                    # noise above the work: bound it by the whole run
+        per_gate = t / g
     full = t_init + per_gate * c.n_gates
     # one core: two gates of the same circuit, scaled the same way
     full_1 = None
@@ -278,7 +281,8 @@ def oracle_sample(seconds_target=15.0, max_gates=None, one_core=True):
         try:
             t1_init = run(0)
             t1 = run(2)
-            full_1 = t1_init + (t1 - t1_init) / 2 * c.n_gates
+            per_gate_1 = (t1 - t1_init) / 2 if t1 > t1_init else t1 / 2
+            full_1 = t1_init + per_gate_1 * c.n_gates
         finally:
             oracle.set_threads(threads)
     return full, (f"FP64 state vector of the 30-qubit circuit (2^30 amplitudes, 16 GiB), first "
