@@ -17,7 +17,10 @@
  * and the small operand is padded to [[Re, -Im], [Im, Re]], so one real GEMM
  * with K -> 2K and N -> 2N does the complex product.  Post-selection keeps the
  * k most probable bitstrings of a correlated subspace (Sec. 1 and Sec. 2,
- * post-processing).
+ * post-processing).  Arbitrary (uncorrelated) bitstrings are planned by
+ * tn_plan_samples, whose last steps contract many gathered tensor pairs at
+ * once (Sec. 3.4.2, sparse state); tn_plan_opts.recompute_log2 splits output
+ * legs into sequential passes (Sec. 3.4.1, recomputation).
  *
  * Conventions
  *   - qubit q of a bitstring x is bit q of x;
