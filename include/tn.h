@@ -124,6 +124,13 @@ typedef struct {
                                  the slices of one part are contiguous.  The
                                  steps before the legs meet the path run once
                                  per call.  0: off; correlated plans only     */
+    int32_t no_scaling;       /* validation only.  1: complex-half tensors are
+                                 stored without their power-of-two scale (every
+                                 exponent 0, no calibration pass), which shows
+                                 what the scaling protects against: the small
+                                 values of deep intermediates fall into FP16's
+                                 subnormal range or flush to zero.  0: scaled
+                                 (default).  Not with fp8_min_log2_flops.     */
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *ctx);
@@ -237,6 +244,36 @@ int tn_plan_step(const tn_plan_t *plan, int32_t i, tn_step_info *out);
 int tn_plan_leaf_source(const tn_plan_t *plan, int32_t i, int32_t *gate, int32_t *qubit);
 
 /*
+ * tn_plan_leaf_tensor: leaf i (0 <= i < n_leaves) as the plan holds it on the
+ * host, before slicing: *rank legs, leg p (outermost first) being the wire of
+ * qubit[p] right after circuit gate after_gate[p] (the first min(capacity,
+ * rank) legs are written; qubit / after_gate may be NULL); data (host,
+ * nullable) receives its 2^rank complex128 values (interleaved re, im),
+ * row-major over the legs.  Errors: TN_EINVAL (NULL plan or rank, i out of
+ * range).
+ */
+int tn_plan_leaf_tensor(const tn_plan_t *plan, int32_t i, int32_t capacity, int32_t *rank,
+                        int32_t *qubit, int32_t *after_gate, double *data);
+
+/*
+ * tn_plan_decode_leaf: slice decoding of one leaf, as tn_contract does it on
+ * the device (Sec. 3.1: a slice fixes the values of the sliced edges; bit j
+ * of the slice id is the value of sliced edge j, LSB first).  Runs the plan's
+ * leaf preparation of leaf i for the pass starting at slice_id (a multiple
+ * of 2^slice_batch_log2 below n_slices) and copies the prepared sub-tensor to
+ * `data` (host, 2^rank complex64, interleaved re, im; nullable: legs only).
+ * Its legs are the leaf's legs minus the sliced edges the pass fixes (edges
+ * run as slice-batch modes stay legs), in the order the schedule lays them
+ * out: leg q (outermost first) is the wire of qubit[q] after gate
+ * after_gate[q].  The values are the leaf's complex128 values rounded to
+ * complex64 (round to nearest even).  Synchronizes `stream`; sets up the
+ * plan's device state if no tn_contract has run.  Errors: TN_EINVAL (NULL
+ * plan or rank, i or slice_id out of range), TN_ENOMEM, TN_ECUDA.
+ */
+int tn_plan_decode_leaf(tn_plan_t *plan, int64_t slice_id, int32_t i, int32_t capacity, int32_t *rank,
+                        int32_t *qubit, int32_t *after_gate, float *data, void *stream);
+
+/*
  * tn_contract: contract slices [slice_begin, slice_begin + slice_count) and
  * add (accumulate != 0) or write (accumulate == 0) their FP64 sum into d_amps
  * (device, 2^n_open complex128, caller-owned).  Slices are summed in
@@ -332,6 +369,21 @@ int tn_sample_noalloc(const double *d_amps, int32_t n_open, int32_t k, int64_t *
  */
 int tn_metrics(const double *d_amps, const double *d_ref, int64_t n, int32_t n_qubits,
                double *out, void *stream);
+
+/*
+ * tn_plan_step_scale: the power-of-two scale state of step i's output after
+ * the last tn_contract pass of a complex-half plan (validation of the
+ * per-tensor scaling).  *exp (nullable) = the output's exponent E, stored
+ * value = true value x 2^E (E adds the exponents of the operands and the
+ * step's own e); *stored_max (nullable) = the largest |re| or |im| of the
+ * values stored in that pass.  With scaling on, e is chosen on the device so
+ * that 2 K max|A| max|B| 2^e <= 2^14, plus a headroom that the first call's
+ * calibration pass fixes per step: on that pass every complex-half output's
+ * stored_max lies in (2^11, 2^14], and in (2^11, 2^12] for steps given a
+ * headroom.  Synchronizes the device.  Errors: TN_EINVAL (NULL, i out of
+ * range, complex64 plan, no tn_contract yet), TN_ECUDA.
+ */
+int tn_plan_step_scale(tn_plan_t *plan, int32_t i, int32_t *exp, float *stored_max);
 
 void tn_plan_destroy(tn_plan_t *plan);
 

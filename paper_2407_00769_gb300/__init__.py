@@ -33,7 +33,7 @@ TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 EXPORTED = [
     "tn_plan", "tn_plan_samples", "tn_plan_opts_default", "tn_plan_info", "tn_plan_sliced_edges",
     "tn_plan_step",
-    "tn_plan_leaf_source",
+    "tn_plan_leaf_source", "tn_plan_leaf_tensor", "tn_plan_decode_leaf", "tn_plan_step_scale",
     "tn_contract", "tn_contract_host", "tn_contract_batch", "tn_sample", "tn_metrics",
     "tn_plan_destroy", "tn_permute", "tn_gemm", "tn_strerror", "tn_last_error",
     "tn_profile", "tn_profile_read", "tn_sample_noalloc", "tn_selftest_wait_timeout",
@@ -82,6 +82,7 @@ class PlanOpts(ctypes.Structure):
                 ("no_tensor_cores", ctypes.c_int32),
                 ("fp8_min_log2_flops", ctypes.c_int32),
                 ("recompute_log2", ctypes.c_int32),
+                ("no_scaling", ctypes.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -157,6 +158,11 @@ def lib():
         L.tn_plan_sliced_edges.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), i32]
         L.tn_plan_step.argtypes = [vp, i32, ctypes.POINTER(StepInfo)]
         L.tn_plan_leaf_source.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.tn_plan_leaf_tensor.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                          ctypes.POINTER(i32), vp]
+        L.tn_plan_decode_leaf.argtypes = [vp, i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                          ctypes.POINTER(i32), vp, vp]
+        L.tn_plan_step_scale.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
         L.tn_contract.argtypes = [vp, i64, i64, vp, ctypes.c_int, vp, ctypes.POINTER(ContractReport)]
         L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp, ctypes.POINTER(ContractReport)]
         L.tn_contract_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
@@ -279,7 +285,7 @@ class Plan:
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
                  no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
-                 recompute_log2: int = 0, _samples=None):
+                 recompute_log2: int = 0, no_scaling: bool = False, _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         if _samples is None:
@@ -298,6 +304,7 @@ class Plan:
         opts.no_tensor_cores = 1 if no_tensor_cores else 0
         opts.fp8_min_log2_flops = int(fp8_min_log2_flops)
         opts.recompute_log2 = int(recompute_log2)
+        opts.no_scaling = 1 if no_scaling else 0
         self._alloc = None
         if torch_allocator:
             self._alloc = _TorchAllocator()
@@ -363,6 +370,41 @@ class Plan:
             _check(lib().tn_plan_leaf_source(self._h, i, ctypes.byref(g), ctypes.byref(q)))
             out.append((g.value, q.value))
         return out
+
+    def leaf_tensor(self, i: int):
+        """Leaf i before slicing: ([(qubit, after_gate) per leg], complex128
+        array of shape (2,) * rank)."""
+        L = lib()
+        r = ctypes.c_int32(0)
+        _check(L.tn_plan_leaf_tensor(self._h, int(i), 0, ctypes.byref(r), None, None, None))
+        n = r.value
+        q = (ctypes.c_int32 * max(1, n))()
+        g = (ctypes.c_int32 * max(1, n))()
+        data = np.zeros(1 << n, dtype=np.complex128)
+        _check(L.tn_plan_leaf_tensor(self._h, int(i), n, ctypes.byref(r), q, g, data.ctypes.data))
+        return [(int(q[p]), int(g[p])) for p in range(n)], data.reshape((2,) * n)
+
+    def decode_leaf(self, slice_id: int, i: int, stream=None):
+        """Leaf i as the device prepares it for the pass at slice_id (slice
+        decoding): ([(qubit, after_gate) per kept leg], complex64 array)."""
+        L = lib()
+        r = ctypes.c_int32(0)
+        _check(L.tn_plan_decode_leaf(self._h, int(slice_id), int(i), 0, ctypes.byref(r), None, None,
+                                     None, None))
+        n = r.value
+        q = (ctypes.c_int32 * max(1, n))()
+        g = (ctypes.c_int32 * max(1, n))()
+        data = np.zeros(1 << n, dtype=np.complex64)
+        _check(L.tn_plan_decode_leaf(self._h, int(slice_id), int(i), n, ctypes.byref(r), q, g,
+                                     data.ctypes.data, _stream_ptr(stream)))
+        return [(int(q[p]), int(g[p])) for p in range(n)], data.reshape((2,) * n)
+
+    def step_scale(self, i: int):
+        """(exponent E, stored max) of step i's output after the last pass."""
+        e = ctypes.c_int32(0)
+        m = ctypes.c_float(0)
+        _check(lib().tn_plan_step_scale(self._h, int(i), ctypes.byref(e), ctypes.byref(m)))
+        return e.value, m.value
 
     def steps(self):
         out = []
@@ -615,12 +657,23 @@ class Batch:
             self._h = None
 
 
-def sample(amps, k: int = 1, stream=None):
-    """Top-k post-selection: (indices, probabilities) as numpy arrays."""
+def _amps_log2(amps, name="amps") -> int:
+    """log2 of the length of a contiguous CUDA complex128 amplitude tensor
+    (the kernels read it as 2^n double2 values at its device address)."""
+    torch = _torch()
+    if not isinstance(amps, torch.Tensor) or amps.dtype != torch.complex128 or not amps.is_cuda \
+            or not amps.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA complex128 tensor")
     n = amps.numel()
     n_open = n.bit_length() - 1
-    if (1 << n_open) != n:
-        raise ValueError("amplitude count must be a power of two")
+    if n < 1 or (1 << n_open) != n:
+        raise ValueError(f"{name}: amplitude count must be a power of two")
+    return n_open
+
+
+def sample(amps, k: int = 1, stream=None):
+    """Top-k post-selection: (indices, probabilities) as numpy arrays."""
+    n_open = _amps_log2(amps)
     idx = np.zeros(k, dtype=np.int64)
     prob = np.zeros(k, dtype=np.float64)
     _check(lib().tn_sample(amps.data_ptr(), n_open, int(k), idx.ctypes.data, prob.ctypes.data,
@@ -630,10 +683,7 @@ def sample(amps, k: int = 1, stream=None):
 
 def sample_noalloc(amps, k: int = 1, stream=None):
     """tn_sample without device allocation (k <= 1024; see include/tn.h)."""
-    n = amps.numel()
-    n_open = n.bit_length() - 1
-    if (1 << n_open) != n:
-        raise ValueError("amplitude count must be a power of two")
+    n_open = _amps_log2(amps)
     idx = np.zeros(k, dtype=np.int64)
     prob = np.zeros(k, dtype=np.float64)
     _check(lib().tn_sample_noalloc(amps.data_ptr(), n_open, int(k), idx.ctypes.data,
@@ -642,6 +692,12 @@ def sample_noalloc(amps, k: int = 1, stream=None):
 
 
 def metrics(amps, ref=None, n_qubits: int = 0, stream=None) -> dict:
+    """FP64 norm, rel-L2, fidelity and linear XEB of amps against ref (tn_metrics)."""
+    _amps_log2(amps)
+    if ref is not None:
+        _amps_log2(ref, "ref")
+        if ref.numel() != amps.numel():
+            raise ValueError("ref must have as many amplitudes as amps")
     out = np.zeros(4, dtype=np.float64)
     _check(lib().tn_metrics(amps.data_ptr(), ref.data_ptr() if ref is not None else None,
                             int(amps.numel()), int(n_qubits), out.ctypes.data,
@@ -658,6 +714,15 @@ def permute(x, perm, out=None, elem_bytes=None, stream=None):
         out = torch.empty_like(x)
     if elem_bytes is None:
         elem_bytes = 8 if x.dtype in (torch.complex64, torch.int64, torch.float64) else 4
+    if elem_bytes not in (4, 8):
+        raise ValueError("elem_bytes must be 4 or 8")
+    for t, name in ((x, "x"), (out, "out")):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.numel() * t.element_size() != elem_bytes << r:
+            raise ValueError(f"{name} must hold exactly 2^rank elements of elem_bytes bytes")
+    if sorted(int(v) for v in perm) != list(range(r)):
+        raise ValueError("perm must be a permutation of 0..rank-1")
     p = (ctypes.c_int32 * max(1, r))(*[int(v) for v in perm])
     _check(lib().tn_permute(x.data_ptr(), out.data_ptr(), r, p, int(elem_bytes),
                             _stream_ptr(stream)))

@@ -192,7 +192,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             e = launch_bprep_perm(ws + op.bprep.src, ws + op.bprep.dst, op.bprep.rank, op.bprep.perm,
                                   op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, op.bprep.tb, dtype,
                                   P->d_stepcorr + op.bprep.step, P->d_tmax, P->d_texp, op.bprep.meta_src,
-                                  op.bprep.meta_dst, s);
+                                  op.bprep.meta_dst, s, P->opts.no_scaling ? 1 : 0);
             ++launches;
             break;
         case OP_GEMM: {
@@ -212,6 +212,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             sr.out_max = P->d_tmax + g.meta_c;
             sr.headroom = g.headroom;
             sr.err = P->d_err;
+            sr.scale_off = P->opts.no_scaling ? 1 : 0;
             switch (g.kernel) {
                 case GK_C64_ROWS:
                     e = launch_gemm_rows_c64((const float2 *)(ws + g.a), (const float2 *)(ws + g.b),
@@ -368,8 +369,11 @@ int time_op(tn_plan_s *P, const Op &op, int64_t slice_base, cudaStream_t s, doub
 // coherently; random-phase sums grow like sqrt(K), so large-K outputs land far
 // below the top of the FP16 range and their small entries lose precision.
 // Run slice 0's pass once: after each GEMM read the stored maximum and, if it
-// is below 2^12, raise that step's exponent (headroom) so the maximum lands in
-// [2^12, 2^13) (16x below the FP16 limit), re-run it, and go on.  The
+// is below 2^12, raise that step's exponent by the largest headroom h that
+// keeps it at or below 2^12 (so it lands in (2^11, 2^12], 16x below the FP16
+// limit), re-run it, and go on.  Outputs already at or above 2^12 keep the
+// bound's exponent, which caps them at 2^14.  So on the calibration pass every
+// complex-half GEMM output's stored maximum lies in (2^11, 2^14].  The
 // headrooms are then fixed, so later calls stay deterministic.
 int calibrate_plan(tn_plan_s *P, cudaStream_t s) {
     Schedule &S = P->sched;
@@ -598,6 +602,9 @@ int check_opts(const tn_plan_opts &o) {
     if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
     if (o.path_anneal_iters < 0) return fail(TN_EINVAL, "path_anneal_iters must be >= 0");
     if (o.recompute_log2 < 0 || o.recompute_log2 > 8) return fail(TN_EINVAL, "recompute_log2 must be in 0..8");
+    if (o.no_scaling != 0 && o.no_scaling != 1) return fail(TN_EINVAL, "no_scaling must be 0 or 1");
+    if (o.no_scaling && o.fp8_min_log2_flops > 0)
+        return fail(TN_EINVAL, "no_scaling does not apply to E4M3 steps (their scale is their range)");
     if (o.n_slice_edges < 0 && o.max_log2_elems <= 0)
         return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0");
     return TN_OK;
@@ -869,6 +876,79 @@ int tn_plan_step(const tn_plan_t *P, int32_t i, tn_step_info *out) {
     return TN_OK;
 }
 
+int tn_plan_step_scale(tn_plan_t *P, int32_t i, int32_t *exp, float *stored_max) {
+    if (!P || (!exp && !stored_max)) return fail(TN_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)P->sched.steps.size()) return fail(TN_EINVAL, "step index out of range");
+    if (P->opts.dtype == TN_C64) return fail(TN_EINVAL, "complex64 plans keep no scale state");
+    if (!P->dev_ready) return fail(TN_EINVAL, "no tn_contract call has run on this plan");
+    int dev = 0;
+    TN_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != P->device) return fail(TN_EINVAL, "plan was set up on another device");
+    int meta = -1;
+    for (const Op &op : P->sched.ops)
+        if (op.kind == OP_GEMM && op.gemm.step == i) meta = op.gemm.meta_c;
+    if (meta < 0) return fail(TN_EINVAL, "step has no GEMM");
+    TN_CUDA(cudaDeviceSynchronize(), "sync");
+    if (exp) TN_CUDA(cudaMemcpy(exp, P->d_texp + meta, 4, cudaMemcpyDeviceToHost), "read exponent");
+    if (stored_max) TN_CUDA(cudaMemcpy(stored_max, P->d_tmax + meta, 4, cudaMemcpyDeviceToHost), "read max");
+    return TN_OK;
+}
+
+int tn_plan_leaf_tensor(const tn_plan_t *P, int32_t i, int32_t capacity, int32_t *rank, int32_t *qubit,
+                        int32_t *after_gate, double *data) {
+    if (!P || !rank) return fail(TN_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)P->net.leaves.size()) return fail(TN_EINVAL, "leaf index out of range");
+    const Leaf &lf = P->net.leaves[i];
+    *rank = (int32_t)lf.legs.size();
+    for (int p = 0; p < (int)lf.legs.size() && p < capacity; ++p) {
+        const Edge &e = P->net.edges[lf.legs[p]];
+        if (qubit) qubit[p] = e.qubit;
+        if (after_gate) after_gate[p] = e.after_gate;
+    }
+    if (data)
+        for (size_t x = 0; x < lf.data.size(); ++x) {
+            data[2 * x] = lf.data[x].real();
+            data[2 * x + 1] = lf.data[x].imag();
+        }
+    return TN_OK;
+}
+
+int tn_plan_decode_leaf(tn_plan_t *P, int64_t slice_id, int32_t i, int32_t capacity, int32_t *rank,
+                        int32_t *qubit, int32_t *after_gate, float *data, void *stream) {
+    if (!P || !rank) return fail(TN_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)P->net.leaves.size()) return fail(TN_EINVAL, "leaf index out of range");
+    const int64_t n_slices = (int64_t)1 << P->sliced.size();
+    const int64_t bsize = (int64_t)1 << P->batch_log2;
+    if (slice_id < 0 || slice_id >= n_slices || slice_id % bsize != 0)
+        return fail(TN_EINVAL, "slice_id must be a pass base (a multiple of 2^slice_batch_log2) below n_slices");
+    int k = -1;
+    for (size_t j = 0; j < P->sched.leaf_jobs.size(); ++j)
+        if (P->sched.leaf_jobs[j].src == P->leaf_offset[i]) k = (int)j;
+    if (k < 0) return fail(TN_EINVAL, "leaf has no preparation job");
+    const LeafJob &job = P->sched.leaf_jobs[k];
+    const Leaf &lf = P->net.leaves[i];
+    *rank = job.rank_out;
+    for (int q = 0; q < job.rank_out && q < capacity; ++q) {
+        // leg q (outermost first) is output bit rank_out-1-q; keep_pos gives
+        // its bit in the full leaf, whose leg p sits at bit rank_in-1-p
+        const int p = job.rank_in - 1 - job.keep_pos[job.rank_out - 1 - q];
+        const Edge &e = P->net.edges[lf.legs[p]];
+        if (qubit) qubit[q] = e.qubit;
+        if (after_gate) after_gate[q] = e.after_gate;
+    }
+    if (!data) return TN_OK;
+    int rc = ensure_device(P);
+    if (rc != TN_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    TN_CUDA(launch_leaf_prep(P->d_jobs + k, 1, P->d_store, P->d_ws, P->opts.dtype, slice_id, P->d_tmax,
+                             P->d_texp, s),
+            "leaf preparation");
+    TN_CUDA(cudaMemcpyAsync(data, P->d_ws + job.dst, (size_t)8 << job.rank_out, cudaMemcpyDeviceToHost, s),
+            "read prepared leaf");
+    TN_CUDA(cudaStreamSynchronize(s), "sync");
+    return TN_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -1031,7 +1111,7 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
     int rc = ensure_device(P);
     if (rc != TN_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!P->calibrated && P->opts.dtype != TN_C64 && P->prof_mask == 0) {
+    if (!P->calibrated && P->opts.dtype != TN_C64 && P->prof_mask == 0 && !P->opts.no_scaling) {
         rc = calibrate_plan(P, s);
         if (rc != TN_OK) return rc;
     }

@@ -54,7 +54,7 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
     if (!A || !B || !C) return fail(TN_EINVAL, "NULL operand");
     auto lg = [](int64_t v) {
         int l = 0;
-        while (((int64_t)1 << l) < v) ++l;
+        while (l < 62 && ((int64_t)1 << l) < v) ++l;
         return (((int64_t)1 << l) == v) ? l : -1;
     };
     const int lm = lg(M), ln = lg(N), lk = lg(K);
@@ -203,7 +203,6 @@ int tn_gemm_gather(int32_t dtype, const void *A, int64_t m_a, const void *B, int
         }
     }
     if (out_m_r) *out_m_r = m_r;
-    if (T > 65535 * 65535LL) return fail(TN_EINVAL, "too many chunk pairs");
     cudaStream_t s = (cudaStream_t)stream;
     const int np = std::max(16, (int)(2 * N));
     int32_t *dz = nullptr;

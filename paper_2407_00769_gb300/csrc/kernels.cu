@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
                                                          int lb, int np,
                                                          const __grid_constant__ PermParams p,
                                                          int rank, double2 *corr, float *tmax,
-                                                         int32_t *texp, int meta_src, int meta_dst) {
+                                                         int32_t *texp, int meta_src, int meta_dst,
+                                                         int scale_off) {
     using L = LpT<DT>;
     const int K = 1 << lk, N = 1 << ln;
     const int64_t total = ((int64_t)np * K) << lb;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
     int bshift = 0;
     {
         const float mb = tmax[meta_src];
-        if (mb > 0.0f && isfinite(mb)) {
+        if (!scale_off && mb > 0.0f && isfinite(mb)) {
             int x;
             const float f = frexpf(mb, &x);
             bshift = 12 - ((f == 0.5f) ? x - 1 : x);
@@ -474,7 +475,8 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
 
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
                               int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
-                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s) {
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s,
+                              int scale_off) {
     const ExpandArgs ex{lk, ln, np};
     // direct-gather table: outer_in[t] = input bit position of target bit t
     PermParams g;
@@ -483,10 +485,12 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
     if (tb == 0) {
         if (dtype == TN_F16)
             bprep_c64_kernel<TN_F16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,
-                                                        np, g, rank, corr, tmax, texp, meta_src, meta_dst);
+                                                        np, g, rank, corr, tmax, texp, meta_src, meta_dst,
+                                                        scale_off);
         else
             bprep_c64_kernel<TN_BF16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,
-                                                         np, g, rank, corr, tmax, texp, meta_src, meta_dst);
+                                                         np, g, rank, corr, tmax, texp, meta_src, meta_dst,
+                                                        scale_off);
         return cudaGetLastError();
     }
     if (rank >= 10 && lk >= 2 && np == 2 << ln) {
@@ -625,7 +629,8 @@ __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     } else {
         // power-of-two scaling (exact): e from the operands' recorded maxima
         int e;
-        if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
+        if (sr.scale_off) e = 0;
+        else if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
         else e = sr.fixed_exp;
         if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
             sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
@@ -960,7 +965,8 @@ __global__ void splitk_reduce_kernel(const float2 *__restrict__ partial, int spl
                                      int64_t n, int lk, ScaleRef sr) {
     int e = 0;
     if (!OUT_C64) {
-        if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
+        if (sr.scale_off) e = 0;
+        else if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
         else e = sr.fixed_exp;
     }
     if (sr.texp && blockIdx.x == 0 && threadIdx.x == 0)

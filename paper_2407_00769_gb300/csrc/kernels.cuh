@@ -36,6 +36,7 @@ struct ScaleRef {          // power-of-two scaling state (complex-half)
     float *out_max;        // where the epilogue records max |C| (atomicMax)
     int32_t headroom;      // added to the bound-based exponent (calibrated per step)
     int32_t *err;          // bit 2 set when a stored value overflowed (inf)
+    int32_t scale_off;     // 1: every exponent e = 0 (tn_plan_opts.no_scaling)
 };
 
 cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_store, char *ws,
@@ -64,9 +65,11 @@ cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int
 // and B is first scaled by an exact 2^s that brings its recorded maximum
 // (tmax[meta_src]) near 2^12; B' gets tmax[meta_dst] and texp[meta_dst] =
 // texp[meta_src] + s.
+// scale_off = 1: no 2^s (s = 0; tn_plan_opts.no_scaling).
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
                               int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
-                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s);
+                              int32_t *texp, int meta_src, int meta_dst, cudaStream_t s,
+                              int scale_off = 0);
 cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
                                    void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
                                    int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,

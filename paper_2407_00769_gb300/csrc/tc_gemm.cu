@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
         const int half = (warp - 2) >> 2;       // which alternate 16-column chunks
         const int row = q * 32 + lane;
         int e;
-        if (args.out_c64)
+        if (args.out_c64 || args.sr.scale_off)
             e = 0;
         else if (args.sr.tmax)
             e = min(120, scale_exp_tc(args.sr.tmax[args.sr.meta_a], args.sr.tmax[args.sr.meta_b], args.lk) +

@@ -2,10 +2,15 @@
 oracle (state vector; per-slice values from wire projectors).
 
 Tolerances: complex64 path rel-L2 <= 1e-5; complex-half (FP16) path
-rel-L2 <= 5e-3 and fidelity >= 0.999.  BF16 keeps 8 mantissa bits (unit
-roundoff 2^-8 vs 2^-11): over ~50 dependent roundings it was predicted to
-miss 5e-3, and measures 6e-2 on the 30-qubit workload; it is held to a
-measured-level bound of 1e-1 (fidelity >= 0.99) and reported."""
+rel-L2 <= 5e-3 and fidelity >= 0.999.  BF16 keeps 8 significand bits
+against FP16's 11 (unit roundoff 2^-8 against 2^-11), and the error of this
+path is set by the roundings of stored tensors, so it scales with the unit
+roundoff: FP16 measures 9.8e-4 on the 30-qubit workload, which predicts
+8 x 9.8e-4 = 7.8e-3 for BF16 (measured 6.5e-3 to 7.7e-3; 9.4e-3 on the
+53-qubit slice).  BF16 therefore misses the 5e-3 budget, as predicted, and
+is held to 2e-2: the predicted error with a 2.5x margin for the deeper
+circuits.  At rel-L2 <= 2e-2, 1 - fidelity <= rel-L2^2 = 4e-4, so BF16 is
+also held to fidelity >= 0.999."""
 import os
 
 import numpy as np
@@ -19,7 +24,7 @@ import paper_2407_00769_gb300 as tn  # noqa: E402
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
-TOL = {tn.C64: 1e-5, tn.F16: 5e-3, tn.BF16: 1e-1}
+TOL = {tn.C64: 1e-5, tn.F16: 5e-3, tn.BF16: 2e-2}
 
 
 def check(got, want, dtype):
@@ -30,7 +35,7 @@ def check(got, want, dtype):
     if dtype == tn.F16:
         assert f >= 0.999, f
     if dtype == tn.BF16:
-        assert f >= 0.99, f
+        assert f >= 0.999, f
     return e, f
 
 

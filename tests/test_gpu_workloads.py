@@ -80,7 +80,7 @@ def _read_plan(path):
     return edges, leaves, steps
 
 
-@pytest.mark.parametrize("dtype,batch,tol", [(tn.C64, 0, 1e-5), (tn.F16, 3, 5e-3), (tn.BF16, 3, 1e-1)])
+@pytest.mark.parametrize("dtype,batch,tol", [(tn.C64, 0, 1e-5), (tn.F16, 3, 5e-3), (tn.BF16, 3, 2e-2)])
 def test_grid53_slice0_against_network_oracle(dtype, batch, tol):
     want = _read_amps(os.path.join(GOLD53, "grid53_slice0.txt"))
     edges, _, steps = _read_plan(os.path.join(GOLD53, "grid53_plan.txt"))
@@ -95,7 +95,7 @@ def test_grid53_slice0_against_network_oracle(dtype, batch, tol):
     rel = oracle.rel_l2(got, want)
     print(f"53-qubit slice 0, {tn.DTYPE_NAMES[dtype]}: rel-L2 {rel:.2e} vs FP64 network oracle")
     assert rel <= tol
-    assert oracle.fidelity(want, got) >= (0.99 if dtype == tn.BF16 else 0.999)
+    assert oracle.fidelity(want, got) >= 0.999
 
 
 def _golden(i):
