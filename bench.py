@@ -244,85 +244,81 @@ def read_golden(name="grid5x6_14c_amps.txt"):
 
 
 # ------------------------------------------------------------- oracle leg
-def oracle_sample(seconds_target=15.0, max_gates=None, one_core=True):
-    """Time the FP64 state-vector oracle on a bounded prefix of the 30-qubit
-    circuit; return (estimated seconds for the whole circuit, sample text,
-    threads)."""
-    import numpy as np
-    import oracle
-    import rqcgen
-    c, _ = rqcgen.grid_30q()
-    oracle.build()
-    threads = oracle.threads()
+GRID30_PLAN = os.path.join(ROOT, "tests", "golden", "grid30_plan.txt")
 
-    def run(g):
-        sub = rqcgen.Circuit(c.n_qubits, c.q0[:g], c.q1[:g], c.mats[:g])
-        t = time.perf_counter()
-        oracle.state_vector(sub)
-        return time.perf_counter() - t
 
-    run(0)                               # first touch of the 16 GiB state, not timed
-    t_init = run(0)                      # allocation + |0> initialisation
-    probe = 8
-    t_probe = run(probe) - t_init
-    per_gate = max(t_probe / probe, 1e-6)
-    g = int(max(probe, min(c.n_gates, (seconds_target - t_init) / per_gate)))
-    if max_gates:
-        g = min(g, max_gates)
-    t = run(g)
-    per_gate = (t - t_init) / g
-    if per_gate <= 0:                    # noise above the work: bound it by the whole run
-        per_gate = t / g
-    full = t_init + per_gate * c.n_gates
-    # one core: two gates of the same circuit, scaled the same way
-    full_1 = None
-    if one_core:
-        oracle.set_threads(1)
+def _blas_threads():
+    """Threads of the BLAS that numpy's tensordot runs on (OpenBLAS's own
+    count, read from the loaded library), else the host's core count."""
+    import ctypes
+    try:
+        libs = {ln.split()[-1] for ln in open("/proc/self/maps") if "openblas" in ln.lower()}
+    except OSError:
+        libs = set()
+    for path in sorted(libs):
         try:
-            t1_init = run(0)
-            t1 = run(2)
-            per_gate_1 = (t1 - t1_init) / 2 if t1 > t1_init else t1 / 2
-            full_1 = t1_init + per_gate_1 * c.n_gates
-        finally:
-            oracle.set_threads(threads)
-    return full, (f"FP64 state vector of the 30-qubit circuit (2^30 amplitudes, 16 GiB), first "
-                  f"{g} of {c.n_gates} gates timed ({t:.1f} s), scaled to all gates"), threads, full_1
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for name in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_",
+                     "openblas_get_num_threads", "scipy_openblas_get_num_threads"):
+            if hasattr(lib, name):
+                return int(getattr(lib, name)())
+    return os.cpu_count() or 1
+
+
+def oracle_slices(n_samples=1, first=0):
+    """Time the FP64 network oracle (oracle/tn.py) on whole slices of the
+    benchmark job: slice s of the 256 is contracted along the benchmark
+    plan's own merge order with its sliced edges fixed (the path, the edges
+    and the plan's flop counts are data in tests/golden/grid30_plan.txt, so
+    the library is not loaded).  Every slice has the same shapes and flops;
+    the job is the sum of all 256.  Returns (seconds per slice, samples,
+    flops record, threads)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import numpy as np  # noqa: F401  (loads the BLAS before counting threads)
+    import dump_plan
+    import rqcgen
+    from oracle import tn as otn
+    c, q = rqcgen.grid_30q()
+    edges, leaves, steps, flops = dump_plan.read(GRID30_PLAN, with_flops=True)
+    keys = [("g", g) if g >= 0 else ("q", qq) for g, qq in leaves]
+    n_slices = 1 << len(edges)
+    times = []
+    for i in range(n_samples):
+        sid = (first + i) % n_slices
+        t = time.perf_counter()
+        otn.contract(c, q, keys, steps, fixed=otn.slice_fixed(edges, sid))
+        times.append(time.perf_counter() - t)
+    return times, n_slices, flops, _blas_threads()
 
 
 def reference_arm(args):
+    """The FP64 oracle on the host cores, same metric and workload.  Each
+    step contracts one whole slice of the 256 (a bounded sample of the job:
+    all slices cost the same); the job time is 256 x the measured slice time
+    and the rate is the job's plan flops over it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    import oracle
-    import rqcgen
-    import paper_2407_00769_gb300 as tn
-    c, q = rqcgen.grid_30q()
-    plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
-                   slice_batch_log2=args.slice_batch, torch_allocator=False)
-    info = plan.info()
-    job_flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
-    oracle.build()
-    per_step = []
-    gates_per_step = None
-    sub_t = None
-    for i in range(args.warmup + args.steps):
-        full, sample, threads, _ = oracle_sample(seconds_target=8.0, max_gates=gates_per_step,
-                                                 one_core=False)
-        if i >= args.warmup:
-            per_step.append(full)
-        sub_t = sample
-    est = statistics.mean(per_step)
-    value = job_flops / est / 1e12
+    times, n_slices, flops, threads = oracle_slices(args.warmup + args.steps)
+    per_slice = statistics.mean(times[args.warmup:])
+    job_s = per_slice * n_slices
+    job_flops = flops["job"]
+    value = job_flops / job_s / 1e12
+    sample = (f"FP64 network oracle (numpy tensordot, {threads} BLAS threads): one whole slice of the "
+              f"{n_slices} per step along the benchmark plan's path, slices 0..{len(times) - 1}; "
+              f"job time = {n_slices} x measured slice time ({per_slice:.2f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "strong",
+            "ms_per_step": per_slice * 1e3, "step": f"one slice (1/{n_slices} of the job)",
+            "ms_per_job": job_s * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "slices": info["n_slices"],
-                       "flops_per_job": job_flops},
-            "slices_per_s": info["n_slices"] / est,
+            "config": {"workload": WORKLOAD, "slices": n_slices, "flops_per_job": job_flops,
+                       "flops_source": "tests/golden/grid30_plan.txt (planner's 8 M N K sums)"},
+            "slices_per_s": 1.0 / per_slice,
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads,
-                             "kind": "oracle", "sample": sub_t},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line, default=_plain), flush=True)
@@ -809,7 +805,9 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    job_flops = info["flops_per_slice"] * n_slices + info["flops_invariant"] * world
+    # the job's work, each slice-invariant step counted once however many
+    # ranks repeat it
+    job_flops = info["flops_per_slice"] * n_slices + info["flops_invariant"]
     launches_per_step = sum(v["launches"] for v in prof.values()) + 1
 
     # accuracy of the timed path against the FP64 reference amplitudes
@@ -1012,13 +1010,16 @@ def main():
         line["recompute"] = leg_recompute(tn, torch, dev, flush, stream)
 
     if not args.no_cpu_baseline and world == 1:
-        full, sample, threads, full_1 = oracle_sample()
-        line["cpu_baseline"] = {"value": job_flops / full / 1e12, "unit": "TFLOP/s",
-                                "cores": threads, "kind": "oracle", "sample": sample,
-                                "est_seconds_per_step": full,
-                                "one_core": {"value": job_flops / full_1 / 1e12,
-                                             "est_seconds_per_step": full_1,
-                                             "sample": "first 2 gates on 1 thread, scaled"}}
+        # one untimed slice first (imports, first touch), then two timed
+        times, n_sl, fl, threads = oracle_slices(3)
+        per_slice = statistics.mean(times[1:])
+        line["cpu_baseline"] = {
+            "value": fl["job"] / (per_slice * n_sl) / 1e12, "unit": "TFLOP/s", "cores": threads,
+            "kind": "oracle",
+            "sample": (f"FP64 network oracle (numpy tensordot): slices 1 and 2 of the {n_sl}, each "
+                       f"contracted whole along the benchmark plan's path ({per_slice:.2f} s per "
+                       f"slice); job time = {n_sl} x slice time"),
+            "seconds_per_slice": per_slice, "est_seconds_per_job": per_slice * n_sl}
     print(json.dumps(line, default=_plain), flush=True)
     if world > 1:
         dist.barrier()

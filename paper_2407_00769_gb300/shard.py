@@ -3,9 +3,11 @@
 Slices are independent sub-networks (paper Sec. 3.1, global level), so rank r
 of N contracts the contiguous range ``slice_range(r, N, S)`` with no data
 exchange, and the FP64 partial amplitude vectors are summed once at the end
-(``allreduce_amplitudes``, an NCCL or gloo all-reduce).  Because a slice range
-is idempotent, a range that a failed rank never delivered can simply be
-contracted again by a surviving rank: ``collect_partials`` publishes each
+(``allreduce_amplitudes``: every rank gathers all partials, at most 2^12
+complex128 each, and adds them in rank order, so every rank holds the same
+bits, equal to the single-process sum of the same partials in the same
+order).  Because a slice range is idempotent, a range that a failed rank
+never delivered can simply be contracted again by a surviving rank: ``collect_partials`` publishes each
 rank's partial sum through a torch.distributed store, rank 0 waits for them
 with a deadline and reports the ranges that never arrived.
 """
@@ -49,13 +51,35 @@ def uncovered(n_slices: int, done: Sequence[Tuple[int, int]]) -> List[Tuple[int,
 
 
 def allreduce_amplitudes(amps, group=None):
-    """Sum complex128 amplitude tensors over all ranks, in place."""
+    """Sum complex128 amplitude tensors over all ranks, in place, in fixed
+    rank order: the partials are all-gathered (one collective) and every rank
+    adds them as ((p_0 + p_1) + p_2) + ...  An all-reduce would leave the
+    order of the additions to the collective's algorithm; this order makes
+    the result bit-identical on every rank, from run to run and to the
+    ordered sum ``ordered_sum`` of the same partials in one process."""
     import torch
     import torch.distributed as dist
     if amps.dtype != torch.complex128:
         raise ValueError("amplitudes must be complex128")
-    dist.all_reduce(torch.view_as_real(amps), group=group)
+    if not amps.is_contiguous():
+        raise ValueError("amplitudes must be contiguous")
+    world = dist.get_world_size(group)
+    flat = torch.view_as_real(amps).reshape(-1)
+    parts = [torch.empty_like(flat) for _ in range(world)]
+    dist.all_gather(parts, flat, group=group)
+    flat.copy_(parts[0])
+    for p in parts[1:]:
+        flat.add_(p)
     return amps
+
+
+def ordered_sum(partials):
+    """The rank-ordered sum that ``allreduce_amplitudes`` computes, for
+    partials held in one process (a list of complex128 arrays)."""
+    total = np.array(partials[0], dtype=np.complex128, copy=True)
+    for p in partials[1:]:
+        total += np.asarray(p, dtype=np.complex128)
+    return total
 
 
 def publish_partial(store, rank: int, rng: Tuple[int, int], partial: np.ndarray) -> None:

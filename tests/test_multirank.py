@@ -48,15 +48,24 @@ def _worker_allreduce(rank, world, port, outdir):
     dist.destroy_process_group()
 
 
-def test_two_rank_allreduce_equals_full():
+@pytest.mark.parametrize("world", [2, 3])
+def test_allreduce_equals_full_and_is_rank_ordered(world):
     port = _free_port()
     with tempfile.TemporaryDirectory() as d:
-        mp.spawn(_worker_allreduce, args=(2, port, d), nprocs=2, join=True)
-        c, q, _, _ = _case()
+        mp.spawn(_worker_allreduce, args=(world, port, d), nprocs=world, join=True)
+        c, q, edges, n = _case()
         full = oracle.amplitudes(c, q)
-        for r in range(2):
+        # the same partials summed in rank order in this process
+        parts = []
+        for r in range(world):
+            b, cnt = shard.slice_range(r, world, n)
+            parts.append(oracle.sliced_amplitudes(c, q, edges, range(b, b + cnt)))
+        want = shard.ordered_sum(parts)
+        for r in range(world):
             got = np.load(os.path.join(d, f"r{r}.npy"))
             assert np.max(np.abs(got - full)) < 1e-13
+            # bit-identical on every rank and to the single-process ordered sum
+            assert got.tobytes() == want.tobytes()
 
 
 def _worker_fail(rank, world, port, outdir):
