@@ -398,6 +398,14 @@ def leg_grid53(tn, torch, dev, flush, stream, peaks, want_records=False):
            "gemm_tc_tflops": g["flops"] / (g["ms"] * 1e-3) / 1e12,
            "gemm_tc_share": g["ms"] / ms, "max_log2_elems": info["max_log2_elems"],
            "peak_tflops": peak}
+    # the same 64 slices (8 passes) as ONE work-queue launch
+    plan.set_queue(True)
+    plan.contract(0, n, out=amps)
+    torch.cuda.synchronize()
+    ms_q = _timed(lambda: plan.contract(0, n, out=amps), stream, flush)
+    plan.set_queue(False)
+    out["queue"] = {"ms": ms_q, "tflops": flops / (ms_q * 1e-3) / 1e12, "kernels": 1,
+                    "frac_of_dense_fp16_peak": flops / (ms_q * 1e-3) / 1e12 / peak}
     recs = []
     if want_records:
         plan.tune()
@@ -407,37 +415,69 @@ def leg_grid53(tn, torch, dev, flush, stream, peaks, want_records=False):
     return out, recs
 
 
-def leg_batch256(tn, torch, dev, flush, stream):
+def leg_batch256(tn, torch, dev, flush, stream, anneal_iters=20000):
     """256 independent uneven circuits (16-28 qubits, 8-16 cycles, 64
-    amplitudes each), FP16, one CUDA graph over 16 streams; tile choices
-    from an autotuner cache built by tuning every 32nd plan."""
+    amplitudes each), FP16, tile choices from an autotuner cache built by
+    tuning every 32nd plan.  Each circuit is planned within a 1 GiB workspace
+    (as many slices per pass as fit), on the greedy path and on a path
+    refined by simulated annealing; each set runs as one CUDA graph of
+    stand-alone launches over 16 streams and as ONE persistent work-queue
+    launch.  Accuracy: every circuit's 64 amplitudes against the stored FP64
+    state-vector values."""
     import time as _t
+    import numpy as np
     import rqcgen
     items = rqcgen.uneven_batch()
-    t0 = _t.perf_counter()
-    plans = [tn.plan_within_budget(c, q, dtype=tn.F16) for c, q in items]
-    t_plan = _t.perf_counter() - t0
-    recs = []
-    for p in plans[::32]:
-        p.tune()
-        recs += p.tune_records()
-    for p in plans:
-        p.apply_tuning(recs)
-    outs = [torch.zeros(64, dtype=torch.complex128, device=dev) for _ in plans]
-    t0 = _t.perf_counter()
-    b = tn.Batch(plans, outs, n_streams=16)
-    t_capture = _t.perf_counter() - t0
-    rep = b.run(stream=stream, report=True)
-    ms = _timed(lambda: b.run(stream=stream), stream, flush, reps=2)
+    gold = [read_golden(os.path.join("batch", f"circuit{i:03d}.txt")) for i in range(len(items))]
     out = {"workload": "256 uneven circuits (16-28 qubits, 8-16 cycles), 64 amplitudes each",
-           "circuits": len(plans), "ms": ms, "circuits_per_s": len(plans) / (ms * 1e-3),
-           "amplitudes_per_s": 64 * len(plans) / (ms * 1e-3),
-           "tflops": rep["flops"] / (ms * 1e-3) / 1e12, "slices": rep["slices"],
-           "kernels_in_graph": rep["kernels"], "plan_s": t_plan, "graph_capture_s": t_capture,
-           "tuned_plans": len(plans[::32])}
-    del b, plans, outs
-    torch.cuda.empty_cache()
-    return out, recs
+           "circuits": len(items)}
+    recs_all = []
+    for name, kw in (("greedy", {}), ("annealed", {"anneal_iters": anneal_iters})):
+        t0 = _t.perf_counter()
+        plans = [tn.plan_within_budget(c, q, dtype=tn.F16, **kw) for c, q in items]
+        t_plan = _t.perf_counter() - t0
+        recs = []
+        for p in plans[::32]:
+            p.tune()
+            recs += p.tune_records()
+        for p in plans:
+            p.apply_tuning(recs)
+        recs_all += recs
+        outs = [torch.zeros(64, dtype=torch.complex128, device=dev) for _ in plans]
+        t0 = _t.perf_counter()
+        b = tn.Batch(plans, outs, n_streams=16)
+        t_capture = _t.perf_counter() - t0
+        rep = b.run(stream=stream, report=True)
+        ms_graph = _timed(lambda: b.run(stream=stream), stream, flush, reps=2)
+        outq = [torch.zeros(64, dtype=torch.complex128, device=dev) for _ in plans]
+        t0 = _t.perf_counter()
+        qu = tn.Queue(plans, outq)
+        t_queue = _t.perf_counter() - t0
+        qu.run(stream=stream, report=True)
+        ms_queue = _timed(lambda: qu.run(stream=stream), stream, flush, reps=3)
+        torch.cuda.synchronize()
+        same = all(bool(torch.equal(torch.view_as_real(a), torch.view_as_real(bq))) for a, bq in zip(outs, outq))
+        errs = [float(np.linalg.norm(o.cpu().numpy() - g) / np.linalg.norm(g))
+                for o, g in zip(outq, gold) if g is not None]
+        qi = qu.info()
+        out[name] = {"plan_s": t_plan, "flops": rep["flops"], "slices": rep["slices"],
+                     "graph": {"ms": ms_graph, "circuits_per_s": len(plans) / (ms_graph * 1e-3),
+                               "tflops": rep["flops"] / (ms_graph * 1e-3) / 1e12,
+                               "kernels": rep["kernels"], "capture_s": t_capture},
+                     "queue": {"ms": ms_queue, "circuits_per_s": len(plans) / (ms_queue * 1e-3),
+                               "tflops": rep["flops"] / (ms_queue * 1e-3) / 1e12, "kernels": 1,
+                               "items": qi["n_items"], "ops": qi["n_ops"], "max_chain": qi["max_chain"],
+                               "build_s": t_queue},
+                     "queue_equals_graph_bitwise": same,
+                     "max_rel_l2": max(errs) if errs else None,
+                     "median_rel_l2": float(np.median(errs)) if errs else None,
+                     "checked_circuits": len(errs), "tuned_plans": len(plans[::32])}
+        del b, qu, plans, outs, outq
+        torch.cuda.empty_cache()
+    best = max((out[k]["queue"]["circuits_per_s"], k) for k in ("greedy", "annealed"))
+    out["circuits_per_s"] = best[0]
+    out["best"] = f"{best[1]} path, one work-queue launch"
+    return out, recs_all
 
 
 def _oversample(recs):

@@ -131,6 +131,13 @@ typedef struct {
                                  values of deep intermediates fall into FP16's
                                  subnormal range or flush to zero.  0: scaled
                                  (default).  Not with fp8_min_log2_flops.     */
+    int32_t pad_;
+    int64_t workspace_budget; /* > 0: the library chooses slice_batch_log2 itself
+                                 (the given value is ignored): the largest
+                                 b <= min(16, summed sliced edges) whose device
+                                 workspace fits in this many bytes, else 0 --
+                                 as many slices per pass as memory allows, one
+                                 path search.  0: slice_batch_log2 as given   */
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *ctx);
@@ -324,6 +331,63 @@ void tn_batch_destroy(tn_batch_t *batch);
 int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps, void *stream);
 
 /*
+ * Persistent work queue: the contraction of many independent plans (uneven
+ * circuits, or slice ranges of one plan) in ONE kernel launch.  Slices and
+ * circuits are independent sub-tasks whose results are summed (Sec. 3.1,
+ * global level); within one pass the steps form a chain.  tn_queue_create
+ * sets up each plan's device state (calibration and tile choice included,
+ * as a first tn_contract would), then compiles every op of the contraction
+ * of slices [slice_begin[i], slice_begin[i] + slice_count[i]) of plans[i]
+ * into d_amps[i] (device, 2^n_open_i complex128, overwritten; NULL range
+ * arrays: every slice) into a device table of ops and a list of (op, tile)
+ * items in dependency order.  tn_queue_run launches one persistent kernel
+ * (one 320-thread CTA per SM, the tensor-core tiles on tcgen05/TMA/TMEM as in
+ * tn_contract, the other ops on the same kernels' device code) that claims
+ * items in order; each item waits for the op before it in its chain through
+ * a per-op counter, a wait bounded by the queue's limit (default 10 s,
+ * tn_queue_set_wait_limit), after which every CTA returns and the run
+ * reports TN_ETIMEOUT (rep != NULL).  Results equal tn_contract's bit for
+ * bit.  rep: optional timing and error check (synchronizes `stream`).
+ * Plans must have profiling off and must not be used elsewhere while the
+ * queue exists; the queue owns its tables (device memory from cudaMalloc).
+ * TN_EUNSUPPORTED: a plan with FP8 steps.
+ */
+typedef struct tn_queue_s tn_queue_t;
+typedef struct {
+    int32_t n_plans;
+    int32_t n_ops;                /* ops in the table                             */
+    int32_t n_items;              /* (op, tile) items claimed by the CTAs         */
+    int32_t max_chain;            /* longest dependency chain (ops)               */
+    int32_t ctas;                 /* CTAs of the launch                           */
+    int32_t pad_;
+    int64_t table_bytes;          /* op parameter records                         */
+    double flops;                 /* real flops of one run                        */
+    int64_t slices;               /* slices summed in one run                     */
+} tn_queue_stats;
+int tn_queue_create(tn_plan_t *const *plans, int32_t n, const int64_t *slice_begin,
+                    const int64_t *slice_count, double *const *d_amps, tn_queue_t **out);
+int tn_queue_run(tn_queue_t *queue, void *stream, tn_contract_report *rep);
+int tn_queue_info(const tn_queue_t *queue, tn_queue_stats *out);
+int tn_queue_set_wait_limit(tn_queue_t *queue, int64_t limit_us);
+void tn_queue_destroy(tn_queue_t *queue);
+
+/*
+ * tn_plan_set_queue: when enable != 0, tn_contract runs the whole call as
+ * one work-queue launch (above), built the first time it is called with a
+ * given (slice range, d_amps, accumulate) and reused on later identical
+ * calls.  Off by default.
+ */
+int tn_plan_set_queue(tn_plan_t *plan, int enable);
+
+/*
+ * tn_selftest_queue_timeout: runs a two-op queue whose second op waits for a
+ * tile count the first never reaches, with a dependency-wait limit of
+ * limit_ms (1..10000); the wait runs out and the call returns TN_ETIMEOUT,
+ * the context still usable.
+ */
+int tn_selftest_queue_timeout(int32_t limit_ms, void *stream);
+
+/*
  * tn_sample: post-selection on one correlated subspace (Sec. 1/2,
  * post-processing): from d_amps (device, 2^n_open complex128) return the k
  * indices of largest |amp|^2 and their probabilities, ties to the lower index,
@@ -449,6 +513,10 @@ int tn_cost_model_predict(tn_cost_model_t *model, const float *h_x, int64_t n, f
                           void *stream);
 /* Feature rows (n x TN_COST_NFEAT) of autotuner records. */
 int tn_cost_features(const tn_tune_record *recs, int32_t n, float *out);
+/* Training targets of autotuner records: log2 of each record's time in
+ * microseconds (times below 1 ns count as 1 ns), the quantity the model
+ * predicts. */
+int tn_cost_targets(const tn_tune_record *recs, int32_t n, float *out);
 /* Attach a model to a plan: with tile_policy TN_TILE_LEARNED the first
  * tn_contract picks every GEMM step's configuration by predicted time. */
 int tn_plan_set_cost_model(tn_plan_t *plan, tn_cost_model_t *model);

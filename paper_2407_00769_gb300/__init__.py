@@ -43,6 +43,8 @@ EXPORTED = [
     "tn_cost_model_create", "tn_cost_model_destroy", "tn_cost_model_params", "tn_cost_model_grad",
     "tn_cost_model_train", "tn_cost_model_predict", "tn_cost_features", "tn_plan_set_cost_model",
     "tn_plan_predict_ms", "tn_plan_apply_tuning", "tn_gemm_gather", "tn_encode", "tn_decode",
+    "tn_queue_create", "tn_queue_run", "tn_queue_info", "tn_queue_set_wait_limit", "tn_queue_destroy",
+    "tn_plan_set_queue", "tn_selftest_queue_timeout", "tn_cost_targets",
 ]
 COST_NFEAT = 26
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum", "quant"]
@@ -82,7 +84,8 @@ class PlanOpts(ctypes.Structure):
                 ("no_tensor_cores", ctypes.c_int32),
                 ("fp8_min_log2_flops", ctypes.c_int32),
                 ("recompute_log2", ctypes.c_int32),
-                ("no_scaling", ctypes.c_int32),
+                ("no_scaling", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("workspace_budget", ctypes.c_int64),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -103,6 +106,12 @@ class ContractReport(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("flops", ctypes.c_double), ("slices", ctypes.c_int64),
                 ("kernels", ctypes.c_int32), ("min_exp", ctypes.c_int32),
                 ("max_exp", ctypes.c_int32)]
+
+
+class QueueStats(ctypes.Structure):
+    _fields_ = [("n_plans", ctypes.c_int32), ("n_ops", ctypes.c_int32), ("n_items", ctypes.c_int32),
+                ("max_chain", ctypes.c_int32), ("ctas", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("table_bytes", ctypes.c_int64), ("flops", ctypes.c_double), ("slices", ctypes.c_int64)]
 
 
 class KernelStats(ctypes.Structure):
@@ -184,6 +193,7 @@ def lib():
                                           ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), vp]
         L.tn_cost_model_predict.argtypes = [vp, f32p, i64, f32p, vp]
         L.tn_cost_features.argtypes = [ctypes.POINTER(TuneRecord), i32, f32p]
+        L.tn_cost_targets.argtypes = [ctypes.POINTER(TuneRecord), i32, f32p]
         L.tn_plan_set_cost_model.argtypes = [vp, vp]
         L.tn_plan_predict_ms.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), vp]
         L.tn_tune_records.argtypes = [vp, ctypes.POINTER(TuneRecord), i32, ctypes.POINTER(i32)]
@@ -192,6 +202,15 @@ def lib():
         L.tn_batch_run.argtypes = [vp, vp, ctypes.POINTER(ContractReport)]
         L.tn_batch_destroy.argtypes = [vp]
         L.tn_batch_destroy.restype = None
+        L.tn_queue_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.tn_queue_run.argtypes = [vp, vp, ctypes.POINTER(ContractReport)]
+        L.tn_queue_info.argtypes = [vp, ctypes.POINTER(QueueStats)]
+        L.tn_queue_set_wait_limit.argtypes = [vp, i64]
+        L.tn_queue_destroy.argtypes = [vp]
+        L.tn_queue_destroy.restype = None
+        L.tn_plan_set_queue.argtypes = [vp, ctypes.c_int]
+        L.tn_selftest_queue_timeout.argtypes = [i32, vp]
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_plan_destroy.restype = None
         L.tn_permute.argtypes = [vp, vp, i32, ctypes.POINTER(i32), i32, vp]
@@ -209,7 +228,7 @@ def lib():
         L.tn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("tn_plan_opts_default", "tn_plan_destroy", "tn_strerror", "tn_last_error",
-                            "tn_batch_destroy", "tn_cost_model_destroy"):
+                            "tn_batch_destroy", "tn_cost_model_destroy", "tn_queue_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -285,7 +304,8 @@ class Plan:
                  slice_batch_log2: int = 0, tile_policy: int = TILE_FIXED,
                  torch_allocator: bool = True, small_log2: int = 0,
                  no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
-                 recompute_log2: int = 0, no_scaling: bool = False, _samples=None):
+                 recompute_log2: int = 0, no_scaling: bool = False, workspace_budget: int = 0,
+                 _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         if _samples is None:
@@ -298,6 +318,7 @@ class Plan:
         opts.path_seed = int(seed)
         opts.path_trials = int(trials)
         opts.path_anneal_iters = int(anneal_iters)
+        opts.workspace_budget = int(workspace_budget)
         opts.slice_batch_log2 = int(slice_batch_log2)
         opts.tile_policy = int(tile_policy)
         opts.small_log2 = int(small_log2)
@@ -470,6 +491,11 @@ class Plan:
         """Capture tn_contract calls into a CUDA graph and replay identical ones."""
         _check(lib().tn_plan_set_graph(self._h, 1 if enable else 0))
 
+    def set_queue(self, enable: bool = True):
+        """Run every contract() call as one work-queue launch (tn_plan_set_queue)."""
+        _check(lib().tn_plan_set_queue(self._h, 1 if enable else 0))
+        return self
+
     def profile(self, classes=None):
         """Start per-kernel-class event timing (names from KC_NAMES; None: off)."""
         mask = 0
@@ -502,18 +528,10 @@ class Plan:
 def plan_within_budget(circuit, query, dtype=F16, max_log2_elems=24, trials=4,
                        workspace_budget=1 << 30, **kw):
     """Plan with automatic slicing under a width cap, running as many of the
-    slices together (slice_batch_log2) as fit in ``workspace_budget`` bytes:
-    fewer launches where memory allows, plain slicing where it does not."""
-    base = Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
-                trials=trials, torch_allocator=False)
-    s = base.info()["n_slice_edges"]
-    for b in range(min(s, 16), -1, -1):
-        p = Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
-                 trials=trials, slice_batch_log2=b, torch_allocator=False)
-        if p.info()["workspace_bytes"] <= workspace_budget or b == 0:
-            return Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
-                        trials=trials, slice_batch_log2=b, **kw)
-    return base
+    slices together (slice_batch_log2) as fit in ``workspace_budget`` bytes
+    (tn_plan_opts.workspace_budget: the library picks the batch)."""
+    return Plan(circuit, query, dtype=dtype, n_slice_edges=-1, max_log2_elems=max_log2_elems,
+                trials=trials, workspace_budget=workspace_budget, **kw)
 
 
 def _f32(a):
@@ -550,9 +568,22 @@ def load_timings(path=None):
     return [dict({k: cols[k][i] for k in keys}, step=-1, pad_=0, ms=ms[i]) for i in range(n)]
 
 
+def _records(records):
+    n = len(records)
+    arr = (TuneRecord * max(1, n))()
+    for i, r in enumerate(records):
+        for f, _ in TuneRecord._fields_:
+            setattr(arr[i], f, r.get(f, 0))
+    return arr, n
+
+
 def cost_targets(records) -> np.ndarray:
-    """Training targets: log2 of each record's time in microseconds."""
-    return np.log2(np.array([max(r["ms"], 1e-6) * 1e3 for r in records], dtype=np.float64)).astype(np.float32)
+    """Training targets (tn_cost_targets): log2 of each record's time in
+    microseconds."""
+    arr, n = _records(records)
+    out = np.zeros(n, dtype=np.float32)
+    _check(lib().tn_cost_targets(arr, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
 
 
 class CostModel:
@@ -655,6 +686,64 @@ class Batch:
             except Exception:
                 pass
             self._h = None
+
+
+class Queue:
+    """Many independent plans (or slice ranges) contracted in ONE persistent
+    kernel launch (tn_queue_*): a device table of (op, tile) items in
+    dependency order, claimed by one CTA per SM.  ranges: optional list of
+    (slice_begin, slice_count) per plan (default: every slice).  run()
+    launches it.  Keeps the plans and output tensors alive."""
+
+    def __init__(self, plans, outs, ranges=None):
+        self.plans, self.outs = list(plans), list(outs)
+        n = len(self.plans)
+        if len(self.outs) != n:
+            raise ValueError("one output tensor per plan")
+        for o, p in zip(self.outs, self.plans):
+            if _amps_log2(o, "outs") != p.info()["n_open"]:
+                raise ValueError("each output must hold 2^n_open amplitudes of its plan")
+        hs = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        ds = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        b = c = None
+        if ranges is not None:
+            b = (ctypes.c_int64 * n)(*[int(r[0]) for r in ranges])
+            c = (ctypes.c_int64 * n)(*[int(r[1]) for r in ranges])
+        h = ctypes.c_void_p()
+        _check(lib().tn_queue_create(hs, n, b, c, ds, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None, report: bool = False):
+        rep = ContractReport() if report else None
+        _check(lib().tn_queue_run(self._h, _stream_ptr(stream),
+                                  ctypes.byref(rep) if rep is not None else None))
+        if report:
+            return {f: getattr(rep, f) for f, _ in ContractReport._fields_}
+        return None
+
+    def info(self) -> dict:
+        st = QueueStats()
+        _check(lib().tn_queue_info(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in QueueStats._fields_ if f != "pad_"}
+
+    def set_wait_limit(self, limit_us: int):
+        _check(lib().tn_queue_set_wait_limit(self._h, int(limit_us)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().tn_queue_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+def selftest_queue_timeout(limit_ms: int = 200, stream=None) -> int:
+    """Status of a work queue whose second op waits for a count that is never
+    reached (tn_selftest_queue_timeout): TN_ETIMEOUT when the bounded wait
+    works."""
+    return int(lib().tn_selftest_queue_timeout(int(limit_ms), _stream_ptr(stream)))
 
 
 def _amps_log2(amps, name="amps") -> int:

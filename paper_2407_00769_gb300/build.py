@@ -22,8 +22,8 @@ LIB = os.path.join(BUILD, "libtn.so")
 
 SOURCES = ["network.cpp", "path.cpp", "anneal.cpp", "schedule.cpp", "kernels.cu", "tc_gemm.cu", "api.cu",
            "api_kernels.cu",
-           "sample_noalloc.cu", "mlp.cu", "codec.cu"]
-HEADERS = ["internal.h", "plan.h", "kernels.cuh"]
+           "sample_noalloc.cu", "mlp.cu", "codec.cu", "queue.cu"]
+HEADERS = ["internal.h", "plan.h", "kernels.cuh", "bodies.cuh", "tc_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -574,6 +574,26 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
 
 int tn::record_error(int code, const std::string &msg) { return fail(code, msg); }
 
+// Device state, scale calibration and tile choice of a plan, as the first
+// tn_contract call does them (each once).
+int tn::prepare_for_contract(tn_plan_s *P, cudaStream_t s) {
+    int rc = ensure_device(P);
+    if (rc != TN_OK) return rc;
+    if (!P->calibrated && P->opts.dtype != TN_C64 && P->prof_mask == 0 && !P->opts.no_scaling) {
+        rc = calibrate_plan(P, s);
+        if (rc != TN_OK) return rc;
+    }
+    if (!P->tuned && P->opts.tile_policy == TN_TILE_EXHAUSTIVE && P->prof_mask == 0) {
+        rc = tune_plan(P, s);
+        if (rc != TN_OK) return rc;
+    }
+    if (!P->tuned && P->opts.tile_policy == TN_TILE_LEARNED && P->cost_model) {
+        rc = choose_by_model(P, P->cost_model, s);
+        if (rc != TN_OK) return rc;
+    }
+    return TN_OK;
+}
+
 extern "C" {
 
 void tn_plan_opts_default(tn_plan_opts *o) {
@@ -607,6 +627,7 @@ int check_opts(const tn_plan_opts &o) {
         return fail(TN_EINVAL, "no_scaling does not apply to E4M3 steps (their scale is their range)");
     if (o.n_slice_edges < 0 && o.max_log2_elems <= 0)
         return fail(TN_EINVAL, "n_slice_edges = -1 needs max_log2_elems > 0");
+    if (o.workspace_budget < 0) return fail(TN_EINVAL, "workspace_budget must be >= 0");
     return TN_OK;
 }
 
@@ -666,10 +687,31 @@ int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
 // Schedule and leaf store of a planned network.
 int finish_plan(tn_plan_s *P, const SampleSpec *spec, std::string &err) {
     const tn_plan_opts &o = P->opts;
-    int rc = build_schedule(P->net, P->path, P->sliced, P->batch_log2, o.dtype,
-                            o.small_log2 > 0 ? o.small_log2 : kSmallLog2, o.no_tensor_cores == 0,
-                            o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, P->sched, err, spec);
-    if (rc != TN_OK) return rc;
+    auto schedule = [&](int b, Schedule &out) {
+        return build_schedule(P->net, P->path, P->sliced, b, o.dtype, o.small_log2 > 0 ? o.small_log2 : kSmallLog2,
+                              o.no_tensor_cores == 0, o.dtype == TN_C64 ? 0 : o.fp8_min_log2_flops, out, err, spec);
+    };
+    int rc;
+    if (o.workspace_budget > 0) {
+        // as many slices per pass as the workspace budget allows (one path,
+        // several schedules): the largest fitting batch, else none
+        const int summed = (int)P->sliced.size() - P->n_recompute;
+        int b = std::min(16, summed);
+        for (; b >= 0; --b) {
+            Schedule S;
+            rc = schedule(b, S);
+            if (rc != TN_OK) return rc;
+            if (S.ws_bytes <= o.workspace_budget || b == 0) {
+                P->sched = std::move(S);
+                break;
+            }
+        }
+        P->batch_log2 = std::max(b, 0);
+        P->opts.slice_batch_log2 = P->batch_log2;
+    } else {
+        rc = schedule(P->batch_log2, P->sched);
+        if (rc != TN_OK) return rc;
+    }
     int64_t offs = 0;
     for (const Leaf &L : P->net.leaves) {
         P->leaf_offset.push_back(offs);
@@ -1057,6 +1099,12 @@ int tn_cost_features(const tn_tune_record *recs, int32_t n, float *out) {
     return TN_OK;
 }
 
+int tn_cost_targets(const tn_tune_record *recs, int32_t n, float *out) {
+    if (n < 0 || (n > 0 && (!recs || !out))) return fail(TN_EINVAL, "bad argument");
+    for (int i = 0; i < n; ++i) out[i] = (float)std::log2(std::max(recs[i].ms, 1e-6) * 1e3);
+    return TN_OK;
+}
+
 int tn_plan_set_cost_model(tn_plan_t *P, tn_cost_model_t *M) {
     if (!P) return fail(TN_EINVAL, "NULL plan");
     P->cost_model = M;
@@ -1091,6 +1139,16 @@ int tn_plan_predict_ms(tn_plan_t *P, tn_cost_model_t *M, double *out_ms, void *s
     return TN_OK;
 }
 
+int tn_plan_set_queue(tn_plan_t *P, int enable) {
+    if (!P) return fail(TN_EINVAL, "NULL plan");
+    P->use_queue = enable != 0;
+    if (!P->use_queue && P->queue) {
+        tn_queue_destroy(P->queue);
+        P->queue = nullptr;
+    }
+    return TN_OK;
+}
+
 int tn_plan_set_graph(tn_plan_t *P, int enable) {
     if (!P) return fail(TN_EINVAL, "NULL plan");
     P->use_graph = enable != 0;
@@ -1108,21 +1166,9 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
     if (slice_begin < 0 || slice_count < 0 || slice_begin + slice_count > n_slices)
         return fail(TN_EINVAL, "slice range outside [0, n_slices)");
     if (!d_amps) return fail(TN_EINVAL, "d_amps is NULL");
-    int rc = ensure_device(P);
-    if (rc != TN_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!P->calibrated && P->opts.dtype != TN_C64 && P->prof_mask == 0 && !P->opts.no_scaling) {
-        rc = calibrate_plan(P, s);
-        if (rc != TN_OK) return rc;
-    }
-    if (!P->tuned && P->opts.tile_policy == TN_TILE_EXHAUSTIVE && P->prof_mask == 0) {
-        rc = tune_plan(P, s);
-        if (rc != TN_OK) return rc;
-    }
-    if (!P->tuned && P->opts.tile_policy == TN_TILE_LEARNED && P->cost_model) {
-        rc = choose_by_model(P, P->cost_model, s);
-        if (rc != TN_OK) return rc;
-    }
+    int rc = prepare_for_contract(P, s);
+    if (rc != TN_OK) return rc;
     const int64_t n_amps = (int64_t)1 << P->net.n_open;
     if (slice_count == 0) {
         if (!accumulate) TN_CUDA(cudaMemsetAsync(d_amps, 0, n_amps * 16, s), "memset");
@@ -1139,7 +1185,24 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
     int launches = 0;
     const bool graph = P->use_graph && s != nullptr && s != cudaStreamLegacy &&
                        s != cudaStreamPerThread && P->prof_mask == 0;
-    if (graph) {
+    if (P->use_queue && P->prof_mask == 0 && !accumulate) {
+        const tn_plan_s::GraphKey key{slice_begin, slice_count, d_amps, accumulate, nullptr};
+        if (!P->queue || !(P->queue_key == key)) {
+            if (P->queue) {
+                tn_queue_destroy(P->queue);
+                P->queue = nullptr;
+            }
+            tn_plan_t *pl[1] = {P};
+            double *am[1] = {d_amps};
+            const int64_t b0[1] = {slice_begin}, c0[1] = {slice_count};
+            rc = tn_queue_create(pl, 1, b0, c0, am, &P->queue);
+            if (rc != TN_OK) return rc;
+            P->queue_key = key;
+        }
+        rc = tn_queue_run(P->queue, stream, nullptr);
+        if (rc != TN_OK) return rc;
+        launches = 1;
+    } else if (graph) {
         const tn_plan_s::GraphKey key{slice_begin, slice_count, d_amps, accumulate, s};
         if (!P->graph_exec || !(P->graph_key == key)) {
             if (P->graph_exec) {
@@ -1434,6 +1497,7 @@ void tn_plan_destroy(tn_plan_t *P) {
     if (!P) return;
     if (P->dev_ready) cudaDeviceSynchronize();
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    if (P->queue) tn_queue_destroy(P->queue);
     for (auto &r : P->prof) {
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);

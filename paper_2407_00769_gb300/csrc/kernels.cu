@@ -10,88 +10,17 @@
 #include <cstring>
 #include <type_traits>
 
+#include "bodies.cuh"
 #include "kernels.cuh"
 
 namespace tn {
 
-// ------------------------------------------------------------ lp helpers --
-template <int DT> struct LpT;
-template <> struct LpT<TN_F16> {
-    using T2 = __half2;
-    static __device__ __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
-    static __device__ __forceinline__ T2 from_f2(float2 v) { return __floats2half2_rn(v.x, v.y); }
-    static __device__ __forceinline__ T2 from_d2(double re, double im) {
-        return __halves2half2(__double2half(re), __double2half(im));
-    }
-};
-template <> struct LpT<TN_BF16> {
-    using T2 = __nv_bfloat162;
-    static __device__ __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ T2 from_f2(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
-    static __device__ __forceinline__ T2 from_d2(double re, double im) {
-        return __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
-    }
-};
-
-__device__ __forceinline__ float warp_max(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(float *addr, float v) {
-    atomicMax(reinterpret_cast<int *>(addr), __float_as_int(v));
-}
-
-// exponent e for a product of two scaled tensors: with |A| <= sqrt2 maxA,
-// |B| <= sqrt2 maxB and K terms, |C| <= 2 K maxA maxB; choose e so that
-// 2 K maxA maxB 2^e <= 2^14 (FP16 max is 65504 ~ 2^16).
-__device__ __forceinline__ int scale_exponent(float maxa, float maxb, int lk) {
-    const float t = 2.0f * maxa * maxb;
-    if (!(t > 0.0f) || !isfinite(t)) return 0;
-    int x;
-    const float f = frexpf(t, &x);            // t = f 2^x, f in [0.5, 1)
-    const int c = (f == 0.5f) ? x - 1 : x;    // ceil(log2 t)
-    int e = 14 - lk - c;
-    return max(-120, min(120, e));
-}
-
-__device__ __forceinline__ float exp2i(int e) {   // exact 2^e, |e| <= 126
-    return __int_as_float((127 + e) << 23);
-}
-
 // ------------------------------------------------------------- leaf prep --
-// One block per leaf.  Output element o (over the kept legs) reads input
-// element in(o) = kept bits placed at keep_pos, fixed legs at the value of
-// their slice-id bit (slice decoding: bit j of the slice id is sliced edge
-// j's value).  Converts complex128 -> the contraction dtype (RN).
+// One block (one warp) per leaf: leaf_warp_body (slice decoding and the
+// complex128 -> complex64 conversion).
 __global__ void leaf_prep_kernel(const LeafJob *jobs, const double2 *store, char *ws,
                                  int64_t slice_base, float *tmax, int32_t *texp) {
-    const LeafJob j = jobs[blockIdx.x];
-    const int n_out = 1 << j.rank_out;
-    float m = 0.0f;
-    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
-        int64_t in = 0;
-        for (int i = 0; i < j.rank_out; ++i)
-            if ((o >> i) & 1) in |= (int64_t)1 << j.keep_pos[i];
-        for (int f = 0; f < j.n_fixed; ++f)
-            in |= ((slice_base >> j.fixed_bit[f]) & 1) << j.fixed_pos[f];
-        const double2 v = store[j.src + in];
-        const float2 w = make_float2((float)v.x, (float)v.y);
-        reinterpret_cast<float2 *>(ws + j.dst)[o] = w;
-        m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
-    }
-    if (tmax) {
-        m = warp_max(m);
-        __shared__ float sm[32];
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float mm = 0.0f;
-            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mm = fmaxf(mm, sm[w]);
-            tmax[j.meta] = mm;
-            texp[j.meta] = 0;
-        }
-    }
+    leaf_warp_body(jobs[blockIdx.x], store, ws, slice_base, tmax, texp, threadIdx.x);
 }
 
 cudaError_t launch_leaf_prep(const LeafJob *d_jobs, int count, const double2 *d_store, char *ws,
@@ -184,143 +113,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) permute_kernel(const T *__restrict__ in, T *__restrict__ out,
                                                       const __grid_constant__ PermParams p) {
     __shared__ T tile[1024 + 32];
-    int64_t bin = 0, bout = 0;
-    const int64_t tid = blockIdx.x;
-    for (int k = 0; k < p.n_outer; ++k)
-        if ((tid >> k) & 1) {
-            bin |= (int64_t)1 << p.outer_in[k];
-            bout |= (int64_t)1 << p.outer_out[k];
-        }
-    const int n = 1 << p.tile_bits;
-    const int lo_mask_in = (1 << p.lin) - 1;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int64_t off = bin + (e & lo_mask_in) + p.rd_hi_off[e >> p.lin];
-        tile[e + (e >> 5)] = in[off];
-    }
-    __syncthreads();
-    const int lo_mask_out = (1 << p.lout) - 1;
-    for (int f = threadIdx.x; f < n; f += blockDim.x) {
-        const int fl = f & lo_mask_out, fh = f >> p.lout;
-        const int e = p.wr_lo_e[fl] | p.wr_hi_e[fh];
-        out[bout + fl + p.wr_hi_off[fh]] = tile[e + (e >> 5)];
-    }
+    permute_tile_body<T, SyncBlock>(in, out, p, blockIdx.x, threadIdx.x, blockDim.x, tile);
 }
 
-// Fast path for tensors of rank >= 10: the tile is always 2^10 elements
-// (32 contiguous input elements x 32 contiguous output elements), and the
-// position of an element inside its tile is the same for every tile, so
-// each thread works out once where its 4 elements come from and go to; per
-// tile only the tile's base offsets change (from 8-bit lookup tables).  Each
-// thread moves its 4 elements with one 16-byte (4-byte elements) or two
-// (8-byte elements) vector loads and stores.  Persistent over tiles.
-//
-// EXPAND (complex-half only): instead of the permuted tensor, write the
-// padded real operand of the tensor-core GEMM (Sec. 3.3, Eq. 6): the
-// permuted order is [batch][N][K] complex and element (b, n, k) = (re, im)
-// goes to B'[b][2n][k] = (re, -im) and B'[b][2n+1][k] = (im, re) (pairs of
-// halves; np rows per batch).
-struct ExpandArgs {
-    int32_t lk, ln, np;
-};
-
+// Fast path for tensors of rank >= 10 (permute_tiled_body), persistent over
+// the tiles; EXPAND writes the padded tensor-core operand B' instead.
 template <typename T, bool EXPAND>
 __global__ void __launch_bounds__(256) permute_tiled_kernel(const T *__restrict__ in,
                                                             void *__restrict__ out_,
                                                             const __grid_constant__ PermParams p,
                                                             int64_t ntiles, ExpandArgs ex) {
-    __shared__ T tile[2][1024 + 32];
-    __shared__ int64_t s_bin[4][256], s_bout[4][256];
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-        const int level = i >> 8, v = i & 255;
-        int64_t bi = 0, bo = 0;
-        for (int b = 0; b < 8; ++b) {
-            const int k = level * 8 + b;
-            if (k < p.n_outer && ((v >> b) & 1)) {
-                bi |= (int64_t)1 << p.outer_in[k];
-                bo |= (int64_t)1 << p.outer_out[k];
-            }
-        }
-        s_bin[level][v] = bi;
-        s_bout[level][v] = bo;
-    }
-    // this thread's 4 elements: read-order e0..e0+3, write-order f0..f0+3
-    const int e0 = threadIdx.x * 4;
-    const int64_t in_off = (e0 & 31) + p.rd_hi_off[e0 >> 5];
-    int rd_slot[4], wr_slot[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        rd_slot[j] = (e0 + j) + ((e0 + j) >> 5);
-        const int f = e0 + j;
-        const int e = p.wr_lo_e[f & 31] | p.wr_hi_e[f >> 5];
-        wr_slot[j] = e + (e >> 5);
-    }
-    const int64_t out_off = (e0 & 31) + p.wr_hi_off[e0 >> 5];
-    __syncthreads();
-    // two tiles per iteration (two 16-byte loads in flight per thread)
-    for (int64_t t0 = blockIdx.x; t0 < ntiles; t0 += 2 * (int64_t)gridDim.x) {
-        const int64_t t1 = t0 + gridDim.x;
-        const bool has1 = t1 < ntiles;
-        T v[2][4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t t = h ? t1 : t0;
-            if (h && !has1) break;
-            const int64_t bin = s_bin[0][t & 255] + s_bin[1][(t >> 8) & 255] +
-                                s_bin[2][(t >> 16) & 255] + s_bin[3][(t >> 24) & 255];
-            if constexpr (sizeof(T) == 4) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
-                v[h][0] = x.x; v[h][1] = x.y; v[h][2] = x.z; v[h][3] = x.w;
-            } else {
-                const uint4 x = *reinterpret_cast<const uint4 *>(in + bin + in_off);
-                const uint4 y = *reinterpret_cast<const uint4 *>(in + bin + in_off + 2);
-                v[h][0] = make_uint2(x.x, x.y); v[h][1] = make_uint2(x.z, x.w);
-                v[h][2] = make_uint2(y.x, y.y); v[h][3] = make_uint2(y.z, y.w);
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h && !has1) break;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) tile[h][rd_slot[j]] = v[h][j];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t t = h ? t1 : t0;
-            if (h && !has1) break;
-            const int64_t bout = s_bout[0][t & 255] + s_bout[1][(t >> 8) & 255] +
-                                 s_bout[2][(t >> 16) & 255] + s_bout[3][(t >> 24) & 255];
-            T w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) w[j] = tile[h][wr_slot[j]];
-            const int64_t f = bout + out_off;
-            if constexpr (EXPAND) {
-                const int K = 1 << ex.lk;
-                const int64_t k0 = f & (K - 1);
-                const int64_t n = (f >> ex.lk) & ((1 << ex.ln) - 1);
-                const int64_t b = f >> (ex.lk + ex.ln);
-                uint32_t *o = reinterpret_cast<uint32_t *>(out_);
-                const int64_t row0 = b * ex.np + 2 * n;
-                uint4 r0, r1;
-                // (re, -im): flip the sign bit of the high half; (im, re): swap halves
-                r0.x = w[0] ^ 0x80000000u; r0.y = w[1] ^ 0x80000000u;
-                r0.z = w[2] ^ 0x80000000u; r0.w = w[3] ^ 0x80000000u;
-                r1.x = __byte_perm(w[0], 0, 0x1032); r1.y = __byte_perm(w[1], 0, 0x1032);
-                r1.z = __byte_perm(w[2], 0, 0x1032); r1.w = __byte_perm(w[3], 0, 0x1032);
-                *reinterpret_cast<uint4 *>(o + row0 * K + k0) = r0;
-                *reinterpret_cast<uint4 *>(o + (row0 + 1) * K + k0) = r1;
-            } else {
-                T *out = reinterpret_cast<T *>(out_);
-                if constexpr (sizeof(T) == 4) {
-                    *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0], w[1], w[2], w[3]);
-                } else {
-                    *reinterpret_cast<uint4 *>(out + f) = make_uint4(w[0].x, w[0].y, w[1].x, w[1].y);
-                    *reinterpret_cast<uint4 *>(out + f + 2) = make_uint4(w[2].x, w[2].y, w[3].x, w[3].y);
-                }
-            }
-        }
-        __syncthreads();
-    }
+    __shared__ PermTiledSmem<T> sm;
+    permute_tiled_body<T, EXPAND, SyncBlock>(in, out_, p, blockIdx.x, ntiles, gridDim.x, ex, threadIdx.x, sm);
 }
 
 static int64_t permute_grid(int64_t ntiles) {
@@ -360,35 +164,13 @@ cudaError_t launch_permute(const void *in, void *out, const PermParams &pp, int 
 __global__ void bprep_gather_kernel(const uint32_t *__restrict__ B, uint32_t *__restrict__ Bp,
                                     int lk, int ln, int lb, int np, const __grid_constant__ PermParams p,
                                     int rank) {
-    // target complex index bits: [batch][N][K], LSB = k bit 0.  For target
-    // bit i the input bit position is in_pos = r-1-perm[r-1-i].
-    const int K = 1 << lk, N = 1 << ln;
-    const int64_t total = ((int64_t)np * K) << lb;    // uint32 pairs of B'
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i % K);
-        const int64_t row = i / K;
-        const int rr = (int)(row % np);
-        const int64_t b = row / np;
-        const int n = rr >> 1, co = rr & 1;
-        uint32_t v = 0;
-        if (n < N) {
-            const int64_t tidx = ((b * N + n) << lk) | k;
-            int64_t src = 0;
-            for (int t = 0; t < rank; ++t)
-                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
-            const uint32_t x = B[src];
-            v = co == 0 ? (x ^ 0x80000000u) : __byte_perm(x, 0, 0x1032);
-        }
-        Bp[i] = v;
-    }
+    const int64_t total = ((int64_t)np << lk) << lb;    // uint32 pairs of B'
+    bprep_gather_body(B, Bp, lk, ln, np, p, rank, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, total,
+                      (int64_t)gridDim.x * blockDim.x);
 }
 
-// Complex64 B (a small tensor) -> B' in complex-half, one block: every
-// element is rounded to the plan's dtype here, and the rounding's component
-// along B, alpha = <B, B~ - B> / <B, B>, is measured (FP64, fixed order) so
-// the final sum can divide the factor (1 + alpha) out exactly (the network is
-// linear in B): corr = 1 / (1 + alpha).
+// Complex64 B (a small tensor) -> B' in complex-half, one block of 1024
+// threads (bprep_c64_body: rounding, 2^s scale, rounding compensation).
 template <int DT>
 __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restrict__ B,
                                                          uint32_t *__restrict__ Bp, int lk, int ln,
@@ -397,80 +179,9 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
                                                          int rank, double2 *corr, float *tmax,
                                                          int32_t *texp, int meta_src, int meta_dst,
                                                          int scale_off) {
-    using L = LpT<DT>;
-    const int K = 1 << lk, N = 1 << ln;
-    const int64_t total = ((int64_t)np * K) << lb;
-    // exact power-of-two scale bringing max |B| to [2^11, 2^12]
-    int bshift = 0;
-    {
-        const float mb = tmax[meta_src];
-        if (!scale_off && mb > 0.0f && isfinite(mb)) {
-            int x;
-            const float f = frexpf(mb, &x);
-            bshift = 12 - ((f == 0.5f) ? x - 1 : x);
-            bshift = max(-120, min(120, bshift));
-        }
-    }
-    const float scale = __int_as_float((127 + bshift) << 23);
-    float bmax = 0.0f;
-    double nr = 0.0, ni = 0.0, den = 0.0;
-    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
-        const int k = (int)(i % K);
-        const int64_t row = i / K;
-        const int rr = (int)(row % np);
-        const int64_t b = row / np;
-        const int n = rr >> 1, co = rr & 1;
-        uint32_t v = 0;
-        if (n < N) {
-            const int64_t tidx = ((b * N + n) << lk) | k;
-            int64_t src = 0;
-            for (int t = 0; t < rank; ++t)
-                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
-            const float2 x0 = B[src];
-            const float2 x = make_float2(x0.x * scale, x0.y * scale);
-            const typename L::T2 h = L::from_f2(x);
-            const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
-            v = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
-            if (co == 0) {
-                const float2 r = L::to_f2(h);
-                bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
-                const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
-                nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
-                ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
-                den += (double)x.x * x.x + (double)x.y * x.y;
-            }
-        }
-        Bp[i] = v;
-    }
-    __shared__ double sh[3][1024];
-    __shared__ float smax[1024];
-    sh[0][threadIdx.x] = nr;
-    sh[1][threadIdx.x] = ni;
-    sh[2][threadIdx.x] = den;
-    smax[threadIdx.x] = bmax;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) {
-            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
-            smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        tmax[meta_dst] = smax[0];
-        texp[meta_dst] = texp[meta_src] + bshift;
-    }
-    if (threadIdx.x == 0 && corr) {
-        double fr = 1.0, fi = 0.0;
-        if (sh[2][0] > 0.0) {
-            // 1 / (1 + alpha)
-            const double ar = 1.0 + sh[0][0] / sh[2][0], ai = sh[1][0] / sh[2][0];
-            const double d = ar * ar + ai * ai;
-            fr = ar / d;
-            fi = -ai / d;
-        }
-        *corr = make_double2(fr, fi);
-    }
+    __shared__ BprepC64Smem<1024> sm;
+    bprep_c64_body<DT, 1024, SyncBlock>(B, Bp, lk, ln, lb, np, p, rank, corr, tmax, texp, meta_src, meta_dst,
+                                        scale_off, threadIdx.x, sm);
 }
 
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
@@ -511,145 +222,15 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 }
 
 // ----------------------------------------------------------- rows GEMMs --
-// C[b][m][n] = sum_k A[b][m][k] B[b][k][n].  A block owns ROWS consecutive
-// rows (one per thread) and NC consecutive columns (grid.y); the A tile is
-// staged through shared memory with coalesced 16-byte loads (its rows are
-// contiguous), B's column chunk sits in shared memory as FP32 complex.
-// K is walked in chunks of KC.
-constexpr int kRows = 128;
-constexpr int kKC = 32;
-constexpr int kFlushK = 256;   // FP32 terms per partial sum before the FP64 add
-
-// operand conversion: complex64 as is, complex-half widened to FP32
-template <typename T, int DT>
-__device__ __forceinline__ float2 widen(T v) {
-    if constexpr (std::is_same<T, float2>::value) return v;
-    else return LpT<DT>::to_f2(v);
-}
-
-// Operand and result storage may differ (complex-half plans keep small
-// tensors in complex64): TA, TB, TC are float2 or the plan's complex-half
-// type, DT the plan's dtype.
+// One block of kRows threads per (row block, column chunk, batch entry):
+// rows_body.
 template <typename TA, typename TB, typename TC, int NC, int DT>
 __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const TA *__restrict__ A, const TB *__restrict__ B, TC *__restrict__ C, int lm, int ln, int lk,
     int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb) {
-    constexpr int KC = kKC;
-    __shared__ __align__(16) TA As[kRows * KC];
-    __shared__ float2 Bs[KC][NC];
-    const int64_t M = (int64_t)1 << lm;
-    const int N = 1 << ln, K = 1 << lk;
-    const int64_t b = blockIdx.z;
-    const int64_t m0 = (int64_t)blockIdx.x * kRows;
-    const int n0 = blockIdx.y * NC;
-    const int nc = min(NC, N);
-    // sparse-state gathers: operand chunks by index instead of by batch entry
-    const TA *Ab = A + (za ? (int64_t)za[b] : b) * sa;
-    const TB *Bb = B + (zb ? (int64_t)zb[b] : b) * sb;
-    TC *Cb = C + b * sc;
-    const int rows = (int)min((int64_t)kRows, M - m0);
-    // FP32 partial sums over at most kFlushK terms, added into FP64: a long
-    // FP32 running sum would lose ~sqrt(K) ulps (2^23-term steps occur)
-    float2 acc[NC];
-    double2 tot[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        acc[j] = make_float2(0.f, 0.f);
-        tot[j] = make_double2(0.0, 0.0);
-    }
-    for (int k0 = 0; k0 < K; k0 += KC) {
-        const int kc = min(KC, K - k0);
-        __syncthreads();
-        // A tile: rows x kc elements; when kc == K the tile is contiguous
-        {
-            const int per16 = 16 / (int)sizeof(TA);
-            const int total = rows * kc;
-            if (kc == K && (total % per16) == 0) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(Ab + m0 * K);
-                uint4 *dst = reinterpret_cast<uint4 *>(As);
-                for (int i = threadIdx.x; i < total / per16; i += kRows) dst[i] = src[i];
-            } else {
-                for (int i = threadIdx.x; i < total; i += kRows) {
-                    const int r = i / kc, kk = i % kc;
-                    As[r * kc + kk] = Ab[(m0 + r) * K + k0 + kk];
-                }
-            }
-        }
-        for (int i = threadIdx.x; i < kc * nc; i += kRows) {
-            const int kk = i / nc, j = i % nc;
-            Bs[kk][j] = widen<TB, DT>(Bb[(int64_t)(k0 + kk) * N + n0 + j]);
-        }
-        __syncthreads();
-        if (threadIdx.x < rows) {
-            for (int kk = 0; kk < kc; ++kk) {
-                const float2 a = widen<TA, DT>(As[threadIdx.x * kc + kk]);
-#pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    if (j < nc) {
-                        const float2 bb = Bs[kk][j];
-                        acc[j].x = fmaf(a.x, bb.x, fmaf(-a.y, bb.y, acc[j].x));
-                        acc[j].y = fmaf(a.x, bb.y, fmaf(a.y, bb.x, acc[j].y));
-                    }
-                }
-            }
-        }
-        if (((k0 + KC) % kFlushK) == 0 || k0 + KC >= K) {
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                tot[j].x += acc[j].x;
-                tot[j].y += acc[j].y;
-                acc[j] = make_float2(0.f, 0.f);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = make_float2((float)tot[j].x, (float)tot[j].y);
-    // every thread stays to the end: the maximum is reduced over the warp and
-    // recorded with one atomic per warp (one per thread serialises on a
-    // single address for steps of 2^30 rows)
-    const bool active = threadIdx.x < rows;
-    const int64_t m = m0 + threadIdx.x;
-    TC *crow = Cb + m * N + n0;
-    if constexpr (std::is_same<TC, float2>::value) {
-        // complex64 result: no rounding to complex-half, no scaling (e = 0);
-        // in complex-half plans its exponent and maximum feed later steps
-        float mx = 0.f;
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-            if (active && j < nc) {
-                crow[j] = acc[j];
-                mx = fmaxf(mx, fmaxf(fabsf(acc[j].x), fabsf(acc[j].y)));
-            }
-        if (sr.tmax) {
-            if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
-                sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b];
-            mx = warp_max(mx);
-            if (sr.out_max && (threadIdx.x & 31) == 0) atomic_max_nonneg(sr.out_max, mx);
-        }
-    } else {
-        // power-of-two scaling (exact): e from the operands' recorded maxima
-        int e;
-        if (sr.scale_off) e = 0;
-        else if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
-        else e = sr.fixed_exp;
-        if (sr.texp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
-            sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
-        const float s = exp2i(e);
-        float mx = 0.f;
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-            if (active && j < nc) {
-                const auto h = LpT<DT>::from_f2(make_float2(acc[j].x * s, acc[j].y * s));
-                crow[j] = h;
-                const float2 f = LpT<DT>::to_f2(h);
-                mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
-            }
-        mx = warp_max(mx);
-        if ((threadIdx.x & 31) == 0) {
-            if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
-            if (DT == TN_F16 && sr.err && !(mx <= 65504.0f)) atomicOr(sr.err, 2);
-        }
-    }
+    __shared__ RowsSmem<TA, NC> sm;
+    rows_body<TA, TB, TC, NC, DT, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, sr, za, zb, blockIdx.x, blockIdx.y,
+                                             blockIdx.z, threadIdx.x, sm);
 }
 
 template <typename TA, typename TB, typename TC, int DT>
@@ -720,103 +301,14 @@ cudaError_t launch_gemm_rows_lp(int dtype, const void *A, const void *B, void *C
 }
 
 // ---------------------------------------------------------- tiled c64 --
-// 64x64 output tile per block of 256 threads, 4x4 complex outputs per
-// thread, K in chunks of 16 staged through shared memory.  Needs M, N >= 64.
-// LONGK: FP32 partial sums over kFlushK terms added into FP64 (for K >
-// 2^12, where one FP32 running sum would lose ~sqrt(K) ulps); the short-K
-// instance keeps the FP32 sum and half the registers.
+// 64x64 output tile per block of 256 threads (tiled_c64_body).
 template <int BM, int BN, int BK, bool LONGK>
 __global__ void __launch_bounds__(256) gemm_tiled_c64_kernel(
     const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ C, int lm,
     int ln, int lk, int64_t sa, int64_t sb, int64_t sc, const int32_t *za, const int32_t *zb) {
-    constexpr int TM = BM / 16, TN = BN / 16;
-    __shared__ float2 As[BK][BM + 1];
-    __shared__ float2 Bs[BK][BN];
-    const int N = 1 << ln, K = 1 << lk;
-    const int64_t b = blockIdx.z;
-    const int64_t m0 = (int64_t)blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
-    const float2 *Ab = A + (za ? (int64_t)za[b] : b) * sa + m0 * K;
-    const float2 *Bb = B + (zb ? (int64_t)zb[b] : b) * sb + n0;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float2 acc[TM][TN];
-    double2 tot[LONGK ? TM : 1][LONGK ? TN : 1];   // FP64 sum of the FP32 partials
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            acc[i][j] = make_float2(0.f, 0.f);
-            if constexpr (LONGK) tot[i][j] = make_double2(0.0, 0.0);
-        }
-    // the next K slice is loaded into registers while the current one is
-    // multiplied out of shared memory
-    constexpr int EA = BM * BK / 256, EB = BK * BN / 256;
-    static_assert(EA * 256 == BM * BK && EB * 256 == BK * BN, "tile not a multiple of the block");
-    float2 ra[EA], rb[EB];
-    auto load_regs = [&](int k0) {
-#pragma unroll
-        for (int e = 0; e < EA; ++e) {
-            const int i = threadIdx.x + 256 * e, r = i / BK, kk = i % BK;
-            ra[e] = Ab[(int64_t)r * K + k0 + kk];
-        }
-#pragma unroll
-        for (int e = 0; e < EB; ++e) {
-            const int i = threadIdx.x + 256 * e, kk = i / BN, c = i % BN;
-            rb[e] = Bb[(int64_t)(k0 + kk) * N + c];
-        }
-    };
-    load_regs(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-        for (int e = 0; e < EA; ++e) {
-            const int i = threadIdx.x + 256 * e;
-            As[i % BK][i / BK] = ra[e];
-        }
-#pragma unroll
-        for (int e = 0; e < EB; ++e) {
-            const int i = threadIdx.x + 256 * e;
-            Bs[i / BN][i % BN] = rb[e];
-        }
-        __syncthreads();
-        if (k0 + BK < K) load_regs(k0 + BK);
-#pragma unroll 4
-        for (int kk = 0; kk < BK; ++kk) {
-            float2 a[TM], bv[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    acc[i][j].x = fmaf(a[i].x, bv[j].x, fmaf(-a[i].y, bv[j].y, acc[i][j].x));
-                    acc[i][j].y = fmaf(a[i].x, bv[j].y, fmaf(a[i].y, bv[j].x, acc[i][j].y));
-                }
-        }
-        __syncthreads();
-        if constexpr (LONGK) {
-            if (((k0 + BK) % kFlushK) == 0 || k0 + BK >= K) {
-#pragma unroll
-                for (int i = 0; i < TM; ++i)
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        tot[i][j].x += acc[i][j].x;
-                        tot[i][j].y += acc[i][j].y;
-                        acc[i][j] = make_float2(0.f, 0.f);
-                    }
-            }
-        }
-    }
-    float2 *Cb = C + b * sc + m0 * N + n0;
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            float2 v = acc[i][j];
-            if constexpr (LONGK) v = make_float2((float)tot[i][j].x, (float)tot[i][j].y);
-            Cb[(int64_t)(ty * TM + i) * N + tx + 16 * j] = v;
-        }
+    __shared__ TiledC64Smem<BM, BN, BK> sm;
+    tiled_c64_body<BM, BN, BK, LONGK, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, za, zb, blockIdx.x, blockIdx.y,
+                                                 blockIdx.z, threadIdx.x, sm);
 }
 
 cudaError_t launch_gemm_tiled_c64(const float2 *A, const float2 *B, float2 *C, int lm, int ln,
@@ -963,39 +455,8 @@ cudaError_t launch_bprep_e4m3(const void *B, void *Bp, int lk, int ln, int64_t b
 template <int DT, bool OUT_C64>
 __global__ void splitk_reduce_kernel(const float2 *__restrict__ partial, int split, void *C,
                                      int64_t n, int lk, ScaleRef sr) {
-    int e = 0;
-    if (!OUT_C64) {
-        if (sr.scale_off) e = 0;
-        else if (sr.tmax) e = min(120, scale_exponent(sr.tmax[sr.meta_a], sr.tmax[sr.meta_b], lk) + sr.headroom);
-        else e = sr.fixed_exp;
-    }
-    if (sr.texp && blockIdx.x == 0 && threadIdx.x == 0)
-        sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b] + e;
-    const float sc = exp2i(e);
-    float mx = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double re = 0.0, im = 0.0;
-        for (int p = 0; p < split; ++p) {
-            const float2 v = partial[(int64_t)p * n + i];
-            re += v.x;
-            im += v.y;
-        }
-        if constexpr (OUT_C64) {
-            const float2 w = make_float2((float)re, (float)im);
-            reinterpret_cast<float2 *>(C)[i] = w;
-            mx = fmaxf(mx, fmaxf(fabsf(w.x), fabsf(w.y)));
-        } else {
-            const auto h = LpT<DT>::from_f2(make_float2((float)re * sc, (float)im * sc));
-            reinterpret_cast<typename LpT<DT>::T2 *>(C)[i] = h;
-            const float2 f = LpT<DT>::to_f2(h);
-            mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
-        }
-    }
-    mx = warp_max(mx);
-    if ((threadIdx.x & 31) == 0 && sr.out_max) atomic_max_nonneg(sr.out_max, mx);
-    if (!OUT_C64 && DT == TN_F16 && sr.err && (threadIdx.x & 31) == 0 && !(mx <= 65504.0f))
-        atomicOr(sr.err, 2);
+    splitk_body<DT, OUT_C64>(partial, split, C, n, lk, sr, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, n,
+                             (int64_t)gridDim.x * blockDim.x, blockIdx.x == 0, threadIdx.x);
 }
 
 cudaError_t launch_splitk_reduce(const float *partial, int split, void *C, int out_c64, int dtype,
@@ -1016,54 +477,14 @@ cudaError_t launch_splitk_reduce(const float *partial, int split, void *C, int o
 }
 
 // ------------------------------------------------------------- slice sum --
-// amp[j] (+)= sum over batch index t in [t_lo, t_hi), ascending, of
-// c * F[idx(j, t)] * 2^-E (FP64; one slice added at a time).  F is stored
-// complex64 or complex-half; c is the product of the per-step rounding
-// compensations of the complex-half plan (1 otherwise).
-// Recomputation: the op's split outputs are absent from F; thread j covers
-// the amplitude whose split bits are split_val and whose other bits, in
-// order, are j's bits.
+// One thread per amplitude (slice_sum_body).
 template <typename TF, int DT>
 __global__ void slice_sum_kernel(const TF *__restrict__ F, const SumOp op, double2 *amps,
                                  int n_open, int t_lo, int t_hi, int overwrite,
                                  const int32_t *texp, const double2 *__restrict__ stepcorr,
                                  int n_steps, uint64_t split_mask, uint64_t split_val) {
-    const int64_t n = (int64_t)1 << (n_open - op.n_split);
-    const int64_t jf = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (jf >= n) return;
-    int64_t base = 0, j = (int64_t)split_val;
-    for (int t = 0, u = 0; t < n_open; ++t) {
-        if ((split_mask >> t) & 1) continue;
-        if ((jf >> u) & 1) {
-            base |= (int64_t)1 << op.open_pos[t];
-            j |= (int64_t)1 << t;
-        }
-        ++u;
-    }
-    const int E = texp ? texp[op.meta] : 0;
-    double cr = 1.0, ci = 0.0;
-    for (int k = 0; k < n_steps; ++k) {
-        const double2 f = stepcorr[k];
-        const double nr = cr * f.x - ci * f.y;
-        ci = cr * f.y + ci * f.x;
-        cr = nr;
-    }
-    double2 a = overwrite ? make_double2(0.0, 0.0) : amps[j];
-    for (int t = t_lo; t < t_hi; ++t) {
-        int64_t idx = base;
-        for (int q = 0; q < op.n_batch; ++q)
-            if ((t >> q) & 1) idx |= (int64_t)1 << op.batch_pos[q];
-        const float2 v = widen<TF, DT>(F[idx]);
-        double re = ldexp((double)v.x, -E), im = ldexp((double)v.y, -E);
-        if (n_steps > 0) {
-            const double nre = cr * re - ci * im;
-            im = cr * im + ci * re;
-            re = nre;
-        }
-        a.x += re;
-        a.y += im;
-    }
-    amps[j] = a;
+    slice_sum_body<TF, DT>(F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps, split_mask,
+                           split_val, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 *amps, int n_open,

@@ -69,6 +69,13 @@ int build_schedule(const Network &net, const Path &path, const std::vector<int> 
 
 }  // namespace tn
 
+struct tn_plan_s;
+namespace tn {
+// Device state (workspace, leaf upload), scale calibration and tile choice
+// of a plan, as the first tn_contract call does them (each once).
+int prepare_for_contract(tn_plan_s *P, cudaStream_t s);
+}  // namespace tn
+
 struct tn_plan_s {
     tn::Network net;
     tn_plan_opts opts{};
@@ -113,6 +120,10 @@ struct tn_plan_s {
     GraphKey graph_key{};
     cudaGraphExec_t graph_exec = nullptr;
     int graph_launches = 0;
+    // work queue of the last tn_contract call (tn_plan_set_queue)
+    bool use_queue = false;
+    struct tn_queue_s *queue = nullptr;
+    GraphKey queue_key{};
     // autotuner: chosen (kernel, tile) per GEMM op live in sched.ops; every
     // timing taken is kept as a record (the cost model's training data)
     bool tuned = false;

@@ -34,296 +34,11 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace tn {
 
 namespace {
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
-constexpr int kEpiThreads = 256;                  // warps 2..9
-constexpr int kTcThreads = 64 + kEpiThreads;      // producer, MMA, epilogue
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// CL: cluster-scope acquire (barriers that CTA-pair peers arrive on).
-// The thread may be suspended in the instruction until the phase completes,
-// for at most kSuspendNs (it resumes as soon as the phase completes), so a
-// waiting warp issues few instructions.
-constexpr uint32_t kSuspendNs = 20000;
-
-template <bool CL = false>
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    if constexpr (CL)
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
-            : "memory");
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
-            : "memory");
-    return ok != 0;
-}
-
-// bounded wait: returns false (and raises the CTA abort flag) on timeout or
-// when another role already aborted
-template <bool CL = false>
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try_wait<CL>(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    while (true) {
-        if (mbar_try_wait<CL>(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitLimitNs) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
-
-// ---- CTA pairs (cluster of 2): one tcgen05.mma with M = 256 spans both SMs
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// shared::cluster address of the same shared variable in CTA `rank`
-__device__ __forceinline__ uint32_t mapa_rank(const void *p, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
-                                            int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// CTA pair: the tile lands in this CTA's shared memory, its byte count on the
-// leader CTA's barrier (bar_cluster: a shared::cluster address)
-__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cluster,
-                                                 int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// completion of this thread's earlier tcgen05 ops arrives on `bar`; a CTA
-// pair arrives on the barrier at the same offset in both CTAs
-template <bool PAIR = false>
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    if constexpr (PAIR)
-        asm volatile(
-            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-            " [%0], %1;" ::"r"(smem_u32(bar)),
-            "h"((uint16_t)3)
-            : "memory");
-    else
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bar))
-                     : "memory");
-}
-
-// the same, on this CTA's barrier only
-__device__ __forceinline__ void tc_commit_pair_local(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-template <bool F8, bool PAIR>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-    if constexpr (F8 && PAIR)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    else if constexpr (F8)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    else if constexpr (PAIR)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-}
-
-// K-major shared-memory matrix descriptor (tcgen05): start address, leading
-// byte offset (unused for swizzled K-major), stride byte offset = 8 rows,
-// descriptor version 1, swizzle mode.  BKB: bytes of one K chunk row.
-template <int BKB>
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    constexpr uint32_t row_bytes = BKB;                // one swizzle row
-    constexpr uint32_t sbo = 8 * row_bytes;            // 8-row core-matrix group
-    constexpr uint64_t layout = BKB == 128 ? 2 : (BKB == 64 ? 4 : 6);  // 128B / 64B / 32B
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                            // LBO (16 B, ignored)
-    d |= (uint64_t)(sbo >> 4) << 32;
-    d |= (uint64_t)1 << 46;                            // version
-    d |= layout << 61;
-    return d;
-}
-
-template <int N>
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ int scale_exp_tc(float maxa, float maxb, int lk) {
-    const float t = 2.0f * maxa * maxb;
-    if (!(t > 0.0f) || !isfinite(t)) return 0;
-    int x;
-    const float f = frexpf(t, &x);
-    const int c = (f == 0.5f) ? x - 1 : x;
-    int e = 14 - lk - c;
-    return max(-120, min(120, e));
-}
-
-struct TcArgs {
-    void *C;
-    int64_t M;
-    int64_t n_mt;          // m tiles per batch
-    int n_nt;              // n tiles
-    int64_t batch;
-    int64_t tiles;
-    int N;                 // complex columns
-    int lk;
-    int nk;                // K chunks
-    int dtype;
-    int batch_a, batch_b;
-    int gm;                // m tiles per raster group
-    int withhold;          // self-test: issue no loads, so consumers' waits run out
-    int out_c64;           // C stored complex64 (no rounding, e = 0)
-    int split;             // K parts (split-K); tiles of part p cover K chunks [p*nk, (p+1)*nk)
-    float *partial;        // split > 1: FP32 partial sums [part][batch][M][N] complex
-    int64_t tiles_per_part;
-    // sparse-state gathers (Sec. 3.4.2): per batch entry b the A chunk za[b],
-    // the B' chunk zb[b] and the output chunk zc[b] (< 0: not stored); NULL:
-    // the batch entry itself
-    const int32_t *za, *zb, *zc;
-    int gather_r;          // > 0: B' tile = gather_r chunks (padded 2-D index), zb/zc [batch][m_r]
-    int m_r, np_chunk;
-    // > 0: C stored in a permuted mode order: bit i of the natural element
-    // index goes to bit out_dpos[i] (bits 0..2 stay)
-    int out_rank;
-    int8_t out_dpos[40];
-    int ln;                // log2 N (bit position of the row part of an element index)
-    ScaleRef sr;
-    int32_t *err;
-};
-
-// Tile t -> (batch, m tile, n tile).  Tiles go in groups of `gm` m-tiles:
-// inside a group the m index runs fastest, so the tiles in flight at once
-// cover about gm m-tiles x (SMs / gm) n-tiles, whose A rows and B' columns
-// fit in L2 together; A and B' are then read from DRAM about once per group
-// instead of once per m-tile.
-// Bits lo..hi-1 of a C element index moved to the consumer's mode order
-// (the fused permutation is a bit permutation, so the parts OR together).
-__device__ __forceinline__ int64_t permute_bits(const TcArgs &a, int64_t e, int lo, int hi) {
-    int64_t d = 0;
-    for (int i = lo; i < hi; ++i) d |= ((e >> i) & 1) << a.out_dpos[i];
-    return d;
-}
-
-__device__ __forceinline__ void tile_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt,
-                                            int &nt) {
-    t %= a.tiles_per_part;          // the K part is t / tiles_per_part
-    const int64_t per_batch = a.n_mt * a.n_nt;
-    b = t / per_batch;
-    const int64_t r = t - b * per_batch;
-    const int64_t span = (int64_t)a.gm * a.n_nt;
-    const int64_t g = r / span;
-    const int64_t in = r - g * span;
-    const int64_t gm = min((int64_t)a.gm, a.n_mt - g * a.gm);
-    mt = g * a.gm + in % gm;
-    nt = (int)(in / gm);
-}
-
-// BROWS: rows of the B' tile this CTA holds (BN, or BN / 2 in a CTA pair)
-template <int BROWS, int BKB, int STAGES>
-struct TcSmem {
-    static constexpr int a_bytes = 128 * BKB;
-    static constexpr int b_bytes = BROWS * BKB;
-    static constexpr int stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
-    static constexpr int ring = STAGES * stage_bytes;
-    static constexpr int bars = (2 * STAGES + 5) * 8;
-    static constexpr int total = 1024 + ring + bars + 16;   // + alignment slack
-};
 
 // BKB: bytes of a K chunk per row (32, 64 or 128); F8: E4M3 operands.
 // PAIR: the kernel runs as clusters of 2 CTAs on 2 SMs; a pair computes a
@@ -557,89 +272,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
                 uint32_t r[16];
                 tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 tmem_wait_ld();
-                int64_t cbk = cb;              // output chunk of these 16 columns
-                int colr = col0 + c;           // their first real column in that chunk
-                int nreal = min(16, col_end - c);
-                if (args.gather_r) {
-                    const int gcol = col0 + c, rr = gcol / args.np_chunk;
-                    colr = gcol - rr * args.np_chunk;
-                    cbk = rr < args.m_r ? (int64_t)args.zc[b * args.m_r + rr] : -1;
-                    nreal = min(16, 2 * args.N - colr);
-                }
-                if (cbk < 0 || nreal <= 0) {
-                    // padded place of the 2-D index (or padding of B'): computed, not stored
-                } else if (m < args.M && (args.out_c64 || args.partial)) {
-                    // complex64 result (or split-K partial): the FP32 accumulators as they are
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        v[j] = __uint_as_float(r[j]);
-                        if (j < nreal) mx = fmaxf(mx, fabsf(v[j]));
-                    }
-                    const int64_t part = t / args.tiles_per_part;
-                    const int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
-                    float *dst = args.partial
-                                     ? args.partial + (((part * args.batch + b) * args.M + m) * (int64_t)args.N +
-                                                       colr / 2) * 2
-                                     : reinterpret_cast<float *>(args.C) + ei * 2;
-                    if (args.out_rank) {
-                        // 8 complex values, each to its permuted place
-                        const int64_t base = prow | permute_bits(args, colr / 2, 3, args.ln);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            reinterpret_cast<float2 *>(args.C)[base | lowtab[j]] = make_float2(v[2 * j], v[2 * j + 1]);
-                    } else if (nreal >= 4) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (4 * q < nreal)
-                                reinterpret_cast<float4 *>(dst)[q] =
-                                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    } else {
-                        reinterpret_cast<float2 *>(dst)[0] = make_float2(v[0], v[1]);
-                    }
-                } else if (m < args.M) {
-                    // nreal: 2, 4, 8 or 16
-                    uint32_t packed[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float re = __uint_as_float(r[2 * j]) * sc;
-                        const float im = __uint_as_float(r[2 * j + 1]) * sc;
-                        float2 back;
-                        if (args.dtype == TN_BF16) {
-                            __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
-                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
-                            back = __bfloat1622float2(h);
-                        } else {
-                            __half2 h = __floats2half2_rn(re, im);
-                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
-                            back = __half22float2(h);
-                        }
-                        if (2 * j < nreal) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
-                    }
-                    const int64_t ei = (cbk * args.M + m) * (int64_t)args.N + colr / 2;
-                    uint32_t *dst = reinterpret_cast<uint32_t *>(args.C) + ei;
-                    if (args.out_rank) {
-                        const int64_t base = prow | permute_bits(args, colr / 2, 3, args.ln);
-                        if (low_kept) {
-                            uint4 *d4 = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(args.C) + base);
-                            d4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                            d4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                reinterpret_cast<uint32_t *>(args.C)[base | lowtab[j]] = packed[j];
-                        }
-                    } else if (nreal == 16) {
-                        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                        reinterpret_cast<uint4 *>(dst)[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-                    } else if (nreal == 8) {
-                        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    } else if (nreal == 4) {
-                        reinterpret_cast<uint2 *>(dst)[0] = make_uint2(packed[0], packed[1]);
-                    } else {
-                        dst[0] = packed[0];
-                    }
-                }
+                tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, sc, mx);
             }
             tc_fence_before();
             if constexpr (PAIR) mbar_arrive_cluster(acce_leader + (uint32_t)(acc * 8));
@@ -883,6 +516,13 @@ cudaError_t tc_prepare() {
     return e;
 }
 
+bool tc_encode_3d(CUtensorMap *m, int dtype, int esz, const void *base, uint64_t inner, uint64_t rows,
+                  uint64_t depth, uint32_t box_inner, uint32_t box_rows) {
+    return encode_3d(m, dtype, esz, base, inner, rows, depth, box_inner, box_rows);
+}
+
+int tc_default_gm(int bn) { return default_gm(bn); }
+
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
 
 // A step runs on CTA pairs when asked and when its tiles are the pair
@@ -918,13 +558,10 @@ size_t tc_split_bytes(int lm, int ln, int lk, int64_t batch) {
     return split > 1 ? (size_t)split * (size_t)(batch << (lm + ln)) * 8 : 0;
 }
 
-cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
+cudaError_t tc_setup(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, bool one_cta, CUtensorMap *ma_out,
+                     CUtensorMap *mb_out, TcArgs *a_out, int *bn_out, int *bk_out, bool *pair_out) {
     if (d.fp8 ? !tc_gemm_supported_fp8(d.lk, d.ln) : !tc_gemm_supported(d.lk, d.ln))
         return cudaErrorInvalidValue;
-    {
-        const cudaError_t e = tc_prepare();
-        if (e != cudaSuccess) return e;
-    }
     const int esz = d.fp8 ? 1 : 2;
     const int kreal = 2 << d.lk;                 // 2K elements
     // K chunk: 128-byte rows where K allows (FP8: always, K >= 64)
@@ -937,9 +574,10 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     const int64_t M = (int64_t)1 << d.lm;
     const bool gathered = d.za || d.zb || d.zc;
     // CTA pairs: 256 x 256 tiles of FP16/BF16 with 128-byte K chunks
-    const bool pair = tc_pair_eligible(d.pair, d.fp8, d.lm, d.ln, d.lk, bn) && !gathered && d.gather_r == 0;
+    const bool pair = !one_cta && tc_pair_eligible(d.pair, d.fp8, d.lm, d.ln, d.lk, bn) && !gathered &&
+                      d.gather_r == 0;
     if (d.half_k && !pair && !d.fp8 && bk == 64) bk = 32;
-    CUtensorMap ma, mb;
+    CUtensorMap &ma = *ma_out, &mb = *mb_out;
     const int64_t depth_a = d.depth_a > 0 ? d.depth_a : (d.batch_a ? d.batch : 1);
     const int64_t depth_b = d.depth_b > 0 ? d.depth_b : (d.batch_b ? d.batch : 1);
     if (!encode_3d(&ma, d.dtype, esz, d.A, (uint64_t)kreal, (uint64_t)M, (uint64_t)depth_a, bk, 128))
@@ -948,7 +586,8 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     if (!encode_3d(&mb, d.dtype, esz, d.Bp, (uint64_t)kreal, (uint64_t)d.np, (uint64_t)depth_b, bk,
                    d.gather_r > 0 ? d.np : (pair ? bn / 2 : bn)))
         return cudaErrorInvalidValue;
-    TcArgs a;
+    TcArgs &a = *a_out;
+    a = TcArgs{};
     a.C = d.C;
     a.M = M;
     a.n_mt = pair ? M / 256 : (M + 127) / 128;
@@ -997,6 +636,25 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     if (pair) a.gm = std::max(1, a.gm / 2);   // gm counts 128-row m tiles
     a.sr = sr;
     a.err = d_err;
+    *bn_out = bn;
+    *bk_out = bk;
+    *pair_out = pair;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
+    {
+        const cudaError_t e = tc_prepare();
+        if (e != cudaSuccess) return e;
+    }
+    CUtensorMap ma, mb;
+    TcArgs a;
+    int bn = 0, bk = 0;
+    bool pair = false;
+    {
+        const cudaError_t e = tc_setup(d, sr, d_err, false, &ma, &mb, &a, &bn, &bk, &pair);
+        if (e != cudaSuccess) return e;
+    }
     cudaError_t e;
     if (pair) {
         e = run_tc_pair<false>(ma, mb, a, s);

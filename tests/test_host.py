@@ -291,3 +291,25 @@ def test_cost_features_mark_cta_pair_tiles():
     assert x[:, 25].tolist() == [0.0, 1.0, 0.0, 0.0, 0.0, 1.0]
     # the pair bit does not change the other features of the record
     assert np.array_equal(np.delete(x[0], 25), np.delete(x[1], 25))
+
+
+def test_workspace_budget_picks_the_largest_fitting_slice_batch():
+    # tn_plan_opts.workspace_budget: one path search, then the largest slice
+    # batch whose workspace fits the budget (else no batching)
+    items = rqcgen.uneven_batch()
+    for i in (2, 14, 17):
+        c, q = items[i]
+        budget = 1 << 30
+        p = tn.plan_within_budget(c, q, dtype=tn.F16, torch_allocator=False, workspace_budget=budget)
+        info = p.info()
+        b, s = info["slice_batch_log2"], info["n_slice_edges"]
+        assert info["workspace_bytes"] <= budget or b == 0
+        if b < min(s, 16):
+            nxt = _plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=24, trials=4, slice_batch_log2=b + 1)
+            assert nxt.info()["workspace_bytes"] > budget
+            assert nxt.sliced_edges() == p.sliced_edges()
+
+
+def test_cost_targets_are_log2_microseconds():
+    recs = [{"ms": 1.0}, {"ms": 0.25}, {"ms": 1e-9}]
+    np.testing.assert_allclose(tn.cost_targets(recs), [np.log2(1e3), np.log2(250.0), np.log2(1e-3)], rtol=1e-6)
