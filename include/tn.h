@@ -369,6 +369,32 @@ int tn_queue_create(tn_plan_t *const *plans, int32_t n, const int64_t *slice_beg
 int tn_queue_run(tn_queue_t *queue, void *stream, tn_contract_report *rep);
 int tn_queue_info(const tn_queue_t *queue, tn_queue_stats *out);
 int tn_queue_set_wait_limit(tn_queue_t *queue, int64_t limit_us);
+/*
+ * Queue profiling: when enabled, each run sums per op kind (index =
+ * TN_QK_*) the items run, the time their CTAs spent waiting for the op
+ * before them and the time spent running them (CTA-milliseconds, from
+ * %globaltimer); tn_queue_profile_read returns the last run's sums (after it
+ * finished) for kinds 0..capacity-1.
+ */
+#define TN_QK_ZERO 1
+#define TN_QK_LEAF 2
+#define TN_QK_PERM 3
+#define TN_QK_PERM_TILED 4
+#define TN_QK_BPREP_GATHER 5
+#define TN_QK_BPREP_C64 6
+#define TN_QK_ROWS 7
+#define TN_QK_TILED_C64 8
+#define TN_QK_TC 9
+#define TN_QK_SPLITK 10
+#define TN_QK_SUM 11
+#define TN_QK_COUNT 12
+typedef struct {
+    int64_t items;
+    double wait_ms;
+    double busy_ms;
+} tn_queue_kind_stats;
+int tn_queue_profile(tn_queue_t *queue, int enable);
+int tn_queue_profile_read(const tn_queue_t *queue, tn_queue_kind_stats *out, int32_t capacity);
 void tn_queue_destroy(tn_queue_t *queue);
 
 /*
@@ -392,6 +418,12 @@ int tn_selftest_queue_timeout(int32_t limit_ms, void *stream);
  * post-processing): from d_amps (device, 2^n_open complex128) return the k
  * indices of largest |amp|^2 and their probabilities, ties to the lower index,
  * in descending order.  out_idx / out_prob: host, length k, caller-owned.
+ * Small problems (k * 2^n_open <= 2^22) run one block that rescans the
+ * amplitudes once per result; larger ones a multi-block radix select over
+ * the bits of |amp|^2 (8 passes over the amplitudes), the collection of the
+ * k kept entries (ties at the threshold to the lowest indices) and a bitonic
+ * sort -- O(2^n_open) reads per pass at any k.  Allocates its results and
+ * scratch on `stream` (stream-ordered allocator) and frees them.
  * Synchronizes `stream`.  Errors: TN_EINVAL (k < 1 or k > 2^n_open, n_open
  * > 30), TN_ENOMEM, TN_ECUDA.
  */
@@ -401,18 +433,22 @@ int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
 /*
  * tn_sample_noalloc: tn_sample for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a deployment variant.
- * tn_sample allocates a small device buffer for the k results on every
- * call; a caller inside a host application that owns all device memory
- * through its own pool, or a latency-critical thread that must not enter
- * the CUDA allocator (cudaMalloc/cudaFree can synchronize the device),
- * cannot.  This call allocates nothing: its scratch is a fixed array in
- * device global memory of TN_SAMPLE_NOALLOC_MAX_K indices and probabilities
- * (16 KiB), present on every GPU that loads the library until the process
- * exits.  Same arguments, results and ordering as tn_sample.
+ * tn_sample allocates a small device buffer for the k results (and the
+ * selection's scratch) on every call; a caller inside a host application
+ * that owns all device memory through its own pool, or a latency-critical
+ * thread that must not enter the CUDA allocator (cudaMalloc/cudaFree can
+ * synchronize the device), cannot.  This call allocates nothing: its
+ * scratch is a fixed array in device global memory holding
+ * TN_SAMPLE_NOALLOC_MAX_K indices and probabilities and the selection's
+ * working space for that many results (44 KiB), present on every GPU that
+ * loads the library until the process exits.  Same arguments, results,
+ * ordering and kernels as tn_sample.
  *   - k > TN_SAMPLE_NOALLOC_MAX_K is rejected with TN_EINVAL (use tn_sample).
  *   - The first call on a device looks up the array's device address
  *     (set-up, once per device, with that device current); make that first
- *     call before any stream capture.
+ *     call before any stream capture.  The address is kept for the life of
+ *     the process: after cudaDeviceReset on a device, do not call this on
+ *     that device again.
  *   - All calls on a device share the one array and it keeps the last
  *     call's contents; calls that overlap on the GPU (different streams or
  *     threads without ordering between them) race and may return each

@@ -44,8 +44,11 @@ EXPORTED = [
     "tn_cost_model_train", "tn_cost_model_predict", "tn_cost_features", "tn_plan_set_cost_model",
     "tn_plan_predict_ms", "tn_plan_apply_tuning", "tn_gemm_gather", "tn_encode", "tn_decode",
     "tn_queue_create", "tn_queue_run", "tn_queue_info", "tn_queue_set_wait_limit", "tn_queue_destroy",
-    "tn_plan_set_queue", "tn_selftest_queue_timeout", "tn_cost_targets",
+    "tn_plan_set_queue", "tn_selftest_queue_timeout", "tn_cost_targets", "tn_queue_profile",
+    "tn_queue_profile_read",
 ]
+QK_NAMES = ["", "zero", "leaf", "permute", "permute_tiled", "bprep_gather", "bprep_c64", "gemm_rows",
+            "gemm_tiled_c64", "gemm_tc", "splitk", "slice_sum"]
 COST_NFEAT = 26
 KC_NAMES = ["leaf", "permute", "bprep", "gemm_tc", "gemm_lp_rows", "gemm_c64", "slice_sum", "quant"]
 
@@ -112,6 +115,10 @@ class QueueStats(ctypes.Structure):
     _fields_ = [("n_plans", ctypes.c_int32), ("n_ops", ctypes.c_int32), ("n_items", ctypes.c_int32),
                 ("max_chain", ctypes.c_int32), ("ctas", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("table_bytes", ctypes.c_int64), ("flops", ctypes.c_double), ("slices", ctypes.c_int64)]
+
+
+class QueueKindStats(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int64), ("wait_ms", ctypes.c_double), ("busy_ms", ctypes.c_double)]
 
 
 class KernelStats(ctypes.Structure):
@@ -210,6 +217,8 @@ def lib():
         L.tn_queue_destroy.argtypes = [vp]
         L.tn_queue_destroy.restype = None
         L.tn_plan_set_queue.argtypes = [vp, ctypes.c_int]
+        L.tn_queue_profile.argtypes = [vp, ctypes.c_int]
+        L.tn_queue_profile_read.argtypes = [vp, ctypes.POINTER(QueueKindStats), i32]
         L.tn_selftest_queue_timeout.argtypes = [i32, vp]
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_plan_destroy.restype = None
@@ -728,6 +737,16 @@ class Queue:
 
     def set_wait_limit(self, limit_us: int):
         _check(lib().tn_queue_set_wait_limit(self._h, int(limit_us)))
+
+    def profile(self, enable: bool = True):
+        """Per op kind: items, CTA-ms waiting for dependencies, CTA-ms running."""
+        _check(lib().tn_queue_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        arr = (QueueKindStats * len(QK_NAMES))()
+        _check(lib().tn_queue_profile_read(self._h, arr, len(QK_NAMES)))
+        return {QK_NAMES[k]: {"items": arr[k].items, "wait_ms": arr[k].wait_ms, "busy_ms": arr[k].busy_ms}
+                for k in range(1, len(QK_NAMES)) if arr[k].items}
 
     def __del__(self):
         h = getattr(self, "_h", None)

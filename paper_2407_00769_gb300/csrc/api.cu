@@ -1294,9 +1294,15 @@ int tn_batch_create(tn_plan_t *const *plans, int32_t n, double *const *d_amps, i
     if (n_streams < 1) n_streams = 1;
     n_streams = std::min(n_streams, std::min(n, 64));
     for (int i = 0; i < n; ++i) {
-        const int rc = ensure_device(plans[i]);
-        if (rc != TN_OK) return rc;
         if (plans[i]->prof_mask) return fail(TN_EINVAL, "profiling must be off for a batch");
+        // device state, scale calibration and tile choice, as a first
+        // tn_contract would do them (outside the capture below)
+        int rc = prepare_for_contract(plans[i], nullptr);
+        if (rc == TN_OK) {
+            const cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) rc = cuda_fail(e, "plan set-up");
+        }
+        if (rc != TN_OK) return rc;
     }
     // longest-processing-time assignment of plans to side streams: by the
     // cost model's predicted time when every plan has a model attached,
@@ -1428,15 +1434,18 @@ int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
     const int64_t n = (int64_t)1 << n_open;
     if (k < 1 || k > n) return fail(TN_EINVAL, "k must be in 1..2^n_open");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t *d_idx = nullptr;
-    double *d_prob = nullptr;
-    TN_CUDA(cudaMallocAsync((void **)&d_idx, (size_t)k * 8, s), "cudaMallocAsync");
-    TN_CUDA(cudaMallocAsync((void **)&d_prob, (size_t)k * 8, s), "cudaMallocAsync");
-    cudaError_t e = launch_topk((const double2 *)d_amps, n, k, d_idx, d_prob, s);
+    // one allocation: the k results, then the selection's scratch
+    const size_t scratch = topk_scratch_bytes(n, k);
+    const size_t res = ((size_t)k * 16 + 255) / 256 * 256;
+    char *d_buf = nullptr;
+    TN_CUDA(cudaMallocAsync((void **)&d_buf, res + scratch, s), "cudaMallocAsync");
+    int64_t *d_idx = (int64_t *)d_buf;
+    double *d_prob = (double *)(d_buf + (size_t)k * 8);
+    cudaError_t e = launch_topk_select((const double2 *)d_amps, n, k, scratch ? d_buf + res : nullptr, d_idx,
+                                       d_prob, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_idx, d_idx, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_prob, d_prob, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(d_idx, s);
-    cudaFreeAsync(d_prob, s);
+    cudaFreeAsync(d_buf, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "tn_sample");
     return TN_OK;

@@ -625,4 +625,263 @@ cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, d
     return cudaGetLastError();
 }
 
+// Top-k over many blocks, O(n) reads per pass: the same total order (p
+// descending, index ascending; p = re*re + im*im rounded as above).  p >= 0,
+// so the bits of p, read as an unsigned 64-bit integer, order like p.
+//  1. radix select, 8 passes of 8 bits from the top: each pass histograms
+//     the next byte of the keys that match the bytes fixed so far, and one
+//     thread fixes the byte at which the count from the top reaches the
+//     number still wanted -- after 8 passes the k-th largest key T is known,
+//     and kk, how many of the keys equal to T belong to the top k;
+//  2. every key above T is kept, and of the keys equal to T the kk with the
+//     lowest indices (per-block counts, an exclusive scan over the blocks,
+//     and a block-wide scan in index order inside each block);
+//  3. the k kept entries are sorted by the total order (bitonic: in shared
+//     memory up to 2048 entries, else over global memory).
+struct TopkHead {
+    uint64_t prefix, mask;
+    int64_t kk;            // keys equal to the threshold that are kept
+    int64_t n_gt;          // keys above the threshold (k - kk at the end)
+    uint32_t gt_pos;       // write cursor of the keys above the threshold
+    uint32_t pad_;
+    uint32_t hist[256];
+};
+constexpr int kTopkMaxBlocks = 1024;
+constexpr int kTopkSmallSort = 2048;
+
+__device__ __forceinline__ uint64_t topk_key(double2 a) {
+    return (uint64_t)__double_as_longlong(__dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)));
+}
+
+__global__ void topk_init_kernel(TopkHead *h, int64_t k) {
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h->hist[t] = 0u;
+    if (threadIdx.x == 0) {
+        h->prefix = 0;
+        h->mask = 0;
+        h->kk = k;
+        h->n_gt = 0;
+        h->gt_pos = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) topk_hist_kernel(const double2 *amps, int64_t n, TopkHead *h, int shift) {
+    __shared__ uint32_t sh[256];
+    sh[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint64_t prefix = h->prefix, mask = h->mask;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = topk_key(amps[i]);
+        if ((key & mask) == prefix) atomicAdd(&sh[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (sh[threadIdx.x]) atomicAdd(&h->hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+__global__ void topk_select_kernel(TopkHead *h, int shift) {
+    if (threadIdx.x != 0) return;
+    int64_t need = h->kk, cum = 0;
+    int digit = 0;
+    for (int v = 255; v >= 0; --v) {
+        const int64_t c = h->hist[v];
+        if (cum + c >= need) {
+            digit = v;
+            break;
+        }
+        cum += c;
+    }
+    h->prefix |= (uint64_t)digit << shift;
+    h->mask |= (uint64_t)0xFF << shift;
+    h->kk = need - cum;
+    for (int t = 0; t < 256; ++t) h->hist[t] = 0u;
+}
+
+__global__ void __launch_bounds__(256) topk_count_kernel(const double2 *amps, int64_t n, const TopkHead *h,
+                                                         int64_t chunk, int64_t *blockcnt) {
+    __shared__ int64_t sw[8];
+    const uint64_t T = h->prefix;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    int64_t c = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) c += topk_key(amps[i]) == T;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < 8; ++w) t += sw[w];
+        blockcnt[blockIdx.x] = t;
+    }
+}
+
+__global__ void topk_offsets_kernel(int64_t *blockcnt, int nblk, TopkHead *h, int64_t k) {
+    if (threadIdx.x != 0) return;
+    int64_t run = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const int64_t c = blockcnt[b];
+        blockcnt[b] = run;
+        run += c;
+    }
+    h->n_gt = k - h->kk;
+    h->gt_pos = 0;
+}
+
+__global__ void __launch_bounds__(256) topk_collect_kernel(const double2 *amps, int64_t n, TopkHead *h,
+                                                           int64_t chunk, const int64_t *offsets, int64_t *cand_idx,
+                                                           double *cand_p) {
+    __shared__ int s_warp[8];
+    const uint64_t T = h->prefix;
+    const int64_t kk = h->kk, n_gt = h->n_gt;
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t run = offsets[blockIdx.x];      // rank of the next equal key in index order
+    for (int64_t base = i0; base < i1; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        uint64_t key = 0;
+        double p = 0.0;
+        const bool valid = i < i1;
+        if (valid) {
+            const double2 a = amps[i];
+            p = __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+            key = (uint64_t)__double_as_longlong(p);
+        }
+        if (valid && key > T) {
+            const uint32_t pos = atomicAdd(&h->gt_pos, 1u);
+            cand_idx[pos] = i;
+            cand_p[pos] = p;
+        }
+        const bool eq = valid && key == T;
+        const uint32_t bal = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        int64_t before = 0, total = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) before += s_warp[w];
+            total += s_warp[w];
+        }
+        if (eq) {
+            const int64_t rank = run + before + __popc(bal & ((1u << lane) - 1u));
+            if (rank < kk) {
+                cand_idx[n_gt + rank] = i;
+                cand_p[n_gt + rank] = p;
+            }
+        }
+        run += total;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void topk_cmpswap(int64_t &ia, double &pa, int64_t &ib, double &pb, bool up) {
+    // up: a must come before b in the total order
+    const bool b_first = before(pb, ib, pa, ia);
+    if (b_first == up) {
+        const int64_t ti = ia;
+        ia = ib;
+        ib = ti;
+        const double tp = pa;
+        pa = pb;
+        pb = tp;
+    }
+}
+
+__global__ void __launch_bounds__(1024) topk_sort_small_kernel(const int64_t *cand_idx, const double *cand_p, int k,
+                                                               int P, int64_t *out_idx, double *out_prob) {
+    __shared__ int64_t si[kTopkSmallSort];
+    __shared__ double sp[kTopkSmallSort];
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        si[t] = t < k ? cand_idx[t] : INT64_MAX;
+        sp[t] = t < k ? cand_p[t] : -1.0;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+                topk_cmpswap(si[i], sp[i], si[j], sp[j], (i & size) == 0);
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+        out_idx[t] = si[t];
+        out_prob[t] = sp[t];
+    }
+}
+
+__global__ void topk_pad_kernel(int64_t *cand_idx, double *cand_p, int64_t k, int64_t P) {
+    for (int64_t t = k + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x) {
+        cand_idx[t] = INT64_MAX;
+        cand_p[t] = -1.0;
+    }
+}
+
+__global__ void topk_bitonic_kernel(int64_t *cand_idx, double *cand_p, int64_t P, int64_t size, int64_t stride) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P / 2; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = 2 * t - (t & (stride - 1)), j = i + stride;
+        int64_t ia = cand_idx[i], ib = cand_idx[j];
+        double pa = cand_p[i], pb = cand_p[j];
+        topk_cmpswap(ia, pa, ib, pb, (i & size) == 0);
+        cand_idx[i] = ia;
+        cand_idx[j] = ib;
+        cand_p[i] = pa;
+        cand_p[j] = pb;
+    }
+}
+
+__global__ void topk_copy_kernel(const int64_t *cand_idx, const double *cand_p, int64_t k, int64_t *out_idx,
+                                 double *out_prob) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += (int64_t)gridDim.x * blockDim.x) {
+        out_idx[t] = cand_idx[t];
+        out_prob[t] = cand_p[t];
+    }
+}
+
+static int64_t topk_pad(int64_t k) {
+    int64_t P = 1;
+    while (P < k) P <<= 1;
+    return P;
+}
+
+bool topk_one_block(int64_t n, int64_t k) { return k * n <= ((int64_t)1 << 22); }
+
+size_t topk_scratch_bytes(int64_t n, int64_t k) {
+    if (topk_one_block(n, k)) return 0;
+    const int64_t P = k <= kTopkSmallSort ? k : topk_pad(k);
+    return 4096 + (size_t)kTopkMaxBlocks * 8 + (size_t)P * 16;
+}
+
+cudaError_t launch_topk_select(const double2 *amps, int64_t n, int64_t k, void *scratch, int64_t *d_idx,
+                               double *d_prob, cudaStream_t s) {
+    if (k < 1 || k > n) return cudaErrorInvalidValue;
+    if (topk_one_block(n, k)) return launch_topk(amps, n, (int)k, d_idx, d_prob, s);
+    if (!scratch) return cudaErrorInvalidValue;
+    const int64_t P = k <= kTopkSmallSort ? k : topk_pad(k);
+    char *base = (char *)scratch;
+    TopkHead *h = (TopkHead *)base;
+    int64_t *blockcnt = (int64_t *)(base + 4096);
+    int64_t *cand_idx = (int64_t *)(base + 4096 + (size_t)kTopkMaxBlocks * 8);
+    double *cand_p = (double *)(cand_idx + P);
+    topk_init_kernel<<<1, 256, 0, s>>>(h, k);
+    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, (int64_t)tc_num_sms() * 4));
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        topk_hist_kernel<<<hist_blocks, 256, 0, s>>>(amps, n, h, shift);
+        topk_select_kernel<<<1, 32, 0, s>>>(h, shift);
+    }
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(kTopkMaxBlocks, (n + 4095) / 4096));
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    topk_count_kernel<<<nblk, 256, 0, s>>>(amps, n, h, chunk, blockcnt);
+    topk_offsets_kernel<<<1, 32, 0, s>>>(blockcnt, nblk, h, k);
+    topk_collect_kernel<<<nblk, 256, 0, s>>>(amps, n, h, chunk, blockcnt, cand_idx, cand_p);
+    if (k <= kTopkSmallSort) {
+        int P2 = 1;
+        while (P2 < k) P2 <<= 1;
+        topk_sort_small_kernel<<<1, 1024, 0, s>>>(cand_idx, cand_p, (int)k, P2, d_idx, d_prob);
+        return cudaGetLastError();
+    }
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P / 2 + 255) / 256, (int64_t)tc_num_sms() * 8));
+    topk_pad_kernel<<<blocks, 256, 0, s>>>(cand_idx, cand_p, k, P);
+    for (int64_t size = 2; size <= P; size <<= 1)
+        for (int64_t stride = size >> 1; stride > 0; stride >>= 1)
+            topk_bitonic_kernel<<<blocks, 256, 0, s>>>(cand_idx, cand_p, P, size, stride);
+    topk_copy_kernel<<<blocks, 256, 0, s>>>(cand_idx, cand_p, k, d_idx, d_prob);
+    return cudaGetLastError();
+}
+
 }  // namespace tn

@@ -85,6 +85,15 @@ cudaError_t launch_metrics(const double2 *r, const double2 *b, int64_t n, double
                            double *d_partials, int n_blocks, cudaStream_t s);
 cudaError_t launch_topk(const double2 *amps, int64_t n, int k, int64_t *d_idx, double *d_prob,
                         cudaStream_t s);
+// Top-k of n amplitudes in the order (|amp|^2 descending, index ascending):
+// the one-block kernel above while k * n <= 2^22, else a multi-block radix
+// select (O(n) reads per pass, 8 passes), a collection of the k entries and
+// a bitonic sort.  scratch: topk_scratch_bytes(n, k) bytes of device memory
+// (0: none needed); d_idx / d_prob: device, k entries each.
+bool topk_one_block(int64_t n, int64_t k);
+size_t topk_scratch_bytes(int64_t n, int64_t k);
+cudaError_t launch_topk_select(const double2 *amps, int64_t n, int64_t k, void *scratch, int64_t *d_idx,
+                               double *d_prob, cudaStream_t s);
 
 // tcgen05 GEMM (complex-half as real, Eq. 5-6).  Tensor maps are encoded
 // by the host (tc_gemm.cu).

@@ -78,11 +78,15 @@ struct QOp {
     int64_t prm;        // byte offset of the parameter record in the blob
 };
 
+constexpr int kQKinds = 12;
 struct QState {
     int32_t head;       // next item to claim
     int32_t abort;      // 1: a wait ran out; every CTA returns
     int32_t err;        // bit 0: a dependency wait ran out
     int32_t fail_item;  // the item whose wait ran out
+    // profiling (tn_queue_profile): per op kind, items run, ns spent waiting
+    // for the dependency, ns running (summed over CTAs)
+    unsigned long long items[kQKinds], wait_ns[kQKinds], busy_ns[kQKinds];
 };
 
 struct QZero { uint32_t *p; int64_t n, per_item; };
@@ -506,7 +510,7 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
 // ------------------------------------------------------------------ kernel --
 __global__ void __launch_bounds__(kQThreads, 1)
     queue_kernel(const QOp *ops, const int2 *items, int32_t n_items, const uint8_t *blob, int32_t *done, QState *st,
-                 uint64_t dep_limit_ns) {
+                 uint64_t dep_limit_ns, int profile) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(ring + kQRing);
@@ -545,9 +549,11 @@ __global__ void __launch_bounds__(kQThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     TcPipe pipe{0, 0, 0, 0, 0, 0, 0, 0};
+    uint64_t t_claim = 0, t_ready = 0;
 
     while (true) {
         if (threadIdx.x == 0) {
+            if (profile) t_claim = globaltimer();
             int i = -1;
             if (!*(volatile int32_t *)&st->abort) {
                 i = atomicAdd(&st->head, 1);
@@ -579,6 +585,7 @@ __global__ void __launch_bounds__(kQThreads, 1)
                 }
             }
             s_item = i;
+            if (profile) t_ready = globaltimer();
         }
         __syncthreads();
         const int i = s_item;
@@ -607,6 +614,12 @@ __global__ void __launch_bounds__(kQThreads, 1)
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(done + it.x, 1);
+            if (profile) {
+                const int kind = op.kind < kQKinds ? op.kind : 0;
+                atomicAdd(&st->items[kind], 1ull);
+                atomicAdd(&st->wait_ns[kind], (unsigned long long)(t_ready - t_claim));
+                atomicAdd(&st->busy_ns[kind], (unsigned long long)(globaltimer() - t_ready));
+            }
         }
     }
     __syncthreads();
@@ -952,6 +965,7 @@ struct tn_queue_s {
     double flops = 0;
     int64_t slices = 0;
     uint64_t dep_limit_ns = 10000000000ull;
+    int profile = 0;
 };
 
 namespace {
@@ -988,7 +1002,8 @@ int queue_finish(tn_queue_s *Q, Builder &Bd) {
     const size_t items_b = (items.size() * sizeof(int2) + 255) / 256 * 256;
     const size_t blob_b = (Bd.blob.size() + 255) / 256 * 256;
     const size_t done_b = (Bd.ops.size() * 4 + 255) / 256 * 256;
-    const size_t total = ops_b + items_b + blob_b + done_b + 256;
+    const size_t state_b = (sizeof(QState) + 255) / 256 * 256;
+    const size_t total = ops_b + items_b + blob_b + done_b + state_b;
     cudaError_t e = cudaMalloc(&Q->d_mem, total);
     if (e != cudaSuccess) return qfail(TN_ENOMEM, std::string("queue tables: ") + cudaGetErrorString(e));
     char *m = (char *)Q->d_mem;
@@ -997,7 +1012,7 @@ int queue_finish(tn_queue_s *Q, Builder &Bd) {
     Q->d_blob = (uint8_t *)(m + ops_b + items_b);
     Q->d_done = (int32_t *)(m + ops_b + items_b + blob_b);
     Q->d_state = (QState *)(m + ops_b + items_b + blob_b + done_b);
-    Q->counters_bytes = done_b + 256;
+    Q->counters_bytes = done_b + state_b;
     Q->blob_bytes = (int64_t)Bd.blob.size();
     e = cudaMemcpy(Q->d_ops, Bd.ops.data(), Bd.ops.size() * sizeof(QOp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -1075,7 +1090,7 @@ int tn_queue_run(tn_queue_t *Q, void *stream, tn_contract_report *rep) {
     cudaError_t e = cudaMemsetAsync(Q->d_done, 0, Q->counters_bytes, s);
     if (e == cudaSuccess) {
         queue_kernel<<<Q->grid, kQThreads, kQSmem, s>>>(Q->d_ops, Q->d_items, Q->n_items, Q->d_blob, Q->d_done,
-                                                       Q->d_state, Q->dep_limit_ns);
+                                                       Q->d_state, Q->dep_limit_ns, Q->profile);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return qfail(TN_ECUDA, std::string("queue launch: ") + cudaGetErrorString(e));
@@ -1126,6 +1141,25 @@ int tn_queue_info(const tn_queue_t *Q, tn_queue_stats *out) {
 int tn_queue_set_wait_limit(tn_queue_t *Q, int64_t limit_us) {
     if (!Q || limit_us < 1) return qfail(TN_EINVAL, "bad wait limit");
     Q->dep_limit_ns = (uint64_t)limit_us * 1000ull;
+    return TN_OK;
+}
+
+int tn_queue_profile(tn_queue_t *Q, int enable) {
+    if (!Q) return qfail(TN_EINVAL, "NULL queue");
+    Q->profile = enable ? 1 : 0;
+    return TN_OK;
+}
+
+int tn_queue_profile_read(const tn_queue_t *Q, tn_queue_kind_stats *out, int32_t capacity) {
+    if (!Q || !out || capacity < 1) return qfail(TN_EINVAL, "bad argument");
+    QState h{};
+    const cudaError_t e = cudaMemcpy(&h, Q->d_state, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return qfail(TN_ECUDA, std::string("read queue state: ") + cudaGetErrorString(e));
+    for (int k = 0; k < capacity; ++k) {
+        out[k].items = k < kQKinds ? (int64_t)h.items[k] : 0;
+        out[k].wait_ms = k < kQKinds ? (double)h.wait_ns[k] * 1e-6 : 0.0;
+        out[k].busy_ms = k < kQKinds ? (double)h.busy_ns[k] * 1e-6 : 0.0;
+    }
     return TN_OK;
 }
 

@@ -20,12 +20,16 @@ namespace {
 
 constexpr int kMaxK = TN_SAMPLE_NOALLOC_MAX_K;
 
+// The k results, then the multi-block selection's scratch for k <= kMaxK
+// (its header, per-block counts and the k kept entries).
+constexpr size_t kSelectBytes = 4096 + 1024 * 8 + (size_t)kMaxK * 16;
 struct SampleScratch {
     int64_t idx[kMaxK];
     double prob[kMaxK];
+    __align__(256) uint8_t select[kSelectBytes];
 };
 
-// 16 KiB in every device that loads this library, kept until the process
+// 44 KiB in every device that loads this library, kept until the process
 // exits.  Host code must not pass this name to a kernel: on the host it is
 // only a stand-in for the symbol, not a device address.
 static __device__ __align__(256) SampleScratch g_sample_scratch;
@@ -75,9 +79,13 @@ extern "C" int tn_sample_noalloc(const double *d_amps, int32_t n_open, int32_t k
     int64_t *d_idx = reinterpret_cast<int64_t *>(base + offsetof(SampleScratch, idx));
     double *d_prob = reinterpret_cast<double *>(base + offsetof(SampleScratch, prob));
     cudaStream_t s = (cudaStream_t)stream;
-    // the kernel writes entries 0..k-1 of both arrays; nothing is read before
-    // it is written, so no clearing is needed
-    cudaError_t e = tn::launch_topk((const double2 *)d_amps, n, k, d_idx, d_prob, s);
+    // the kernels write entries 0..k-1 of both arrays and initialise the
+    // selection's header themselves; nothing is read before it is written,
+    // so no clearing is needed
+    if (tn::topk_scratch_bytes(n, k) > kSelectBytes)
+        return tn::record_error(TN_EUNSUPPORTED, "tn_sample_noalloc: selection scratch exceeds its fixed size");
+    cudaError_t e = tn::launch_topk_select((const double2 *)d_amps, n, k, base + offsetof(SampleScratch, select),
+                                           d_idx, d_prob, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_idx, d_idx, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_prob, d_prob, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
