@@ -339,14 +339,18 @@ int tn_contract_batch(tn_plan_t *const *plans, int32_t n, double *const *d_amps,
  * as a first tn_contract would), then compiles every op of the contraction
  * of slices [slice_begin[i], slice_begin[i] + slice_count[i]) of plans[i]
  * into d_amps[i] (device, 2^n_open_i complex128, overwritten; NULL range
- * arrays: every slice) into a device table of ops and a list of (op, tile)
- * items in dependency order.  tn_queue_run launches one persistent kernel
- * (one 320-thread CTA per SM, the tensor-core tiles on tcgen05/TMA/TMEM as in
- * tn_contract, the other ops on the same kernels' device code) that claims
- * items in order; each item waits for the op before it in its chain through
- * a per-op counter, a wait bounded by the queue's limit (default 10 s,
- * tn_queue_set_wait_limit), after which every CTA returns and the run
- * reports TN_ETIMEOUT (rep != NULL).  Results equal tn_contract's bit for
+ * arrays: every slice) into a device table of ops, each cut into tiles
+ * (items) and chained to the op after it.  tn_queue_run launches one
+ * persistent kernel (one 320-thread CTA per SM, the tensor-core tiles on
+ * tcgen05/TMA/TMEM as in tn_contract, the other ops on the same kernels'
+ * device code) whose CTAs claim tiles from a list, one atomic ticket each:
+ * the tiles of the chains' first ops are listed at launch, and an op's
+ * tiles are listed by the CTA that counts its predecessor's last tile done
+ * (per-op counters), so a claimed tile never waits on another.  A CTA whose
+ * ticket is not listed yet waits for running tiles to list more, a wait
+ * bounded by the queue's limit (default 10 s, tn_queue_set_wait_limit),
+ * after which every CTA returns and the run reports TN_ETIMEOUT
+ * (rep != NULL).  Results equal tn_contract's bit for
  * bit.  rep: optional timing and error check (synchronizes `stream`).
  * Plans must have profiling off and must not be used elsewhere while the
  * queue exists; the queue owns its tables (device memory from cudaMalloc).
@@ -356,7 +360,7 @@ typedef struct tn_queue_s tn_queue_t;
 typedef struct {
     int32_t n_plans;
     int32_t n_ops;                /* ops in the table                             */
-    int32_t n_items;              /* (op, tile) items claimed by the CTAs         */
+    int32_t n_items;              /* tiles (items) claimed by the CTAs, all ops   */
     int32_t max_chain;            /* longest dependency chain (ops)               */
     int32_t ctas;                 /* CTAs of the launch                           */
     int32_t pad_;
@@ -371,8 +375,8 @@ int tn_queue_info(const tn_queue_t *queue, tn_queue_stats *out);
 int tn_queue_set_wait_limit(tn_queue_t *queue, int64_t limit_us);
 /*
  * Queue profiling: when enabled, each run sums per op kind (index =
- * TN_QK_*) the items run, the time their CTAs spent waiting for the op
- * before them and the time spent running them (CTA-milliseconds, from
+ * TN_QK_*) the items run, the time their CTAs spent waiting for the
+ * item's list entry to be written and the time spent running them (CTA-milliseconds, from
  * %globaltimer); tn_queue_profile_read returns the last run's sums (after it
  * finished) for kinds 0..capacity-1.
  */
@@ -406,10 +410,10 @@ void tn_queue_destroy(tn_queue_t *queue);
 int tn_plan_set_queue(tn_plan_t *plan, int enable);
 
 /*
- * tn_selftest_queue_timeout: runs a two-op queue whose second op waits for a
- * tile count the first never reaches, with a dependency-wait limit of
- * limit_ms (1..10000); the wait runs out and the call returns TN_ETIMEOUT,
- * the context still usable.
+ * tn_selftest_queue_timeout: runs a queue holding an op that nothing ever
+ * lists, with a wait limit of limit_ms (1..10000); the wait of the CTA
+ * holding that op's ticket runs out and the call returns TN_ETIMEOUT, the
+ * context still usable.
  */
 int tn_selftest_queue_timeout(int32_t limit_ms, void *stream);
 

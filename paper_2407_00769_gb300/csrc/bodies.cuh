@@ -293,18 +293,22 @@ __device__ __forceinline__ void bprep_gather_body(const uint32_t *B, uint32_t *B
 // threads: every element is rounded to the plan's dtype here, and the
 // rounding's component along B, alpha = <B, B~ - B> / <B, B>, is measured
 // (FP64, fixed order) so the final sum can divide the factor (1 + alpha) out
-// exactly (the network is linear in B): corr = 1 / (1 + alpha).
-template <int NT>
+// exactly (the network is linear in B): corr = 1 / (1 + alpha).  The FP64
+// sums follow one fixed order whatever NT is: VT virtual threads (v takes
+// elements v, v + VT, ...), then a tree over the VT partial sums; each real
+// thread plays VT / NT of them.
+template <int VT>
 struct BprepC64Smem {
-    double sh[3][NT];
-    float smax[NT];
+    double sh[3][VT];
+    float smax[VT];
 };
 
-template <int DT, int NT, class Sync>
+template <int DT, int NT, int VT, class Sync>
 __device__ __forceinline__ void bprep_c64_body(const float2 *B, uint32_t *Bp, int lk, int ln, int lb, int np,
                                                const PermParams &p, int rank, double2 *corr, float *tmax,
                                                int32_t *texp, int meta_src, int meta_dst, int scale_off, int tid,
-                                               BprepC64Smem<NT> &sm) {
+                                               BprepC64Smem<VT> &sm) {
+    static_assert(VT % NT == 0, "virtual threads must be a multiple of the block");
     using L = LpT<DT>;
     const int K = 1 << lk, N = 1 << ln;
     const int64_t total = ((int64_t)np * K) << lb;
@@ -320,45 +324,47 @@ __device__ __forceinline__ void bprep_c64_body(const float2 *B, uint32_t *Bp, in
         }
     }
     const float scale = __int_as_float((127 + bshift) << 23);
-    float bmax = 0.0f;
-    double nr = 0.0, ni = 0.0, den = 0.0;
-    for (int64_t i = tid; i < total; i += NT) {
-        const int k = (int)(i % K);
-        const int64_t row = i / K;
-        const int rr = (int)(row % np);
-        const int64_t b = row / np;
-        const int n = rr >> 1, co = rr & 1;
-        uint32_t v = 0;
-        if (n < N) {
-            const int64_t tidx = ((b * N + n) << lk) | k;
-            int64_t src = 0;
-            for (int t = 0; t < rank; ++t)
-                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
-            const float2 x0 = B[src];
-            const float2 x = make_float2(x0.x * scale, x0.y * scale);
-            const typename L::T2 h = L::from_f2(x);
-            const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
-            v = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
-            if (co == 0) {
-                const float2 r = L::to_f2(h);
-                bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
-                const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
-                nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
-                ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
-                den += (double)x.x * x.x + (double)x.y * x.y;
+    for (int v = tid; v < VT; v += NT) {
+        float bmax = 0.0f;
+        double nr = 0.0, ni = 0.0, den = 0.0;
+        for (int64_t i = v; i < total; i += VT) {
+            const int k = (int)(i % K);
+            const int64_t row = i / K;
+            const int rr = (int)(row % np);
+            const int64_t b = row / np;
+            const int n = rr >> 1, co = rr & 1;
+            uint32_t val = 0;
+            if (n < N) {
+                const int64_t tidx = ((b * N + n) << lk) | k;
+                int64_t src = 0;
+                for (int t = 0; t < rank; ++t)
+                    if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
+                const float2 x0 = B[src];
+                const float2 x = make_float2(x0.x * scale, x0.y * scale);
+                const typename L::T2 h = L::from_f2(x);
+                const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
+                val = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
+                if (co == 0) {
+                    const float2 r = L::to_f2(h);
+                    bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+                    const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
+                    nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
+                    ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
+                    den += (double)x.x * x.x + (double)x.y * x.y;
+                }
             }
+            Bp[i] = val;
         }
-        Bp[i] = v;
+        sm.sh[0][v] = nr;
+        sm.sh[1][v] = ni;
+        sm.sh[2][v] = den;
+        sm.smax[v] = bmax;
     }
-    sm.sh[0][tid] = nr;
-    sm.sh[1][tid] = ni;
-    sm.sh[2][tid] = den;
-    sm.smax[tid] = bmax;
     Sync::sync();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if (tid < w) {
-            for (int q = 0; q < 3; ++q) sm.sh[q][tid] += sm.sh[q][tid + w];
-            sm.smax[tid] = fmaxf(sm.smax[tid], sm.smax[tid + w]);
+    for (int w = VT / 2; w > 0; w >>= 1) {
+        for (int x = tid; x < w; x += NT) {
+            for (int q = 0; q < 3; ++q) sm.sh[q][x] += sm.sh[q][x + w];
+            sm.smax[x] = fmaxf(sm.smax[x], sm.smax[x + w]);
         }
         Sync::sync();
     }

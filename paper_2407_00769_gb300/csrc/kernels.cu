@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
                                                          int32_t *texp, int meta_src, int meta_dst,
                                                          int scale_off) {
     __shared__ BprepC64Smem<1024> sm;
-    bprep_c64_body<DT, 1024, SyncBlock>(B, Bp, lk, ln, lb, np, p, rank, corr, tmax, texp, meta_src, meta_dst,
-                                        scale_off, threadIdx.x, sm);
+    bprep_c64_body<DT, 1024, 1024, SyncBlock>(B, Bp, lk, ln, lb, np, p, rank, corr, tmax, texp, meta_src, meta_dst,
+                                              scale_off, threadIdx.x, sm);
 }
 
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,

@@ -7,19 +7,18 @@
 // the workspace is reused between steps).  The host compiles the ops of all
 // plans into a table of ops (leaf preparation with slice decoding,
 // permutations, B' builds, CUDA-core GEMMs, tensor-core GEMM tiles, split-K
-// reductions, FP64 slice sums, clears) and a list of items (op, tile): every
-// op is cut into tiles that any CTA can run.  Items are listed in
-// topological order -- depth-major over the plans' chains -- and each op
-// depends on the op before it in its chain.
+// reductions, FP64 slice sums, clears); every op is cut into tiles that any
+// CTA can run, and each op depends on the op before it in its chain.
 //
-// One CTA of 320 threads per SM claims items in list order from a global
-// counter; before running an item it waits (bounded, on %globaltimer) until
-// every tile of the op it depends on has been counted done; after the item
-// it counts its own op's tile done (release: fence + atomic).  A CTA only
-// waits for items earlier in the list, which CTAs that are running have
-// already claimed, so the queue always progresses whether or not every CTA
-// is resident.  A wait that runs out raises the queue's abort flag and every
-// CTA returns; the host reports TN_ETIMEOUT.
+// One CTA of 320 threads per SM takes items from a list (see queue_kernel):
+// an op's tiles are listed only when its predecessor's last tile is done
+// (release: fence + atomic), so a claimed tile never waits on another and
+// no CTA holds its SM while a dependency runs elsewhere.  The tiles of the
+// chains' first ops are listed at launch, longest chain first.  The queue
+// always progresses whether or not every CTA is resident: a CTA whose entry
+// is not listed yet only waits for tiles that CTAs are running.  That wait is
+// bounded (%globaltimer); when it runs out, every CTA returns and the host
+// reports TN_ETIMEOUT.
 //
 // Tensor-core items run the same tcgen05 pipeline as the stand-alone GEMM
 // (tc_gemm.cu: warp 0 TMA producer, warp 1 MMA issuer, warps 2..9 epilogue,
@@ -47,9 +46,8 @@ namespace {
 
 constexpr int kQThreads = kTcThreads;            // 320: producer, MMA, 8 epilogue warps
 constexpr int kQSimt = 256;                      // SIMT items: warps 0..7
-constexpr int kQStageBytes = 128 * 128 + 256 * 128;   // A + B' tile at BN = 256, 128-byte K chunks
-constexpr int kQStages = 4;
-constexpr int kQRing = kQStages * kQStageBytes;  // 192 KiB
+constexpr int kQRing = 4 * (128 * 128 + 256 * 128);  // 192 KiB: 4 stages at BN = 256, 128-byte K chunks
+constexpr int kQStages = 12;                     // most stages of a ring of smaller tiles
 constexpr int kQBars = 2 * kQStages + 5;
 constexpr int kQSmem = 1024 + kQRing + kQBars * 8 + 16;
 constexpr uint32_t kQTmemCols = 512;             // two accumulators of up to 256 columns
@@ -72,20 +70,21 @@ enum QKind : int32_t {
 struct QOp {
     int32_t kind, sub;
     int32_t ntiles;     // items of this op
-    int32_t dep;        // op this one waits for (-1: none)
-    int32_t dep_need;   // items of `dep` that must be done
-    int32_t chain;
+    int32_t next;       // the op after this one in its chain (-1: last)
+    int32_t chain, pad_;
     int64_t prm;        // byte offset of the parameter record in the blob
 };
 
 constexpr int kQKinds = 12;
 struct QState {
-    int32_t head;       // next item to claim
+    int32_t head;       // next ticket: the list entry the next claiming CTA takes
+    int32_t tail;       // list entries reserved by the ops listed so far
     int32_t abort;      // 1: a wait ran out; every CTA returns
-    int32_t err;        // bit 0: a dependency wait ran out
-    int32_t fail_item;  // the item whose wait ran out
+    int32_t err;        // bit 0: a listed entry did not appear within the wait limit
+    int32_t idle_at;    // list entry whose wait ran out
+    int32_t pad_;
     // profiling (tn_queue_profile): per op kind, items run, ns spent waiting
-    // for the dependency, ns running (summed over CTAs)
+    // for the list entry, ns running (summed over CTAs)
     unsigned long long items[kQKinds], wait_ns[kQKinds], busy_ns[kQKinds];
 };
 
@@ -204,9 +203,10 @@ __device__ __noinline__ void q_bprep_gather(const QBprepGather &r, int64_t tile,
 
 template <int DT>
 __device__ __noinline__ void q_bprep_c64(const QBprepC64 &r, int tid, uint8_t *scratch) {
-    bprep_c64_body<DT, kQSimt, SyncNamed<1, kQSimt>>(r.B, r.Bp, r.lk, r.ln, r.lb, r.np, r.g, r.rank, r.corr, r.tmax,
-                                                     r.texp, r.meta_src, r.meta_dst, r.scale_off, tid,
-                                                     *reinterpret_cast<BprepC64Smem<kQSimt> *>(scratch));
+    // the stand-alone kernel's 1024-thread summation order, played by 256 threads
+    bprep_c64_body<DT, kQSimt, 1024, SyncNamed<1, kQSimt>>(r.B, r.Bp, r.lk, r.ln, r.lb, r.np, r.g, r.rank, r.corr,
+                                                           r.tmax, r.texp, r.meta_src, r.meta_dst, r.scale_off, tid,
+                                                           *reinterpret_cast<BprepC64Smem<1024> *>(scratch));
 }
 
 // two 128-row blocks per item, one per group of 4 warps (named barriers 2, 3)
@@ -362,9 +362,16 @@ __device__ __forceinline__ void q_mma_chunk(uint32_t d_tmem, uint32_t a_addr, ui
     }
 }
 
-struct TcPipe {          // ring and accumulator positions, kept across items
-    int p_stage, m_stage, m_acc, e_acc;
-    uint32_t p_phase, m_phase, m_acc_phase, e_acc_phase;
+// Ring and accumulator state kept across items.  A tensor-core item cuts
+// the ring into as many stages as its tile size allows (up to kQStages) and
+// walks them from stage 0; each stage barrier's phase parity is tracked per
+// stage (bit s of the masks), so items with different stage counts follow
+// one another.
+struct TcPipe {
+    uint32_t p_bits;     // producer: parity of the next fill of stage s
+    uint32_t m_bits;     // MMA: parity of the next consumption of stage s
+    int m_acc, e_acc;
+    uint32_t m_acc_phase, e_acc_phase;
 };
 
 // One walker (tiles w, w + W, ...) of a tensor-core GEMM.  Returns false
@@ -378,6 +385,8 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
     const int bn = R.bn, bkb = R.bkb;
     const int bk = bkb / 2;                 // K chunk in FP16/BF16 elements
     const uint32_t a_bytes = 128u * bkb, b_bytes = (uint32_t)bn * bkb;
+    const uint32_t stage_bytes = (a_bytes + b_bytes + 1023u) / 1024u * 1024u;
+    const int n_st = min(kQStages, (int)(kQRing / stage_bytes));
     const int64_t tiles = args.tiles;
     bool ok = true;
     if (warp == 0) {
@@ -388,22 +397,25 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
             asm volatile("fence.proxy.async.global;" ::: "memory");
             int8_t armed[kQStages];
             for (int s = 0; s < kQStages; ++s) armed[s] = -1;
+            int stage = 0;
             for (int64_t t = walker; t < tiles && ok; t += walkers) {
                 int64_t b, mt;
                 int nt;
                 tile_coords(args, t, b, mt, nt);
                 const int kbase = (int)(t / args.tiles_per_part) * args.nk * bk;
                 for (int kc = 0; kc < args.nk; ++kc) {
-                    if (!mbar_wait(&empty[st.p_stage], st.p_phase ^ 1, abort_flag)) { ok = false; break; }
-                    uint8_t *sa = ring + st.p_stage * kQStageBytes;
+                    const uint32_t par = (st.p_bits >> stage) & 1u;
+                    if (!mbar_wait(&empty[stage], par ^ 1u, abort_flag)) { ok = false; break; }
+                    uint8_t *sa = ring + stage * stage_bytes;
                     uint8_t *sb = sa + a_bytes;
                     const int zA = args.za ? args.za[b] : (args.batch_a ? (int)b : 0);
                     const int zB = args.zb ? max(0, args.zb[b]) : (args.batch_b ? (int)b : 0);
-                    mbar_expect_tx(&full[st.p_stage], a_bytes + b_bytes);
-                    tma_load_3d(sa, &R.ma, &full[st.p_stage], kbase + kc * bk, (int)(mt * 128), zA);
-                    tma_load_3d(sb, &R.mb, &full[st.p_stage], kbase + kc * bk, nt * bn, zB);
-                    armed[st.p_stage] = (int8_t)st.p_phase;
-                    if (++st.p_stage == kQStages) { st.p_stage = 0; st.p_phase ^= 1; }
+                    mbar_expect_tx(&full[stage], a_bytes + b_bytes);
+                    tma_load_3d(sa, &R.ma, &full[stage], kbase + kc * bk, (int)(mt * 128), zA);
+                    tma_load_3d(sb, &R.mb, &full[stage], kbase + kc * bk, nt * bn, zB);
+                    armed[stage] = (int8_t)par;
+                    st.p_bits ^= 1u << stage;
+                    if (++stage == n_st) stage = 0;
                 }
             }
             if (!ok) {
@@ -426,21 +438,23 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
             idesc |= (uint32_t)(bn >> 3) << 17;                // N
             idesc |= (uint32_t)(128 >> 4) << 24;               // M
             bool issued = false;
+            int stage = 0;
             for (int64_t t = walker; t < tiles && ok; t += walkers) {
                 if (!mbar_wait(&acce[st.m_acc], st.m_acc_phase ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(st.m_acc * kQAccStride);
                 for (int kc = 0; kc < args.nk; ++kc) {
-                    if (!mbar_wait(&full[st.m_stage], st.m_phase, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(&full[stage], (st.m_bits >> stage) & 1u, abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(ring + st.m_stage * kQStageBytes);
+                    const uint32_t a_addr = smem_u32(ring + stage * stage_bytes);
                     const uint32_t b_addr = a_addr + a_bytes;
                     if (bkb == 128) q_mma_chunk<128>(d_tmem, a_addr, b_addr, idesc, kc == 0);
                     else if (bkb == 64) q_mma_chunk<64>(d_tmem, a_addr, b_addr, idesc, kc == 0);
                     else q_mma_chunk<32>(d_tmem, a_addr, b_addr, idesc, kc == 0);
                     issued = true;
-                    tc_commit(&empty[st.m_stage]);
-                    if (++st.m_stage == kQStages) { st.m_stage = 0; st.m_phase ^= 1; }
+                    tc_commit(&empty[stage]);
+                    st.m_bits ^= 1u << stage;
+                    if (++stage == n_st) stage = 0;
                 }
                 if (!ok) break;
                 tc_commit(&accf[st.m_acc]);
@@ -508,9 +522,24 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
 }
 
 // ------------------------------------------------------------------ kernel --
+// Scheduling: a list of items (op << 32 | tile), one entry per tile of every
+// op.  The tiles of the chains' first ops are listed at launch; when the
+// last tile of an op is counted done, the CTA that counted it reserves
+// entries for every tile of the op's successor (one atomic on the tail) and
+// writes them with all its threads.  A CTA claims the next entry with one
+// atomic on the head (a ticket) and runs it as soon as it is written -- so a
+// tile is only run when everything it depends on has finished, and an entry
+// is taken by the first CTA free.  Only a CTA whose ticket is not yet listed
+// waits, for tiles that other CTAs are running; that wait is bounded.
+__device__ __forceinline__ long long ld_acquire64(const long long *p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __global__ void __launch_bounds__(kQThreads, 1)
-    queue_kernel(const QOp *ops, const int2 *items, int32_t n_items, const uint8_t *blob, int32_t *done, QState *st,
-                 uint64_t dep_limit_ns, int profile) {
+    queue_kernel(const QOp *ops, int32_t n_items, const uint8_t *blob, int32_t *done, long long *list, QState *st,
+                 uint64_t idle_limit_ns, int profile) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(ring + kQRing);
@@ -519,7 +548,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
     uint64_t *acce = accf + 2;
     uint64_t *drain = acce + 2;
     volatile uint32_t *tmem_slot = (volatile uint32_t *)(drain + 1);
-    __shared__ int s_item;
+    __shared__ int s_op, s_tile;
+    __shared__ int s_push_op, s_push_n, s_push_at;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x / 32;
@@ -548,57 +578,53 @@ __global__ void __launch_bounds__(kQThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    TcPipe pipe{0, 0, 0, 0, 0, 0, 0, 0};
+    TcPipe pipe{0u, 0u, 0, 0, 0u, 0u};
     uint64_t t_claim = 0, t_ready = 0;
 
     while (true) {
         if (threadIdx.x == 0) {
-            if (profile) t_claim = globaltimer();
-            int i = -1;
-            if (!*(volatile int32_t *)&st->abort) {
-                i = atomicAdd(&st->head, 1);
-                if (i >= n_items) i = -1;
-            }
-            if (i >= 0) {
-                const QOp &op = ops[items[i].x];
-                if (op.dep >= 0) {
-                    const int32_t *cnt = done + op.dep;
-                    if (ld_acquire(cnt) < op.dep_need) {
-                        const uint64_t t0 = globaltimer();
-                        uint32_t ns = 32;
-                        while (ld_acquire(cnt) < op.dep_need) {
-                            if (*(volatile int32_t *)&st->abort) { i = -1; break; }
-                            if (globaltimer() - t0 > dep_limit_ns) {
-                                atomicOr(&st->err, 1);
-                                atomicExch(&st->fail_item, i);
-                                atomicExch(&st->abort, 1);
-                                i = -1;
-                                break;
-                            }
-                            nanosleep_ns(ns);
-                            if (ns < 1024) ns *= 2;
-                        }
+            t_claim = globaltimer();
+            int op_id = -1, tile = 0;
+            const int32_t h = *(volatile int32_t *)&st->abort ? n_items : atomicAdd(&st->head, 1);
+            if (h < n_items) {
+                long long e = ld_acquire64(list + h);
+                uint32_t ns = 32;
+                while (e < 0) {
+                    if (*(volatile int32_t *)&st->abort) break;
+                    if (globaltimer() - t_claim > idle_limit_ns) {
+                        atomicOr(&st->err, 1);
+                        atomicExch(&st->idle_at, h);
+                        atomicExch(&st->abort, 1);
+                        break;
                     }
-                    // the results of the op waited for, written by other
-                    // CTAs through the generic proxy, before any load here
-                    __threadfence();
+                    nanosleep_ns(ns);
+                    if (ns < 256) ns *= 2;
+                    e = ld_acquire64(list + h);
+                }
+                if (e >= 0) {
+                    op_id = (int)(e >> 32);
+                    tile = (int)(e & 0xffffffffll);
                 }
             }
-            s_item = i;
-            if (profile) t_ready = globaltimer();
+            // the op's inputs, written by other CTAs through the generic
+            // proxy, before any load here
+            __threadfence();
+            s_op = op_id;
+            s_tile = tile;
+            t_ready = globaltimer();
         }
         __syncthreads();
-        const int i = s_item;
-        if (i < 0) break;
-        const int2 it = items[i];
-        const QOp &op = ops[it.x];
+        const int op_id = s_op;
+        if (op_id < 0) break;
+        const int tile = s_tile;
+        const QOp &op = ops[op_id];
         if (op.kind == Q_TC) {
             const QTc &R = *reinterpret_cast<const QTc *>(blob + op.prm);
-            const bool ok = q_tc(R, it.y, op.ntiles, ring, full, empty, accf, acce, drain, tmem_base, &abort_flag, pipe);
+            const bool ok = q_tc(R, tile, op.ntiles, ring, full, empty, accf, acce, drain, tmem_base, &abort_flag, pipe);
             (void)ok;
             tc_fence_before();
         } else if (threadIdx.x < kQSimt) {
-            q_simt(op, blob, it.y, threadIdx.x, ring);
+            q_simt(op, blob, tile, threadIdx.x, ring);
             // generic writes to the ring before later TMA loads into it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
@@ -606,20 +632,36 @@ __global__ void __launch_bounds__(kQThreads, 1)
         if (abort_flag) {
             if (threadIdx.x == 0) {
                 atomicOr(&st->err, 1);
-                atomicExch(&st->fail_item, i);
                 atomicExch(&st->abort, 1);
             }
             break;
         }
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(done + it.x, 1);
+            const int32_t d = atomicAdd(done + op_id, 1) + 1;
+            s_push_n = 0;
+            if (d == op.ntiles && op.next >= 0) {
+                // every tile of this op is done (the other tiles' writes are
+                // ordered before their counts): list the successor's tiles
+                __threadfence();
+                const int32_t n = ops[op.next].ntiles;
+                s_push_op = op.next;
+                s_push_n = n;
+                s_push_at = atomicAdd(&st->tail, n);
+            }
             if (profile) {
                 const int kind = op.kind < kQKinds ? op.kind : 0;
                 atomicAdd(&st->items[kind], 1ull);
                 atomicAdd(&st->wait_ns[kind], (unsigned long long)(t_ready - t_claim));
                 atomicAdd(&st->busy_ns[kind], (unsigned long long)(globaltimer() - t_ready));
             }
+        }
+        __syncthreads();
+        if (s_push_n > 0) {
+            __threadfence();
+            const long long hi = (long long)s_push_op << 32;
+            for (int t = threadIdx.x; t < s_push_n; t += kQThreads)
+                *(volatile long long *)(list + s_push_at + t) = hi | (long long)t;
         }
     }
     __syncthreads();
@@ -648,8 +690,7 @@ struct Builder {
         o.kind = kind;
         o.sub = sub;
         o.ntiles = (int32_t)std::max<int64_t>(1, ntiles);
-        o.dep = -1;
-        o.dep_need = 0;
+        o.next = -1;
         o.chain = chain;
         o.prm = prm;
         ops.push_back(o);
@@ -953,18 +994,22 @@ using namespace tn;
 struct tn_queue_s {
     int device = -1;
     std::vector<tn_plan_s *> plans;
-    void *d_mem = nullptr;      // ops | items | blob | done | state
+    void *d_mem = nullptr;      // ops | blob | run state | its initial copy
     QOp *d_ops = nullptr;
-    int2 *d_items = nullptr;
     uint8_t *d_blob = nullptr;
+    // run state: done[n_ops] | list[n_items] | QState, reset from d_init
+    // before every run
+    char *d_run = nullptr, *d_init = nullptr;
     int32_t *d_done = nullptr;
+    long long *d_list = nullptr;
     QState *d_state = nullptr;
     int32_t n_ops = 0, n_items = 0, max_chain = 0, grid = 0;
-    size_t counters_bytes = 0;
+    size_t run_bytes = 0;
     int64_t blob_bytes = 0;
+    int32_t n_heads = 0;
     double flops = 0;
     int64_t slices = 0;
-    uint64_t dep_limit_ns = 10000000000ull;
+    uint64_t idle_limit_ns = 10000000000ull;
     int profile = 0;
 };
 
@@ -972,8 +1017,10 @@ namespace {
 
 int qfail(int code, const std::string &msg) { return record_error(code, msg); }
 
-int queue_finish(tn_queue_s *Q, Builder &Bd) {
-    // items: depth-major over the chains, longest chains first within a depth
+// heads: the chains whose first op is listed at launch (all, normally).
+int queue_finish(tn_queue_s *Q, Builder &Bd, const std::vector<int> *heads = nullptr) {
+    // successors along each chain; the chains' first ops listed longest
+    // chain first (the longest chains bound the run)
     std::vector<int> order(Bd.chains.size());
     for (size_t c = 0; c < order.size(); ++c) order[c] = (int)c;
     std::stable_sort(order.begin(), order.end(),
@@ -981,44 +1028,58 @@ int queue_finish(tn_queue_s *Q, Builder &Bd) {
     size_t maxd = 0;
     for (auto &ch : Bd.chains) maxd = std::max(maxd, ch.size());
     for (auto &ch : Bd.chains)
-        for (size_t d = 1; d < ch.size(); ++d) {
-            Bd.ops[ch[d]].dep = ch[d - 1];
-            Bd.ops[ch[d]].dep_need = Bd.ops[ch[d - 1]].ntiles;
-        }
-    std::vector<int2> items;
-    for (size_t d = 0; d < maxd; ++d)
-        for (int c : order) {
-            const auto &ch = Bd.chains[c];
-            if (d >= ch.size()) continue;
-            const int op = ch[d];
-            for (int t = 0; t < Bd.ops[op].ntiles; ++t) items.push_back(make_int2(op, t));
-        }
-    if (items.size() > (size_t)0x7fffffff) return qfail(TN_EUNSUPPORTED, "queue: too many items");
-    Q->n_ops = (int32_t)Bd.ops.size();
-    Q->n_items = (int32_t)items.size();
+        for (size_t d = 0; d + 1 < ch.size(); ++d) Bd.ops[ch[d]].next = ch[d + 1];
+    const int n_ops = (int)Bd.ops.size();
+    int64_t n_items = 0;
+    for (const QOp &o : Bd.ops) n_items += o.ntiles;
+    if (n_items > 0x7fffffff) return qfail(TN_EUNSUPPORTED, "queue: too many items");
+    // the list: every tile of the listed first ops, the rest empty (-1)
+    std::vector<long long> list((size_t)std::max<int64_t>(1, n_items), -1ll);
+    int64_t n_listed = 0;
+    int n_heads = 0;
+    auto list_op = [&](int op) {
+        for (int t = 0; t < Bd.ops[op].ntiles; ++t) list[n_listed++] = ((long long)op << 32) | t;
+        ++n_heads;
+    };
+    if (heads) {
+        for (int op : *heads) list_op(op);
+    } else {
+        for (int c : order)
+            if (!Bd.chains[c].empty()) list_op(Bd.chains[c][0]);
+    }
+    Q->n_ops = n_ops;
+    Q->n_items = (int32_t)n_items;
+    Q->n_heads = n_heads;
     Q->max_chain = (int32_t)maxd;
-    Q->grid = std::max(1, std::min(g_queue_sms, Q->n_items));
-    const size_t ops_b = (Bd.ops.size() * sizeof(QOp) + 255) / 256 * 256;
-    const size_t items_b = (items.size() * sizeof(int2) + 255) / 256 * 256;
+    Q->grid = (int)std::max<int64_t>(1, std::min<int64_t>(g_queue_sms, n_items));
+    const size_t ops_b = ((size_t)std::max(1, n_ops) * sizeof(QOp) + 255) / 256 * 256;
     const size_t blob_b = (Bd.blob.size() + 255) / 256 * 256;
-    const size_t done_b = (Bd.ops.size() * 4 + 255) / 256 * 256;
+    const size_t done_b = ((size_t)std::max(1, n_ops) * 4 + 255) / 256 * 256;
+    const size_t list_b = (list.size() * 8 + 255) / 256 * 256;
     const size_t state_b = (sizeof(QState) + 255) / 256 * 256;
-    const size_t total = ops_b + items_b + blob_b + done_b + state_b;
+    Q->run_bytes = done_b + list_b + state_b;
+    const size_t total = ops_b + blob_b + 2 * Q->run_bytes;
     cudaError_t e = cudaMalloc(&Q->d_mem, total);
     if (e != cudaSuccess) return qfail(TN_ENOMEM, std::string("queue tables: ") + cudaGetErrorString(e));
     char *m = (char *)Q->d_mem;
     Q->d_ops = (QOp *)m;
-    Q->d_items = (int2 *)(m + ops_b);
-    Q->d_blob = (uint8_t *)(m + ops_b + items_b);
-    Q->d_done = (int32_t *)(m + ops_b + items_b + blob_b);
-    Q->d_state = (QState *)(m + ops_b + items_b + blob_b + done_b);
-    Q->counters_bytes = done_b + state_b;
+    Q->d_blob = (uint8_t *)(m + ops_b);
+    Q->d_run = m + ops_b + blob_b;
+    Q->d_init = Q->d_run + Q->run_bytes;
+    Q->d_done = (int32_t *)Q->d_run;
+    Q->d_list = (long long *)(Q->d_run + done_b);
+    Q->d_state = (QState *)(Q->d_run + done_b + list_b);
     Q->blob_bytes = (int64_t)Bd.blob.size();
-    e = cudaMemcpy(Q->d_ops, Bd.ops.data(), Bd.ops.size() * sizeof(QOp), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(Q->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    std::vector<char> init(Q->run_bytes, 0);
+    std::memcpy(init.data() + done_b, list.data(), list.size() * 8);
+    QState s0{};
+    s0.head = 0;
+    s0.tail = (int32_t)n_listed;
+    std::memcpy(init.data() + done_b + list_b, &s0, sizeof(s0));
+    e = cudaMemcpy(Q->d_ops, Bd.ops.data(), (size_t)n_ops * sizeof(QOp), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !Bd.blob.empty())
         e = cudaMemcpy(Q->d_blob, Bd.blob.data(), Bd.blob.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(Q->d_init, init.data(), Q->run_bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return qfail(TN_ECUDA, std::string("queue upload: ") + cudaGetErrorString(e));
     return TN_OK;
 }
@@ -1087,10 +1148,10 @@ int tn_queue_run(tn_queue_t *Q, void *stream, tn_contract_report *rep) {
             return qfail(TN_ECUDA, "event");
         cudaEventRecord(ev0, s);
     }
-    cudaError_t e = cudaMemsetAsync(Q->d_done, 0, Q->counters_bytes, s);
+    cudaError_t e = cudaMemcpyAsync(Q->d_run, Q->d_init, Q->run_bytes, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
-        queue_kernel<<<Q->grid, kQThreads, kQSmem, s>>>(Q->d_ops, Q->d_items, Q->n_items, Q->d_blob, Q->d_done,
-                                                       Q->d_state, Q->dep_limit_ns, Q->profile);
+        queue_kernel<<<Q->grid, kQThreads, kQSmem, s>>>(Q->d_ops, Q->n_items, Q->d_blob, Q->d_done, Q->d_list,
+                                                       Q->d_state, Q->idle_limit_ns, Q->profile);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return qfail(TN_ECUDA, std::string("queue launch: ") + cudaGetErrorString(e));
@@ -1111,8 +1172,8 @@ int tn_queue_run(tn_queue_t *Q, void *stream, tn_contract_report *rep) {
         e = cudaMemcpy(&h, Q->d_state, sizeof(h), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return qfail(TN_ECUDA, "read queue state");
         if (h.err & 1)
-            return qfail(TN_ETIMEOUT, "a bounded device wait of the work queue gave up (item " +
-                                          std::to_string(h.fail_item) + ")");
+            return qfail(TN_ETIMEOUT, "a bounded device wait of the work queue gave up (list entry " +
+                                          std::to_string(h.idle_at) + " was never written)");
         for (tn_plan_s *P : Q->plans) {
             int32_t herr = 0;
             e = cudaMemcpy(&herr, P->d_err, 4, cudaMemcpyDeviceToHost);
@@ -1140,7 +1201,7 @@ int tn_queue_info(const tn_queue_t *Q, tn_queue_stats *out) {
 
 int tn_queue_set_wait_limit(tn_queue_t *Q, int64_t limit_us) {
     if (!Q || limit_us < 1) return qfail(TN_EINVAL, "bad wait limit");
-    Q->dep_limit_ns = (uint64_t)limit_us * 1000ull;
+    Q->idle_limit_ns = (uint64_t)limit_us * 1000ull;
     return TN_OK;
 }
 
@@ -1169,9 +1230,10 @@ void tn_queue_destroy(tn_queue_t *Q) {
     delete Q;
 }
 
-// A two-op queue whose second op waits for a tile count its predecessor
-// never reaches ("a flag nothing sets"): the wait runs out after limit_ms and
-// the call returns TN_ETIMEOUT with the context intact.
+// A queue with an op that nothing ever lists: the wait of the CTA holding its
+// list entry
+// runs out after limit_ms and the call returns TN_ETIMEOUT with the context
+// intact.
 int tn_selftest_queue_timeout(int32_t limit_ms, void *stream) {
     if (limit_ms < 1 || limit_ms > 10000) return qfail(TN_EINVAL, "limit_ms must be in 1..10000");
     cudaError_t e = queue_prepare();
@@ -1181,22 +1243,19 @@ int tn_selftest_queue_timeout(int32_t limit_ms, void *stream) {
     void *scratch = nullptr;
     e = cudaMalloc(&scratch, 4096);
     if (e != cudaSuccess) return qfail(TN_ENOMEM, "self-test buffer");
+    // two one-op chains, only the first of which is listed: after it runs,
+    // the second is never listed by anything ("a flag nothing sets"), so the
+    // wait for that list entry runs out
     Builder Bd;
-    Bd.chains.resize(1);
+    Bd.chains.resize(2);
     Bd.zero(0, scratch, 16);
-    Bd.zero(0, (char *)scratch + 64, 16);
+    Bd.zero(1, (char *)scratch + 64, 16);
     tn_queue_s *Q = new tn_queue_s();
     Q->device = dev;
-    int rc = queue_finish(Q, Bd);
+    const std::vector<int> heads = {0};
+    int rc = queue_finish(Q, Bd, &heads);
     if (rc == TN_OK) {
-        // the second op needs two done tiles of the first, which has one
-        QOp second = Bd.ops[1];
-        second.dep_need = 2;
-        e = cudaMemcpy(Q->d_ops + 1, &second, sizeof(QOp), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) rc = qfail(TN_ECUDA, "self-test upload");
-    }
-    if (rc == TN_OK) {
-        Q->dep_limit_ns = (uint64_t)limit_ms * 1000000ull;
+        Q->idle_limit_ns = (uint64_t)limit_ms * 1000000ull;
         tn_contract_report rep;
         rc = tn_queue_run(Q, stream, &rep);
     }
