@@ -380,7 +380,9 @@ struct TcPipe {
 __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walkers, uint8_t *ring, uint64_t *full,
                                      uint64_t *empty, uint64_t *accf, uint64_t *acce, uint64_t *drain,
                                      uint32_t tmem_base, volatile int *abort_flag, TcPipe &st) {
-    const TcArgs &args = R.a;
+    // a private copy: the epilogue's stores to global memory cannot alias it,
+    // so its fields stay in registers across them
+    const TcArgs args = R.a;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int bn = R.bn, bkb = R.bkb;
     const int bk = bkb / 2;                 // K chunk in FP16/BF16 elements
