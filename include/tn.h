@@ -613,7 +613,10 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  *   rows, 1 complex64 tiled, 2 complex-half rows, 3 complex-half tensor
  *   cores, 4 complex-half tensor cores on CTA pairs (clusters of 2 SMs,
  *   256-row tiles; shapes with M >= 256, N >= 128, K >= 32, else as 3),
- *   5 complex-half tensor cores with 64-byte K chunks (K >= 32, else as 3).
+ *   5 complex-half tensor cores with 64-byte K chunks (K >= 32, else as 3),
+ *   6 complex-half tensor cores with each CTA's B' slice resident in shared
+ *   memory across its tiles (short K: the whole K of a B' tile within
+ *   64 KiB, one K part; else as 3).
  * out_max: optional device float, receives max |component| of the stored C.
  */
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,

@@ -247,6 +247,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.gm = tc_tile_gm(g.tile);
                     d.pair = (g.tile & kTcPairTile) ? 1 : 0;
                     d.half_k = (g.tile & kTcHalfKTile) ? 1 : 0;
+                    d.bres = (g.tile & kTcBresTile) ? 1 : 0;
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
                     d.fp8 = g.fp8;
@@ -325,9 +326,14 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
             const int bn = tc_tile_bn(tc_effective_tile(code, g.ln));
             return !gathered && tc_pair_eligible(1, g.fp8, g.lm, g.ln, g.lk, bn);
         };
+        auto bres_ok = [&](int code) {
+            const int bn = tc_tile_bn(tc_effective_tile(code, g.ln));
+            return !g.fp8 && tc_bres_eligible(g.lm, g.ln, g.lk, (int64_t)1 << g.lb, bn, 0, gathered ? 1 : 0);
+        };
         for (int code : codes) {
             c.push_back({GK_LP_TC, code});
             if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
+            if (bres_ok(code)) c.push_back({GK_LP_TC, code | kTcBresTile});
             // (64-byte K chunks, tile bit 9, lost to 128-byte chunks on
             // every step of the 30-qubit workload: not a candidate)
         }
@@ -491,6 +497,10 @@ void cost_features(const tn_tune_record &r, float *f) {
             if (gc < 5) f[19 + gc] = 1.0f;
             // CTA pairs (slot 25 is the permutation size in permute records)
             if ((r.tile & kTcPairTile) && tc_pair_eligible(1, 0, r.lm, r.ln, r.lk, tc_tile_bn(eff))) f[25] = 1.0f;
+            // the B'-resident kernel (slot 24 is the stride class in permute records)
+            if ((r.tile & kTcBresTile) &&
+                tc_bres_eligible(r.lm, r.ln, r.lk, (int64_t)1 << r.lb, tc_tile_bn(eff), 0, 0))
+                f[24] = 1.0f;
         }
     } else {
         f[9] = 1.0f;

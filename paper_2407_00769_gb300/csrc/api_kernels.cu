@@ -110,7 +110,8 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
         int kk = kernel;
         const bool pair = kk == 4;            // tensor cores on CTA pairs
         const bool half_k = kk == 5;          // tensor cores, 64-byte K chunks
-        if (pair || half_k) kk = GK_LP_TC;
+        const bool bres = kk == 6;            // tensor cores, B' slice resident in shared memory
+        if (pair || half_k || bres) kk = GK_LP_TC;
         if (kk < 0) kk = tc_gemm_supported(lk, ln) ? GK_LP_TC : GK_LP_ROWS;
         if (kk == GK_LP_ROWS) {
             e = launch_gemm_rows_lp(dtype, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
@@ -132,6 +133,7 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                 d.np = np;
                 d.pair = pair ? 1 : 0;
                 d.half_k = half_k ? 1 : 0;
+                d.bres = bres ? 1 : 0;
                 const size_t pb = tc_split_bytes(lm, ln, lk, batch);
                 if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
                 if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);

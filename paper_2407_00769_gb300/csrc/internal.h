@@ -75,9 +75,12 @@ enum GemmKernel : int32_t {
 
 // Tensor-core tile code: bits 0-3 N-tile width code, bits 4-7 raster-group
 // code, bit 8 CTA pairs (256-row tiles on a cluster of 2 SMs), bit 9 64-byte
-// K chunks (twice the ring stages of 128-byte chunks in the same memory).
+// K chunks (twice the ring stages of 128-byte chunks in the same memory),
+// bit 10 the B'-resident kernel (each walker keeps its B' slice in shared
+// memory; short-K steps).
 constexpr int kTcPairTile = 0x100;
 constexpr int kTcHalfKTile = 0x200;
+constexpr int kTcBresTile = 0x400;   // bit 10: B' slice resident in shared memory (short K)
 // whether a step of this shape runs on CTA pairs when asked (bn: the N tile
 // in real columns the launch uses)
 bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);

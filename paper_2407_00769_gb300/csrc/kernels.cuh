@@ -128,6 +128,9 @@ struct TcGemmDesc {
     int pair = 0;
     // 1: 64-byte K chunks (FP16/BF16, 1-CTA tiles): a deeper ring
     int half_k = 0;
+    // 1: keep each walker's B' slice resident in shared memory (short-K
+    // steps, gemm_tc_bres_kernel) where the step allows it
+    int bres = 0;
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs
@@ -165,6 +168,10 @@ inline int tc_tile_gm(int tile) { return kTcGm[((tile >> 4) & 15) < 6 ? ((tile >
 // really uses for N = 2^ln (tile 0 and explicit codes may coincide).
 int tc_effective_tile(int tile, int ln);
 bool tc_gemm_supported(int lk, int ln);
+// whether a step of this shape can run on the B'-resident kernel with an N
+// tile of bn real columns (1-CTA FP16/BF16, one K part, no gathers, the whole
+// K of a B' slice within 64 KiB)
+bool tc_bres_eligible(int lm, int ln, int lk, int64_t batch, int bn, int fp8, int gathered);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);
 int tc_num_sms();

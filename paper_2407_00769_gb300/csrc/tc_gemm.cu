@@ -323,6 +323,283 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
     }
 }
 
+// ------------------------------------------------ B'-resident variant --
+// Short-K steps (the whole K of a B' tile fits in shared memory) are bound
+// by L2 rather than by the tensor pipe: the kernel above reloads each tile's
+// B' slice (BN rows x 2K) with every tile, while only the A tile and the C
+// tile are new.  Here each walker keeps its B' slice resident in one of two
+// shared-memory slots and reloads it only when the tile's (n tile, B batch
+// entry) changes; the ring carries A alone (more stages).  Tiles are walked
+// n-fastest (t -> b, m tile, n tile) and the grid is a multiple of the number
+// of n tiles, so a walker's n tile never changes and consecutive walkers
+// share the same A tile in L2.  Same MMA, same epilogue (same bits).
+// Barriers: bfull[s] -- the B' slice in slot s landed (TMA bytes);
+// bfree[s] -- the MMAs that read slot s finished (tcgen05.commit when the
+// MMA warp moves to the other slot).  1-CTA, FP16/BF16, no gathers, one K
+// part.
+struct BresCfg {
+    int bn;                 // N tile (real columns), 16..256
+    int stages;             // A stages in the ring
+    uint32_t chunk_bytes;   // one K chunk of the slice (bn x BKB), rounded up to 1 KiB
+    uint32_t slot_bytes;    // nk chunks, <= 64 KiB
+};
+
+__device__ __forceinline__ void bres_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt, int &nt) {
+    nt = (int)(t % a.n_nt);
+    const int64_t r = t / a.n_nt;
+    mt = r % a.n_mt;
+    b = r / a.n_mt;
+}
+
+constexpr int kBresMaxStages = 12;
+
+template <int BKB>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB,
+                                                              const TcArgs args, const BresCfg cfg) {
+    constexpr int BK = BKB / 2;
+    constexpr uint32_t a_bytes = 128 * BKB;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int bn = cfg.bn, stages = cfg.stages;
+    uint8_t *bslot0 = smem + (size_t)stages * a_bytes;           // B' slots after the A ring
+    uint64_t *full = (uint64_t *)(bslot0 + 2 * (size_t)cfg.slot_bytes);
+    uint64_t *empty = full + kBresMaxStages;
+    uint64_t *accf = empty + kBresMaxStages;
+    uint64_t *acce = accf + 2;
+    uint64_t *bfull = acce + 2;
+    uint64_t *bfree = bfull + 2;
+    uint64_t *drain = bfree + 2;
+    volatile uint32_t *tmem_slot = (volatile uint32_t *)(drain + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = 2 * bn < 32 ? 32 : 2 * bn;
+    const int64_t walker = blockIdx.x, walkers = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], kEpiThreads);
+            mbar_init(&bfull[i], 1);
+            mbar_init(&bfree[i], 1);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int8_t armed[kBresMaxStages];
+            for (int s = 0; s < kBresMaxStages; ++s) armed[s] = -1;
+            int8_t barmed[2] = {-1, -1};
+            uint32_t bfree_bits = 0;       // parity of the next load into slot s
+            int slot = 1;
+            int64_t cur_key = -1;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
+                int64_t b, mt;
+                int nt;
+                bres_coords(args, t, b, mt, nt);
+                const int zA = args.batch_a ? (int)b : 0;
+                const int zB = args.batch_b ? (int)b : 0;
+                const int64_t key = (int64_t)zB * args.n_nt + nt;
+                if (key != cur_key) {
+                    // the whole K of this tile's B' slice into the next slot,
+                    // once the MMAs that read that slot before have finished
+                    slot ^= 1;
+                    const uint32_t par = (bfree_bits >> slot) & 1u;
+                    if (!mbar_wait(&bfree[slot], par ^ 1u, &abort_flag)) { ok = false; break; }
+                    bfree_bits ^= 1u << slot;
+                    uint8_t *sb = bslot0 + (size_t)slot * cfg.slot_bytes;
+                    mbar_expect_tx(&bfull[slot], (uint32_t)args.nk * (uint32_t)bn * BKB);
+                    for (int kc = 0; kc < args.nk; ++kc)
+                        tma_load_3d(sb + (size_t)kc * cfg.chunk_bytes, &tmB, &bfull[slot], kc * BK, nt * bn, zB);
+                    barmed[slot] = (int8_t)par;
+                    cur_key = key;
+                }
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
+                    uint8_t *sa = smem + (size_t)stage * a_bytes;
+                    mbar_expect_tx(&full[stage], a_bytes);
+                    tma_load_3d(sa, &tmA, &full[stage], kc * BK, (int)(mt * 128), zA);
+                    armed[stage] = (int8_t)phase;
+                    if (++stage == stages) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (!ok) {
+                // drain (bounded): loads still in flight land before shared memory goes
+                for (int s = 0; s < stages; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&full[s], (uint32_t)armed[s]) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                    }
+                }
+                for (int s = 0; s < 2; ++s) {
+                    if (barmed[s] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&bfull[s], (uint32_t)barmed[s]) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------- MMA issue --
+        if (lane == 0) {
+            uint32_t idesc = 0;
+            idesc |= 1u << 4;                                  // D = F32
+            const uint32_t fmt = args.dtype == TN_BF16 ? 1u : 0u;
+            idesc |= fmt << 7;                                 // A format
+            idesc |= fmt << 10;                                // B format
+            idesc |= (uint32_t)(bn >> 3) << 17;                // N
+            idesc |= (uint32_t)(128 >> 4) << 24;               // M
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            uint32_t bfull_bits = 0;       // parity of the next use of slot s
+            int slot = 1;
+            int64_t cur_key = -1;
+            bool ok = true;
+            bool issued = false;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
+                int64_t b, mt;
+                int nt;
+                bres_coords(args, t, b, mt, nt);
+                const int zB = args.batch_b ? (int)b : 0;
+                const int64_t key = (int64_t)zB * args.n_nt + nt;
+                if (key != cur_key) {
+                    // the MMAs issued so far read the old slot: release it
+                    // when they finish, then wait for the new slice
+                    if (cur_key >= 0) tc_commit(&bfree[slot]);
+                    slot ^= 1;
+                    if (!mbar_wait(&bfull[slot], (bfull_bits >> slot) & 1u, &abort_flag)) { ok = false; break; }
+                    bfull_bits ^= 1u << slot;
+                    tc_fence_after();
+                    cur_key = key;
+                }
+                if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * bn);
+                const uint32_t b_base = smem_u32(bslot0 + (size_t)slot * cfg.slot_bytes);
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(smem + (size_t)stage * a_bytes);
+                    const uint32_t b_addr = b_base + (uint32_t)kc * cfg.chunk_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < BKB / 32; ++kk) {     // 32 bytes of K per MMA
+                        const uint64_t ad = smem_desc<BKB>(a_addr + kk * 32);
+                        const uint64_t bd = smem_desc<BKB>(b_addr + kk * 32);
+                        tc_mma<false, false>(d_tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    issued = true;
+                    tc_commit(&empty[stage]);
+                    if (++stage == stages) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                tc_commit(&accf[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+            if (!ok && issued) {
+                tc_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue --
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        int e;
+        if (args.out_c64 || args.sr.scale_off) e = 0;
+        else if (args.sr.tmax)
+            e = min(120, scale_exp_tc(args.sr.tmax[args.sr.meta_a], args.sr.tmax[args.sr.meta_b], args.lk) +
+                             args.sr.headroom);
+        else e = args.sr.fixed_exp;
+        if (args.sr.texp && blockIdx.x == 0 && threadIdx.x == 64)
+            args.sr.texp[args.sr.meta_c] = args.sr.texp[args.sr.meta_a] + args.sr.texp[args.sr.meta_b] + e;
+        const float sc = __int_as_float((127 + e) << 23);
+        int64_t lowtab[8];
+        bool low_kept = true;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            lowtab[j] = args.out_rank ? permute_bits(args, j, 0, 3) : j;
+            low_kept = low_kept && lowtab[j] == j;
+        }
+        float mx = 0.f;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t t = walker; t < args.tiles; t += walkers) {
+            int64_t b, mt;
+            int nt;
+            bres_coords(args, t, b, mt, nt);
+            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
+            tc_fence_after();
+            const int64_t m = mt * 128 + row;
+            const int col0 = nt * bn;
+            const int64_t cb = b;
+            int64_t prow = 0;
+            if (args.out_rank) prow = permute_bits(args, (cb * args.M + m) * (int64_t)args.N, args.ln, args.out_rank);
+            const int col_end = min(bn, 2 * args.N - col0);
+            for (int c = 16 * half; c < col_end; c += 32) {
+                uint32_t r[16];
+                tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * bn + c), r);
+                tmem_wait_ld();
+                tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, sc, mx);
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[acc]);
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && args.sr.out_max)
+            atomicMax(reinterpret_cast<int *>(args.sr.out_max), __float_as_int(mx));
+        if (lane == 0 && args.sr.err && args.dtype == TN_F16 && !args.out_c64 && !(mx <= 65504.0f))
+            atomicOr(args.sr.err, 2);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0 && args.err) atomicOr(args.err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// shared memory of the B'-resident kernel: A ring + two B' slots + barriers
+constexpr int kBresSmemBudget = 196 * 1024;
+constexpr int kBresSmemTotal = 1024 + kBresSmemBudget + (2 * kBresMaxStages + 9) * 8 + 16;
+
 // ------------------------------------------------------------ host side --
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                               const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -512,6 +789,12 @@ cudaError_t tc_prepare() {
     if (e == cudaSuccess) e = set_attr_bn<128, false>();
     if (e == cudaSuccess) e = set_attr_bn<128, true>();
     if (e == cudaSuccess) e = prepare_pair<false>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tc_bres_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBresSmemTotal);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tc_bres_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBresSmemTotal);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tc_bres_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBresSmemTotal);
     if (e == cudaSuccess && dev < 31) done_mask |= 1 << dev;
     return e;
 }
@@ -522,6 +805,15 @@ bool tc_encode_3d(CUtensorMap *m, int dtype, int esz, const void *base, uint64_t
 }
 
 int tc_default_gm(int bn) { return default_gm(bn); }
+
+bool tc_bres_eligible(int lm, int ln, int lk, int64_t batch, int bn, int fp8, int gathered) {
+    if (fp8 || gathered || !tc_gemm_supported(lk, ln) || lk > kSplitLog2K) return false;
+    if (tc_split(lm, ln, lk, batch) != 1) return false;
+    const int kreal = 2 << lk;
+    const int bk = kreal >= 64 ? 64 : kreal;
+    const uint32_t chunk = ((uint32_t)bn * 2 * bk + 1023u) / 1024u * 1024u;
+    return (uint64_t)(kreal / bk) * chunk <= 65536;
+}
 
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
 
@@ -642,6 +934,33 @@ cudaError_t tc_setup(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, bo
     return cudaSuccess;
 }
 
+// B'-resident launch (gemm_tc_bres_kernel) when the step allows it: one K
+// part, no gathers, 1-CTA FP16/BF16 tiles, the whole K of a B' slice within
+// 64 KiB.  Returns false when it does not apply.
+bool bres_config(const TcArgs &a, int bn, int bkb, bool pair, int fp8, BresCfg &cfg) {
+    if (pair || fp8 || a.split != 1 || a.za || a.zb || a.zc || a.gather_r || a.withhold) return false;
+    const uint32_t chunk = ((uint32_t)bn * bkb + 1023u) / 1024u * 1024u;
+    const uint64_t slot = (uint64_t)a.nk * chunk;
+    if (slot > 65536) return false;
+    const int stages = (int)std::min<uint64_t>(kBresMaxStages, (kBresSmemBudget - 2 * slot) / (128u * bkb));
+    if (stages < 2) return false;
+    cfg.bn = bn;
+    cfg.stages = stages;
+    cfg.chunk_bytes = chunk;
+    cfg.slot_bytes = (uint32_t)slot;
+    return true;
+}
+
+template <int BKB>
+cudaError_t run_tc_bres(const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a, const BresCfg &cfg,
+                        cudaStream_t s) {
+    // a grid that is a multiple of the n tiles keeps each walker on one n tile
+    int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
+    if (a.n_nt > 1 && a.n_nt <= grid) grid = grid / a.n_nt * a.n_nt;
+    gemm_tc_bres_kernel<BKB><<<(unsigned)grid, kTcThreads, kBresSmemTotal, s>>>(ma, mb, a, cfg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, cudaStream_t s) {
     {
         const cudaError_t e = tc_prepare();
@@ -656,6 +975,14 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         if (e != cudaSuccess) return e;
     }
     cudaError_t e;
+    BresCfg bc;
+    if (d.bres && bres_config(a, bn, 2 * bk, pair, d.fp8, bc)) {
+        switch (bk) {
+            case 16: return run_tc_bres<32>(ma, mb, a, bc, s);
+            case 32: return run_tc_bres<64>(ma, mb, a, bc, s);
+            default: return run_tc_bres<128>(ma, mb, a, bc, s);
+        }
+    }
     if (pair) {
         e = run_tc_pair<false>(ma, mb, a, s);
     } else if (d.fp8) {

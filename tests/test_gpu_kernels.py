@@ -208,6 +208,43 @@ def test_gemm_tensor_cores_half_k_chunks(M, N, K):
     _lp_case(tn.BF16, M, N, K, 2, tn.GEMM_TC_HALF_K)
 
 
+# B'-resident kernel (each CTA keeps its B' slice in shared memory across its
+# tiles; short K): against the reference within the rounding bound, and bit
+# for bit against the 1-CTA kernel (same MMAs, same epilogue).  Shapes: one
+# tile, N tiles that do / do not divide the grid (walkers whose slice changes),
+# M below 128 (a partial tile), K = 8 .. 64 (32-, 64- and 128-byte K chunks), a K
+# whose B' slice no longer fits (run by the 1-CTA kernel), many tiles per CTA.
+BRES_SHAPES = [(128, 16, 8), (1024, 128, 16), (2048, 256, 32), (4096, 512, 64), (64, 64, 64),
+               (65536, 32, 64), (1 << 17, 128, 16), (512, 1024, 8), (1024, 128, 256), (256, 4096, 64)]
+
+
+def _gemm_bits(dtype, M, N, K, batch, ba, bb, kernel, seed=3):
+    g = torch.Generator(device="cuda").manual_seed(seed + M + N + K)
+    tdt = torch.float16 if dtype == tn.F16 else torch.bfloat16
+    a = (torch.randn(batch if ba else 1, M, K, 2, generator=g, device="cuda") * 0.5).to(tdt)
+    b = (torch.randn(batch if bb else 1, K, N, 2, generator=g, device="cuda") / K ** 0.5).to(tdt)
+    c = torch.zeros(batch, M, N, 2, dtype=tdt, device="cuda")
+    tn.gemm(dtype, a, b, c, M, N, K, batch=batch, batch_a=ba, batch_b=bb, scale_exp=2, kernel=kernel)
+    return c.view(torch.int16).cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", BRES_SHAPES)
+def test_gemm_tensor_cores_b_resident(M, N, K):
+    _lp_case(tn.F16, M, N, K, 1, tn.GEMM_TC_BRES)
+    assert np.array_equal(_gemm_bits(tn.F16, M, N, K, 1, True, True, tn.GEMM_TC_BRES),
+                          _gemm_bits(tn.F16, M, N, K, 1, True, True, 3))
+
+
+@pytest.mark.parametrize("ba,bb", [(True, True), (True, False), (False, True)])
+def test_gemm_tensor_cores_b_resident_batched(ba, bb):
+    # a batched B changes each walker's slice with the batch entry
+    _lp_case(tn.F16, 1024, 128, 32, 3, tn.GEMM_TC_BRES, ba, bb)
+    _lp_case(tn.BF16, 512, 256, 64, 4, tn.GEMM_TC_BRES, ba, bb)
+    for dt in (tn.F16, tn.BF16):
+        assert np.array_equal(_gemm_bits(dt, 2048, 64, 16, 5, ba, bb, tn.GEMM_TC_BRES),
+                              _gemm_bits(dt, 2048, 64, 16, 5, ba, bb, 3))
+
+
 def test_gemm_tensor_cores_cta_pairs_long_k():
     # K = 2^16 complex: split into K parts (FP32 partials, FP64 reduction)
     M, N, K = 256, 128, 1 << 16
