@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--pair", action="store_true", help="--case gemm_tc on CTA pairs (256-row tiles)")
     ap.add_argument("--bres", action="store_true",
                     help="--case gemm_tc with the B' slice resident in shared memory (short K)")
+    ap.add_argument("--tma-store", action="store_true",
+                    help="--case gemm_tc --bres with C tiles written by TMA stores")
     ap.add_argument("--sustain", type=float, default=0.0,
                     help="--case gemm_tc: also time calls back to back for this many seconds "
                          "(the power-capped rate), and cuBLAS on the same real GEMM")
@@ -95,7 +97,8 @@ def kernel_case(args):
             dt = tn.FP8
         run = lambda: tn.gemm(dt, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
                               scale_exp=-12 if args.fp8 else 0,
-                              kernel=tn.GEMM_TC_PAIR if args.pair else (tn.GEMM_TC_BRES if args.bres else 3))
+                              kernel=tn.GEMM_TC_PAIR if args.pair else
+                              (tn.GEMM_TC_BRES_STORE if args.tma_store else (tn.GEMM_TC_BRES if args.bres else 3)))
         work, unit = 8.0 * M * N * K * b, "TFLOP/s"
     elif args.case == "gather":
         # sparse-state contraction of many tensor pairs: 2048 A chunks of
@@ -918,8 +921,11 @@ def main():
         v = roofline["per_class"].get(k)
         if v and v["launches"] and hbm:
             v["frac_of_hbm"] = v["gbs"] / hbm
-    # DRAM traffic per launch from the committed ncu capture, only while the
-    # kernel source is the one that was captured
+    # DRAM traffic of the dominant launch from the committed ncu capture (a
+    # small case of the same step, scaled by its batch), only while the kernel
+    # source is the one that was captured; `traffic` (per launch, averaged
+    # like `achieved` over all the kernel's launches) stays null: the other
+    # launches are not captured at this size
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_file):
         try:
@@ -929,8 +935,10 @@ def main():
             sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
             if (tr.get("kernel") == name and tr.get("dtype") == args.dtype
                     and tr.get("kernel_sha256_16") == sha and sb == 8):
-                roofline["traffic"] = tr.get("bytes_per_launch")
-                roofline["traffic_source"] = tr.get("source")
+                roofline["traffic_dominant_launch"] = {
+                    "bytes": tr.get("bytes_dominant_launch"),
+                    "algorithmic_bytes": tr.get("algorithmic_bytes_dominant_launch"),
+                    "scope": tr.get("scope"), "source": tr.get("source")}
         except Exception:
             pass
     # the autotuner's timings of the dominant step, one per candidate

@@ -616,7 +616,8 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  *   5 complex-half tensor cores with 64-byte K chunks (K >= 32, else as 3),
  *   6 complex-half tensor cores with each CTA's B' slice resident in shared
  *   memory across its tiles (short K: the whole K of a B' tile within
- *   64 KiB, one K part; else as 3).
+ *   64 KiB, one K part; else as 3), 7 as 6 with the C tiles staged in
+ *   shared memory and written by TMA stores (N >= 32; else as 6).
  * out_max: optional device float, receives max |component| of the stored C.
  */
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,

@@ -28,6 +28,7 @@ KERNEL_NAMES = {0: "c64_rows", 1: "c64_tiled", 2: "lp_rows", 3: "lp_tc"}
 GEMM_TC_PAIR = 4   # tn_gemm kernel index: tensor cores on CTA pairs
 GEMM_TC_HALF_K = 5  # tn_gemm kernel index: tensor cores, 64-byte K chunks
 GEMM_TC_BRES = 6    # tn_gemm kernel index: tensor cores, B' slice resident in shared memory
+GEMM_TC_BRES_STORE = 7  # ... and C tiles written by TMA stores
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 

@@ -77,10 +77,12 @@ enum GemmKernel : int32_t {
 // code, bit 8 CTA pairs (256-row tiles on a cluster of 2 SMs), bit 9 64-byte
 // K chunks (twice the ring stages of 128-byte chunks in the same memory),
 // bit 10 the B'-resident kernel (each walker keeps its B' slice in shared
-// memory; short-K steps).
+// memory; short-K steps), bit 11 (with bit 10) its C tiles staged in shared
+// memory and written by TMA stores.
 constexpr int kTcPairTile = 0x100;
 constexpr int kTcHalfKTile = 0x200;
 constexpr int kTcBresTile = 0x400;   // bit 10: B' slice resident in shared memory (short K)
+constexpr int kTcStoreTile = 0x800;  // bit 11 (with bit 10): C tiles written by TMA stores
 // whether a step of this shape runs on CTA pairs when asked (bn: the N tile
 // in real columns the launch uses)
 bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);

@@ -131,6 +131,9 @@ struct TcGemmDesc {
     // 1: keep each walker's B' slice resident in shared memory (short-K
     // steps, gemm_tc_bres_kernel) where the step allows it
     int bres = 0;
+    // with bres: write C tiles staged in shared memory with TMA stores
+    // (complex-half C in natural order, N tiles of 64-column multiples)
+    int tma_store = 0;
 };
 
 // E4M3 operands of an FP8 tensor-core step: n_pairs FP16/BF16 values pairs
@@ -172,6 +175,9 @@ bool tc_gemm_supported(int lk, int ln);
 // tile of bn real columns (1-CTA FP16/BF16, one K part, no gathers, the whole
 // K of a B' slice within 64 KiB)
 bool tc_bres_eligible(int lm, int ln, int lk, int64_t batch, int bn, int fp8, int gathered);
+// the same with the C tiles written by TMA stores (complex-half C in natural
+// order, bn a multiple of 64, room for two staged C tiles)
+bool tc_bres_store_eligible(int lm, int ln, int lk, int64_t batch, int bn);
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err,
                            cudaStream_t s);
 int tc_num_sms();

@@ -31,6 +31,7 @@
 #include <cuda_fp8.h>
 
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -342,7 +343,30 @@ struct BresCfg {
     int stages;             // A stages in the ring
     uint32_t chunk_bytes;   // one K chunk of the slice (bn x BKB), rounded up to 1 KiB
     uint32_t slot_bytes;    // nk chunks, <= 64 KiB
+    int tma_store;          // 1: C tiles staged in shared memory and written by TMA stores
+    uint32_t stage_c_bytes; // one staged C tile: bn / 64 panels of 128 rows x 128 bytes
 };
+
+// AND of a predicate over the 256 epilogue threads (named barrier 2): the
+// epilogue's decisions to stop must agree before any of them waits on a
+// named barrier the others would never reach
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 2, 256, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// TMA store of one staged 128-row panel of C (bulk group of this thread)
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(map),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
 
 __device__ __forceinline__ void bres_coords(const TcArgs &a, int64_t t, int64_t &b, int64_t &mt, int &nt) {
     nt = (int)(t % a.n_nt);
@@ -356,6 +380,7 @@ constexpr int kBresMaxStages = 12;
 template <int BKB>
 __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB,
+                                                              const __grid_constant__ CUtensorMap tmC,
                                                               const TcArgs args, const BresCfg cfg) {
     constexpr int BK = BKB / 2;
     constexpr uint32_t a_bytes = 128 * BKB;
@@ -363,7 +388,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int bn = cfg.bn, stages = cfg.stages;
     uint8_t *bslot0 = smem + (size_t)stages * a_bytes;           // B' slots after the A ring
-    uint64_t *full = (uint64_t *)(bslot0 + 2 * (size_t)cfg.slot_bytes);
+    uint8_t *cstage = bslot0 + 2 * (size_t)cfg.slot_bytes;       // staged C tiles (two)
+    uint64_t *full = (uint64_t *)(cstage + (cfg.tma_store ? 2 * (size_t)cfg.stage_c_bytes : 0));
     uint64_t *empty = full + kBresMaxStages;
     uint64_t *accf = empty + kBresMaxStages;
     uint64_t *acce = accf + 2;
@@ -557,11 +583,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
         float mx = 0.f;
         int acc = 0;
         uint32_t acc_phase = 0;
+        int64_t ntile = 0;
         for (int64_t t = walker; t < args.tiles; t += walkers) {
             int64_t b, mt;
             int nt;
             bres_coords(args, t, b, mt, nt);
-            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
+            const bool got = mbar_wait(&accf[acc], acc_phase, &abort_flag);
+            if (cfg.tma_store ? !epi_all(got) : !got) break;
             tc_fence_after();
             const int64_t m = mt * 128 + row;
             const int col0 = nt * bn;
@@ -569,6 +597,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
             int64_t prow = 0;
             if (args.out_rank) prow = permute_bits(args, (cb * args.M + m) * (int64_t)args.N, args.ln, args.out_rank);
             const int col_end = min(bn, 2 * args.N - col0);
+            if (cfg.tma_store) {
+                // the tile's rounded values go to a staged C tile in shared
+                // memory (128-byte swizzle: 16-byte unit u of row r at unit
+                // u ^ (r & 7) of its 128-byte line), then one thread writes
+                // the bn / 64 panels with TMA stores -- full lines, no
+                // row-per-thread global stores.  Two staged tiles alternate;
+                // before one is rewritten its stores must have read it.
+                uint8_t *stg = cstage + (size_t)(ntile & 1) * cfg.stage_c_bytes;
+                if (threadIdx.x == 64 && ntile >= 2)
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+                for (int c = 16 * half; c < col_end; c += 32) {
+                    uint32_t r[16];
+                    tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * bn + c), r);
+                    tmem_wait_ld();
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float re = __uint_as_float(r[2 * j]) * sc;
+                        const float im = __uint_as_float(r[2 * j + 1]) * sc;
+                        float2 back;
+                        if (args.dtype == TN_BF16) {
+                            __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                            back = __bfloat1622float2(h);
+                        } else {
+                            __half2 h = __floats2half2_rn(re, im);
+                            packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                            back = __half22float2(h);
+                        }
+                        if (m < args.M) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
+                    }
+                    const int p = c >> 6, u = (c & 63) >> 3;
+                    uint8_t *line = stg + (size_t)p * 16384 + (size_t)row * 128;
+                    *reinterpret_cast<uint4 *>(line + (((u) ^ (row & 7)) << 4)) =
+                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    *reinterpret_cast<uint4 *>(line + (((u + 1) ^ (row & 7)) << 4)) =
+                        make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[acc]);          // TMEM is read: the MMA may reuse it
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+                if (threadIdx.x == 64) {
+                    for (int p = 0; p < bn / 64; ++p)
+                        tma_store_3d(&tmC, stg + (size_t)p * 16384, col0 + 64 * p, (int)(mt * 128), (int)cb);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+                ++ntile;
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+                continue;
+            }
             for (int c = 16 * half; c < col_end; c += 32) {
                 uint32_t r[16];
                 tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * bn + c), r);
@@ -579,6 +659,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
             mbar_arrive(&acce[acc]);
             if (++acc == 2) { acc = 0; acc_phase ^= 1; }
         }
+        // every TMA store written out before the kernel ends
+        if (cfg.tma_store && threadIdx.x == 64) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0 && args.sr.out_max)
             atomicMax(reinterpret_cast<int *>(args.sr.out_max), __float_as_int(mx));
@@ -815,6 +897,15 @@ bool tc_bres_eligible(int lm, int ln, int lk, int64_t batch, int bn, int fp8, in
     return (uint64_t)(kreal / bk) * chunk <= 65536;
 }
 
+bool tc_bres_store_eligible(int lm, int ln, int lk, int64_t batch, int bn) {
+    if (!tc_bres_eligible(lm, ln, lk, batch, bn, 0, 0) || bn < 64 || bn % 64) return false;
+    const int kreal = 2 << lk;
+    const int bk = kreal >= 64 ? 64 : kreal;
+    const uint64_t chunk = ((uint64_t)bn * 2 * bk + 1023u) / 1024u * 1024u;
+    const uint64_t slot = (uint64_t)(kreal / bk) * chunk, stage_c = (uint64_t)(bn / 64) * 16384;
+    return 2 * slot + 2 * stage_c + 2 * 128u * 2 * bk <= (uint64_t)kBresSmemBudget;
+}
+
 bool tc_gemm_supported(int lk, int ln) { return lk >= 3 && lk <= 24 && ln <= 24; }
 
 // A step runs on CTA pairs when asked and when its tiles are the pair
@@ -937,17 +1028,24 @@ cudaError_t tc_setup(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, bo
 // B'-resident launch (gemm_tc_bres_kernel) when the step allows it: one K
 // part, no gathers, 1-CTA FP16/BF16 tiles, the whole K of a B' slice within
 // 64 KiB.  Returns false when it does not apply.
-bool bres_config(const TcArgs &a, int bn, int bkb, bool pair, int fp8, BresCfg &cfg) {
+bool bres_config(const TcArgs &a, int bn, int bkb, bool pair, int fp8, bool tma_store, BresCfg &cfg) {
     if (pair || fp8 || a.split != 1 || a.za || a.zb || a.zc || a.gather_r || a.withhold) return false;
     const uint32_t chunk = ((uint32_t)bn * bkb + 1023u) / 1024u * 1024u;
     const uint64_t slot = (uint64_t)a.nk * chunk;
     if (slot > 65536) return false;
-    const int stages = (int)std::min<uint64_t>(kBresMaxStages, (kBresSmemBudget - 2 * slot) / (128u * bkb));
+    // TMA stores of staged C tiles: complex-half C in natural order, N tiles
+    // of whole 64-column panels
+    const bool st = tma_store && !a.out_c64 && a.out_rank == 0 && !a.partial && bn >= 64 && bn % 64 == 0;
+    const uint64_t stage_c = st ? (uint64_t)(bn / 64) * 16384 : 0;
+    if (2 * slot + 2 * stage_c >= (uint64_t)kBresSmemBudget) return false;
+    const int stages = (int)std::min<uint64_t>(kBresMaxStages, (kBresSmemBudget - 2 * slot - 2 * stage_c) / (128u * bkb));
     if (stages < 2) return false;
     cfg.bn = bn;
     cfg.stages = stages;
     cfg.chunk_bytes = chunk;
     cfg.slot_bytes = (uint32_t)slot;
+    cfg.tma_store = st ? 1 : 0;
+    cfg.stage_c_bytes = (uint32_t)stage_c;
     return true;
 }
 
@@ -957,7 +1055,12 @@ cudaError_t run_tc_bres(const CUtensorMap &ma, const CUtensorMap &mb, const TcAr
     // a grid that is a multiple of the n tiles keeps each walker on one n tile
     int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
     if (a.n_nt > 1 && a.n_nt <= grid) grid = grid / a.n_nt * a.n_nt;
-    gemm_tc_bres_kernel<BKB><<<(unsigned)grid, kTcThreads, kBresSmemTotal, s>>>(ma, mb, a, cfg);
+    CUtensorMap mc;
+    std::memset(&mc, 0, sizeof(mc));
+    if (cfg.tma_store &&
+        !encode_3d(&mc, a.dtype, 2, a.C, (uint64_t)(2 * a.N), (uint64_t)a.M, (uint64_t)a.batch, 64, 128))
+        return cudaErrorInvalidValue;
+    gemm_tc_bres_kernel<BKB><<<(unsigned)grid, kTcThreads, kBresSmemTotal, s>>>(ma, mb, mc, a, cfg);
     return cudaGetLastError();
 }
 
@@ -976,7 +1079,7 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
     }
     cudaError_t e;
     BresCfg bc;
-    if (d.bres && bres_config(a, bn, 2 * bk, pair, d.fp8, bc)) {
+    if (d.bres && bres_config(a, bn, 2 * bk, pair, d.fp8, d.tma_store != 0, bc)) {
         switch (bk) {
             case 16: return run_tc_bres<32>(ma, mb, a, bc, s);
             case 32: return run_tc_bres<64>(ma, mb, a, bc, s);

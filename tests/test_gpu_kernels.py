@@ -228,10 +228,13 @@ def _gemm_bits(dtype, M, N, K, batch, ba, bb, kernel, seed=3):
     return c.view(torch.int16).cpu().numpy()
 
 
+@pytest.mark.parametrize("kernel", [tn.GEMM_TC_BRES, tn.GEMM_TC_BRES_STORE])
 @pytest.mark.parametrize("M,N,K", BRES_SHAPES)
-def test_gemm_tensor_cores_b_resident(M, N, K):
-    _lp_case(tn.F16, M, N, K, 1, tn.GEMM_TC_BRES)
-    assert np.array_equal(_gemm_bits(tn.F16, M, N, K, 1, True, True, tn.GEMM_TC_BRES),
+def test_gemm_tensor_cores_b_resident(M, N, K, kernel):
+    # (GEMM_TC_BRES_STORE: C staged in shared memory and written by TMA
+    # stores where N >= 32; the narrower shapes run as GEMM_TC_BRES)
+    _lp_case(tn.F16, M, N, K, 1, kernel)
+    assert np.array_equal(_gemm_bits(tn.F16, M, N, K, 1, True, True, kernel),
                           _gemm_bits(tn.F16, M, N, K, 1, True, True, 3))
 
 
@@ -240,9 +243,11 @@ def test_gemm_tensor_cores_b_resident_batched(ba, bb):
     # a batched B changes each walker's slice with the batch entry
     _lp_case(tn.F16, 1024, 128, 32, 3, tn.GEMM_TC_BRES, ba, bb)
     _lp_case(tn.BF16, 512, 256, 64, 4, tn.GEMM_TC_BRES, ba, bb)
+    _lp_case(tn.F16, 1024, 128, 32, 3, tn.GEMM_TC_BRES_STORE, ba, bb)
     for dt in (tn.F16, tn.BF16):
-        assert np.array_equal(_gemm_bits(dt, 2048, 64, 16, 5, ba, bb, tn.GEMM_TC_BRES),
-                              _gemm_bits(dt, 2048, 64, 16, 5, ba, bb, 3))
+        for kern in (tn.GEMM_TC_BRES, tn.GEMM_TC_BRES_STORE):
+            assert np.array_equal(_gemm_bits(dt, 2048, 64, 16, 5, ba, bb, kern),
+                                  _gemm_bits(dt, 2048, 64, 16, 5, ba, bb, 3))
 
 
 def test_gemm_tensor_cores_cta_pairs_long_k():

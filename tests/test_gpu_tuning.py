@@ -127,16 +127,33 @@ def test_learned_policy_against_fixed_and_exhaustive():
             p_ = np.argsort(np.argsort([pred[(i,) + k] for k in keys]))
             ranks.append(np.corrcoef(m, p_)[0, 1])
     rank_corr = float(np.nanmean(ranks)) if ranks else float("nan")
-    # whole-plan device time of the three choices, median of 15 calls each
+    # per step, the recorded time of each policy's choice (one exhaustive
+    # tuning pass timed every candidate, so this comparison has no run-to-run
+    # noise): the learned choices against the best and the fixed heuristic's
     fx = _plan(c, q, n_slice_edges=6, slice_batch_log2=6, tile_policy=tn.TILE_FIXED)
+    t_best = t_learn = t_fixed = 0.0
+    for i, (sl, sf) in enumerate(zip(lp.steps(), fx.steps())):
+        cand = by_step.get(i)
+        if not cand:
+            continue
+        t_best += min(cand.values())
+        t_learn += cand.get((sl["kernel"], sl["tile"]), min(cand.values()))
+        t_fixed += cand.get((sf["kernel"], sf["tile"]), min(cand.values()))
+    # whole-plan device time of the three choices, median of 15 calls each
     fixed, learned, best = (_median_ms(p) for p in (fx, lp, held))
-    print(f"held-out plan: fixed {fixed:.3f} ms, learned {learned:.3f} ms, exhaustive {best:.3f} ms; "
+    print(f"held-out plan: recorded step sums fixed {t_fixed:.3f} ms, learned {t_learn:.3f} ms, best "
+          f"{t_best:.3f} ms; measured fixed {fixed:.3f} ms, learned {learned:.3f} ms, exhaustive {best:.3f} ms; "
           f"selection: exhaustive tuning {t_exhaustive:.2f} s, learned first call {t_learned_call:.2f} s; "
           f"mean within-step rank correlation {rank_corr:.2f}")
     assert rank_corr > 0.2
-    assert learned <= 1.08 * fixed
-    assert learned <= 1.15 * best
-    assert t_learned_call < t_exhaustive
+    # choice quality: within 3% of exhaustive tuning and no worse than the
+    # fixed heuristic (which is itself within about 1% of exhaustive on these
+    # workloads, so 1% of slack is the measurement's resolution)
+    assert t_learn <= 1.03 * t_best
+    assert t_learn <= 1.01 * t_fixed
+    assert learned <= 1.05 * best
+    # what the model gains over exhaustive tuning at that quality: selection time
+    assert t_learned_call * 3 < t_exhaustive
 
 
 def _median_ms(plan, n=15):
