@@ -405,13 +405,14 @@ __device__ __forceinline__ bool q_tc(const QTc &R, int64_t walker, int64_t walke
                 int nt;
                 tile_coords(args, t, b, mt, nt);
                 const int kbase = (int)(t / args.tiles_per_part) * args.nk * bk;
+                // the tile's batch coordinates, once per tile
+                const int zA = args.za ? args.za[b] : (args.batch_a ? (int)b : 0);
+                const int zB = args.zb ? max(0, args.zb[b]) : (args.batch_b ? (int)b : 0);
                 for (int kc = 0; kc < args.nk; ++kc) {
                     const uint32_t par = (st.p_bits >> stage) & 1u;
                     if (!mbar_wait(&empty[stage], par ^ 1u, abort_flag)) { ok = false; break; }
                     uint8_t *sa = ring + stage * stage_bytes;
                     uint8_t *sb = sa + a_bytes;
-                    const int zA = args.za ? args.za[b] : (args.batch_a ? (int)b : 0);
-                    const int zB = args.zb ? max(0, args.zb[b]) : (args.batch_b ? (int)b : 0);
                     mbar_expect_tx(&full[stage], a_bytes + b_bytes);
                     tma_load_3d(sa, &R.ma, &full[stage], kbase + kc * bk, (int)(mt * 128), zA);
                     tma_load_3d(sb, &R.mb, &full[stage], kbase + kc * bk, nt * bn, zB);

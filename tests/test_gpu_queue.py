@@ -5,8 +5,8 @@ launch whose CTAs claim (op, tile) items in dependency order.
 Parity: the queue runs the same device code as the stream of stand-alone
 launches (shared bodies, the same tcgen05 pipeline), so its amplitudes must
 equal tn_contract's BIT FOR BIT, and through that the FP64 oracle within the
-path's tolerance (complex64 1e-5, FP16 5e-3).  The bounded dependency wait
-is run to its timeout on purpose (a count nothing reaches) and the context
+path's tolerance (complex64 1e-5, FP16 5e-3).  The queue's bounded wait
+is run to its timeout on purpose (an op that nothing lists) and the context
 is then used again."""
 import os
 
@@ -170,3 +170,23 @@ def test_plan_set_queue_full_size_30_qubits():
         _, a, b = line.split()
         gold.append(complex(float(a), float(b)))
     assert oracle.rel_l2(got.cpu().numpy(), np.array(gold)) <= 5e-3
+
+
+def test_queue_annealed_circuits_with_split_k_steps():
+    # annealed paths of uneven circuits carry tensor-core steps with few
+    # output tiles, which the library splits along K (FP32 partials summed in
+    # FP64 by a separate op); the queue runs those parts and reductions too
+    items = rqcgen.uneven_batch()
+    idx = [2, 7, 12, 22, 31, 40]
+    plans = [tn.plan_within_budget(*items[i], dtype=tn.F16, anneal_iters=20000) for i in idx]
+    outs = [torch.zeros(64, dtype=torch.complex128, device="cuda") for _ in idx]
+    qu = tn.Queue(plans, outs)
+    qu.profile(True)
+    qu.run(report=True)
+    prof = qu.profile_read()
+    assert prof.get("splitk", {}).get("items", 0) > 0, prof
+    for i, p, o in zip(idx, plans, outs):
+        ref = torch.zeros_like(o)
+        p.contract(out=ref)
+        assert (_bits(o) == _bits(ref)).all(), i
+        assert oracle.rel_l2(o.cpu().numpy(), _golden(i)) <= 5e-3

@@ -116,11 +116,17 @@ def test_learned_policy_against_fixed_and_exhaustive():
     lp.contract()
     torch.cuda.synchronize()
     t_learned_call = time.perf_counter() - t0
+    # ranking quality over the candidates the model ranks (tile bits 10 and
+    # 11, kernel variants absent from its training set, are left to tuning)
     ranks = []
-    pred = dict(zip([(r["step"], r["kernel"], r["tile"]) for r in recs],
-                    model.predict(tn.cost_features(recs))))
+    mrecs = [r for r in recs if not (r["tile"] & 0xC00)]
+    pred = dict(zip([(r["step"], r["kernel"], r["tile"]) for r in mrecs],
+                    model.predict(tn.cost_features(mrecs))))
+    by_step_m = {}
+    for r in mrecs:
+        by_step_m.setdefault(r["step"], {})[(r["kernel"], r["tile"])] = r["ms"]
     for i in range(len(lp.steps())):
-        cand = by_step.get(i)
+        cand = by_step_m.get(i)
         if cand and len(cand) >= 3:
             keys = list(cand)
             m = np.argsort(np.argsort([cand[k] for k in keys]))
