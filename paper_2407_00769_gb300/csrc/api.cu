@@ -1219,7 +1219,9 @@ int tn_contract(tn_plan_t *P, int64_t slice_begin, int64_t slice_count, double *
             if (rc != TN_OK) return rc;
             P->queue_key = key;
         }
-        rc = tn_queue_run(P->queue, stream, nullptr);
+        // with a report requested the run is synchronized and its waits checked
+        tn_contract_report qrep;
+        rc = tn_queue_run(P->queue, stream, rep ? &qrep : nullptr);
         if (rc != TN_OK) return rc;
         launches = 1;
     } else if (graph) {
