@@ -147,7 +147,7 @@ __device__ __forceinline__ void permute_tile_body(const T *in, T *out, const Per
 // and go to; per tile only the tile's base offsets change (from 8-bit lookup
 // tables).  Each thread moves its 4 elements with one 16-byte (4-byte
 // elements) or two (8-byte elements) vector loads and stores.  The body walks
-// tiles first, first + step, ... below end, two per iteration (two 16-byte
+// tiles first, first + step, ... below end, NT per iteration (NT 16-byte
 // loads in flight per thread).
 //
 // EXPAND (complex-half only): instead of the permuted tensor, write the
@@ -159,16 +159,16 @@ struct ExpandArgs {
     int32_t lk, ln, np;
 };
 
-template <typename T>
+template <typename T, int NT = 2>
 struct PermTiledSmem {
-    T tile[2][1024 + 32];
+    T tile[NT][1024 + 32];
     int64_t s_bin[4][256], s_bout[4][256];
 };
 
-template <typename T, bool EXPAND, class Sync>
+template <typename T, bool EXPAND, class Sync, int NT = 2>
 __device__ __forceinline__ void permute_tiled_body(const T *in, void *out_, const PermParams &p, int64_t first,
                                                    int64_t end, int64_t step, ExpandArgs ex, int tid,
-                                                   PermTiledSmem<T> &sm) {
+                                                   PermTiledSmem<T, NT> &sm) {
     for (int i = tid; i < 1024; i += 256) {
         const int level = i >> 8, v = i & 255;
         int64_t bi = 0, bo = 0;
@@ -195,14 +195,12 @@ __device__ __forceinline__ void permute_tiled_body(const T *in, void *out_, cons
     }
     const int64_t out_off = (e0 & 31) + p.wr_hi_off[e0 >> 5];
     Sync::sync();
-    for (int64_t t0 = first; t0 < end; t0 += 2 * step) {
-        const int64_t t1 = t0 + step;
-        const bool has1 = t1 < end;
-        T v[2][4];
+    for (int64_t t0 = first; t0 < end; t0 += NT * step) {
+        T v[NT][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t t = h ? t1 : t0;
-            if (h && !has1) break;
+        for (int h = 0; h < NT; ++h) {
+            const int64_t t = t0 + h * step;
+            if (t >= end) break;
             const int64_t bin = sm.s_bin[0][t & 255] + sm.s_bin[1][(t >> 8) & 255] +
                                 sm.s_bin[2][(t >> 16) & 255] + sm.s_bin[3][(t >> 24) & 255];
             if constexpr (sizeof(T) == 4) {
@@ -216,16 +214,16 @@ __device__ __forceinline__ void permute_tiled_body(const T *in, void *out_, cons
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h && !has1) break;
+        for (int h = 0; h < NT; ++h) {
+            if (t0 + h * step >= end) break;
 #pragma unroll
             for (int j = 0; j < 4; ++j) sm.tile[h][rd_slot[j]] = v[h][j];
         }
         Sync::sync();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t t = h ? t1 : t0;
-            if (h && !has1) break;
+        for (int h = 0; h < NT; ++h) {
+            const int64_t t = t0 + h * step;
+            if (t >= end) break;
             const int64_t bout = sm.s_bout[0][t & 255] + sm.s_bout[1][(t >> 8) & 255] +
                                  sm.s_bout[2][(t >> 16) & 255] + sm.s_bout[3][(t >> 24) & 255];
             T w[4];
@@ -262,6 +260,55 @@ __device__ __forceinline__ void permute_tiled_body(const T *in, void *out_, cons
 }
 
 // ------------------------------------------------------------------ bprep --
+// B already in [batch][N][K] order (complex-half, K >= 4) -> B' as a
+// stream: unit u covers 4 consecutive k of one row pair (b, pr) of B'
+// (pr < N: B row (b, pr) gives B' rows 2 pr = (re, -im) and 2 pr + 1 =
+// (im, re); pr >= N: the zero rows that pad B' to np rows).  One 16-byte
+// load and two 16-byte stores per unit, U units in flight per thread.
+// Units u = first, first + step, ... < end.
+template <int U>
+__device__ __forceinline__ void bprep_stream_body(const uint4 *B, uint4 *Bp, int lk, int ln, int np, int64_t first,
+                                                  int64_t end, int64_t step) {
+    const int lq = lk - 2;                      // log2 of 16-byte units per row
+    const int half = np >> 1;                   // row pairs of B' per batch entry
+    const int N = 1 << ln;
+    for (int64_t u0 = first; u0 < end; u0 += (int64_t)U * step) {
+        uint4 x[U];
+        int64_t dst[U];
+        bool live[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int64_t u = u0 + (int64_t)j * step;
+            x[j] = make_uint4(0u, 0u, 0u, 0u);
+            dst[j] = -1;
+            live[j] = false;
+            if (u < end) {
+                const int64_t q = u & (((int64_t)1 << lq) - 1);
+                const int64_t row = u >> lq;           // b * half + pr
+                const int pr = (int)(row % half);
+                const int64_t b = row / half;
+                live[j] = pr < N;
+                if (live[j]) x[j] = B[(((b << ln) + pr) << lq) + q];
+                dst[j] = ((b * np + 2 * pr) << lq) + q;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (dst[j] < 0) continue;
+            const uint4 w = x[j];
+            uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = r0;
+            if (live[j]) {
+                // (re, -im): flip the sign bit of the high half; (im, re): swap halves
+                r0 = make_uint4(w.x ^ 0x80000000u, w.y ^ 0x80000000u, w.z ^ 0x80000000u, w.w ^ 0x80000000u);
+                r1 = make_uint4(__byte_perm(w.x, 0, 0x1032), __byte_perm(w.y, 0, 0x1032),
+                                __byte_perm(w.z, 0, 0x1032), __byte_perm(w.w, 0, 0x1032));
+            }
+            Bp[dst[j]] = r0;
+            Bp[dst[j] + ((int64_t)1 << lq)] = r1;
+        }
+    }
+}
+
 // B (complex-half, any mode order) -> B' by a direct gather: target complex
 // index bits [batch][N][K] (LSB = k bit 0); for target bit t the input bit
 // position is p.outer_in[t].  Elements i = first, first + step, ... < end of
@@ -397,7 +444,10 @@ constexpr int kFlushK = 256;   // FP32 terms per partial sum before the FP64 add
 
 template <typename TA, int NC>
 struct RowsSmem {
-    __align__(16) TA As[kRows * kKC];
+    // A tile rows padded to kc + 1 elements: each thread reads its own row,
+    // so an unpadded power-of-two row stride would put all 32 lanes of a
+    // warp on one bank
+    TA As[kRows * (kKC + 1)];
     float2 Bs[kKC][NC];
 };
 
@@ -431,21 +481,33 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
         acc[j] = make_float2(0.f, 0.f);
         tot[j] = make_double2(0.0, 0.0);
     }
+    // K and KC are powers of two: every chunk holds kc = min(KC, K) terms
+    const int lkc = min(lk, 5);
+    static_assert(KC == 32, "lkc assumes 32-term chunks");
+    const int ld = (1 << lkc) + 1;
     for (int k0 = 0; k0 < K; k0 += KC) {
-        const int kc = min(KC, K - k0);
+        const int kc = 1 << lkc;
         Sync::sync();
-        // A tile: rows x kc elements; when kc == K the tile is contiguous
+        // A tile: rows x kc elements, row r at As[r * ld]; when kc == K the
+        // tile is contiguous in memory and read with 16-byte loads
         {
-            const int per16 = 16 / (int)sizeof(TA);
+            constexpr int per16 = 16 / (int)sizeof(TA);
             const int total = rows * kc;
             if (kc == K && (total % per16) == 0) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(Ab + m0 * K);
-                uint4 *dst = reinterpret_cast<uint4 *>(As);
-                for (int i = tid; i < total / per16; i += kRows) dst[i] = src[i];
+                for (int i = tid; i < total / per16; i += kRows) {
+                    const uint4 x = src[i];
+                    const TA *xv = reinterpret_cast<const TA *>(&x);
+#pragma unroll
+                    for (int u = 0; u < per16; ++u) {
+                        const int e = i * per16 + u;
+                        As[(e >> lkc) * ld + (e & (kc - 1))] = xv[u];
+                    }
+                }
             } else {
                 for (int i = tid; i < total; i += kRows) {
-                    const int r = i / kc, kk = i % kc;
-                    As[r * kc + kk] = Ab[(m0 + r) * K + k0 + kk];
+                    const int r = i >> lkc, kk = i & (kc - 1);
+                    As[r * ld + kk] = Ab[(m0 + r) * K + k0 + kk];
                 }
             }
         }
@@ -456,7 +518,7 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
         Sync::sync();
         if (tid < rows) {
             for (int kk = 0; kk < kc; ++kk) {
-                const float2 a = widen<TA, DT>(As[tid * kc + kk]);
+                const float2 a = widen<TA, DT>(As[tid * ld + kk]);
 #pragma unroll
                 for (int j = 0; j < NC; ++j) {
                     if (j < nc) {

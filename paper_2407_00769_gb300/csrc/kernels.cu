@@ -169,6 +169,13 @@ __global__ void bprep_gather_kernel(const uint32_t *__restrict__ B, uint32_t *__
                       (int64_t)gridDim.x * blockDim.x);
 }
 
+// B in [batch][N][K] order already: bprep_stream_body, grid-stride
+__global__ void __launch_bounds__(256) bprep_stream_kernel(const uint4 *__restrict__ B, uint4 *__restrict__ Bp,
+                                                           int lk, int ln, int np, int64_t units) {
+    bprep_stream_body<4>(B, Bp, lk, ln, np, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, units,
+                         (int64_t)gridDim.x * blockDim.x);
+}
+
 // Complex64 B (a small tensor) -> B' in complex-half, one block of 1024
 // threads (bprep_c64_body: rounding, 2^s scale, rounding compensation).
 template <int DT>
@@ -202,6 +209,16 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
             bprep_c64_kernel<TN_BF16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,
                                                          np, g, rank, corr, tmax, texp, meta_src, meta_dst,
                                                         scale_off);
+        return cudaGetLastError();
+    }
+    bool ident = true;
+    for (int i = 0; i < rank; ++i) ident = ident && perm[i] == i;
+    if (ident && lk >= 2 && rank == lk + ln + lb && (((uintptr_t)B | (uintptr_t)Bp) & 15) == 0) {
+        // 16-byte units: np / 2 row pairs x K / 4 per batch entry
+        const int64_t units = ((int64_t)(np >> 1) << (lk - 2)) << lb;
+        const int threads = 256;
+        const int64_t blocks = std::min<int64_t>((units + threads - 1) / threads, (int64_t)tc_num_sms() * 8);
+        bprep_stream_kernel<<<(unsigned)blocks, threads, 0, s>>>((const uint4 *)B, (uint4 *)Bp, lk, ln, np, units);
         return cudaGetLastError();
     }
     if (rank >= 10 && lk >= 2 && np == 2 << ln) {

@@ -201,6 +201,13 @@ __device__ __noinline__ void q_bprep_gather(const QBprepGather &r, int64_t tile,
     bprep_gather_body(r.B, r.Bp, r.lk, r.ln, r.np, r.g, r.rank, i0 + tid, i1, kQSimt);
 }
 
+// B already in [batch][N][K] order: per_item 16-byte units of B' row pairs
+__device__ __noinline__ void q_bprep_stream(const QBprepGather &r, int64_t tile, int tid) {
+    const int64_t i0 = tile * r.per_item, i1 = min(r.total, i0 + r.per_item);
+    bprep_stream_body<4>(reinterpret_cast<const uint4 *>(r.B), reinterpret_cast<uint4 *>(r.Bp), r.lk, r.ln, r.np,
+                         i0 + tid, i1, kQSimt);
+}
+
 template <int DT>
 __device__ __noinline__ void q_bprep_c64(const QBprepC64 &r, int tid, uint8_t *scratch) {
     // the stand-alone kernel's 1024-thread summation order, played by 256 threads
@@ -314,7 +321,10 @@ __device__ __noinline__ void q_simt(const QOp &op, const uint8_t *blob, int64_t 
             else q_perm_tiled<uint2, false>(r, tile, tid, scratch);
             break;
         }
-        case Q_BPREP_GATHER: q_bprep_gather(*reinterpret_cast<const QBprepGather *>(rec), tile, tid); break;
+        case Q_BPREP_GATHER:
+            if (op.sub == 1) q_bprep_stream(*reinterpret_cast<const QBprepGather *>(rec), tile, tid);
+            else q_bprep_gather(*reinterpret_cast<const QBprepGather *>(rec), tile, tid);
+            break;
         case Q_BPREP_C64:
             if (op.sub == TN_F16) q_bprep_c64<TN_F16>(*reinterpret_cast<const QBprepC64 *>(rec), tid, scratch);
             else q_bprep_c64<TN_BF16>(*reinterpret_cast<const QBprepC64 *>(rec), tid, scratch);
@@ -761,6 +771,19 @@ int emit_op(Builder &Bd, int chain, tn_plan_s *P, const Op &op, int64_t slice_ba
                 r.scale_off = P->opts.no_scaling ? 1 : 0;
                 r.g = g;
                 Bd.add(chain, Q_BPREP_C64, dtype, 1, Bd.rec(r));
+                return TN_OK;
+            }
+            bool ident = true;
+            for (int i = 0; i < b.rank; ++i) ident = ident && b.perm[i] == i;
+            if (ident && b.lk >= 2 && b.rank == b.lk + b.ln + b.lb && ((b.src | b.dst) & 15) == 0) {
+                // B in [batch][N][K] order already: the streaming expansion
+                QBprepGather r{};
+                r.B = (const uint32_t *)(ws + b.src);
+                r.Bp = (uint32_t *)(ws + b.dst);
+                r.total = ((int64_t)(b.np >> 1) << (b.lk - 2)) << b.lb;   // 16-byte units
+                r.per_item = 8 * kQSimt * 4;
+                r.lk = b.lk; r.ln = b.ln; r.np = b.np; r.rank = b.rank;
+                Bd.add(chain, Q_BPREP_GATHER, 1, cdiv(r.total, r.per_item), Bd.rec(r));
                 return TN_OK;
             }
             if (b.rank >= 10 && b.lk >= 2 && b.np == 2 << b.ln) {
