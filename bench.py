@@ -497,17 +497,20 @@ def _oversample(recs):
     return out
 
 
-def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
+def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000, iters30=1000000):
     """Paths refined by simulated annealing (tree rotations under the memory
     cap, sliced edges given back where the refined path allows): the 30-qubit
-    job (8 sliced edges, all 256 slices) and the 53-qubit circuit at cap 2^30
-    (slices 0-63 timed, the time of all slices extrapolated).  Reported as
-    time to solution against the greedy plans of the main line and grid53."""
+    job (8 sliced edges, all 256 slices; iters30 moves per chain) and the
+    53-qubit circuit at cap 2^30 (slices 0-63 timed, the time of all slices
+    extrapolated).  Reported as time to solution against the greedy plans of
+    the main line and grid53."""
     import rqcgen
     out = {}
     c, q = rqcgen.grid_30q()
+    t0 = time.perf_counter()
     plan = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
-                   slice_batch_log2=8, anneal_iters=iters, tile_policy=tn.TILE_EXHAUSTIVE)
+                   slice_batch_log2=8, anneal_iters=iters30, tile_policy=tn.TILE_EXHAUSTIVE)
+    plan_s = time.perf_counter() - t0
     info = plan.info()
     amps = torch.zeros(1 << info["n_open"], dtype=torch.complex128, device=dev)
     for _ in range(3):
@@ -515,7 +518,8 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000):
     ms = _timed(lambda: plan.contract(out=amps), stream, flush, reps=3)
     flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
     out["grid30"] = {"job_flops": flops, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-                     "slices_per_s": info["n_slices"] / (ms * 1e-3), "max_log2_elems": info["max_log2_elems"]}
+                     "slices_per_s": info["n_slices"] / (ms * 1e-3), "max_log2_elems": info["max_log2_elems"],
+                     "anneal_iters": iters30, "plan_s": plan_s}
     if gold is not None:
         m = tn.metrics(amps, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
         out["grid30"].update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]})

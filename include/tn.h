@@ -131,7 +131,11 @@ typedef struct {
                                  values of deep intermediates fall into FP16's
                                  subnormal range or flush to zero.  0: scaled
                                  (default).  Not with fp8_min_log2_flops.     */
-    int32_t pad_;
+    int32_t anneal_kappa;     /* path_anneal_iters > 0: the flops one element
+                                 of a step's operands and result counts for in
+                                 the annealer's cost (its HBM traffic against
+                                 tensor work).  0: 1000 (complex-half), 100
+                                 (complex64)                                  */
     int64_t workspace_budget; /* > 0: the library chooses slice_batch_log2 itself
                                  (the given value is ignored): the largest
                                  b <= min(16, summed sliced edges) whose device
@@ -449,16 +453,16 @@ int tn_sample(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,
  * ordering and kernels as tn_sample.
  *   - k > TN_SAMPLE_NOALLOC_MAX_K is rejected with TN_EINVAL (use tn_sample).
  *   - The first call on a device looks up the array's device address
- *     (set-up, once per device, with that device current); make that first
- *     call before any stream capture.  The address is kept for the life of
- *     the process: after cudaDeviceReset on a device, do not call this on
- *     that device again.
+ *     (set-up, once per device, with that device current).  The address is
+ *     kept for the life of the process: after cudaDeviceReset on a device,
+ *     do not call this on that device again.
  *   - All calls on a device share the one array and it keeps the last
  *     call's contents; calls that overlap on the GPU (different streams or
  *     threads without ordering between them) race and may return each
  *     other's results.  Each call writes every entry it reads back, so
  *     nothing has to start at zero.
- * Synchronizes `stream`.
+ * Synchronizes `stream` (the results are copied to the host), so it cannot be
+ * called on a stream that is being captured into a graph.
  */
 #define TN_SAMPLE_NOALLOC_MAX_K 1024
 int tn_sample_noalloc(const double *d_amps, int32_t n_open, int32_t k, int64_t *out_idx,

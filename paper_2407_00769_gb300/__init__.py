@@ -89,7 +89,7 @@ class PlanOpts(ctypes.Structure):
                 ("no_tensor_cores", ctypes.c_int32),
                 ("fp8_min_log2_flops", ctypes.c_int32),
                 ("recompute_log2", ctypes.c_int32),
-                ("no_scaling", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("no_scaling", ctypes.c_int32), ("anneal_kappa", ctypes.c_int32),
                 ("workspace_budget", ctypes.c_int64),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
@@ -316,7 +316,7 @@ class Plan:
                  torch_allocator: bool = True, small_log2: int = 0,
                  no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
                  recompute_log2: int = 0, no_scaling: bool = False, workspace_budget: int = 0,
-                 _samples=None):
+                 anneal_kappa: int = 0, _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         if _samples is None:
@@ -329,6 +329,7 @@ class Plan:
         opts.path_seed = int(seed)
         opts.path_trials = int(trials)
         opts.path_anneal_iters = int(anneal_iters)
+        opts.anneal_kappa = int(anneal_kappa)
         opts.workspace_budget = int(workspace_budget)
         opts.slice_batch_log2 = int(slice_batch_log2)
         opts.tile_policy = int(tile_policy)

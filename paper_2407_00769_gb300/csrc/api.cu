@@ -637,6 +637,7 @@ int check_opts(const tn_plan_opts &o) {
     if (o.path_trials < 1 || o.path_trials > 4096) return fail(TN_EINVAL, "path_trials must be in 1..4096");
     if (o.n_slice_edges < -1 || o.n_slice_edges > 40) return fail(TN_EINVAL, "n_slice_edges must be in -1..40");
     if (o.max_log2_elems > 40) return fail(TN_EINVAL, "max_log2_elems must be <= 40");
+    if (o.anneal_kappa < 0) return fail(TN_EINVAL, "anneal_kappa must be >= 0");
     if (o.slice_batch_log2 < 0 || o.slice_batch_log2 > 16) return fail(TN_EINVAL, "slice_batch_log2 must be in 0..16");
     if (o.tile_policy < 0 || o.tile_policy > 2) return fail(TN_EINVAL, "bad tile_policy");
     if (o.small_log2 < 0) return fail(TN_EINVAL, "small_log2 must be >= 0");
@@ -676,12 +677,41 @@ int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
     const Network &plan_net = o.recompute_log2 > 0 ? split_net : plan_net_in;
     rc = choose_slices(plan_net, o.path_seed, o.path_trials, n_target, cap, P->path, P->sliced, err);
     if (rc != TN_OK) return rc;
-    if (o.path_anneal_iters > 0)
+    if (o.path_anneal_iters > 0) {
         // kappa: flops one element of HBM traffic is worth at the ridge
         // (complex-half 4 B x ~250 flop/B on the tensor cores; complex64
         // 8 B x ~12 flop/B on the CUDA cores)
-        refine_plan(plan_net, n_target, cap, o.path_seed, o.path_anneal_iters,
-                    o.dtype == TN_C64 ? 100.0 : 1000.0, o.path_trials, P->path, P->sliced);
+        const double kappa =
+            o.anneal_kappa > 0 ? (double)o.anneal_kappa : (o.dtype == TN_C64 ? 100.0 : 1000.0);
+        // which edges are sliced is fixed by the greedy start (with a fixed
+        // slice count annealing does not change it) and decides much of what
+        // annealing can reach: anneal from path_trials starts (greedy
+        // slicings under different seeds), two chains each, and keep the
+        // cheapest job
+        const int starts = std::max(1, o.path_trials);
+        // slices per pass: as given, or (a workspace budget picks it later)
+        // assumed all of them.  With recomputation the split output legs,
+        // fixed while the path is planned, loop over every pass too: the
+        // steps they reach are not known here, so no step is weighted
+        const int bl = o.recompute_log2 > 0 ? -1 : o.workspace_budget > 0 ? 64 : std::max(0, o.slice_batch_log2);
+        double best = 0;
+        refine_plan(plan_net, n_target, cap, o.path_seed, o.path_anneal_iters, kappa, bl, 2, P->path, P->sliced,
+                    &best);
+        for (int st = 1; st < starts; ++st) {
+            Path p2;
+            std::vector<int> s2;
+            std::string e2;
+            const uint64_t sd = o.path_seed + 0xD1B54A32D192ED03ull * (uint64_t)st;
+            if (choose_slices(plan_net, sd, o.path_trials, n_target, cap, p2, s2, e2) != TN_OK) continue;
+            double c2 = 0;
+            refine_plan(plan_net, n_target, cap, sd, o.path_anneal_iters, kappa, bl, 2, p2, s2, &c2);
+            if (c2 < best) {
+                best = c2;
+                P->path = std::move(p2);
+                P->sliced = std::move(s2);
+            }
+        }
+    }
     if (cap > 0 && P->path.max_log2 > cap) {
         err = "the slicing does not reach the cap (largest intermediate 2^" + std::to_string(P->path.max_log2) + ")";
         return TN_EINVAL;

@@ -18,15 +18,17 @@ constexpr int kSplitLog2KHost = 15;
 
 // Refine `path` (on the network with `sliced` removed) by simulated
 // annealing over tree rotations; intermediates stay within
-// max(width_cap, current width).  Keeps the input when nothing improves.
+// max(width_cap, current width); a step's cost counts as often as the step
+// runs when all slices are contracted, 2^batch_log2 per pass.  Keeps the
+// input when nothing improves.
 int anneal_path(const Network &net, const std::vector<int> &sliced, int width_cap, uint64_t seed,
-                int iters, double kappa, Path &path);
+                int iters, double kappa, int batch_log2, Path &path);
 // `chains` independent annealing chains (3 rounds each) on the chosen path
-// and slices, the cheapest job kept; with a cap (n_target < 0) a sliced edge
-// is given back whenever the refined path stays within the cap and the
-// job's cost (2^S x per-slice) drops.
+// and slices, the cheapest job kept (*cost_out: its roofline cost); with a
+// cap (n_target < 0) a sliced edge is given back whenever the refined path
+// stays within the cap and the job's cost (2^S x per-slice) drops.
 int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
-                int chains, Path &path, std::vector<int> &sliced);
+                int batch_log2, int chains, Path &path, std::vector<int> &sliced, double *cost_out = nullptr);
 int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, int cap, Path &path,
                   std::vector<int> &sliced, std::string &err);
 // Recomputation (Sec. 3.4.1): append r open output legs to `sliced`, each

@@ -181,15 +181,17 @@ def test_fp8_steps_are_marked_and_quantized():
     assert not any(s["storage"] & 8 for s in c64.steps())
 
 
-@pytest.mark.parametrize("n_slice,cap", [(2, 0), (-1, 7)])
-def test_annealed_path_is_valid_and_cheaper(n_slice, cap):
+@pytest.mark.parametrize("n_slice,cap,batch", [(2, 0, 0), (-1, 7, 0), (3, 0, 3)])
+def test_annealed_path_is_valid_and_cheaper(n_slice, cap, batch):
     # simulated annealing over tree rotations (Sec. 3 path search): the
     # refined path and its slices still give the projector state vector's
     # slices (FP64 network oracle, path as data), within the same width,
-    # for no more flops than the greedy path
+    # for no more flops than the greedy path -- as the plan runs them (with
+    # all slices in one batched pass, a step counts once per slice reaching it)
     from oracle import tn as otn
     c, q = rqcgen.small_grid(3, 4, 8, seed=3, n_open=4)
-    kw = dict(dtype=tn.C64, n_slice_edges=n_slice, max_log2_elems=cap, torch_allocator=False)
+    kw = dict(dtype=tn.C64, n_slice_edges=n_slice, max_log2_elems=cap, torch_allocator=False,
+              slice_batch_log2=batch)
     g = tn.Plan(c, q, **kw)
     a = tn.Plan(c, q, anneal_iters=20000, **kw)
     gi, ai = g.info(), a.info()
