@@ -741,16 +741,20 @@ def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
     t_tune = _t.perf_counter() - t0
     ms_exh = _timed(lambda: pe.contract(0, n_meas, out=amps), stream, flush)
     recs = [r for r in pe.tune_records() if r["kind"] == 0]
-    # per-step regret of the model's own pick among the timed candidates,
-    # weighted by each step's best time
+    # per-step regret of the model's own pick among the timed candidates it
+    # ranks (as the library's learned policy: not the tile-bit 10/11 variants,
+    # which its training set does not hold), weighted by each step's best
+    # time over all candidates
     by = {}
     for r, y in zip(recs, model.predict(tn.cost_features(recs))):
-        by.setdefault(r["step"], []).append((y, r["ms"], r["kernel"] == 3 and r["tile"] == 0))
+        by.setdefault(r["step"], []).append((y, r["ms"], r["kernel"] == 3 and r["tile"] == 0,
+                                             not (r["tile"] & 0xC00)))
     num = den = dfl = 0.0
     for v in by.values():
-        pick = min(v)[1]
-        best = min(m for _, m, _ in v)
-        d = [m for _, m, is_d in v if is_d]
+        ranked = [x for x in v if x[3]] or v
+        pick = min(ranked)[1]
+        best = min(x[1] for x in v)
+        d = [x[1] for x in v if x[2]]
         num += pick
         den += best
         dfl += d[0] if d else pick

@@ -458,7 +458,7 @@ template <typename TA, typename TB, typename TC, int NC, int DT, class Sync>
 __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int lm, int ln, int lk, int64_t sa,
                                           int64_t sb, int64_t sc, const ScaleRef &sr, const int32_t *za,
                                           const int32_t *zb, int64_t bx, int by, int64_t bz, int tid,
-                                          RowsSmem<TA, NC> &sm) {
+                                          RowsSmem<TA, NC> &sm, float &mx_run) {
     constexpr int KC = kKC;
     TA *As = sm.As;
     const int64_t M = (int64_t)1 << lm;
@@ -473,7 +473,11 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
     TC *Cb = C + b * sc;
     const int rows = (int)min((int64_t)kRows, M - m0);
     // FP32 partial sums over at most kFlushK terms, added into FP64: a long
-    // FP32 running sum would lose ~sqrt(K) ulps (2^23-term steps occur)
+    // FP32 running sum would lose ~sqrt(K) ulps (2^23-term steps occur).
+    // With K <= kFlushK the one partial is the sum (the FP64 round trip is
+    // exact), and the FP64 pipe -- a small fraction of the FP32 rate on this
+    // part -- is left out: it bounded steps of 2^22 rows and K = 4
+    const bool longk = K > kFlushK;
     float2 acc[NC];
     double2 tot[NC];
 #pragma unroll
@@ -529,7 +533,7 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
                 }
             }
         }
-        if (((k0 + KC) % kFlushK) == 0 || k0 + KC >= K) {
+        if (longk && (((k0 + KC) % kFlushK) == 0 || k0 + KC >= K)) {
 #pragma unroll
             for (int j = 0; j < NC; ++j) {
                 tot[j].x += acc[j].x;
@@ -538,11 +542,18 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
             }
         }
     }
+    if (longk) {
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = make_float2((float)tot[j].x, (float)tot[j].y);
-    // every thread stays to the end: the maximum is reduced over the warp and
-    // recorded with one atomic per warp (one per thread serialises on a
-    // single address for steps of 2^30 rows)
+        for (int j = 0; j < NC; ++j) acc[j] = make_float2((float)tot[j].x, (float)tot[j].y);
+    } else {
+        // + 0: a -0 partial becomes +0, as 0.0 + (-0.0) does in the FP64 sum
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[j] = make_float2(acc[j].x + 0.0f, acc[j].y + 0.0f);
+    }
+    // the maximum of the stored values goes to mx_run (this thread's running
+    // maximum); rows_flush records it once per warp after all of a CTA's row
+    // blocks (an atomic per thread, or per warp and row block, serialises on
+    // one address for steps of 2^22+ rows)
     const bool active = tid < rows;
     const bool first_block = bx == 0 && by == 0 && bz == 0 && tid == 0;
     const int64_t m = m0 + tid;
@@ -559,8 +570,7 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
             }
         if (sr.tmax) {
             if (sr.texp && first_block) sr.texp[sr.meta_c] = sr.texp[sr.meta_a] + sr.texp[sr.meta_b];
-            mx = warp_max(mx);
-            if (sr.out_max && (tid & 31) == 0) atomic_max_nonneg(sr.out_max, mx);
+            mx_run = fmaxf(mx_run, mx);
         }
     } else {
         // power-of-two scaling (exact): e from the operands' recorded maxima
@@ -579,6 +589,21 @@ __device__ __forceinline__ void rows_body(const TA *A, const TB *B, TC *C, int l
                 const float2 f = LpT<DT>::to_f2(h);
                 mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
             }
+        mx_run = fmaxf(mx_run, mx);
+    }
+}
+
+// Record a rows GEMM thread's running maximum (rows_body's mx_run): reduced
+// over the warp, one atomic per warp (the maximum is exact and order-free);
+// for complex-half results also the FP16 overflow flag.  Every thread of the
+// warp calls it.
+template <typename TC, int DT>
+__device__ __forceinline__ void rows_flush(const ScaleRef &sr, float mx, int tid) {
+    if constexpr (std::is_same<TC, float2>::value) {
+        if (!sr.tmax) return;
+        mx = warp_max(mx);
+        if (sr.out_max && (tid & 31) == 0) atomic_max_nonneg(sr.out_max, mx);
+    } else {
         mx = warp_max(mx);
         if ((tid & 31) == 0) {
             if (sr.out_max) atomic_max_nonneg(sr.out_max, mx);
@@ -741,11 +766,24 @@ __device__ __forceinline__ void splitk_body(const float2 *partial, int split, vo
 // Recomputation: the op's split outputs are absent from F; thread jf covers
 // the amplitude whose split bits are split_val and whose other bits, in
 // order, are jf's bits.
+__device__ __forceinline__ double2 slice_corr(const double2 *stepcorr, int n_steps) {
+    double cr = 1.0, ci = 0.0;
+    for (int k = 0; k < n_steps; ++k) {
+        const double2 f = stepcorr[k];
+        const double nr = cr * f.x - ci * f.y;
+        ci = cr * f.y + ci * f.x;
+        cr = nr;
+    }
+    return make_double2(cr, ci);
+}
+
+// corr: slice_corr(stepcorr, n_steps), the same for every amplitude (one
+// thread of a block computes it: FP64 runs at a small fraction of the FP32
+// rate here)
 template <typename TF, int DT>
 __device__ __forceinline__ void slice_sum_body(const TF *F, const SumOp &op, double2 *amps, int n_open, int t_lo,
-                                               int t_hi, int overwrite, const int32_t *texp,
-                                               const double2 *stepcorr, int n_steps, uint64_t split_mask,
-                                               uint64_t split_val, int64_t jf) {
+                                               int t_hi, int overwrite, const int32_t *texp, double2 corr,
+                                               int n_steps, uint64_t split_mask, uint64_t split_val, int64_t jf) {
     const int64_t n = (int64_t)1 << (n_open - op.n_split);
     if (jf >= n) return;
     int64_t base = 0, j = (int64_t)split_val;
@@ -758,27 +796,40 @@ __device__ __forceinline__ void slice_sum_body(const TF *F, const SumOp &op, dou
         ++u;
     }
     const int E = texp ? texp[op.meta] : 0;
-    double cr = 1.0, ci = 0.0;
-    for (int k = 0; k < n_steps; ++k) {
-        const double2 f = stepcorr[k];
-        const double nr = cr * f.x - ci * f.y;
-        ci = cr * f.y + ci * f.x;
-        cr = nr;
-    }
+    const double cr = corr.x, ci = corr.y;
     double2 a = overwrite ? make_double2(0.0, 0.0) : amps[j];
-    for (int t = t_lo; t < t_hi; ++t) {
-        int64_t idx = base;
-        for (int q = 0; q < op.n_batch; ++q)
-            if ((t >> q) & 1) idx |= (int64_t)1 << op.batch_pos[q];
-        const float2 v = widen<TF, DT>(F[idx]);
-        double re = ldexp((double)v.x, -E), im = ldexp((double)v.y, -E);
-        if (n_steps > 0) {
-            const double nre = cr * re - ci * im;
-            im = cr * im + ci * re;
-            re = nre;
+    // x 2^-E as one multiplication where 2^-E is a normal or subnormal double
+    // (exact, the same value as ldexp); ldexp itself outside that range
+    const bool mul = E >= -1000 && E <= 1000;
+    const double sc = mul ? ldexp(1.0, -E) : 1.0;
+    // the slices in order t_lo, t_lo + 1, ... (a fixed summation order); the
+    // loads of 8 slices are issued before their adds so that their latencies
+    // overlap instead of adding up
+    constexpr int U = 8;
+    for (int t0 = t_lo; t0 < t_hi; t0 += U) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u;
+            if (t >= t_hi) break;
+            int64_t idx = base;
+            for (int q = 0; q < op.n_batch; ++q)
+                if ((t >> q) & 1) idx |= (int64_t)1 << op.batch_pos[q];
+            v[u] = widen<TF, DT>(F[idx]);
         }
-        a.x += re;
-        a.y += im;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (t0 + u >= t_hi) break;
+            double re = mul ? (double)v[u].x * sc : ldexp((double)v[u].x, -E);
+            double im = mul ? (double)v[u].y * sc : ldexp((double)v[u].y, -E);
+            if (n_steps > 0) {
+                const double nre = cr * re - ci * im;
+                im = cr * im + ci * re;
+                re = nre;
+            }
+            a.x += re;
+            a.y += im;
+        }
     }
     amps[j] = a;
 }

@@ -239,15 +239,19 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 }
 
 // ----------------------------------------------------------- rows GEMMs --
-// One block of kRows threads per (row block, column chunk, batch entry):
-// rows_body.
+// Blocks of kRows threads over (row block, column chunk, batch entry):
+// rows_body for row blocks blockIdx.x, + gridDim.x, ... < gx (the grid is
+// capped at a few waves; each thread's maximum is recorded once at the end).
 template <typename TA, typename TB, typename TC, int NC, int DT>
 __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const TA *__restrict__ A, const TB *__restrict__ B, TC *__restrict__ C, int lm, int ln, int lk,
-    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb) {
+    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb, int64_t gx) {
     __shared__ RowsSmem<TA, NC> sm;
-    rows_body<TA, TB, TC, NC, DT, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, sr, za, zb, blockIdx.x, blockIdx.y,
-                                             blockIdx.z, threadIdx.x, sm);
+    float mx = 0.f;
+    for (int64_t bx = blockIdx.x; bx < gx; bx += gridDim.x)
+        rows_body<TA, TB, TC, NC, DT, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, sr, za, zb, bx, blockIdx.y,
+                                                 blockIdx.z, threadIdx.x, sm, mx);
+    rows_flush<TC, DT>(sr, mx, threadIdx.x);
 }
 
 template <typename TA, typename TB, typename TC, int DT>
@@ -259,14 +263,24 @@ static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, 
     const int N = 1 << ln;
     const int64_t gx = (M + kRows - 1) / kRows;
     if (gx > 0x7fffffffLL || batch > 65535) return cudaErrorInvalidValue;
+    // columns per thread: fewer when that is what fills the GPU (a step of
+    // few row blocks, e.g. M = 128, N = 128, K = 512, else runs on a handful
+    // of SMs); every output's sum is the same whichever thread computes it
+    const int64_t fill = 2 * (int64_t)tc_num_sms();
+    int ncv = N >= 16 ? 16 : N;
+    while (ncv > 1 && gx * ((N + ncv - 1) / ncv) * batch < fill) ncv >>= 1;
+    // row blocks per column chunk and batch entry: at most enough for about
+    // 8 resident blocks per SM (the rest are looped over)
+    const int64_t per = std::max<int64_t>(1, (int64_t)tc_num_sms() * 8 / ((N + ncv - 1) / ncv * batch));
+    const int64_t gxl = std::min(gx, per);
 #define TN_ROWS_CASE(NCV)                                                                        \
     {                                                                                             \
-        dim3 g((unsigned)gx, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);                   \
+        dim3 g((unsigned)gxl, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);                  \
         gemm_rows_kernel<TA, TB, TC, NCV, DT><<<g, kRows, 0, s>>>(                                \
-            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr, za, zb);           \
+            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr, za, zb, gx);       \
         break;                                                                                    \
     }
-    switch (N >= 16 ? 16 : N) {
+    switch (ncv) {
         case 1: TN_ROWS_CASE(1)
         case 2: TN_ROWS_CASE(2)
         case 4: TN_ROWS_CASE(4)
@@ -500,7 +514,10 @@ __global__ void slice_sum_kernel(const TF *__restrict__ F, const SumOp op, doubl
                                  int n_open, int t_lo, int t_hi, int overwrite,
                                  const int32_t *texp, const double2 *__restrict__ stepcorr,
                                  int n_steps, uint64_t split_mask, uint64_t split_val) {
-    slice_sum_body<TF, DT>(F, op, amps, n_open, t_lo, t_hi, overwrite, texp, stepcorr, n_steps, split_mask,
+    __shared__ double2 corr;
+    if (threadIdx.x == 0) corr = slice_corr(stepcorr, n_steps);
+    __syncthreads();
+    slice_sum_body<TF, DT>(F, op, amps, n_open, t_lo, t_hi, overwrite, texp, corr, n_steps, split_mask,
                            split_val, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -512,7 +529,10 @@ cudaError_t launch_slice_sum(const void *F, int dtype, const SumOp &op, double2 
     for (int i = 0; i < op.n_split; ++i) split_mask |= 1ull << op.split_t[i];
     if ((split_val & ~split_mask) != 0) return cudaErrorInvalidValue;
     const int64_t n = (int64_t)1 << (n_open - op.n_split);
-    const int threads = 256;
+    // one thread per amplitude, each summing every slice in FP64: blocks of
+    // as few as 32 threads so that the FP64 work spreads over the SMs
+    int threads = 32;
+    while (threads < 256 && n / (2 * threads) >= tc_num_sms()) threads *= 2;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     if (dtype == TN_C64)
         slice_sum_kernel<float2, TN_C64><<<blocks, threads, 0, s>>>(

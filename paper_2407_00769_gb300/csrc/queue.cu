@@ -230,12 +230,14 @@ __device__ __noinline__ void q_rows(const QRows &r, int64_t tile, int tid, uint8
     const TA *A = reinterpret_cast<const TA *>(r.A);
     const TB *B = reinterpret_cast<const TB *>(r.B);
     TC *C = reinterpret_cast<TC *>(r.C);
+    float mx = 0.f;
     if (g == 0)
         rows_body<TA, TB, TC, NC, DT, SyncNamed<2, 128>>(A, B, C, r.lm, r.ln, r.lk, r.sa, r.sb, r.sc, r.sr, r.za, r.zb,
-                                                         bx, by, bz, tid & 127, *sm);
+                                                         bx, by, bz, tid & 127, *sm, mx);
     else
         rows_body<TA, TB, TC, NC, DT, SyncNamed<3, 128>>(A, B, C, r.lm, r.ln, r.lk, r.sa, r.sb, r.sc, r.sr, r.za, r.zb,
-                                                         bx, by, bz, tid & 127, *sm);
+                                                         bx, by, bz, tid & 127, *sm, mx);
+    rows_flush<TC, DT>(r.sr, mx, tid);
 }
 
 template <typename TA, typename TB, typename TC, int DT>
@@ -288,9 +290,12 @@ __device__ __noinline__ void q_splitk(const QSplitK &r, int64_t tile, int tid) {
 }
 
 template <typename TF, int DT>
-__device__ __noinline__ void q_sum(const QSum &r, int64_t tile, int tid) {
+__device__ __noinline__ void q_sum(const QSum &r, int64_t tile, int tid, uint8_t *scratch) {
+    double2 *corr = reinterpret_cast<double2 *>(scratch);
+    if (tid == 0) *corr = slice_corr(r.stepcorr, r.n_steps);
+    SyncNamed<1, kQSimt>::sync();
     slice_sum_body<TF, DT>(reinterpret_cast<const TF *>(r.F), r.op, r.amps, r.n_open, r.t_lo, r.t_hi, r.overwrite,
-                           r.texp, r.stepcorr, r.n_steps, r.split_mask, r.split_val, tile * kQSimt + tid);
+                           r.texp, *corr, r.n_steps, r.split_mask, r.split_val, tile * kQSimt + tid);
 }
 
 __device__ __noinline__ void q_simt(const QOp &op, const uint8_t *blob, int64_t tile, int tid, uint8_t *scratch) {
@@ -349,11 +354,11 @@ __device__ __noinline__ void q_simt(const QOp &op, const uint8_t *blob, int64_t 
         case Q_SUM: {
             const QSum &r = *reinterpret_cast<const QSum *>(rec);
             const int dt = op.sub & 15, tf = op.sub >> 4;
-            if (dt == TN_C64) q_sum<float2, TN_C64>(r, tile, tid);
-            else if (tf == 0 && dt == TN_F16) q_sum<float2, TN_F16>(r, tile, tid);
-            else if (tf == 0) q_sum<float2, TN_BF16>(r, tile, tid);
-            else if (dt == TN_F16) q_sum<__half2, TN_F16>(r, tile, tid);
-            else q_sum<__nv_bfloat162, TN_BF16>(r, tile, tid);
+            if (dt == TN_C64) q_sum<float2, TN_C64>(r, tile, tid, scratch);
+            else if (tf == 0 && dt == TN_F16) q_sum<float2, TN_F16>(r, tile, tid, scratch);
+            else if (tf == 0) q_sum<float2, TN_BF16>(r, tile, tid, scratch);
+            else if (dt == TN_F16) q_sum<__half2, TN_F16>(r, tile, tid, scratch);
+            else q_sum<__nv_bfloat162, TN_BF16>(r, tile, tid, scratch);
             break;
         }
         default: break;
