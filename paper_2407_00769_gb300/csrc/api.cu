@@ -70,8 +70,9 @@ int ensure_device(tn_plan_s *P) {
                                                                (int64_t)1 << op.gemm.lb));
     P->d_splitk = (float *)plan_dev_alloc(P, split_bytes);
     P->d_gidx = (int32_t *)plan_dev_alloc(P, std::max<size_t>(64, S.gidx.size() * 4));
+    P->d_bpart = plan_dev_alloc(P, bprep_c64_scratch_bytes());
     if (!P->d_ws || !P->d_store || !P->d_jobs || !P->d_tmax || !P->d_texp || !P->d_err || !P->d_stepcorr ||
-        !P->d_splitk || !P->d_gidx) {
+        !P->d_splitk || !P->d_gidx || !P->d_bpart) {
         plan_dev_free_all(P);
         return fail(TN_ENOMEM, "device allocation of the plan workspace (" +
                                    std::to_string(S.ws_bytes) + " bytes) failed");
@@ -192,7 +193,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
             e = launch_bprep_perm(ws + op.bprep.src, ws + op.bprep.dst, op.bprep.rank, op.bprep.perm,
                                   op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, op.bprep.tb, dtype,
                                   P->d_stepcorr + op.bprep.step, P->d_tmax, P->d_texp, op.bprep.meta_src,
-                                  op.bprep.meta_dst, s, P->opts.no_scaling ? 1 : 0);
+                                  op.bprep.meta_dst, s, P->opts.no_scaling ? 1 : 0, P->d_bpart);
             ++launches;
             break;
         case OP_GEMM: {

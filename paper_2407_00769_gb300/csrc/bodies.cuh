@@ -350,63 +350,63 @@ struct BprepC64Smem {
     float smax[VT];
 };
 
-template <int DT, int NT, int VT, class Sync>
-__device__ __forceinline__ void bprep_c64_body(const float2 *B, uint32_t *Bp, int lk, int ln, int lb, int np,
-                                               const PermParams &p, int rank, double2 *corr, float *tmax,
-                                               int32_t *texp, int meta_src, int meta_dst, int scale_off, int tid,
-                                               BprepC64Smem<VT> &sm) {
-    static_assert(VT % NT == 0, "virtual threads must be a multiple of the block");
+// Exact power-of-two scale 2^bshift bringing max |B| = mb to [2^11, 2^12].
+__device__ __forceinline__ int bprep_c64_shift(float mb, int scale_off) {
+    int bshift = 0;
+    if (!scale_off && mb > 0.0f && isfinite(mb)) {
+        int x;
+        const float f = frexpf(mb, &x);
+        bshift = 12 - ((f == 0.5f) ? x - 1 : x);
+        bshift = max(-120, min(120, bshift));
+    }
+    return bshift;
+}
+
+// Virtual thread v of VT: the elements v, v + VT, ... of B' (written), with
+// their FP64 sums (fixed order) and the maximum of the rounded values.
+template <int DT, int VT>
+__device__ __forceinline__ void bprep_c64_vthread(const float2 *B, uint32_t *Bp, int lk, int ln, int np, int64_t total,
+                                                  const PermParams &p, int rank, float scale, int v, double &nr,
+                                                  double &ni, double &den, float &bmax) {
     using L = LpT<DT>;
     const int K = 1 << lk, N = 1 << ln;
-    const int64_t total = ((int64_t)np * K) << lb;
-    // exact power-of-two scale bringing max |B| to [2^11, 2^12]
-    int bshift = 0;
-    {
-        const float mb = tmax[meta_src];
-        if (!scale_off && mb > 0.0f && isfinite(mb)) {
-            int x;
-            const float f = frexpf(mb, &x);
-            bshift = 12 - ((f == 0.5f) ? x - 1 : x);
-            bshift = max(-120, min(120, bshift));
-        }
-    }
-    const float scale = __int_as_float((127 + bshift) << 23);
-    for (int v = tid; v < VT; v += NT) {
-        float bmax = 0.0f;
-        double nr = 0.0, ni = 0.0, den = 0.0;
-        for (int64_t i = v; i < total; i += VT) {
-            const int k = (int)(i % K);
-            const int64_t row = i / K;
-            const int rr = (int)(row % np);
-            const int64_t b = row / np;
-            const int n = rr >> 1, co = rr & 1;
-            uint32_t val = 0;
-            if (n < N) {
-                const int64_t tidx = ((b * N + n) << lk) | k;
-                int64_t src = 0;
-                for (int t = 0; t < rank; ++t)
-                    if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
-                const float2 x0 = B[src];
-                const float2 x = make_float2(x0.x * scale, x0.y * scale);
-                const typename L::T2 h = L::from_f2(x);
-                const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
-                val = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
-                if (co == 0) {
-                    const float2 r = L::to_f2(h);
-                    bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
-                    const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
-                    nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
-                    ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
-                    den += (double)x.x * x.x + (double)x.y * x.y;
-                }
+    bmax = 0.0f;
+    nr = 0.0, ni = 0.0, den = 0.0;
+    for (int64_t i = v; i < total; i += VT) {
+        const int k = (int)(i % K);
+        const int64_t row = i / K;
+        const int rr = (int)(row % np);
+        const int64_t b = row / np;
+        const int n = rr >> 1, co = rr & 1;
+        uint32_t val = 0;
+        if (n < N) {
+            const int64_t tidx = ((b * N + n) << lk) | k;
+            int64_t src = 0;
+            for (int t = 0; t < rank; ++t)
+                if ((tidx >> t) & 1) src |= (int64_t)1 << p.outer_in[t];
+            const float2 x0 = B[src];
+            const float2 x = make_float2(x0.x * scale, x0.y * scale);
+            const typename L::T2 h = L::from_f2(x);
+            const uint32_t u = *reinterpret_cast<const uint32_t *>(&h);
+            val = co == 0 ? (u ^ 0x80000000u) : __byte_perm(u, 0, 0x1032);
+            if (co == 0) {
+                const float2 r = L::to_f2(h);
+                bmax = fmaxf(bmax, fmaxf(fabsf(r.x), fabsf(r.y)));
+                const double dr = (double)r.x - x.x, di = (double)r.y - x.y;
+                nr += (double)x.x * dr + (double)x.y * di;     // Re conj(x) d
+                ni += (double)x.x * di - (double)x.y * dr;     // Im conj(x) d
+                den += (double)x.x * x.x + (double)x.y * x.y;
             }
-            Bp[i] = val;
         }
-        sm.sh[0][v] = nr;
-        sm.sh[1][v] = ni;
-        sm.sh[2][v] = den;
-        sm.smax[v] = bmax;
+        Bp[i] = val;
     }
+}
+
+// The tree over the VT partials in sm (pairs x, x + w for w = VT/2 .. 1) and
+// the results: tmax / texp of B', and corr = 1 / (1 + alpha).
+template <int NT, int VT, class Sync>
+__device__ __forceinline__ void bprep_c64_finish(double2 *corr, float *tmax, int32_t *texp, int meta_src,
+                                                 int meta_dst, int bshift, int tid, BprepC64Smem<VT> &sm) {
     Sync::sync();
     for (int w = VT / 2; w > 0; w >>= 1) {
         for (int x = tid; x < w; x += NT) {
@@ -430,6 +430,27 @@ __device__ __forceinline__ void bprep_c64_body(const float2 *B, uint32_t *Bp, in
         }
         *corr = make_double2(fr, fi);
     }
+}
+
+template <int DT, int NT, int VT, class Sync>
+__device__ __forceinline__ void bprep_c64_body(const float2 *B, uint32_t *Bp, int lk, int ln, int lb, int np,
+                                               const PermParams &p, int rank, double2 *corr, float *tmax,
+                                               int32_t *texp, int meta_src, int meta_dst, int scale_off, int tid,
+                                               BprepC64Smem<VT> &sm) {
+    static_assert(VT % NT == 0, "virtual threads must be a multiple of the block");
+    const int64_t total = ((int64_t)np << lk) << lb;
+    const int bshift = bprep_c64_shift(tmax[meta_src], scale_off);
+    const float scale = __int_as_float((127 + bshift) << 23);
+    for (int v = tid; v < VT; v += NT) {
+        double nr, ni, den;
+        float bmax;
+        bprep_c64_vthread<DT, VT>(B, Bp, lk, ln, np, total, p, rank, scale, v, nr, ni, den, bmax);
+        sm.sh[0][v] = nr;
+        sm.sh[1][v] = ni;
+        sm.sh[2][v] = den;
+        sm.smax[v] = bmax;
+    }
+    bprep_c64_finish<NT, VT, Sync>(corr, tmax, texp, meta_src, meta_dst, bshift, tid, sm);
 }
 
 // ----------------------------------------------------------- rows GEMMs --

@@ -191,15 +191,61 @@ __global__ void __launch_bounds__(1024) bprep_c64_kernel(const float2 *__restric
                                               scale_off, threadIdx.x, sm);
 }
 
+// The same build over 16 blocks of 64 threads (virtual thread v = one
+// thread: the FP64 sums of B's rounding spread over 16 SMs instead of one),
+// each virtual thread's sums to part; then one block runs the same tree
+// over them (bit-identical to bprep_c64_kernel).
+template <int DT>
+__global__ void __launch_bounds__(64) bprep_c64_part_kernel(const float2 *__restrict__ B, uint32_t *__restrict__ Bp,
+                                                            int lk, int ln, int lb, int np,
+                                                            const __grid_constant__ PermParams p, int rank,
+                                                            const float *tmax, int meta_src, int scale_off,
+                                                            BprepC64Smem<1024> *part) {
+    const int v = blockIdx.x * 64 + threadIdx.x;
+    const int64_t total = ((int64_t)np << lk) << lb;
+    const float scale = __int_as_float((127 + bprep_c64_shift(tmax[meta_src], scale_off)) << 23);
+    double nr, ni, den;
+    float bmax;
+    bprep_c64_vthread<DT, 1024>(B, Bp, lk, ln, np, total, p, rank, scale, v, nr, ni, den, bmax);
+    part->sh[0][v] = nr;
+    part->sh[1][v] = ni;
+    part->sh[2][v] = den;
+    part->smax[v] = bmax;
+}
+
+__global__ void __launch_bounds__(1024) bprep_c64_reduce_kernel(const BprepC64Smem<1024> *part, double2 *corr,
+                                                                float *tmax, int32_t *texp, int meta_src,
+                                                                int meta_dst, int scale_off) {
+    __shared__ BprepC64Smem<1024> sm;
+    const int t = threadIdx.x;
+    for (int q = 0; q < 3; ++q) sm.sh[q][t] = part->sh[q][t];
+    sm.smax[t] = part->smax[t];
+    const int bshift = bprep_c64_shift(tmax[meta_src], scale_off);
+    bprep_c64_finish<1024, 1024, SyncBlock>(corr, tmax, texp, meta_src, meta_dst, bshift, t, sm);
+}
+
+size_t bprep_c64_scratch_bytes() { return sizeof(BprepC64Smem<1024>); }
+
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
                               int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
                               int32_t *texp, int meta_src, int meta_dst, cudaStream_t s,
-                              int scale_off) {
+                              int scale_off, void *scratch) {
     const ExpandArgs ex{lk, ln, np};
     // direct-gather table: outer_in[t] = input bit position of target bit t
     PermParams g;
     std::memset(&g, 0, sizeof(g));
     for (int i = 0; i < rank; ++i) g.outer_in[rank - 1 - i] = (int8_t)(rank - 1 - perm[i]);
+    if (tb == 0 && scratch) {
+        auto *part = (BprepC64Smem<1024> *)scratch;
+        if (dtype == TN_F16)
+            bprep_c64_part_kernel<TN_F16><<<16, 64, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb, np, g,
+                                                            rank, tmax, meta_src, scale_off, part);
+        else
+            bprep_c64_part_kernel<TN_BF16><<<16, 64, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb, np, g,
+                                                             rank, tmax, meta_src, scale_off, part);
+        bprep_c64_reduce_kernel<<<1, 1024, 0, s>>>(part, corr, tmax, texp, meta_src, meta_dst, scale_off);
+        return cudaGetLastError();
+    }
     if (tb == 0) {
         if (dtype == TN_F16)
             bprep_c64_kernel<TN_F16><<<1, 1024, 0, s>>>((const float2 *)B, (uint32_t *)Bp, lk, ln, lb,

@@ -66,10 +66,13 @@ cudaError_t launch_bprep(int dtype, const void *B, void *Bp, int lk, int ln, int
 // (tmax[meta_src]) near 2^12; B' gets tmax[meta_dst] and texp[meta_dst] =
 // texp[meta_src] + s.
 // scale_off = 1: no 2^s (s = 0; tn_plan_opts.no_scaling).
+// scratch (tb = 0, nullable): bprep_c64_scratch_bytes() of device memory for
+// the multi-block build; NULL: one block.
 cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *perm, int lk, int ln,
                               int lb, int np, int tb, int dtype, double2 *corr, float *tmax,
                               int32_t *texp, int meta_src, int meta_dst, cudaStream_t s,
-                              int scale_off = 0);
+                              int scale_off = 0, void *scratch = nullptr);
+size_t bprep_c64_scratch_bytes();
 cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
                                    void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
                                    int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,
