@@ -526,8 +526,15 @@ def leg_anneal(tn, torch, dev, flush, stream, gold, iters=200000, iters30=100000
         gs.synchronize()
         ms = _timed(lambda: plan.contract(out=amps, stream=gs), gs, flush, reps=3)
     plan.set_graph(False)
+    # one more call with every kernel class timed (events around each launch)
+    plan.profile(tn.KC_NAMES)
+    plan.contract(out=amps)
+    torch.cuda.synchronize()
+    per_class = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)}
+                 for k, v in plan.profile_read().items() if v["launches"]}
+    plan.profile(None)
     flops = info["flops_per_slice"] * info["n_slices"] + info["flops_invariant"]
-    out["grid30"] = {"job_flops": flops, "ms": ms, "ms_direct_launches": ms_direct,
+    out["grid30"] = {"job_flops": flops, "ms": ms, "ms_direct_launches": ms_direct, "per_class": per_class,
                      "tflops": flops / (ms * 1e-3) / 1e12,
                      "slices_per_s": info["n_slices"] / (ms * 1e-3), "max_log2_elems": info["max_log2_elems"],
                      "anneal_iters": iters30, "plan_s": plan_s, "graph": True}
