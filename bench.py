@@ -760,13 +760,13 @@ def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
     ms_exh = _timed(lambda: pe.contract(0, n_meas, out=amps), stream, flush)
     recs = [r for r in pe.tune_records() if r["kind"] == 0]
     # per-step regret of the model's own pick among the timed candidates it
-    # ranks (as the library's learned policy: not the tile-bit 10/11 variants,
+    # ranks (as the library's learned policy: not the tile-bit 10-12 variants,
     # which its training set does not hold), weighted by each step's best
     # time over all candidates
     by = {}
     for r, y in zip(recs, model.predict(tn.cost_features(recs))):
         by.setdefault(r["step"], []).append((y, r["ms"], r["kernel"] == 3 and r["tile"] == 0,
-                                             not (r["tile"] & 0xC00)))
+                                             not (r["tile"] & 0x1C00)))
     num = den = dfl = 0.0
     for v in by.values():
         ranked = [x for x in v if x[3]] or v

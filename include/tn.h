@@ -505,7 +505,12 @@ typedef struct {
     int32_t dtype;
     int32_t kernel;        /* GEMM kernel variant (perm: -1)                   */
     int32_t tile;          /* tile configuration (perm: stride class 0..5 =
-                              low output bits that stay low input bits)       */
+                              low output bits that stay low input bits).
+                              Tensor-core steps: bits 0-3 N-tile code, 4-7
+                              raster-group code, 8 CTA pairs, 9 64-byte K
+                              chunks, 10 B' resident in shared memory, 11
+                              (with 10) TMA-store epilogue, 12 staged
+                              whole-sector stores                             */
     int32_t step;          /* plan step of a GEMM record (perm: -1)            */
     int32_t pad_;
     double ms;             /* CUDA-event time of one launch                    */
@@ -621,7 +626,9 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  *   6 complex-half tensor cores with each CTA's B' slice resident in shared
  *   memory across its tiles (short K: the whole K of a B' tile within
  *   64 KiB, one K part; else as 3), 7 as 6 with the C tiles staged in
- *   shared memory and written by TMA stores (N >= 32; else as 6).
+ *   shared memory and written by TMA stores (N >= 32; else as 6), 8 as 3
+ *   with each warp's results staged in shared memory and stored in whole
+ *   32-byte sectors (N >= 8; else as 3).
  * out_max: optional device float, receives max |component| of the stored C.
  */
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,

@@ -250,6 +250,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.half_k = (g.tile & kTcHalfKTile) ? 1 : 0;
                     d.bres = (g.tile & kTcBresTile) ? 1 : 0;
                     d.tma_store = (g.tile & kTcStoreTile) ? 1 : 0;
+                    d.staged = (g.tile & kTcStagedTile) ? 1 : 0;
                     d.out_c64 = g.tc == 0;
                     d.partial = P->d_splitk;
                     d.fp8 = g.fp8;
@@ -332,8 +333,13 @@ std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
             const int bn = tc_tile_bn(tc_effective_tile(code, g.ln));
             return !g.fp8 && tc_bres_eligible(g.lm, g.ln, g.lk, (int64_t)1 << g.lb, bn, 0, gathered ? 1 : 0);
         };
+        // the staged-store epilogue where the C write matters: short K, a
+        // complex-half result, no split, no 2-D gather
+        const bool staged_ok = g.lk <= 9 && g.tc == 1 && !gathered && g.ln >= 3 &&
+                               tc_split(g.lm, g.ln, g.lk, (int64_t)1 << g.lb) == 1;
         for (int code : codes) {
             c.push_back({GK_LP_TC, code});
+            if (staged_ok) c.push_back({GK_LP_TC, code | kTcStagedTile});
             if (pair_ok(code)) c.push_back({GK_LP_TC, code | kTcPairTile});
             if (bres_ok(code)) {
                 c.push_back({GK_LP_TC, code | kTcBresTile});
@@ -537,10 +543,11 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         if (op.kind != OP_GEMM) continue;
         const GemmOp &g = op.gemm;
         for (const auto &cand : gemm_candidates(g)) {
-            // the kernel variants of tile bits 10 and 11 (B'-resident, TMA
-            // stores) are left to exhaustive tuning: the bundled training
-            // timings hold none of them, so the model would extrapolate
-            if (cand.second & (kTcBresTile | kTcStoreTile)) continue;
+            // the kernel variants of tile bits 10-12 (B'-resident, TMA
+            // stores, staged stores) are left to exhaustive tuning: the
+            // bundled training timings hold none of them, so the model would
+            // extrapolate
+            if (cand.second & (kTcBresTile | kTcStoreTile | kTcStagedTile)) continue;
             recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second,
                                           g.step, 0, 0});
             who.push_back({i, cand});

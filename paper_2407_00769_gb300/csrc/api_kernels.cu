@@ -112,7 +112,8 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
         const bool half_k = kk == 5;          // tensor cores, 64-byte K chunks
         const bool bres = kk == 6 || kk == 7; // tensor cores, B' slice resident in shared memory
         const bool tma_store = kk == 7;       // ... and C tiles written by TMA stores
-        if (pair || half_k || bres) kk = GK_LP_TC;
+        const bool staged = kk == 8;          // tensor cores, C through per-warp staging
+        if (pair || half_k || bres || staged) kk = GK_LP_TC;
         if (kk < 0) kk = tc_gemm_supported(lk, ln) ? GK_LP_TC : GK_LP_ROWS;
         if (kk == GK_LP_ROWS) {
             e = launch_gemm_rows_lp(dtype, A, B, C, lm, ln, lk, batch, sa, sb, sc, sr, s);
@@ -136,6 +137,7 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
                 d.half_k = half_k ? 1 : 0;
                 d.bres = bres ? 1 : 0;
                 d.tma_store = tma_store ? 1 : 0;
+                d.staged = staged ? 1 : 0;
                 const size_t pb = tc_split_bytes(lm, ln, lk, batch);
                 if (pb) e = cudaMallocAsync((void **)&d.partial, pb, s);
                 if (e == cudaSuccess) e = launch_gemm_tc(d, sr, nullptr, s);

@@ -83,6 +83,7 @@ constexpr int kTcPairTile = 0x100;
 constexpr int kTcHalfKTile = 0x200;
 constexpr int kTcBresTile = 0x400;   // bit 10: B' slice resident in shared memory (short K)
 constexpr int kTcStoreTile = 0x800;  // bit 11 (with bit 10): C tiles written by TMA stores
+constexpr int kTcStagedTile = 0x1000; // bit 12: complex-half C through per-warp staging, whole-sector stores
 // whether a step of this shape runs on CTA pairs when asked (bn: the N tile
 // in real columns the launch uses)
 bool tc_pair_eligible(int want, int fp8, int lm, int ln, int lk, int bn);

@@ -131,6 +131,10 @@ struct TcGemmDesc {
     int pair = 0;
     // 1: 64-byte K chunks (FP16/BF16, 1-CTA tiles): a deeper ring
     int half_k = 0;
+    // 1: complex-half results through a per-warp staging area in shared
+    // memory, every store instruction writing whole 32-byte sectors
+    // (tc_store_block; 1-CTA and pair kernels)
+    int staged = 0;
     // 1: keep each walker's B' slice resident in shared memory (short-K
     // steps, gemm_tc_bres_kernel) where the step allows it
     int bres = 0;

@@ -267,6 +267,7 @@ struct TcArgs {
     int out_rank;
     int8_t out_dpos[40];
     int ln;                // log2 N (bit position of the row part of an element index)
+    int staged;            // 1: complex-half results by tc_store_block (where tc_staged_ok)
     ScaleRef sr;
     int32_t *err;
 };
@@ -313,7 +314,12 @@ struct TcSmem {
     static constexpr int stage_bytes = (a_bytes + b_bytes + 1023) / 1024 * 1024;
     static constexpr int ring = STAGES * stage_bytes;
     static constexpr int bars = (2 * STAGES + 5) * 8;
-    static constexpr int total = 1024 + ring + bars + 16;   // + alignment slack
+    // epilogue staging (tc_store_block): 8 warps x 32 rows x 128 bytes, after
+    // the barriers
+    static constexpr int stg = ring + 1024;
+    static constexpr int total = 1024 + stg + 8 * 4096;   // + alignment slack
+    static_assert(bars + 16 <= 1024, "barriers overflow their kilobyte");
+    static_assert(total <= 232448, "over the 227 KiB of shared memory a CTA may have");
 };
 
 // One tcgen05.ld of the epilogue: 16 accumulator columns of this thread's
@@ -409,6 +415,73 @@ __device__ __forceinline__ void tc_store16(const TcArgs &args, const uint32_t (&
             dst[0] = packed[0];
         }
     }
+}
+
+// Staged stores of complex-half results (no complex64 result, no split-K
+// partial, no 2-D gather index, a fused permutation that keeps the low 3
+// bits).  tc_store16 has each thread store its own row, so a warp's 16-byte
+// stores land in 32 different rows: every store instruction becomes 32
+// partial-sector requests to L2.  Here a warp rounds the w real columns (16,
+// 32 or 64) of block c of its 32 rows into a 32 x 128-byte staging area of
+// its own (16-byte unit u of row r at unit u ^ (r & 7): conflict-free both
+// ways), then writes them row segment by row segment: one instruction covers
+// 32 / (w / 8) rows x 2w bytes, whole 32-byte sectors.  Values, rounding and
+// the running max are tc_store16's.  taddr: the warp's TMEM lane quadrant and
+// accumulator; m: this lane's row; prow: its row part of the fused
+// permutation; cb: output chunk (>= 0).  Which of the two store paths wins
+// depends on the step: the autotuner times both (tile bit 12).
+__device__ __forceinline__ bool tc_staged_ok(const TcArgs &a, bool low_kept) {
+    return !a.out_c64 && !a.partial && !a.gather_r && a.ln >= 3 && (a.out_rank == 0 || low_kept);
+}
+
+__device__ __forceinline__ void tc_store_block(const TcArgs &args, uint32_t taddr, int c, int w, int64_t m,
+                                               int lane, int col0, int64_t cb, int64_t prow, float sc, float &mx,
+                                               uint8_t *stg) {
+    uint8_t *line = stg + lane * 128;
+    for (int cc = 0; cc < w; cc += 16) {
+        uint32_t r[16];
+        tmem_ld16<16>(taddr + (uint32_t)(c + cc), r);
+        tmem_wait_ld();
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float re = __uint_as_float(r[2 * j]) * sc;
+            const float im = __uint_as_float(r[2 * j + 1]) * sc;
+            float2 back;
+            if (args.dtype == TN_BF16) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+                packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                back = __bfloat1622float2(h);
+            } else {
+                __half2 h = __floats2half2_rn(re, im);
+                packed[j] = *reinterpret_cast<uint32_t *>(&h);
+                back = __half22float2(h);
+            }
+            if (m < args.M) mx = fmaxf(mx, fmaxf(fabsf(back.x), fabsf(back.y)));
+        }
+        const int u = cc >> 3;
+        *reinterpret_cast<uint4 *>(line + ((u ^ (lane & 7)) << 4)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        *reinterpret_cast<uint4 *>(line + (((u + 1) ^ (lane & 7)) << 4)) =
+            make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    }
+    __syncwarp();
+    const int lu = w == 64 ? 3 : (w == 32 ? 2 : 1);     // log2 of 16-byte units per row
+    const int u = lane & ((1 << lu) - 1);
+    const int64_t m0 = m - lane;
+    const int64_t jc = (int64_t)((col0 + c) >> 1) + 4 * u;   // first complex column of this unit
+    const int64_t colpart = args.out_rank ? (permute_bits(args, jc, 3, args.ln) | (jc & 7)) : 0;
+    uint32_t *C = reinterpret_cast<uint32_t *>(args.C);
+    for (int i = 0; i < 32; i += 32 >> lu) {
+        const int rr = i + (lane >> lu);
+        const uint4 v = *reinterpret_cast<const uint4 *>(stg + rr * 128 + ((u ^ (rr & 7)) << 4));
+        const int64_t pr = __shfl_sync(0xffffffffu, prow, rr);
+        const int64_t mr = m0 + rr;
+        if (mr < args.M) {
+            const int64_t ei = args.out_rank ? (pr | colpart) : (cb * args.M + mr) * (int64_t)args.N + jc;
+            *reinterpret_cast<uint4 *>(C + ei) = v;
+        }
+    }
+    __syncwarp();
 }
 
 }  // namespace tn

@@ -250,6 +250,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             lowtab[j] = args.out_rank ? permute_bits(args, j, 0, 3) : j;
             low_kept = low_kept && lowtab[j] == j;
         }
+        const bool staged = args.staged && tc_staged_ok(args, low_kept);
+        uint8_t *stg = smem + S::stg + (warp - 2) * 4096;
+        // staged stores: blocks of WB real columns, alternating between the
+        // quadrant's two warps
+        constexpr int WB = BN >= 128 ? 64 : (BN >= 32 ? BN / 2 : 16);
         float mx = 0.f;
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -269,11 +274,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const __grid_con
             // gather_r: the tile's columns are gather_r chunks of np_chunk real
             // columns, chunk r of row b going to output chunk zc[b m_r + r]
             const int col_end = args.gather_r ? BN : min(BN, 2 * args.N - col0);   // warp-uniform
-            for (int c = 16 * half; c < col_end; c += 32) {
-                uint32_t r[16];
-                tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
-                tmem_wait_ld();
-                tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, sc, mx);
+            if (staged) {
+                if (cb >= 0)
+                    for (int c = WB * half; c < col_end; c += 2 * WB)
+                        tc_store_block(args, tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN), c,
+                                       min(WB, col_end - c), m, lane, col0, cb, prow, sc, mx, stg);
+            } else {
+                for (int c = 16 * half; c < col_end; c += 32) {
+                    uint32_t r[16];
+                    tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                    tmem_wait_ld();
+                    tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, sc, mx);
+                }
             }
             tc_fence_before();
             if constexpr (PAIR) mbar_arrive_cluster(acce_leader + (uint32_t)(acc * 8));
@@ -727,7 +739,7 @@ template <int BN, int BKB, bool PAIR = false>
 struct TcCfg {
     static constexpr int brows = PAIR ? BN / 2 : BN;
     static constexpr int stage_bytes = (128 * BKB + brows * BKB + 1023) / 1024 * 1024;
-    static constexpr int stages0 = (196 * 1024) / stage_bytes;
+    static constexpr int stages0 = (192 * 1024) / stage_bytes;
     static constexpr int STAGES = stages0 > 12 ? 12 : (stages0 < 2 ? 2 : stages0);
 };
 
@@ -1003,6 +1015,7 @@ cudaError_t tc_setup(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, bo
     a.np_chunk = d.np;
     a.out_rank = d.out_rank;
     a.ln = d.ln;
+    a.staged = d.staged;
     for (int i = 0; i < 40; ++i) a.out_dpos[i] = i < d.out_rank ? d.out_dpos[i] : 0;
     if (a.out_rank > 0 && (a.N < 8 || a.out_rank > 40)) return cudaErrorInvalidValue;
     a.out_c64 = d.out_c64;

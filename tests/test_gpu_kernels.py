@@ -250,6 +250,24 @@ def test_gemm_tensor_cores_b_resident_batched(ba, bb):
                                   _gemm_bits(dt, 2048, 64, 16, 5, ba, bb, 3))
 
 
+# Staged-store epilogue (each warp's rounded results through shared memory,
+# whole 32-byte sectors per store): the same values as the row-per-thread
+# stores, bit for bit, on tiles of 16-256 real columns, a partial M tile,
+# batches and both half types; N = 4 (2N < 16) runs the row-per-thread path.
+STAGED_SHAPES = [(128, 8, 8), (1024, 16, 16), (256, 32, 64), (4096, 64, 32), (64, 128, 128),
+                 (1 << 14, 256, 16), (2048, 512, 256), (512, 4, 64)]
+
+
+@pytest.mark.parametrize("M,N,K", STAGED_SHAPES)
+def test_gemm_tensor_cores_staged_stores(M, N, K):
+    _lp_case(tn.F16, M, N, K, 1, tn.GEMM_TC_STAGED)
+    for dt in (tn.F16, tn.BF16):
+        assert np.array_equal(_gemm_bits(dt, M, N, K, 1, True, True, tn.GEMM_TC_STAGED),
+                              _gemm_bits(dt, M, N, K, 1, True, True, 3))
+    assert np.array_equal(_gemm_bits(tn.F16, M, N, K, 3, True, False, tn.GEMM_TC_STAGED),
+                          _gemm_bits(tn.F16, M, N, K, 3, True, False, 3))
+
+
 def test_gemm_tensor_cores_cta_pairs_long_k():
     # K = 2^16 complex: split into K parts (FP32 partials, FP64 reduction)
     M, N, K = 256, 128, 1 << 16
