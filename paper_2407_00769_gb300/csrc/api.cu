@@ -163,9 +163,11 @@ int run_op(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, int t_
     const int cls = op_class(P, op, fl, by);
     if (cls < 0 || !((P->prof_mask >> cls) & 1))
         return run_op_raw(P, op, slice_base, amps, t_lo, t_hi, overwrite, s, launches);
-    tn_plan_s::ProfRec r{cls, take_event(P), take_event(P), fl, by};
+    tn_plan_s::ProfRec r{cls, take_event(P), take_event(P), fl, by, 0};
     cudaEventRecord(r.e0, s);
+    const int before = launches;
     const int rc = run_op_raw(P, op, slice_base, amps, t_lo, t_hi, overwrite, s, launches);
+    r.kernels = launches - before;
     cudaEventRecord(r.e1, s);
     P->prof.push_back(r);
     return rc;
@@ -194,7 +196,7 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                                   op.bprep.lk, op.bprep.ln, op.bprep.lb, op.bprep.np, op.bprep.tb, dtype,
                                   P->d_stepcorr + op.bprep.step, P->d_tmax, P->d_texp, op.bprep.meta_src,
                                   op.bprep.meta_dst, s, P->opts.no_scaling ? 1 : 0, P->d_bpart);
-            ++launches;
+            launches += (op.bprep.tb == 0 && P->d_bpart) ? 2 : 1;   // complex64 B: partial sums, then the tree
             break;
         case OP_GEMM: {
             const GemmOp &g = op.gemm;
@@ -257,6 +259,8 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     d.out_rank = g.out_rank;
                     for (int i = 0; i < g.out_rank && i < 40; ++i) d.out_dpos[i] = g.out_dpos[i];
                     e = launch_gemm_tc(d, sr, P->d_err, s);
+                    // split K: the parts' FP64 sum is a second kernel
+                    if (!(za || zb) && g.out_rank == 0 && tc_split(g.lm, g.ln, g.lk, batch) > 1) ++launches;
                     break;
                 }
                 default:
@@ -1554,7 +1558,7 @@ int tn_profile_read(tn_plan_t *P, tn_kernel_stats *out) {
         TN_CUDA(cudaEventSynchronize(r.e1), "event sync");
         float ms = 0;
         TN_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1), "event time");
-        out[r.cls].launches += 1;
+        out[r.cls].launches += r.kernels;
         out[r.cls].ms += ms;
         out[r.cls].flops += r.flops;
         out[r.cls].bytes += r.bytes;

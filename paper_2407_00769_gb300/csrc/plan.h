@@ -104,7 +104,7 @@ struct tn_plan_s {
     void *h_store_pinned = nullptr;     // pinned copy of the leaf store
     // per-kernel-class event timing (tn_profile)
     uint32_t prof_mask = 0;
-    struct ProfRec { int cls; cudaEvent_t e0, e1; double flops, bytes; };
+    struct ProfRec { int cls; cudaEvent_t e0, e1; double flops, bytes; int kernels; };
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<void *> owned;          // allocations to free
