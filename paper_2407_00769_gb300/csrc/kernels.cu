@@ -286,17 +286,20 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 
 // ----------------------------------------------------------- rows GEMMs --
 // Blocks of kRows threads over (row block, column chunk, batch entry):
-// rows_body for row blocks blockIdx.x, + gridDim.x, ... < gx (the grid is
-// capped at a few waves; each thread's maximum is recorded once at the end).
+// rows_body for row blocks blockIdx.x, + gridDim.x, ... < gx and column
+// chunks blockIdx.y, + gridDim.y, ... < gy (the grid is capped at a few
+// waves and at 65535 chunks; each thread's maximum is recorded once at the
+// end).
 template <typename TA, typename TB, typename TC, int NC, int DT>
 __global__ void __launch_bounds__(kRows) gemm_rows_kernel(
     const TA *__restrict__ A, const TB *__restrict__ B, TC *__restrict__ C, int lm, int ln, int lk,
-    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb, int64_t gx) {
+    int64_t sa, int64_t sb, int64_t sc, ScaleRef sr, const int32_t *za, const int32_t *zb, int64_t gx, int gy) {
     __shared__ RowsSmem<TA, NC> sm;
     float mx = 0.f;
-    for (int64_t bx = blockIdx.x; bx < gx; bx += gridDim.x)
-        rows_body<TA, TB, TC, NC, DT, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, sr, za, zb, bx, blockIdx.y,
-                                                 blockIdx.z, threadIdx.x, sm, mx);
+    for (int by = blockIdx.y; by < gy; by += gridDim.y)
+        for (int64_t bx = blockIdx.x; bx < gx; bx += gridDim.x)
+            rows_body<TA, TB, TC, NC, DT, SyncBlock>(A, B, C, lm, ln, lk, sa, sb, sc, sr, za, zb, bx, by,
+                                                     blockIdx.z, threadIdx.x, sm, mx);
     rows_flush<TC, DT>(sr, mx, threadIdx.x);
 }
 
@@ -321,9 +324,10 @@ static cudaError_t rows_dispatch(const void *A, const void *B, void *C, int lm, 
     const int64_t gxl = std::min(gx, per);
 #define TN_ROWS_CASE(NCV)                                                                        \
     {                                                                                             \
-        dim3 g((unsigned)gxl, (unsigned)((N + NCV - 1) / NCV), (unsigned)batch);                  \
+        const int gy = (N + NCV - 1) / NCV;                                                      \
+        dim3 g((unsigned)gxl, (unsigned)std::min(gy, 65535), (unsigned)batch);                   \
         gemm_rows_kernel<TA, TB, TC, NCV, DT><<<g, kRows, 0, s>>>(                                \
-            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr, za, zb, gx);       \
+            (const TA *)A, (const TB *)B, (TC *)C, lm, ln, lk, sa, sb, sc, sr, za, zb, gx, gy);   \
         break;                                                                                    \
     }
     switch (ncv) {

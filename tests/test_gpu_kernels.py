@@ -176,10 +176,14 @@ def test_gemm_f16_tensor_cores_batched(ba, bb):
     _lp_case(tn.F16, 256, 16, 32, 3, 3, ba, bb)
 
 
-@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 4, 2), (300, 16, 4), (1024, 64, 1), (256, 8, 64)])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 4, 2), (300, 16, 4), (1024, 64, 1), (256, 8, 64),
+                                   (128, 128, 512), (1 << 16, 4, 4), (16, 1 << 20, 4)])
 def test_gemm_f16_rows(M, N, K):
+    # (128, 128, 512): few row blocks, fewer columns per thread to fill the
+    # GPU, FP64 partials (K > 256); (2^16, 4, 4): row blocks looped over by a
+    # capped grid; (16, 2^20, 4): 65536 column chunks, more than a grid holds
     M = 1 << int(np.ceil(np.log2(M)))
-    _lp_case(tn.F16, M, N, K, 2, 2)
+    _lp_case(tn.F16, M, N, K, 1 if N > 4096 else 2, 2)
 
 
 # CTA pairs (cluster of 2, one M = 256 tcgen05.mma over both SMs): one tile,
