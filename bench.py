@@ -55,6 +55,8 @@ def parse():
                     help="time one kernel on one shape instead (profiling aid)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
     ap.add_argument("--pair", action="store_true", help="--case gemm_tc on CTA pairs (256-row tiles)")
+    ap.add_argument("--c64", action="store_true",
+                    help="--case gemm_tc with complex64 operands on the tensor cores (TF32 parts)")
     ap.add_argument("--bres", action="store_true",
                     help="--case gemm_tc with the B' slice resident in shared memory (short K)")
     ap.add_argument("--tma-store", action="store_true",
@@ -90,6 +92,11 @@ def kernel_case(args):
         B = (torch.randn(b, K, N, 2, device="cuda", generator=g) / (K ** 0.5)).half()
         C = torch.empty(b, M, N, 2, dtype=torch.float16, device="cuda")
         dt = tn.F16
+        if args.c64:
+            A = torch.randn(b, M, K, dtype=torch.complex64, device="cuda", generator=g)
+            B = torch.randn(b, K, N, dtype=torch.complex64, device="cuda", generator=g) / (K ** 0.5)
+            C = torch.empty(b, M, N, dtype=torch.complex64, device="cuda")
+            dt = tn.C64
         if args.fp8:
             # E4M3 operands (kind::f8f6f4), same shape
             A = (A.float() * 64).to(torch.float8_e4m3fn)
@@ -97,7 +104,7 @@ def kernel_case(args):
             dt = tn.FP8
         run = lambda: tn.gemm(dt, A, B, C, M, N, K, batch=b, batch_a=True, batch_b=True,
                               scale_exp=-12 if args.fp8 else 0,
-                              kernel=tn.GEMM_TC_PAIR if args.pair else
+                              kernel=tn.GEMM_C64_TC if args.c64 else tn.GEMM_TC_PAIR if args.pair else
                               (tn.GEMM_TC_BRES_STORE if args.tma_store else (tn.GEMM_TC_BRES if args.bres else 3)))
         work, unit = 8.0 * M * N * K * b, "TFLOP/s"
     elif args.case == "gather":

@@ -628,7 +628,11 @@ int tn_permute(const void *in, void *out, int32_t rank, const int32_t *perm,
  *   64 KiB, one K part; else as 3), 7 as 6 with the C tiles staged in
  *   shared memory and written by TMA stores (N >= 32; else as 6), 8 as 3
  *   with each warp's results staged in shared memory and stored in whole
- *   32-byte sectors (N >= 8; else as 3).
+ *   32-byte sectors (N >= 8; else as 3); with dtype TN_C64, 9 = the
+ *   complex64 GEMM on the tensor cores: each FP32 operand of Eq. 6's real
+ *   form split into a TF32 part and its remainder, A B'^T = A_hi B'_hi +
+ *   A_hi B'_lo + A_lo B'_hi by three kind::tf32 MMAs per K slice, FP32
+ *   accumulation (K >= 8; the split arrays are allocated per call).
  * out_max: optional device float, receives max |component| of the stored C.
  */
 int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int64_t N,

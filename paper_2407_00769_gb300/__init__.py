@@ -30,6 +30,7 @@ GEMM_TC_HALF_K = 5  # tn_gemm kernel index: tensor cores, 64-byte K chunks
 GEMM_TC_BRES = 6    # tn_gemm kernel index: tensor cores, B' slice resident in shared memory
 GEMM_TC_BRES_STORE = 7  # ... and C tiles written by TMA stores
 GEMM_TC_STAGED = 8      # tensor cores, results stored in whole 32-byte sectors via staging
+GEMM_C64_TC = 9         # complex64 on the tensor cores: TF32 parts, three MMAs per K slice
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 

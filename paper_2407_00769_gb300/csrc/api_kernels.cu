@@ -67,7 +67,44 @@ int tn_gemm(int32_t dtype, const void *A, const void *B, void *C, int64_t M, int
     if (dtype == TN_C64) {
         int kk = kernel;
         if (kk < 0) kk = (lm >= 6 && ln >= 6 && lk >= 4) ? GK_C64_TILED : GK_C64_ROWS;
-        if (kk == GK_C64_TILED)
+        if (kk == 9) {
+            // tensor cores, TF32 in three parts (hi x hi + hi x lo + lo x hi)
+            if (!tc_gemm_supported(lk, ln)) return fail(TN_EUNSUPPORTED, "tensor-core path needs K >= 8");
+            const int np = std::max(16, (int)(2 * N));
+            const int64_t abatch = batch_a ? batch : 1, bbatch = batch_b ? batch : 1;
+            const size_t abytes = (size_t)abatch * M * K * 8, bbytes = (size_t)bbatch * np * K * 8;
+            void *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+            TN_CUDA(cudaMallocAsync(&ah, abytes, s), "cudaMallocAsync");
+            TN_CUDA(cudaMallocAsync(&al, abytes, s), "cudaMallocAsync");
+            TN_CUDA(cudaMallocAsync(&bh, bbytes, s), "cudaMallocAsync");
+            TN_CUDA(cudaMallocAsync(&bl, bbytes, s), "cudaMallocAsync");
+            e = launch_split_tf32(A, ah, al, abatch * M * K * 2, s);
+            if (e == cudaSuccess) e = launch_bprep_x3(B, bh, bl, lk, ln, bbatch, np, s);
+            float *part = nullptr;
+            if (e == cudaSuccess) {
+                TcGemmDesc d;
+                d.dtype = TN_C64;
+                d.A = ah; d.A2 = al; d.Bp = bh; d.Bp2 = bl; d.C = C;
+                d.lm = lm; d.ln = ln; d.lk = lk;
+                d.batch = batch;
+                d.batch_a = batch_a ? 1 : 0;
+                d.batch_b = batch_b ? 1 : 0;
+                d.np = np;
+                d.x3 = 1;
+                d.out_c64 = 1;
+                const size_t pb = tc_split_bytes(lm, ln, lk, batch);
+                if (pb) e = cudaMallocAsync((void **)&part, pb, s);
+                d.partial = part;
+                ScaleRef sr0{};
+                sr0.out_max = out_max;
+                if (e == cudaSuccess) e = launch_gemm_tc(d, sr0, nullptr, s);
+            }
+            if (part) cudaFreeAsync(part, s);
+            cudaFreeAsync(ah, s);
+            cudaFreeAsync(al, s);
+            cudaFreeAsync(bh, s);
+            cudaFreeAsync(bl, s);
+        } else if (kk == GK_C64_TILED)
             e = launch_gemm_tiled_c64((const float2 *)A, (const float2 *)B, (float2 *)C, lm, ln, lk,
                                       batch, sa, sb, sc, 0, s);
         else if (kk == GK_C64_ROWS)

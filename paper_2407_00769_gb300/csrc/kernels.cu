@@ -284,6 +284,74 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
     return cudaGetLastError();
 }
 
+// ------------------------------------------- TF32 hi / lo splits (x3) --
+// x = hi + lo with hi = x whose 13 low mantissa bits are cleared (exactly a
+// TF32 value, what the tensor cores read of an FP32 word) and lo = x - hi
+// (exact: hi agrees with x in sign, exponent and leading bits)
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    lo = x - hi;
+}
+
+__global__ void split_tf32_kernel(const float4 *__restrict__ x, float4 *__restrict__ hi, float4 *__restrict__ lo,
+                                  int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        float4 h, l;
+        split_tf32(v.x, h.x, l.x);
+        split_tf32(v.y, h.y, l.y);
+        split_tf32(v.z, h.z, l.z);
+        split_tf32(v.w, h.w, l.w);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+
+cudaError_t launch_split_tf32(const void *x, void *hi, void *lo, int64_t n, cudaStream_t s) {
+    if (n % 4 || ((uintptr_t)x | (uintptr_t)hi | (uintptr_t)lo) & 15) return cudaErrorInvalidValue;
+    const int64_t n4 = n / 4;
+    const int threads = 256;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n4 + threads - 1) / threads, (int64_t)tc_num_sms() * 8));
+    split_tf32_kernel<<<(unsigned)blocks, threads, 0, s>>>((const float4 *)x, (float4 *)hi, (float4 *)lo, n4);
+    return cudaGetLastError();
+}
+
+// complex64 B [batch][K][N] -> the real B' [batch][np][2K] of Eq. 6 in FP32
+// as hi and lo parts: row 2n holds (re, -im) and row 2n + 1 (im, re) of
+// B[k][n] at columns 2k, 2k + 1; rows 2N .. np - 1 are zero.  One thread per
+// (batch entry, B' row, k).
+__global__ void bprep_x3_kernel(const float2 *__restrict__ B, float2 *__restrict__ bh, float2 *__restrict__ bl,
+                                int lk, int ln, int np, int64_t total) {
+    const int K = 1 << lk, N = 1 << ln;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i & (K - 1));
+        const int64_t row = i >> lk;
+        const int rr = (int)(row % np);
+        const int64_t b = row / np;
+        const int n = rr >> 1;
+        float2 v = make_float2(0.f, 0.f);
+        if (n < N) {
+            const float2 x = B[((b << lk) + k) * (int64_t)N + n];
+            v = (rr & 1) ? make_float2(x.y, x.x) : make_float2(x.x, -x.y);
+        }
+        float2 h, l;
+        split_tf32(v.x, h.x, l.x);
+        split_tf32(v.y, h.y, l.y);
+        bh[i] = h;
+        bl[i] = l;
+    }
+}
+
+cudaError_t launch_bprep_x3(const void *B, void *bh, void *bl, int lk, int ln, int64_t batch, int np, cudaStream_t s) {
+    const int64_t total = (batch * np) << lk;
+    const int threads = 256;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + threads - 1) / threads, (int64_t)tc_num_sms() * 8));
+    bprep_x3_kernel<<<(unsigned)blocks, threads, 0, s>>>((const float2 *)B, (float2 *)bh, (float2 *)bl, lk, ln, np,
+                                                         total);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------- rows GEMMs --
 // Blocks of kRows threads over (row block, column chunk, batch entry):
 // rows_body for row blocks blockIdx.x, + gridDim.x, ... < gx and column

@@ -73,6 +73,11 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
                               int32_t *texp, int meta_src, int meta_dst, cudaStream_t s,
                               int scale_off = 0, void *scratch = nullptr);
 size_t bprep_c64_scratch_bytes();
+// complex64 on the tensor cores (TcGemmDesc::x3): x -> hi + lo parts of n
+// FP32 values (n a multiple of 4, 16-byte aligned), and complex64 B
+// [batch][K][N] -> the FP32 B' [batch][np][2K] of Eq. 6 as hi and lo parts
+cudaError_t launch_split_tf32(const void *x, void *hi, void *lo, int64_t n, cudaStream_t s);
+cudaError_t launch_bprep_x3(const void *B, void *bh, void *bl, int lk, int ln, int64_t batch, int np, cudaStream_t s);
 cudaError_t launch_gemm_rows_mixed(int dtype, int ta, int tb, int tc, const void *A, const void *B,
                                    void *C, int lm, int ln, int lk, int64_t batch, int64_t sa,
                                    int64_t sb, int64_t sc, const ScaleRef &sr, cudaStream_t s,
@@ -131,6 +136,13 @@ struct TcGemmDesc {
     int pair = 0;
     // 1: 64-byte K chunks (FP16/BF16, 1-CTA tiles): a deeper ring
     int half_k = 0;
+    // 1: complex64 operands on the tensor cores (kind::tf32, three MMAs per
+    // K slice): A / Bp hold the TF32 "hi" parts (FP32 words with 13 low
+    // mantissa bits clear) and A2 / Bp2 the remainders, all FP32 in the
+    // layouts of A and B'; C complex64 (out_c64 = 1); 1-CTA tiles, N tile <=
+    // 128, no gathers
+    int x3 = 0;
+    const void *A2 = nullptr, *Bp2 = nullptr;
     // 1: complex-half results through a per-warp staging area in shared
     // memory, every store instruction writing whole 32-byte sectors
     // (tc_store_block; 1-CTA and pair kernels)

@@ -196,6 +196,16 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
             : "memory");
 }
 
+// kind::tf32 (FP32 words read as TF32, FP32 accumulation), one CTA
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // K-major shared-memory matrix descriptor (tcgen05): start address, leading
 // byte offset (unused for swizzled K-major), stride byte offset = 8 rows,
 // descriptor version 1, swizzle mode.  BKB: bytes of one K chunk row.

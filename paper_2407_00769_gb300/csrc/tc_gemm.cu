@@ -690,6 +690,229 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
     }
 }
 
+// ------------------------------------------- complex64 on TF32 (x3) --
+// Complex64 steps on the tensor cores: the real GEMM of Eq. 6 with FP32
+// operands, each split as x = hi + lo, hi = x with its 13 low mantissa bits
+// cleared (exactly a TF32 value) and lo = x - hi (exact); then
+// A B'^T = A_hi B'_hi + A_hi B'_lo + A_lo B'_hi + (A_lo B'_lo, below FP32
+// rounding), three kind::tf32 MMAs per 8-element K slice into one FP32
+// accumulator.  The four operands come from hi / lo arrays built beforehand
+// (split_tf32, bprep_x3).  Same roles as gemm_tc_kernel (1-CTA, 320
+// threads, bounded waits, double-buffered accumulators); the result is
+// complex64 (the epilogue's FP32 path: no rounding, no scale).
+template <int BN, int BKB>
+struct X3Smem {
+    static constexpr int a_bytes = 128 * BKB;
+    static constexpr int b_bytes = BN * BKB;
+    // a stage: A_hi | B'_hi | A_lo | B'_lo (each a whole number of KiB)
+    static constexpr int stage_bytes = (2 * (a_bytes + b_bytes) + 1023) / 1024 * 1024;
+    static constexpr int stages0 = (192 * 1024) / stage_bytes;
+    static constexpr int STAGES = stages0 > 8 ? 8 : (stages0 < 2 ? 2 : stages0);
+    static constexpr int ring = STAGES * stage_bytes;
+    static constexpr int total = 1024 + ring + 1024;
+    static_assert(total <= 232448, "over the 227 KiB of shared memory a CTA may have");
+    static_assert((2 * STAGES + 5) * 8 + 16 <= 1024, "barriers overflow their kilobyte");
+};
+
+template <int BN, int BKB>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_x3_kernel(const __grid_constant__ CUtensorMap tmAh,
+                                                            const __grid_constant__ CUtensorMap tmAl,
+                                                            const __grid_constant__ CUtensorMap tmBh,
+                                                            const __grid_constant__ CUtensorMap tmBl,
+                                                            const TcArgs args) {
+    using S = X3Smem<BN, BKB>;
+    constexpr int STAGES = S::STAGES;
+    constexpr int BK = BKB / 4;                        // FP32 elements per K chunk
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + S::ring);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint64_t *acce = accf + 2;
+    uint64_t *drain = acce + 2;
+    volatile uint32_t *tmem_slot = (volatile uint32_t *)(drain + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr uint32_t tmem_cols = (2 * BN < 32) ? 32 : 2 * BN;
+    const int64_t walker = blockIdx.x, walkers = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], kEpiThreads);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmAh) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmAl) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmBh) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmBl) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void *)tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer --
+        if (lane == 0 && !args.withhold) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int8_t armed[STAGES];
+            for (int st = 0; st < STAGES; ++st) armed[st] = -1;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
+                int64_t b, mt;
+                int nt;
+                tile_coords(args, t, b, mt, nt);
+                const int kbase = (int)(t / args.tiles_per_part) * args.nk * BK;
+                const int zA = args.batch_a ? (int)b : 0, zB = args.batch_b ? (int)b : 0;
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1, &abort_flag)) { ok = false; break; }
+                    uint8_t *sa = smem + stage * S::stage_bytes;
+                    uint8_t *sb = sa + S::a_bytes;
+                    uint8_t *sa2 = sb + S::b_bytes;
+                    uint8_t *sb2 = sa2 + S::a_bytes;
+                    mbar_expect_tx(&full[stage], 2 * (S::a_bytes + S::b_bytes));
+                    const int x = kbase + kc * BK;
+                    tma_load_3d(sa, &tmAh, &full[stage], x, (int)(mt * 128), zA);
+                    tma_load_3d(sb, &tmBh, &full[stage], x, nt * BN, zB);
+                    tma_load_3d(sa2, &tmAl, &full[stage], x, (int)(mt * 128), zA);
+                    tma_load_3d(sb2, &tmBl, &full[stage], x, nt * BN, zB);
+                    armed[stage] = (int8_t)phase;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (!ok) {
+                // drain: only the last STAGES loads can still be in flight
+                for (int st = 0; st < STAGES; ++st) {
+                    if (armed[st] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&full[st], (uint32_t)armed[st]) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------- MMA issue --
+        if (lane == 0) {
+            uint32_t idesc = 0;
+            idesc |= 1u << 4;                                  // D = F32
+            idesc |= 2u << 7;                                  // A = TF32
+            idesc |= 2u << 10;                                 // B = TF32
+            idesc |= (uint32_t)(BN >> 3) << 17;                // N
+            idesc |= (uint32_t)(128 >> 4) << 24;               // M
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            bool issued = false;
+            for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
+                if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                for (int kc = 0; kc < args.nk; ++kc) {
+                    if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
+                    const uint32_t b_addr = a_addr + S::a_bytes;
+                    const uint32_t a2_addr = b_addr + S::b_bytes;
+                    const uint32_t b2_addr = a2_addr + S::a_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < BKB / 32; ++kk) {     // 8 FP32 of K per MMA
+                        const uint64_t ah = smem_desc<BKB>(a_addr + kk * 32);
+                        const uint64_t bh = smem_desc<BKB>(b_addr + kk * 32);
+                        const uint64_t al = smem_desc<BKB>(a2_addr + kk * 32);
+                        const uint64_t bl = smem_desc<BKB>(b2_addr + kk * 32);
+                        tc_mma_tf32(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        tc_mma_tf32(d_tmem, ah, bl, idesc, 1u);
+                        tc_mma_tf32(d_tmem, al, bh, idesc, 1u);
+                    }
+                    issued = true;
+                    tc_commit(&empty[stage]);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                }
+                if (!ok) break;
+                tc_commit(&accf[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+            if (!ok && issued) {
+                tc_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kWaitLimitNs / 4) {
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue --
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        int64_t lowtab[8];
+        bool low_kept = true;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            lowtab[j] = args.out_rank ? permute_bits(args, j, 0, 3) : j;
+            low_kept = low_kept && lowtab[j] == j;
+        }
+        float mx = 0.f;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t t = walker; t < args.tiles; t += walkers) {
+            int64_t b, mt;
+            int nt;
+            tile_coords(args, t, b, mt, nt);
+            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
+            tc_fence_after();
+            const int64_t m = mt * 128 + row;
+            const int col0 = nt * BN;
+            const int64_t cb = b;
+            int64_t prow = 0;
+            if (args.out_rank) prow = permute_bits(args, (cb * args.M + m) * (int64_t)args.N, args.ln, args.out_rank);
+            const int col_end = min(BN, 2 * args.N - col0);
+            for (int c = 16 * half; c < col_end; c += 32) {
+                uint32_t r[16];
+                tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                tmem_wait_ld();
+                tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, 1.0f, mx);
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[acc]);
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && args.sr.out_max && !args.partial)
+            atomicMax(reinterpret_cast<int *>(args.sr.out_max), __float_as_int(mx));
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0 && args.err) atomicOr(args.err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
 // shared memory of the B'-resident kernel: A ring + two B' slots + barriers
 constexpr int kBresSmemBudget = 196 * 1024;
 constexpr int kBresSmemTotal = 1024 + kBresSmemBudget + (2 * kBresMaxStages + 9) * 8 + 16;
@@ -728,6 +951,7 @@ bool encode_3d(CUtensorMap *m, int dtype, int esz, const void *base, uint64_t in
                                   : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                     : CU_TENSOR_MAP_SWIZZLE_32B;
     const CUtensorMapDataType dt = esz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : dtype == TN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
@@ -832,6 +1056,39 @@ cudaError_t run_tc_bn(int bn, const CUtensorMap &ma, const CUtensorMap &mb, cons
     }
 }
 
+template <int BN, int BKB>
+cudaError_t set_attr_x3() {
+    return cudaFuncSetAttribute(gemm_tc_x3_kernel<BN, BKB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                X3Smem<BN, BKB>::total);
+}
+
+template <int BKB>
+cudaError_t set_attr_x3_bn() {
+    cudaError_t e = set_attr_x3<16, BKB>();
+    if (e == cudaSuccess) e = set_attr_x3<32, BKB>();
+    if (e == cudaSuccess) e = set_attr_x3<64, BKB>();
+    if (e == cudaSuccess) e = set_attr_x3<128, BKB>();
+    return e;
+}
+
+template <int BKB>
+cudaError_t run_tc_x3(int bn, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh,
+                      const CUtensorMap &bl, const TcArgs &a, cudaStream_t s) {
+    const int64_t grid = std::min<int64_t>(a.tiles, tc_num_sms());
+#define TN_X3_CASE(BNV)                                                                              \
+    gemm_tc_x3_kernel<BNV, BKB><<<(unsigned)grid, kTcThreads, X3Smem<BNV, BKB>::total, s>>>(ah, al, bh, bl, a); \
+    break;
+    switch (bn) {
+        case 16: TN_X3_CASE(16)
+        case 32: TN_X3_CASE(32)
+        case 64: TN_X3_CASE(64)
+        case 128: TN_X3_CASE(128)
+        default: return cudaErrorInvalidValue;
+    }
+#undef TN_X3_CASE
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int tc_num_sms() {
@@ -889,6 +1146,9 @@ cudaError_t tc_prepare() {
         e = cudaFuncSetAttribute(gemm_tc_bres_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBresSmemTotal);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gemm_tc_bres_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBresSmemTotal);
+    if (e == cudaSuccess) e = set_attr_x3_bn<32>();
+    if (e == cudaSuccess) e = set_attr_x3_bn<64>();
+    if (e == cudaSuccess) e = set_attr_x3_bn<128>();
     if (e == cudaSuccess && dev < 31) done_mask |= 1 << dev;
     return e;
 }
@@ -957,15 +1217,18 @@ cudaError_t tc_setup(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_err, bo
                      CUtensorMap *mb_out, TcArgs *a_out, int *bn_out, int *bk_out, bool *pair_out) {
     if (d.fp8 ? !tc_gemm_supported_fp8(d.lk, d.ln) : !tc_gemm_supported(d.lk, d.ln))
         return cudaErrorInvalidValue;
-    const int esz = d.fp8 ? 1 : 2;
+    if (d.x3 && (d.fp8 || d.pair || d.za || d.zb || d.zc || d.gather_r || !d.out_c64 || !d.A2 || !d.Bp2))
+        return cudaErrorInvalidValue;
+    const int esz = d.x3 ? 4 : d.fp8 ? 1 : 2;
     const int kreal = 2 << d.lk;                 // 2K elements
     // K chunk: 128-byte rows where K allows (FP8: always, K >= 64)
-    int bk = d.fp8 ? 128 : (kreal >= 64 ? 64 : kreal);
-    int bn = d.np >= 256 ? 256 : d.np;           // 16 .. 256
+    int bk = d.x3 ? (kreal >= 32 ? 32 : kreal) : d.fp8 ? 128 : (kreal >= 64 ? 64 : kreal);
+    int bn = d.np >= (d.x3 ? 128 : 256) ? (d.x3 ? 128 : 256) : d.np;   // 16 .. 256 (x3: 128)
     if (d.bn > 0) {
         if ((d.bn & (d.bn - 1)) != 0 || d.bn < 16 || d.bn > 256) return cudaErrorInvalidValue;
         bn = (d.bn < bn || d.gather_r > 0) ? d.bn : bn;   // B_P tiles span several chunks
     }
+    if (d.x3 && bn > 128) bn = 128;
     const int64_t M = (int64_t)1 << d.lm;
     const bool gathered = d.za || d.zb || d.zc;
     // CTA pairs: 256 x 256 tiles of FP16/BF16 with 128-byte K chunks
@@ -1091,6 +1354,24 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, const ScaleRef &sr, int32_t *d_e
         if (e != cudaSuccess) return e;
     }
     cudaError_t e;
+    if (d.x3) {
+        // the remainder maps: the same shapes and boxes over A2 and Bp2
+        CUtensorMap ma2, mb2;
+        const int kreal = 2 << d.lk;
+        const uint64_t M = (uint64_t)1 << d.lm;
+        if (!encode_3d(&ma2, d.dtype, 4, d.A2, (uint64_t)kreal, M, (uint64_t)(d.batch_a ? d.batch : 1), bk, 128) ||
+            !encode_3d(&mb2, d.dtype, 4, d.Bp2, (uint64_t)kreal, (uint64_t)d.np, (uint64_t)(d.batch_b ? d.batch : 1),
+                       bk, bn))
+            return cudaErrorInvalidValue;
+        switch (bk) {
+            case 8: e = run_tc_x3<32>(bn, ma, ma2, mb, mb2, a, s); break;
+            case 16: e = run_tc_x3<64>(bn, ma, ma2, mb, mb2, a, s); break;
+            default: e = run_tc_x3<128>(bn, ma, ma2, mb, mb2, a, s); break;
+        }
+        if (e == cudaSuccess && a.split > 1)
+            e = launch_splitk_reduce(a.partial, a.split, d.C, 1, d.dtype, d.batch, d.lm, d.ln, d.lk, sr, s);
+        return e;
+    }
     BresCfg bc;
     if (d.bres && bres_config(a, bn, 2 * bk, pair, d.fp8, d.tma_store != 0, bc)) {
         switch (bk) {

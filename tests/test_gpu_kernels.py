@@ -116,6 +116,41 @@ def test_gemm_c64(M, N, K, batch):
         assert np.all(err <= 1e-6 * bound(a, b, K) * max(1, np.sqrt(K)) + 1e-30), kernel
 
 
+# complex64 on the tensor cores (tn_gemm kernel 9): each FP32 operand split
+# into a TF32 part and its remainder, three kind::tf32 MMAs per K slice.
+# Per product the dropped and truncated parts are below ~2^-19 of |a||b|, so
+# the error bound is the complex64 path's with a few units of FP32 rounding,
+# and rel-L2 stays within the complex64 budget (1e-5).
+@pytest.mark.parametrize("M,N,K,batch", [(128, 8, 8, 1), (256, 64, 64, 2), (1024, 256, 512, 1),
+                                         (64, 16, 16, 3), (4096, 128, 32, 1), (512, 512, 2048, 1)])
+def test_gemm_c64_tensor_cores(M, N, K, batch):
+    rng = np.random.default_rng(M * 11 + N * 5 + K)
+    a = to_c64(crandn(rng, batch, M, K))
+    b = to_c64(crandn(rng, batch, K, N))
+    c = torch.zeros(batch, M, N, dtype=torch.complex64, device="cuda")
+    mx = torch.zeros(1, dtype=torch.float32, device="cuda")
+    tn.gemm(tn.C64, dev(a), dev(b), c, M, N, K, batch=batch, batch_a=True, batch_b=True, kernel=9, out_max=mx)
+    got = c.cpu().numpy().astype(np.complex128)
+    want = ref_gemm(a, b)
+    err = np.abs(got - want)
+    assert np.all(err <= 4e-6 * bound(a, b, K) * max(1, np.sqrt(K)) + 1e-30)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+    # the recorded maximum is that of the stored components
+    assert mx.item() == pytest.approx(float(np.max(np.abs(np.stack([got.real, got.imag])))), rel=1e-6)
+
+
+def test_gemm_c64_tensor_cores_broadcast_b():
+    rng = np.random.default_rng(9)
+    M, N, K, batch = 256, 32, 64, 4
+    a = to_c64(crandn(rng, batch, M, K))
+    b = to_c64(crandn(rng, K, N))
+    c = torch.zeros(batch, M, N, dtype=torch.complex64, device="cuda")
+    tn.gemm(tn.C64, dev(a), dev(b), c, M, N, K, batch=batch, batch_a=True, batch_b=False, kernel=9)
+    want = ref_gemm(a, np.broadcast_to(b, (batch, K, N)))
+    got = c.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
 def test_gemm_c64_broadcast_b():
     rng = np.random.default_rng(5)
     M, N, K, batch = 256, 8, 8, 4
