@@ -1027,32 +1027,39 @@ def main():
 
     # complex64 path on the same workload (fewer steps: it is the slow path)
     if not args.no_c64 and dtype != tn.C64 and world == 1:
-        p64 = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
-                      slice_batch_log2=sb)
-        a64 = torch.zeros_like(amps)
-        p64.contract(0, n_slices, out=a64)
-        torch.cuda.synchronize()
-        tt = []
-        for _ in range(2):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        def c64_run(tensor_cores):
+            p64 = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=N_SLICE_EDGES, trials=PATH_TRIALS,
+                          slice_batch_log2=sb, c64_tensor_cores=tensor_cores)
+            a64 = torch.zeros_like(amps)
             p64.contract(0, n_slices, out=a64)
-            e1.record(stream)
-            e1.synchronize()
-            tt.append(e0.elapsed_time(e1))
-        m64 = statistics.mean(tt)
-        i64 = p64.info()
-        f64 = i64["flops_per_slice"] * n_slices + i64["flops_invariant"]
-        c64 = {"tflops": f64 / (m64 * 1e-3) / 1e12, "slices_per_s": n_slices / (m64 * 1e-3),
-               "ms_per_step": m64}
-        if gold is not None:
-            m = tn.metrics(a64, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
-            c64.update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]})
+            torch.cuda.synchronize()
+            tt = []
+            for _ in range(2):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p64.contract(0, n_slices, out=a64)
+                e1.record(stream)
+                e1.synchronize()
+                tt.append(e0.elapsed_time(e1))
+            m64 = statistics.mean(tt)
+            i64 = p64.info()
+            f64 = i64["flops_per_slice"] * n_slices + i64["flops_invariant"]
+            r = {"tflops": f64 / (m64 * 1e-3) / 1e12, "slices_per_s": n_slices / (m64 * 1e-3),
+                 "ms_per_step": m64}
+            if gold is not None:
+                m = tn.metrics(a64, torch.from_numpy(gold).to(dev), n_qubits=c.n_qubits)
+                r.update({"rel_l2": m["rel_l2"], "fidelity": m["fidelity"]})
+            del p64, a64
+            torch.cuda.empty_cache()
+            return r, m64
+        c64, m64 = c64_run(False)
+        # the large complex64 steps on the tensor cores (TF32 parts, three
+        # MMAs per K slice; tn_plan_opts.c64_tensor_cores)
+        c64["tensor_cores"], _ = c64_run(True)
         line["c64"] = c64
         line["speedup_vs_c64"] = m64 / ms
-        del p64, a64
 
     # end to end through the public API from host memory (leaves uploaded,
     # amplitudes downloaded, every step)

@@ -93,6 +93,7 @@ class PlanOpts(ctypes.Structure):
                 ("recompute_log2", ctypes.c_int32),
                 ("no_scaling", ctypes.c_int32), ("anneal_kappa", ctypes.c_int32),
                 ("workspace_budget", ctypes.c_int64),
+                ("c64_tensor_cores", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
@@ -318,7 +319,7 @@ class Plan:
                  torch_allocator: bool = True, small_log2: int = 0,
                  no_tensor_cores: bool = False, fp8_min_log2_flops: int = 0, anneal_iters: int = 0,
                  recompute_log2: int = 0, no_scaling: bool = False, workspace_budget: int = 0,
-                 anneal_kappa: int = 0, _samples=None):
+                 anneal_kappa: int = 0, c64_tensor_cores: bool = False, _samples=None):
         L = lib()
         self._c, self._gates = circuit_struct(circuit)
         if _samples is None:
@@ -332,6 +333,7 @@ class Plan:
         opts.path_trials = int(trials)
         opts.path_anneal_iters = int(anneal_iters)
         opts.anneal_kappa = int(anneal_kappa)
+        opts.c64_tensor_cores = 1 if c64_tensor_cores else 0
         opts.workspace_budget = int(workspace_budget)
         opts.slice_batch_log2 = int(slice_batch_log2)
         opts.tile_policy = int(tile_policy)

@@ -16,6 +16,22 @@ namespace {
 
 thread_local std::string g_err;
 
+// complex64 step that the tensor cores can run (tn_plan_opts.c64_tensor_cores)
+bool x3_eligible(const tn_plan_s *P, const GemmOp &g) {
+    return P->opts.dtype == TN_C64 && P->opts.c64_tensor_cores && tc_gemm_supported(g.lk, g.ln) &&
+           g.idx_a < 0 && g.idx_b < 0 && g.out_rank == 0 && g.lm <= 30;
+}
+
+// scratch of such a step: hi and lo parts of A ([batch][M][2K] FP32) and of
+// B' ([batch][np][2K] FP32)
+int64_t x3_bytes(const GemmOp &g) {
+    const int64_t ba = (g.lb > 0 && !g.bcast_a) ? (int64_t)1 << g.lb : 1;
+    const int64_t bb = (g.lb > 0 && !g.bcast_b) ? (int64_t)1 << g.lb : 1;
+    const int64_t np = std::max(16, 2 << g.ln);
+    return 2 * (ba << (g.lm + g.lk)) * 8 + 2 * ((bb * np) << g.lk) * 8;
+}
+
+
 int fail(int code, const std::string &msg) {
     g_err = msg;
     return code;
@@ -64,13 +80,24 @@ int ensure_device(tn_plan_s *P) {
     P->d_err = (int32_t *)plan_dev_alloc(P, 64);
     P->d_stepcorr = (double2 *)plan_dev_alloc(P, std::max<size_t>(64, S.steps.size() * sizeof(double2)));
     size_t split_bytes = 64;
+    int64_t x3b = 0;
     for (const Op &op : S.ops)
-        if (op.kind == OP_GEMM && op.gemm.kernel == GK_LP_TC)
+        if (op.kind == OP_GEMM && (op.gemm.kernel == GK_LP_TC || x3_eligible(P, op.gemm))) {
             split_bytes = std::max(split_bytes, tc_split_bytes(op.gemm.lm, op.gemm.ln, op.gemm.lk,
                                                                (int64_t)1 << op.gemm.lb));
+            if (op.gemm.kernel != GK_LP_TC) x3b = std::max(x3b, x3_bytes(op.gemm));
+        }
     P->d_splitk = (float *)plan_dev_alloc(P, split_bytes);
     P->d_gidx = (int32_t *)plan_dev_alloc(P, std::max<size_t>(64, S.gidx.size() * 4));
     P->d_bpart = plan_dev_alloc(P, bprep_c64_scratch_bytes());
+    if (x3b > 0) {
+        P->d_x3 = (float *)plan_dev_alloc(P, (size_t)x3b);
+        if (!P->d_x3) {
+            plan_dev_free_all(P);
+            return fail(TN_ENOMEM, "device allocation of the complex64 tensor-core scratch (" + std::to_string(x3b) +
+                                       " bytes) failed");
+        }
+    }
     if (!P->d_ws || !P->d_store || !P->d_jobs || !P->d_tmax || !P->d_texp || !P->d_err || !P->d_stepcorr ||
         !P->d_splitk || !P->d_gidx || !P->d_bpart) {
         plan_dev_free_all(P);
@@ -231,6 +258,37 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
                     e = launch_gemm_rows_mixed(dtype, g.ta, g.tb, g.tc, ws + g.a, ws + g.b, ws + g.c, g.lm,
                                                g.ln, g.lk, batch, sa, sb, sc, sr, s, za, zb);
                     break;
+                case GK_C64_TC: {
+                    // TF32 parts of A and of B' (from B [batch][K][N]), then
+                    // three kind::tf32 MMAs per K slice
+                    if (!P->d_x3 || !x3_eligible(P, g)) return fail(TN_EINVAL, "complex64 tensor-core step not set up");
+                    const int np = std::max(16, 2 << g.ln);
+                    const int64_t ba = g.bcast_a ? 1 : batch, bb = g.bcast_b ? 1 : batch;
+                    const int64_t na = (ba << (g.lm + g.lk)) * 2, nb = ((bb * np) << g.lk) * 2;   // FP32 values
+                    float *ah = P->d_x3, *al = ah + na, *bh = al + na, *bl = bh + nb;
+                    e = launch_split_tf32(ws + g.a, ah, al, na, s);
+                    if (e == cudaSuccess) e = launch_bprep_x3(ws + g.b, bh, bl, g.lk, g.ln, bb, np, s);
+                    launches += 2;
+                    if (e != cudaSuccess) break;
+                    TcGemmDesc d;
+                    d.dtype = TN_C64;
+                    d.A = ah; d.A2 = al;
+                    d.Bp = bh; d.Bp2 = bl;
+                    d.C = ws + g.c;
+                    d.lm = g.lm; d.ln = g.ln; d.lk = g.lk;
+                    d.batch = batch;
+                    d.batch_a = g.lb > 0 && !g.bcast_a;
+                    d.batch_b = g.lb > 0 && !g.bcast_b;
+                    d.np = np;
+                    d.bn = tc_tile_bn(g.tile);
+                    d.gm = tc_tile_gm(g.tile);
+                    d.x3 = 1;
+                    d.out_c64 = 1;
+                    d.partial = P->d_splitk;
+                    e = launch_gemm_tc(d, ScaleRef{}, P->d_err, s);
+                    if (tc_split(g.lm, g.ln, g.lk, batch) > 1) ++launches;
+                    break;
+                }
                 case GK_LP_TC: {
                     TcGemmDesc d;
                     d.dtype = dtype;
@@ -297,11 +355,12 @@ int run_op_raw(tn_plan_s *P, const Op &op, int64_t slice_base, double2 *amps, in
 
 // Legal (kernel, tile) configurations of a GEMM op: N tile x raster group,
 // each also on CTA pairs where the shape allows.
-std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g) {
+std::vector<std::pair<int, int>> gemm_candidates(const GemmOp &g, bool x3 = false) {
     std::vector<std::pair<int, int>> c;
-    if (g.kernel == GK_C64_ROWS || g.kernel == GK_C64_TILED) {
+    if (g.kernel == GK_C64_ROWS || g.kernel == GK_C64_TILED || g.kernel == GK_C64_TC) {
         c.push_back({GK_C64_ROWS, 0});
         if (g.lm >= 6 && g.ln >= 6 && g.lk >= 4) c.push_back({GK_C64_TILED, 0});
+        if (x3) c.push_back({GK_C64_TC, 0});
     } else if (g.kernel == GK_LP_ROWS) {
         c.push_back({GK_LP_ROWS, 0});
     } else {
@@ -446,7 +505,7 @@ int tune_plan(tn_plan_s *P, cudaStream_t s) {
                 GemmOp &g = op.gemm;
                 double best = 1e30;
                 std::pair<int, int> pick{g.kernel, g.tile};
-                for (const auto &cand : gemm_candidates(g)) {
+                for (const auto &cand : gemm_candidates(g, x3_eligible(P, g))) {
                     Op trial = op;
                     trial.gemm.kernel = cand.first;
                     trial.gemm.tile = cand.second;
@@ -546,12 +605,13 @@ int choose_by_model(tn_plan_s *P, tn_cost_model_t *M, cudaStream_t s) {
         const Op &op = S.ops[i];
         if (op.kind != OP_GEMM) continue;
         const GemmOp &g = op.gemm;
-        for (const auto &cand : gemm_candidates(g)) {
+        for (const auto &cand : gemm_candidates(g, x3_eligible(P, g))) {
             // the kernel variants of tile bits 10-12 (B'-resident, TMA
             // stores, staged stores) are left to exhaustive tuning: the
             // bundled training timings hold none of them, so the model would
             // extrapolate
             if (cand.second & (kTcBresTile | kTcStoreTile | kTcStagedTile)) continue;
+            if (cand.first == GK_C64_TC) continue;
             recs.push_back(tn_tune_record{0, g.lm, g.ln, g.lk, g.lb, P->opts.dtype, cand.first, cand.second,
                                           g.step, 0, 0});
             who.push_back({i, cand});
@@ -656,6 +716,7 @@ int check_opts(const tn_plan_opts &o) {
     if (o.path_anneal_iters < 0) return fail(TN_EINVAL, "path_anneal_iters must be >= 0");
     if (o.recompute_log2 < 0 || o.recompute_log2 > 8) return fail(TN_EINVAL, "recompute_log2 must be in 0..8");
     if (o.no_scaling != 0 && o.no_scaling != 1) return fail(TN_EINVAL, "no_scaling must be 0 or 1");
+    if (o.c64_tensor_cores != 0 && o.c64_tensor_cores != 1) return fail(TN_EINVAL, "c64_tensor_cores must be 0 or 1");
     if (o.no_scaling && o.fp8_min_log2_flops > 0)
         return fail(TN_EINVAL, "no_scaling does not apply to E4M3 steps (their scale is their range)");
     if (o.n_slice_edges < 0 && o.max_log2_elems <= 0)
@@ -781,6 +842,14 @@ int finish_plan(tn_plan_s *P, const SampleSpec *spec, std::string &err) {
         offs += (int64_t)L.data.size();
     }
     for (LeafJob &j : P->sched.leaf_jobs) j.src = P->leaf_offset[j.src];
+    // complex64 on the tensor cores (opt-in): the fixed choice for the large
+    // steps, where the split passes are small against the GEMM
+    for (Op &op : P->sched.ops)
+        if (op.kind == OP_GEMM && x3_eligible(P, op.gemm) &&
+            op.gemm.lm + op.gemm.ln + op.gemm.lk + op.gemm.lb + 3 >= 36) {
+            op.gemm.kernel = GK_C64_TC;
+            op.gemm.tile = 0;
+        }
     return TN_OK;
 }
 
@@ -1118,7 +1187,9 @@ int tn_plan_tune(tn_plan_t *P, void *stream) {
 
 int tn_plan_apply_tuning(tn_plan_t *P, const tn_tune_record *recs, int32_t n) {
     if (!P || n < 0 || (n > 0 && !recs)) return fail(TN_EINVAL, "bad argument");
-    auto family = [](int k) { return (k == GK_C64_ROWS || k == GK_C64_TILED) ? 0 : (k == GK_LP_ROWS ? 1 : 2); };
+    auto family = [](int k) {
+        return (k == GK_C64_ROWS || k == GK_C64_TILED || k == GK_C64_TC) ? 0 : (k == GK_LP_ROWS ? 1 : 2);
+    };
     Schedule &S = P->sched;
     for (Op &op : S.ops) {
         if (op.kind != OP_GEMM) continue;

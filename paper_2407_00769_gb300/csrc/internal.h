@@ -71,6 +71,7 @@ enum GemmKernel : int32_t {
     GK_C64_TILED = 1,  // complex64, 2-D shared-memory tiles
     GK_LP_ROWS = 2,    // complex-half, FP32 math, thread per row
     GK_LP_TC = 3,      // complex-half as real, tcgen05 + TMA, FP32 in TMEM
+    GK_C64_TC = 4,     // complex64 as real, tcgen05 kind::tf32 on hi / lo parts
 };
 
 // Tensor-core tile code: bits 0-3 N-tile width code, bits 4-7 raster-group

@@ -285,12 +285,18 @@ cudaError_t launch_bprep_perm(const void *B, void *Bp, int rank, const int32_t *
 }
 
 // ------------------------------------------- TF32 hi / lo splits (x3) --
-// x = hi + lo with hi = x whose 13 low mantissa bits are cleared (exactly a
-// TF32 value, what the tensor cores read of an FP32 word) and lo = x - hi
-// (exact: hi agrees with x in sign, exponent and leading bits)
+// x ~ hi + lo with hi = x rounded to 11 significant bits (TF32: 13 low
+// mantissa bits zero, round half away from zero) and lo = x - hi (exact in
+// FP32) rounded the same way: both are exactly TF32 values, so the tensor
+// cores read them unchanged; |x - hi| <= 2^-11 |x| and lo's own rounding
+// <= 2^-23 |x|, and the dropped lo x lo product is <= 2^-22 of |x||y|
+__device__ __forceinline__ float round_tf32(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    lo = x - hi;
+    hi = round_tf32(x);
+    lo = round_tf32(x - hi);
 }
 
 __global__ void split_tf32_kernel(const float4 *__restrict__ x, float4 *__restrict__ hi, float4 *__restrict__ lo,

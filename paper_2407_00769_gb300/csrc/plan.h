@@ -100,6 +100,7 @@ struct tn_plan_s {
     double2 *d_stepcorr = nullptr;      // per step: 1/(1+alpha) of its B' rounding
     float *d_splitk = nullptr;          // FP32 partials of split-K tensor-core steps
     void *d_bpart = nullptr;            // partial sums of the multi-block complex64 B' build
+    float *d_x3 = nullptr;              // complex64 on the tensor cores: TF32 parts of A and B'
     int32_t *d_gidx = nullptr;          // index table of sparse-state gather steps
     void *h_store_pinned = nullptr;     // pinned copy of the leaf store
     // per-kernel-class event timing (tn_profile)

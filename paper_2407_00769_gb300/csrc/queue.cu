@@ -881,6 +881,8 @@ int emit_op(Builder &Bd, int chain, tn_plan_s *P, const Op &op, int64_t slice_ba
             }
             // tensor cores (1-CTA tiles)
             if (g.fp8) return record_error(TN_EUNSUPPORTED, "queue: FP8 steps are not queued");
+            if (g.kernel == GK_C64_TC)
+                return record_error(TN_EUNSUPPORTED, "queue: complex64 tensor-core steps are not queued");
             TcGemmDesc d;
             d.dtype = dtype;
             d.A = ws + g.a;

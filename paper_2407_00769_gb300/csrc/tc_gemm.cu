@@ -692,14 +692,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
 
 // ------------------------------------------- complex64 on TF32 (x3) --
 // Complex64 steps on the tensor cores: the real GEMM of Eq. 6 with FP32
-// operands, each split as x = hi + lo, hi = x with its 13 low mantissa bits
-// cleared (exactly a TF32 value) and lo = x - hi (exact); then
-// A B'^T = A_hi B'_hi + A_hi B'_lo + A_lo B'_hi + (A_lo B'_lo, below FP32
-// rounding), three kind::tf32 MMAs per 8-element K slice into one FP32
-// accumulator.  The four operands come from hi / lo arrays built beforehand
+// operands, each split as x ~ hi + lo, both exactly TF32 values (hi = x
+// rounded to 11 significant bits, lo = the rounded remainder); then
+// A B'^T ~ A_hi B'_hi + A_hi B'_lo + A_lo B'_hi (A_lo B'_lo is about 2^-22
+// of the product), three kind::tf32 MMAs per 8-element K slice, each part of
+// kX3Part K chunks in a fresh TMEM accumulator whose values the epilogue adds
+// in FP32 registers.  The four operands come from hi / lo arrays built beforehand
 // (split_tf32, bprep_x3).  Same roles as gemm_tc_kernel (1-CTA, 320
 // threads, bounded waits, double-buffered accumulators); the result is
 // complex64 (the epilogue's FP32 path: no rounding, no scale).
+// K chunks per accumulation part of the x3 kernel (the epilogue adds the
+// parts in FP32 registers): 8 chunks of 128 bytes = 256 real K terms
+constexpr int kX3Part = 8;
+
 template <int BN, int BKB>
 struct X3Smem {
     static constexpr int a_bytes = 128 * BKB;
@@ -811,6 +816,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_x3_kernel(const __grid_
         }
     } else if (warp == 1) {
         // --------------------------------------------------- MMA issue --
+        // each tile's K range in parts of kX3Part chunks, each part into a
+        // fresh TMEM accumulator (the epilogue sums the parts in registers)
         if (lane == 0) {
             uint32_t idesc = 0;
             idesc |= 1u << 4;                                  // D = F32
@@ -825,33 +832,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_x3_kernel(const __grid_
             bool ok = true;
             bool issued = false;
             for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
-                if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-                for (int kc = 0; kc < args.nk; ++kc) {
-                    if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                for (int k0 = 0; k0 < args.nk && ok; k0 += kX3Part) {
+                    const int k1 = min(args.nk, k0 + kX3Part);
+                    if (!mbar_wait(&acce[acc], acc_phase ^ 1, &abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
-                    const uint32_t b_addr = a_addr + S::a_bytes;
-                    const uint32_t a2_addr = b_addr + S::b_bytes;
-                    const uint32_t b2_addr = a2_addr + S::a_bytes;
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                    for (int kc = k0; kc < k1; ++kc) {
+                        if (!mbar_wait(&full[stage], phase, &abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a_addr = smem_u32(smem + stage * S::stage_bytes);
+                        const uint32_t b_addr = a_addr + S::a_bytes;
+                        const uint32_t a2_addr = b_addr + S::b_bytes;
+                        const uint32_t b2_addr = a2_addr + S::a_bytes;
 #pragma unroll
-                    for (int kk = 0; kk < BKB / 32; ++kk) {     // 8 FP32 of K per MMA
-                        const uint64_t ah = smem_desc<BKB>(a_addr + kk * 32);
-                        const uint64_t bh = smem_desc<BKB>(b_addr + kk * 32);
-                        const uint64_t al = smem_desc<BKB>(a2_addr + kk * 32);
-                        const uint64_t bl = smem_desc<BKB>(b2_addr + kk * 32);
-                        tc_mma_tf32(d_tmem, ah, bh, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                        tc_mma_tf32(d_tmem, ah, bl, idesc, 1u);
-                        tc_mma_tf32(d_tmem, al, bh, idesc, 1u);
+                        for (int kk = 0; kk < BKB / 32; ++kk) {     // 8 FP32 of K per MMA
+                            const uint64_t ah = smem_desc<BKB>(a_addr + kk * 32);
+                            const uint64_t bh = smem_desc<BKB>(b_addr + kk * 32);
+                            const uint64_t al = smem_desc<BKB>(a2_addr + kk * 32);
+                            const uint64_t bl = smem_desc<BKB>(b2_addr + kk * 32);
+                            tc_mma_tf32(d_tmem, ah, bh, idesc, (kc > k0 || kk > 0) ? 1u : 0u);
+                            tc_mma_tf32(d_tmem, ah, bl, idesc, 1u);
+                            tc_mma_tf32(d_tmem, al, bh, idesc, 1u);
+                        }
+                        issued = true;
+                        tc_commit(&empty[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
-                    issued = true;
-                    tc_commit(&empty[stage]);
-                    if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    if (!ok) break;
+                    tc_commit(&accf[acc]);
+                    if (++acc == 2) { acc = 0; acc_phase ^= 1; }
                 }
-                if (!ok) break;
-                tc_commit(&accf[acc]);
-                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
             }
             if (!ok && issued) {
                 tc_commit(drain);
@@ -863,9 +873,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_x3_kernel(const __grid_
         __syncwarp();
     } else {
         // ---------------------------------------------------- epilogue --
+        // per tile: the K parts' accumulators added in FP32 registers (IEEE
+        // adds; the tensor cores' own accumulation drifts over long K), then
+        // stored as complex64 (or as a split-K partial)
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row = q * 32 + lane;
+        constexpr int NCH = (BN + 31) / 32;                // this warp's 16-column chunks
         int64_t lowtab[8];
         bool low_kept = true;
 #pragma unroll
@@ -876,27 +890,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_x3_kernel(const __grid_
         float mx = 0.f;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t t = walker; t < args.tiles; t += walkers) {
+        bool ok = true;
+        for (int64_t t = walker; t < args.tiles && ok; t += walkers) {
             int64_t b, mt;
             int nt;
             tile_coords(args, t, b, mt, nt);
-            if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) break;
-            tc_fence_after();
-            const int64_t m = mt * 128 + row;
             const int col0 = nt * BN;
+            const int col_end = min(BN, 2 * args.N - col0);
+            float sum[NCH][16];
+#pragma unroll
+            for (int i = 0; i < NCH; ++i)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) sum[i][j] = 0.f;
+            for (int k0 = 0; k0 < args.nk; k0 += kX3Part) {
+                if (!mbar_wait(&accf[acc], acc_phase, &abort_flag)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int i = 0; i < NCH; ++i) {
+                    const int c = 16 * half + 32 * i;
+                    if (c < col_end) {
+                        uint32_t r[16];
+                        tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) sum[i][j] += __uint_as_float(r[j]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            }
+            if (!ok) break;
+            const int64_t m = mt * 128 + row;
             const int64_t cb = b;
             int64_t prow = 0;
             if (args.out_rank) prow = permute_bits(args, (cb * args.M + m) * (int64_t)args.N, args.ln, args.out_rank);
-            const int col_end = min(BN, 2 * args.N - col0);
-            for (int c = 16 * half; c < col_end; c += 32) {
-                uint32_t r[16];
-                tmem_ld16<16>(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
-                tmem_wait_ld();
-                tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, 1.0f, mx);
+#pragma unroll
+            for (int i = 0; i < NCH; ++i) {
+                const int c = 16 * half + 32 * i;
+                if (c < col_end) {
+                    uint32_t r[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(sum[i][j]);
+                    tc_store16(args, r, b, m, t, col0, c, col_end, cb, prow, lowtab, low_kept, 1.0f, mx);
+                }
             }
-            tc_fence_before();
-            mbar_arrive(&acce[acc]);
-            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0 && args.sr.out_max && !args.partial)

@@ -186,6 +186,36 @@ def test_grid_30q_sliced_full_size(dtype, batch, policy):
     print(f"grid30 {tn.DTYPE_NAMES[dtype]} batch 2^{batch} policy {policy}: rel_l2={e:.3e} fidelity={f:.6f}")
 
 
+@pytest.mark.parametrize("policy", [tn.TILE_FIXED, tn.TILE_EXHAUSTIVE])
+def test_grid_30q_complex64_on_tensor_cores(policy):
+    # tn_plan_opts.c64_tensor_cores: the large complex64 steps on the tensor
+    # cores (TF32 parts and remainders, three MMAs per K slice, K parts summed
+    # in FP32 registers).  Each such GEMM measures ~1.9e-6 against FP64
+    # (~1e-6 on the CUDA cores), which the network carries to ~1e-5 on this
+    # job; the bound here is 2e-5, fidelity 1 - 1e-9
+    want = _golden("grid5x6_14c_amps.txt")
+    c, q = rqcgen.grid_30q()
+    p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=8, trials=4, slice_batch_log2=8, tile_policy=policy,
+                c64_tensor_cores=True)
+    got = p.contract().cpu().numpy()
+    e = oracle.rel_l2(got, want)
+    assert e <= 2e-5, e
+    assert oracle.fidelity(want, got) >= 1 - 1e-9
+    print(f"grid30 complex64 on tensor cores, policy {policy}: rel_l2={e:.3e}")
+
+
+def test_complex64_tensor_cores_small_plans():
+    # the 12-qubit circuit, with slices, batches and a step small enough for
+    # the CUDA cores beside the large ones: the autotuner's mix
+    c, q = rqcgen.grid_12q()
+    want = oracle.amplitudes(c, q)
+    for sl, b in [(0, 0), (3, 2)]:
+        p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=sl, slice_batch_log2=b, tile_policy=tn.TILE_EXHAUSTIVE,
+                    c64_tensor_cores=True)
+        got = p.contract().cpu().numpy()
+        assert oracle.rel_l2(got, want) <= 2e-5
+
+
 @pytest.mark.parametrize("dtype", [tn.C64, tn.F16])
 def test_graph_replay_matches_direct_launches(dtype):
     c, q = rqcgen.small_grid(4, 5, 12, seed=8, n_open=6)
