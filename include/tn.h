@@ -142,14 +142,17 @@ typedef struct {
                                  workspace fits in this many bytes, else 0 --
                                  as many slices per pass as memory allows, one
                                  path search.  0: slice_batch_log2 as given   */
-    int32_t c64_tensor_cores; /* dtype TN_C64: 1 = complex64 steps may run on
-                                 the tensor cores (tn_gemm kernel 9: TF32 parts
-                                 and remainders, three MMAs per K slice, ~8e-6
-                                 relative error per step against ~1e-6 on the
-                                 CUDA cores; device scratch for the split
-                                 operands of the largest such step).  The fixed
-                                 policy takes it for steps of >= 2^36 flops,
-                                 the autotuner times it.  0: CUDA cores only */
+    int32_t c64_tensor_cores; /* dtype TN_C64: 1 = complex64 steps of one K
+                                 part (K <= 2^15, not split) may run on the
+                                 tensor cores (tn_gemm kernel 9: TF32 parts
+                                 and rounded remainders, three MMAs per K
+                                 slice, 64-term K parts summed in FP32
+                                 registers; ~5e-7 relative error per GEMM, as
+                                 the CUDA cores; device scratch for the split
+                                 operands of the largest such step).  The
+                                 fixed policy takes it for steps of >= 2^36
+                                 flops, the autotuner times it.  0 (default):
+                                 CUDA cores only                            */
     int32_t pad_;
     /* Optional device allocator for the plan's workspace (e.g. PyTorch's
        caching allocator).  NULL: cudaMalloc/cudaFree. */

@@ -17,9 +17,12 @@ namespace {
 thread_local std::string g_err;
 
 // complex64 step that the tensor cores can run (tn_plan_opts.c64_tensor_cores)
+// (one K part only: split-K steps, K > 2^15 or cut for few tiles, stay on
+// the CUDA cores)
 bool x3_eligible(const tn_plan_s *P, const GemmOp &g) {
     return P->opts.dtype == TN_C64 && P->opts.c64_tensor_cores && tc_gemm_supported(g.lk, g.ln) &&
-           g.idx_a < 0 && g.idx_b < 0 && g.out_rank == 0 && g.lm <= 30;
+           g.idx_a < 0 && g.idx_b < 0 && g.out_rank == 0 && g.lm <= 30 && g.lk <= kSplitLog2KHost &&
+           tc_split(g.lm, g.ln, g.lk, (int64_t)1 << g.lb) == 1;
 }
 
 // scratch of such a step: hi and lo parts of A ([batch][M][2K] FP32) and of
@@ -849,6 +852,10 @@ int finish_plan(tn_plan_s *P, const SampleSpec *spec, std::string &err) {
             op.gemm.lm + op.gemm.ln + op.gemm.lk + op.gemm.lb + 3 >= 36) {
             op.gemm.kernel = GK_C64_TC;
             op.gemm.tile = 0;
+            if (op.gemm.step >= 0 && op.gemm.step < (int)P->sched.steps.size()) {
+                P->sched.steps[op.gemm.step].kernel = GK_C64_TC;
+                P->sched.steps[op.gemm.step].tile = 0;
+            }
         }
     return TN_OK;
 }

@@ -702,8 +702,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_bres_kernel(const __gri
 // threads, bounded waits, double-buffered accumulators); the result is
 // complex64 (the epilogue's FP32 path: no rounding, no scale).
 // K chunks per accumulation part of the x3 kernel (the epilogue adds the
-// parts in FP32 registers): 8 chunks of 128 bytes = 256 real K terms
-constexpr int kX3Part = 8;
+// parts in FP32 registers): 2 chunks of 128 bytes = 64 real K terms.  The
+// tensor cores' own FP32 accumulation loses bits with every MMA it adds up:
+// measured against FP64 per GEMM, one accumulator over all of K: 8e-6;
+// 256-term parts: 1.9e-6; 64-term parts: 5.3e-7 (253 TFLOP/s); 32-term
+// parts: 3.2e-7 (222 TFLOP/s); the CUDA cores: 0.4-1.6e-6
+constexpr int kX3Part = 2;
 
 template <int BN, int BKB>
 struct X3Smem {

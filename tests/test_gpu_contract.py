@@ -188,20 +188,24 @@ def test_grid_30q_sliced_full_size(dtype, batch, policy):
 
 @pytest.mark.parametrize("policy", [tn.TILE_FIXED, tn.TILE_EXHAUSTIVE])
 def test_grid_30q_complex64_on_tensor_cores(policy):
-    # tn_plan_opts.c64_tensor_cores: the large complex64 steps on the tensor
-    # cores (TF32 parts and remainders, three MMAs per K slice, K parts summed
-    # in FP32 registers).  Each such GEMM measures ~1.9e-6 against FP64
-    # (~1e-6 on the CUDA cores), which the network carries to ~1e-5 on this
-    # job; the bound here is 2e-5, fidelity 1 - 1e-9
+    # tn_plan_opts.c64_tensor_cores (opt-in): the large complex64
+    # steps on the tensor cores (TF32 parts and remainders, three MMAs per K
+    # slice, 64-term K parts summed in FP32 registers), against the same steps
+    # on the CUDA cores: both within the complex64 budget (1e-5)
     want = _golden("grid5x6_14c_amps.txt")
     c, q = rqcgen.grid_30q()
-    p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=8, trials=4, slice_batch_log2=8, tile_policy=policy,
-                c64_tensor_cores=True)
-    got = p.contract().cpu().numpy()
-    e = oracle.rel_l2(got, want)
-    assert e <= 2e-5, e
-    assert oracle.fidelity(want, got) >= 1 - 1e-9
-    print(f"grid30 complex64 on tensor cores, policy {policy}: rel_l2={e:.3e}")
+    for tcores in (True, False):
+        p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=8, trials=4, slice_batch_log2=8, tile_policy=policy,
+                    c64_tensor_cores=tcores)
+        if tcores:
+            assert any(s["kernel"] == 4 for s in p.steps()) or policy == tn.TILE_EXHAUSTIVE
+        got = p.contract().cpu().numpy()
+        e = oracle.rel_l2(got, want)
+        assert e <= 1e-5, (tcores, e)
+        assert oracle.fidelity(want, got) >= 1 - 1e-9
+        print(f"grid30 complex64, tensor cores {tcores}, policy {policy}: rel_l2={e:.3e}")
+        del p
+        torch.cuda.empty_cache()
 
 
 def test_complex64_tensor_cores_small_plans():
@@ -213,7 +217,7 @@ def test_complex64_tensor_cores_small_plans():
         p = tn.Plan(c, q, dtype=tn.C64, n_slice_edges=sl, slice_batch_log2=b, tile_policy=tn.TILE_EXHAUSTIVE,
                     c64_tensor_cores=True)
         got = p.contract().cpu().numpy()
-        assert oracle.rel_l2(got, want) <= 2e-5
+        assert oracle.rel_l2(got, want) <= 1e-5
 
 
 @pytest.mark.parametrize("dtype", [tn.C64, tn.F16])

@@ -136,19 +136,24 @@ def test_learned_policy_against_fixed_and_exhaustive():
     # per step, the recorded time of each policy's choice (one exhaustive
     # tuning pass timed every candidate, so this comparison has no run-to-run
     # noise): the learned choices against the best and the fixed heuristic's
+    # the best is taken over the candidates the model ranks: the kernel
+    # variants of tile bits 10-12 are left to exhaustive tuning (reported)
     fx = _plan(c, q, n_slice_edges=6, slice_batch_log2=6, tile_policy=tn.TILE_FIXED)
-    t_best = t_learn = t_fixed = 0.0
+    t_best = t_learn = t_fixed = t_best_all = 0.0
     for i, (sl, sf) in enumerate(zip(lp.steps(), fx.steps())):
         cand = by_step.get(i)
         if not cand:
             continue
-        t_best += min(cand.values())
-        t_learn += cand.get((sl["kernel"], sl["tile"]), min(cand.values()))
-        t_fixed += cand.get((sf["kernel"], sf["tile"]), min(cand.values()))
+        cov = by_step_m.get(i) or cand
+        t_best += min(cov.values())
+        t_best_all += min(cand.values())
+        t_learn += cand.get((sl["kernel"], sl["tile"]), min(cov.values()))
+        t_fixed += cand.get((sf["kernel"], sf["tile"]), min(cov.values()))
     # whole-plan device time of the three choices, median of 15 calls each
     fixed, learned, best = (_median_ms(p) for p in (fx, lp, held))
     print(f"held-out plan: recorded step sums fixed {t_fixed:.3f} ms, learned {t_learn:.3f} ms, best "
-          f"{t_best:.3f} ms; measured fixed {fixed:.3f} ms, learned {learned:.3f} ms, exhaustive {best:.3f} ms; "
+          f"{t_best:.3f} ms (all variants {t_best_all:.3f} ms); measured fixed {fixed:.3f} ms, learned "
+          f"{learned:.3f} ms, exhaustive {best:.3f} ms; "
           f"selection: exhaustive tuning {t_exhaustive:.2f} s, learned first call {t_learned_call:.2f} s; "
           f"mean within-step rank correlation {rank_corr:.2f}")
     assert rank_corr > 0.2
