@@ -298,7 +298,18 @@ class _TorchAllocator:
         self._live = {}
 
         def alloc(nbytes, ctx):
-            t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            # an exception must not leave this callback: ctypes would hand the
+            # library an undefined pointer.  Out of memory: release PyTorch's
+            # cached blocks and try once more, else NULL (the library then
+            # returns TN_ENOMEM)
+            try:
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+            except Exception:
+                try:
+                    torch.cuda.empty_cache()
+                    t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+                except Exception:
+                    return None
             p = t.data_ptr()
             self._live[p] = t
             return p

@@ -11,3 +11,14 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+@pytest.fixture(autouse=True)
+def _drop_failed_frames():
+    """pytest keeps a failed test's traceback in sys.last_traceback, and with
+    it every local of the test: plans holding tens of GB of device memory
+    would stay resident through the following tests."""
+    yield
+    for name in ("last_type", "last_value", "last_traceback", "last_exc"):
+        if hasattr(sys, name):
+            setattr(sys, name, None)
