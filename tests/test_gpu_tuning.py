@@ -167,7 +167,7 @@ def test_learned_policy_against_fixed_and_exhaustive():
     # 5.4% above that best and the learned choices 3.5-3.9% above it
     assert t_learn <= 1.05 * t_best
     assert t_learn <= 1.01 * t_fixed
-    assert learned <= 1.05 * best
+    assert learned <= 1.03 * best
     # what the model gains over exhaustive tuning at that quality: selection time
     assert t_learned_call * 3 < t_exhaustive
 
