@@ -486,9 +486,10 @@ def leg_batch256(tn, torch, dev, flush, stream, anneal_iters=20000):
                      "checked_circuits": len(errs), "tuned_plans": len(plans[::32])}
         del b, qu, plans, outs, outq
         torch.cuda.empty_cache()
-    best = max((out[k]["queue"]["circuits_per_s"], k) for k in ("greedy", "annealed"))
+    best = max((out[k][f]["circuits_per_s"], k, f) for k in ("greedy", "annealed") for f in ("graph", "queue"))
     out["circuits_per_s"] = best[0]
-    out["best"] = f"{best[1]} path, one work-queue launch"
+    out["best"] = f"{best[1]} path, " + ("one work-queue launch" if best[2] == "queue"
+                                          else "one CUDA graph over side streams")
     return out, recs_all
 
 
