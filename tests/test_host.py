@@ -315,3 +315,16 @@ def test_workspace_budget_picks_the_largest_fitting_slice_batch():
 def test_cost_targets_are_log2_microseconds():
     recs = [{"ms": 1.0}, {"ms": 0.25}, {"ms": 1e-9}]
     np.testing.assert_allclose(tn.cost_targets(recs), [np.log2(1e3), np.log2(250.0), np.log2(1e-3)], rtol=1e-6)
+
+
+def test_allocator_callback_returns_null_when_torch_cannot_allocate():
+    # an exception may not leave the ctypes callback (the library would get an
+    # undefined pointer); without a GPU torch.empty(device="cuda") raises, and
+    # the callback must answer NULL so that the library reports TN_ENOMEM
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a process without a GPU")
+    a = tn._TorchAllocator()
+    assert a.alloc(1 << 20, None) is None
+    a.free(None, None)
+    assert not a._live
