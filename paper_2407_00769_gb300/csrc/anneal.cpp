@@ -21,7 +21,11 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <exception>
+#include <functional>
 #include <random>
+#include <system_error>
+#include <thread>
 
 #include "internal.h"
 #include "plan.h"
@@ -282,27 +286,53 @@ static double refine_chain(const Network &net, int n_target, int cap, uint64_t s
     return std::ldexp(roof, (int)sliced.size());
 }
 
-int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
-                int batch_log2, int chains, Path &path, std::vector<int> &sliced, double *cost_out) {
-    // independent chains from the same start; the cheapest job wins (the
-    // lowest time complexity found under the cap)
-    Path best_path;
-    std::vector<int> best_sliced;
-    double best = 0;
-    for (int c = 0; c < std::max(1, chains); ++c) {
-        Path p = path;
-        std::vector<int> s = sliced;
-        const double cost = refine_chain(net, n_target, cap, seed + 0x9E3779B97F4A7C15ull * (uint64_t)c, iters,
-                                         kappa, batch_log2, p, s);
-        if (c == 0 || cost < best) {
-            best = cost;
-            best_path = std::move(p);
-            best_sliced = std::move(s);
+void run_parallel(int n, const std::function<void(int)> &fn) {
+    std::vector<std::exception_ptr> err(std::max(0, n));
+    auto body = [&](int i) {
+        try {
+            fn(i);
+        } catch (...) {
+            err[i] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    int spawned = 0;
+    if (std::thread::hardware_concurrency() > 1) {
+        for (int i = 1; i < n; ++i) {
+            try {
+                th.emplace_back(body, i);
+                ++spawned;
+            } catch (const std::system_error &) {
+                break;  // no more threads: the rest run on this one
+            }
         }
     }
-    path = std::move(best_path);
-    sliced = std::move(best_sliced);
-    if (cost_out) *cost_out = best;
+    if (n > 0) body(0);
+    for (int i = spawned + 1; i < n; ++i) body(i);
+    for (auto &t : th) t.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
+}
+
+int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int iters, double kappa,
+                int batch_log2, int chains, Path &path, std::vector<int> &sliced, double *cost_out) {
+    // independent chains from the same start, one thread each; the cheapest
+    // job wins (the lowest time complexity found under the cap), ties to the
+    // lower chain index, so the result does not depend on the threads
+    const int nc = std::max(1, chains);
+    std::vector<Path> ps(nc, path);
+    std::vector<std::vector<int>> ss(nc, sliced);
+    std::vector<double> cost(nc, 0.0);
+    run_parallel(nc, [&](int c) {
+        cost[c] = refine_chain(net, n_target, cap, seed + 0x9E3779B97F4A7C15ull * (uint64_t)c, iters, kappa,
+                               batch_log2, ps[c], ss[c]);
+    });
+    int best = 0;
+    for (int c = 1; c < nc; ++c)
+        if (cost[c] < cost[best]) best = c;
+    path = std::move(ps[best]);
+    sliced = std::move(ss[best]);
+    if (cost_out) *cost_out = cost[best];
     return TN_OK;
 }
 

@@ -770,23 +770,27 @@ int plan_path(tn_plan_s *P, const Network &plan_net_in, std::string &err) {
         // fixed while the path is planned, loop over every pass too: the
         // steps they reach are not known here, so no step is weighted
         const int bl = o.recompute_log2 > 0 ? -1 : o.workspace_budget > 0 ? 64 : std::max(0, o.slice_batch_log2);
-        double best = 0;
-        refine_plan(plan_net, n_target, cap, o.path_seed, o.path_anneal_iters, kappa, bl, 2, P->path, P->sliced,
-                    &best);
-        for (int st = 1; st < starts; ++st) {
-            Path p2;
-            std::vector<int> s2;
+        // the starts run on threads of their own (they share no mutable
+        // state); the cheapest wins, ties to the lower start, as in order
+        std::vector<Path> ps(starts);
+        std::vector<std::vector<int>> ss(starts);
+        std::vector<double> cost(starts, 0.0);
+        std::vector<char> ok(starts, 0);
+        ps[0] = P->path;
+        ss[0] = P->sliced;
+        run_parallel(starts, [&](int st) {
+            const uint64_t sd = st == 0 ? o.path_seed : o.path_seed + 0xD1B54A32D192ED03ull * (uint64_t)st;
             std::string e2;
-            const uint64_t sd = o.path_seed + 0xD1B54A32D192ED03ull * (uint64_t)st;
-            if (choose_slices(plan_net, sd, o.path_trials, n_target, cap, p2, s2, e2) != TN_OK) continue;
-            double c2 = 0;
-            refine_plan(plan_net, n_target, cap, sd, o.path_anneal_iters, kappa, bl, 2, p2, s2, &c2);
-            if (c2 < best) {
-                best = c2;
-                P->path = std::move(p2);
-                P->sliced = std::move(s2);
-            }
-        }
+            if (st > 0 && choose_slices(plan_net, sd, o.path_trials, n_target, cap, ps[st], ss[st], e2) != TN_OK)
+                return;
+            refine_plan(plan_net, n_target, cap, sd, o.path_anneal_iters, kappa, bl, 2, ps[st], ss[st], &cost[st]);
+            ok[st] = 1;
+        });
+        int best = 0;
+        for (int st = 1; st < starts; ++st)
+            if (ok[st] && cost[st] < cost[best]) best = st;
+        P->path = std::move(ps[best]);
+        P->sliced = std::move(ss[best]);
     }
     if (cap > 0 && P->path.max_log2 > cap) {
         err = "the slicing does not reach the cap (largest intermediate 2^" + std::to_string(P->path.max_log2) + ")";

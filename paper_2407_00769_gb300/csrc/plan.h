@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,11 @@ int refine_plan(const Network &net, int n_target, int cap, uint64_t seed, int it
                 int batch_log2, int chains, Path &path, std::vector<int> &sliced, double *cost_out = nullptr);
 int choose_slices(const Network &net, uint64_t seed, int trials, int n_target, int cap, Path &path,
                   std::vector<int> &sliced, std::string &err);
+// fn(0), ..., fn(n-1), each on a thread of its own (fn(0) on the caller's;
+// all on the caller's with one hardware thread or when no thread can be
+// started); returns when all have ended and rethrows the first exception
+// (by index) that one of them threw.  The calls must share no mutable state.
+void run_parallel(int n, const std::function<void(int)> &fn);
 // Recomputation (Sec. 3.4.1): append r open output legs to `sliced`, each
 // the one whose removal shrinks the largest intermediate of `path` most
 // (then its flops); updates the path's size and flops.

@@ -107,6 +107,17 @@ def test_plan_is_deterministic():
     assert a.sliced_edges() == b.sliced_edges() and a.steps() == b.steps()
 
 
+def test_annealed_plan_does_not_depend_on_the_threads():
+    # the annealing starts and chains run on threads of their own; the plan
+    # they choose must be the same on every run (ties go to the lower start)
+    c, q = rqcgen.small_grid(5, 6, 12, seed=2, n_open=8)
+    kw = dict(n_slice_edges=-1, max_log2_elems=16, trials=4, seed=5, anneal_iters=3000)
+    runs = [_plan(c, q, **kw) for _ in range(4)]
+    ref = (runs[0].sliced_edges(), runs[0].steps(), runs[0].info()["flops_per_slice"])
+    for p in runs[1:]:
+        assert (p.sliced_edges(), p.steps(), p.info()["flops_per_slice"]) == ref
+
+
 def test_rejects_bad_inputs():
     c, q = rqcgen.small_grid(3, 3, 4, seed=1, n_open=3)
     bad = rqcgen.Circuit(c.n_qubits, c.q0.copy(), c.q1.copy(), c.mats.copy())
