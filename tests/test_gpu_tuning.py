@@ -151,7 +151,7 @@ def test_learned_policy_against_fixed_and_exhaustive():
         t_fixed += cand.get((sf["kernel"], sf["tile"]), min(cov.values()))
     # whole-plan device time of the three choices, median of 15 calls each
     fixed, learned, best = (_median_ms(p) for p in (fx, lp, held))
-    # the three plans hold ~68 GB of workspace each: release them before the
+    # the three plans hold ~68 GiB of workspace each: release them before the
     # checks, so that a failure does not keep them resident
     del fx, lp, held
     torch.cuda.empty_cache()
