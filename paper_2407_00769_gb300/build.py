@@ -83,7 +83,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         libdir = cuda_lib_dir()
         tmp = LIB + f".{os.getpid()}.tmp"
         run([cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs +
-            ["-L", libdir, "-Xlinker", "-rpath," + libdir])
+            ["-L", libdir, "-Xlinker", "-rpath," + libdir, "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 
