@@ -51,8 +51,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--legs", default="grid12,grid53,batch256,bf16,fp8,anneal,samples,recompute,grid40",
                     help="extra workloads timed after the main line (comma list, or 'none')")
-    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec"],
-                    help="time one kernel on one shape instead (profiling aid)")
+    ap.add_argument("--case", default=None, choices=["gemm_tc", "permute", "gather", "codec", "time_space"],
+                    help="time one kernel on one shape instead (profiling aid); time_space: the "
+                         "planner's time-space table on the host (no GPU)")
+    ap.add_argument("--anneal-iters", type=int, default=500000,
+                    help="--case time_space: annealing moves per chain")
+    ap.add_argument("--path-trials", type=int, default=8,
+                    help="--case time_space: greedy restarts, and annealing starts (2 chains each)")
     ap.add_argument("--fp8", action="store_true", help="--case gemm_tc with E4M3 operands")
     ap.add_argument("--pair", action="store_true", help="--case gemm_tc on CTA pairs (256-row tiles)")
     ap.add_argument("--c64", action="store_true",
@@ -803,8 +808,41 @@ def leg_grid40(tn, torch, dev, flush, stream, train_recs, n_meas=8):
 
 
 # --------------------------------------------------------------- our arm
+def time_space_case(args):
+    """The time-space trade-off of path search (Sec. 3: the contraction path
+    is searched by simulated annealing under a memory cap, and the lowest
+    time complexity is taken for each cap), on the host only: for the 53-,
+    40- and 30-qubit circuits and caps 2^24..2^32 elements per intermediate,
+    the whole job's flops (all slices) of the greedy slicing (restarts) and
+    of the annealed path (--path-trials starts x 2 chains) under two objectives: kappa =
+    1, flops alone to within one flop per element moved (the paper's time
+    complexity), and the planner's default roofline objective (kappa = 1000
+    for complex-half).  One JSON line per workload and cap."""
+    import rqcgen
+    import paper_2407_00769_gb300 as tn
+    variants = (("greedy", 0, 0), ("annealed_flops", args.anneal_iters, 1),
+                ("annealed_roofline", args.anneal_iters, 0))
+    for make in (rqcgen.grid_53q, rqcgen.grid_40q, rqcgen.grid_30q):
+        c, q = make()
+        for cap in (24, 26, 28, 30, 32):
+            row = {"case": "time_space", "workload": c.label, "n_qubits": int(c.n_qubits), "cap_log2": cap,
+                   "anneal_iters": args.anneal_iters, "path_trials": args.path_trials}
+            for label, iters, kappa in variants:
+                t0 = time.perf_counter()
+                p = tn.Plan(c, q, dtype=tn.F16, n_slice_edges=-1, max_log2_elems=cap, trials=args.path_trials,
+                            anneal_iters=iters, anneal_kappa=kappa, torch_allocator=False)
+                i = p.info()
+                row[label] = {"flops": i["flops_per_slice"] * i["n_slices"] + i["flops_invariant"],
+                              "n_slices": i["n_slices"], "max_log2_elems": i["max_log2_elems"],
+                              "plan_s": round(time.perf_counter() - t0, 3)}
+                del p
+            print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
+    if args.case == "time_space":
+        return time_space_case(args)
     if args.case:
         return kernel_case(args)
     if args.impl == "reference":
