@@ -44,3 +44,18 @@ def test_reference_arm_reads_the_recorded_plan():
     edges, leaves, steps, flops = dump_plan.read(bench.GRID30_PLAN, with_flops=True)
     assert len(edges) == 8 and len(steps) == len(leaves) - 1
     assert flops["job"] == pytest.approx(flops["per_slice"] * 256 + flops["invariant"])
+
+
+def test_time_space_case_runs_on_the_host(monkeypatch, capsys):
+    # the planner's time-space table needs no GPU: one line per workload and
+    # cap, every plan within its cap, annealing no worse than its greedy start
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--case", "time_space", "--anneal-iters", "2000",
+                                      "--path-trials", "1"])
+    bench.main()
+    rows = [json.loads(l) for l in capsys.readouterr().out.strip().splitlines()]
+    assert len(rows) == 15
+    assert {r["cap_log2"] for r in rows} == {24, 26, 28, 30, 32}
+    for r in rows:
+        for k in ("greedy", "annealed_flops", "annealed_roofline"):
+            assert r[k]["max_log2_elems"] <= r["cap_log2"] and r[k]["flops"] > 0
+        assert r["annealed_flops"]["flops"] <= 1.01 * r["greedy"]["flops"]
