@@ -339,3 +339,31 @@ def test_allocator_callback_returns_null_when_torch_cannot_allocate():
     assert a.alloc(1 << 20, None) is None
     a.free(None, None)
     assert not a._live
+
+
+@pytest.mark.parametrize("kind", ["sliced", "annealed", "recompute", "samples"])
+def test_plan_flops_are_the_steps_8mnk(kind):
+    # the TFLOP/s figures divide the plan's flops by time: they must be the
+    # method's own work, 8 M N K real flops per complex GEMM step (Sec. 3.3,
+    # Eq. 6), each step counted once per pass of 2^b slices, or once per
+    # call for the steps that no looped sliced edge reaches
+    c, q = rqcgen.small_grid(4, 5, 12, seed=4, n_open=8)
+    if kind == "sliced":
+        p = _plan(c, q, n_slice_edges=4, slice_batch_log2=2)
+    elif kind == "annealed":
+        c, q = rqcgen.small_grid(5, 6, 12, seed=2, n_open=8)
+        p = _plan(c, q, n_slice_edges=-1, max_log2_elems=16, anneal_iters=3000, slice_batch_log2=1)
+    elif kind == "recompute":
+        p = _plan(c, q, n_slice_edges=2, recompute_log2=2, slice_batch_log2=1)
+    else:
+        bits = np.random.default_rng(1).integers(0, 2, size=(100, c.n_qubits)).astype(np.uint8)
+        p = tn.Plan.from_samples(c, bits, dtype=tn.F16, n_slice_edges=2, slice_batch_log2=1,
+                                 torch_allocator=False)
+    i = p.info()
+    passes = i["n_slices"] >> i["slice_batch_log2"]
+    total = 0.0
+    for s in p.steps():
+        f = 8.0 * 2.0 ** (s["log2_m"] + s["log2_n"] + s["log2_k"] + s["log2_batch"])
+        total += f if s["slice_invariant"] else f * passes
+    assert total == i["flops_per_slice"] * i["n_slices"] + i["flops_invariant"]
+    assert any(not s["slice_invariant"] for s in p.steps()) or i["n_slices"] == 1
