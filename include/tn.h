@@ -94,11 +94,16 @@ typedef struct {
                                  -1: as many as the cap needs                    */
     uint64_t path_seed;       /* seed of the randomized greedy path search       */
     int32_t path_trials;      /* greedy restarts (>= 1); trial 0 is noiseless    */
-    int32_t path_anneal_iters;/* > 0: refine the chosen path by simulated
-                                 annealing: path_trials independent chains of
-                                 3 rounds of this many tree rotations, the
-                                 cheapest kept; with a cap, sliced edges the
-                                 refined path no longer needs are given back */
+    int32_t path_anneal_iters;/* > 0: refine the path by simulated annealing
+                                 (Sec. 3): path_trials starts (greedy
+                                 slicings under different seeds), two chains
+                                 each of 3 rounds of this many tree
+                                 rotations; the job of lowest roofline cost
+                                 is kept (ties to the lower start and chain:
+                                 the starts and chains run on host threads of
+                                 their own and the result does not depend on
+                                 them); with a cap, sliced edges the refined
+                                 path no longer needs are given back        */
     int32_t slice_batch_log2; /* run 2^this consecutive slices in one pass, the
                                  batch carried as an extra tensor mode (>= 0;
                                  slicing to a cap: lowered to the number of
