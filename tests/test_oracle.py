@@ -229,3 +229,30 @@ def test_stored_grid12_amplitudes_are_the_oracles():
     c, q = rqcgen.grid_12q()
     assert np.allclose(stored, oracle.amplitudes(c, q), rtol=0, atol=1e-15)
     assert abs(np.vdot(stored, stored).real - 1.0) < 1e-12
+
+
+def test_oracle_and_product_share_no_code():
+    # the oracle is the independent check of the CUDA path: neither side may
+    # import, include or link the other (the seeded input generators in
+    # rqcgen serve both and hold none of the method's arithmetic)
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2407_00769_gb300")
+    orc = os.path.join(root, "oracle")
+
+    def sources(top, exts):
+        for d, dirs, files in os.walk(top):
+            dirs[:] = [x for x in dirs if x not in ("_build", "__pycache__")]
+            for f in files:
+                if f.endswith(exts):
+                    yield os.path.join(d, f)
+
+    imports_oracle = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)|#include\s+[\"<][^\">]*oracle", re.M)
+    for path in sources(pkg, (".py", ".cu", ".cuh", ".cpp", ".h")):
+        assert not imports_oracle.search(open(path).read()), path
+    imports_pkg = re.compile(r"^\s*(import\s+paper_2407_00769_gb300|from\s+paper_2407_00769_gb300\b)"
+                             r"|#include\s+[\"<][^\">]*(tn\.h|csrc)", re.M)
+    for path in sources(orc, (".py", ".c", ".h")):
+        assert not imports_pkg.search(open(path).read()), path
+    src = open(os.path.join(root, "rqcgen", "__init__.py")).read()
+    assert not re.search(r"^\s*(import|from)\s+(oracle|paper_2407_00769_gb300)\b", src, re.M)
