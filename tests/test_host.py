@@ -367,3 +367,21 @@ def test_plan_flops_are_the_steps_8mnk(kind):
         total += f if s["slice_invariant"] else f * passes
     assert total == i["flops_per_slice"] * i["n_slices"] + i["flops_invariant"]
     assert any(not s["slice_invariant"] for s in p.steps()) or i["n_slices"] == 1
+
+
+def test_no_fallback_when_the_library_cannot_load(monkeypatch, tmp_path):
+    # there is no CPU path behind the binding: a library that cannot be
+    # built or loaded makes every call raise
+    bad = tmp_path / "libtn.so"
+    bad.write_bytes(b"not a shared library")
+    monkeypatch.setattr(tn, "_lib", None)
+    monkeypatch.setattr(tn._build_mod, "build", lambda force=False: str(bad))
+    c, q = rqcgen.small_grid(3, 3, 4, seed=1, n_open=3)
+    with pytest.raises(OSError):
+        tn.Plan(c, q, torch_allocator=False)
+
+    def no_toolkit(force=False):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
+    monkeypatch.setattr(tn._build_mod, "build", no_toolkit)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        tn.lib()
