@@ -296,6 +296,7 @@ void run_parallel(int n, const std::function<void(int)> &fn) {
         }
     };
     std::vector<std::thread> th;
+    th.reserve(std::max(0, n));  // no reallocation (and no throw) once threads run
     int spawned = 0;
     if (std::thread::hardware_concurrency() > 1) {
         for (int i = 1; i < n; ++i) {
